@@ -1,0 +1,2 @@
+"""FP64 CPU oracle (test infrastructure only; see nadmm_oracle)."""
+from .nadmm_oracle import *  # noqa: F401,F403
