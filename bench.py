@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark: Nesterov-accelerated ADMM registration of 128x128x96 pairs.
+
+Metric: ms per 128x128x96 registration (plus voxel-ADMM-iters/s and the
+dominant kernel's HBM GB/s against the measured peak).  A step registers one
+synthetic cardiac-shaped pair for each regulariser order n = 1, 2, 3 with
+10 compositions x 10 ADMM iterations (lambda = 10, theta = 0.1, s = 2).
+Inputs are device-resident when the timed region starts; L2 is flushed
+(a 256 MB write) between timed steps, outside each step's events.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU: one process per GPU (torchrun); pairs are independent, so every
+rank registers its own pairs with no data-path collective (replicas);
+timing is the max over ranks and the value aggregates all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (128, 128, 96)
+ORDERS = (1, 2, 3)
+OUTER, INNER = 10, 10
+LAM, THETA = 10.0, 0.1
+METRIC = "ms per 128x128x96 registration; voxel-ADMM-iters/s; HBM GB/s vs peak"
+WORKLOAD = ("128x128x96 synthetic cardiac phantom pairs (ellipsoidal shells 0.9/0.5/0.1, noise "
+            "0.02, 8-bump scaling-and-squaring warp <= 3 voxels), one pair per regulariser order "
+            "n = 1, 2, 3; 10 compositions x 10 Nesterov-ADMM iterations, lambda=10, theta=0.1, s=2, "
+            "velocity bound kappa=0.5, delta=1")
+
+
+def algorithmic_bytes_per_voxel(nx):
+    """Bytes each kernel class must move per voxel in this design (fp32;
+    the half spectrum holds 3 (nx/2 + 1) complex values per x-row)."""
+    spec = 3 * (nx // 2 + 1) * 8.0 / nx
+    return {
+        "plane": 64.0 + spec + 36.0 + spec,      # read spec, y, w/b prev, J, c; write w, b, y, spec
+        "plane_k1": 40.0 + spec + 36.0 + spec,   # as above without the w^{k-2}, b^{k-2} reads
+        "plane_first": 16.0 + 12.0 + spec,       # read J, c; write y, spec
+        "plane_final": spec + 12.0,              # read spec; write w
+        "pencil": 2 * spec,                      # read + write the half spectrum
+        "warp": 12.0 + 4.0 + 4.0,                # read u, I1 (gathered once); write I1w
+        "grad": 8.0 + 16.0,                      # read I1w, I0; write J, c
+        "bound": 12.0,                           # read w
+        "compose": 36.0,                         # read w, u; write u
+    }
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("admm_kernels.cu", "fft_device.cuh", "nadmm_internal.h"):
+        with open(os.path.join(ROOT, "paper_2109_12688_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_plane_pass_128x128x96.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch\[%s\]:\s*([0-9.]+)\s+kernel_sha:\s*([0-9a-f]+)"
+                  % re.escape(kernel_class), text)
+    if not m or m.group(2) != kernel_source_sha():
+        return None
+    return float(m.group(1))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def oracle_sample_ms(pair, n):
+    """One of the 10 outer steps of the oracle registration (linearise, 10
+    ADMM iterations, bound, compose), timed on the host; returns ms."""
+    import numpy as np
+    import oracle as O
+    I0 = pair["fixed"].astype(np.float64)
+    I1 = pair["moving"].astype(np.float64)
+    t0 = time.perf_counter()
+    u = np.zeros((3,) + I0.shape)
+    J, c, _ = O.linearise(I0, I1, u)
+    w = O.admm(J, c, LAM, THETA, n, INNER)
+    s, _, _ = O.bound_scale(w, 0.5, 1.0)
+    O.compose(u, s * w)
+    return (time.perf_counter() - t0) * 1e3
+
+
+ORACLE_SAMPLE = ("1 of the 10 outer steps (re-linearise + 10 ADMM iterations + bound + compose) "
+                 "of the 128x128x96 n=2 registration, FP64 numpy oracle, extrapolated x10 to one "
+                 "registration")
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from paper_2109_12688_gb300 import synth
+    pair = synth.make_pair(DIMS, seed=0)
+    for _ in range(args.warmup):
+        oracle_sample_ms(pair, 2)
+    times = [oracle_sample_ms(pair, 2) * OUTER for _ in range(args.steps)]
+    ms = sum(times) / len(times)
+    V = DIMS[0] * DIMS[1] * DIMS[2]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("one pair per regulariser order n = 1, 2, 3",
+                                                "n = 2 pair, bounded sample"),
+                   "dims": list(DIMS), "outer": OUTER, "inner": INNER},
+        "voxel_admm_iters_per_s": V * OUTER * INNER / (ms / 1e3),
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": ORACLE_SAMPLE},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    if local == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2109_12688_gb300 import nadmm, synth
+    nadmm.load()
+
+    nx, ny, nz = DIMS
+    V = nx * ny * nz
+    pairs = [synth.make_pair(DIMS, seed=100 * rank + n) for n in ORDERS]
+    I0 = [torch.from_numpy(p["fixed"]).to(dev) for p in pairs]
+    I1 = [torch.from_numpy(p["moving"]).to(dev) for p in pairs]
+    U = [torch.empty((3, nz, ny, nx), dtype=torch.float32, device=dev) for _ in ORDERS]
+    regs = [nadmm.Registration(DIMS, device=dev, order_n=n, lam=LAM, theta=THETA, outer=OUTER,
+                               inner=INNER) for n in ORDERS]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        for r, a, b, u in zip(regs, I0, I1, U):
+            nadmm.nadmm_register(r.handle, a, b, u, stream)
+
+    for i in range(args.warmup):
+        flush.fill_(i & 0xFF)
+        step()
+    torch.cuda.synchronize()
+    for r in regs:
+        st = nadmm.nadmm_get_status(r.handle, stream)
+        if st != nadmm.NADMM_OK:
+            raise RuntimeError(f"device status {nadmm.nadmm_status_string(st)}")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for i in range(args.steps):
+        flush.fill_((i + 7) & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    regs_total = args.steps * len(ORDERS) * world
+    ms_per_reg = total_ms / regs_total
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the C ABI with pinned host buffers (copies timed)
+    hf = [torch.from_numpy(p["fixed"]).pin_memory() for p in pairs]
+    hm = [torch.from_numpy(p["moving"]).pin_memory() for p in pairs]
+    hu = [torch.empty((3, nz, ny, nx), dtype=torch.float32).pin_memory() for _ in ORDERS]
+    for r, a, b, u in zip(regs, hf, hm, hu):
+        nadmm.nadmm_register_host(r.handle, a, b, u, stream)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for r, a, b, u in zip(regs, hf, hm, hu):
+            nadmm.nadmm_register_host(r.handle, a, b, u, stream)
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_per_reg = float(te.item()) / regs_total
+
+    # per-kernel device time: events on the launch stream around every kernel
+    prof = {}
+    for r, a, b, u in zip(regs, I0, I1, U):
+        flush.fill_(3)
+        for k, (ms, n) in nadmm.nadmm_register_profiled(r.handle, a, b, u, stream).items():
+            pm, pn = prof.get(k, (0.0, 0))
+            prof[k] = (pm + ms, pn + n)
+    launches_per_reg = sum(n for _, n in prof.values()) / len(ORDERS)
+    bpv = algorithmic_bytes_per_voxel(nx)
+    dominant = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dominant]
+    avg_s = dom_ms / dom_n / 1e3
+    achieved = bpv[dominant] * V / avg_s / 1e9
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        ms = oracle_sample_ms(pairs[1], 2) * OUTER
+        cpu = {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE}
+
+    total_kernel_ms = sum(m for m, _ in prof.values())
+    line = {
+        "metric": METRIC, "value": ms_per_reg, "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dims": list(DIMS), "orders": list(ORDERS),
+                   "outer": OUTER, "inner": INNER, "registrations_per_step": len(ORDERS),
+                   "l2": "flushed between timed steps (256 MB write outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "voxel_admm_iters_per_s": V * OUTER * INNER * regs_total / (total_ms / 1e3),
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                     "traffic": ncu_traffic(dominant),
+                     "algorithmic_bytes_per_launch": bpv[dominant] * V,
+                     "avg_launch_us": avg_s * 1e6, "launches_measured": dom_n},
+        "kernels": {k: {"ms": round(m, 4), "launches": n, "share": round(m / total_kernel_ms, 4),
+                        "gbs": round(bpv[k] * V * n / (m / 1e3) / 1e9, 1) if m > 0 else None}
+                    for k, (m, n) in prof.items()},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_per_reg, "unit": "ms",
+                "h2d_bytes_per_step": len(ORDERS) * 2 * V * 4,
+                "d2h_bytes_per_step": len(ORDERS) * 3 * V * 4},
+        "gpu_launches": int(launches_per_reg * len(ORDERS) * args.steps),
+        "clocks": clk,
+        "paper_runtime_context": "1.37-2.17 s per 128x128x96 registration with a 3-level pyramid "
+                                 "on a 16 GB Tesla V100 (Table 1), not the same schedule",
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

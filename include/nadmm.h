@@ -1,0 +1,215 @@
+/*
+ * nadmm.h -- C ABI of the GB300 (sm_103a) Nesterov-accelerated ADMM
+ * diffeomorphic registration library (arXiv 2109.12688).
+ *
+ * Method (paper sections):
+ *   Sec. 2, Eq. 1 (N = 1) -- greedy composition phi <- phi o (Id + v), each
+ *     outer step re-warping the ORIGINAL moving image and re-linearising;
+ *   Eq. 2 -- model (1/s)||rho(v)||^s + (lambda/2)||grad^n v||^2,
+ *     rho(v) = <grad I1, v> + I1 - I0, s in {1, 2};
+ *   Eq. 5 -- Nesterov-accelerated ADMM (v, w, b, alpha, w_hat, b_hat),
+ *     w_hat^0 = b_hat^0 = 0, alpha^0 = 1;
+ *   Eq. 6 -- closed-form per-voxel v-step (s = 1 thresholding, s = 2
+ *     Sherman-Morrison) and the w-step as a division in the 3D DFT spectrum.
+ *
+ * Readings of the paper this library implements (the FP64 oracle follows
+ * the same ones):
+ *   w-step  w = F^-1[ F(v + b_hat) / (1 + (lambda/theta) K^n) ],
+ *           K = 2 (3 - cos 2pi p/M - cos 2pi q/N - cos 2pi r/H), periodic;
+ *   J = grad(I1 o phi) by central differences with clamped indices;
+ *   trilinear sampling with coordinates clamped to [0, dim - 1];
+ *   velocity composed per outer step = s * w^K with the global bound
+ *   s = min(1, kappa / max ||D w||_inf, delta / max |w|_inf)
+ *   (kappa = delta = INFINITY is the paper-literal, unbounded form);
+ *   ADMM state reset at every outer step.
+ *
+ * Conventions for every entry point:
+ *   - Volumes are fp32, C-contiguous [nz][ny][nx] (x fastest); vector fields
+ *     are SoA [3][nz][ny][nx] with component 0 along x.  (nx, ny, nz) are the
+ *     paper's (M, N, H).  Displacements are in voxels, phi(x) = x + u(x).
+ *   - "device" pointers are CUDA global-memory addresses on the current
+ *     device, 16-byte aligned; "host" pointers are ordinary host memory.
+ *     The library never allocates device memory: scratch comes from a
+ *     caller-owned workspace (nadmm_workspace_size / nadmm_set_workspace),
+ *     and the library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued asynchronously on it; host-detectable
+ *     errors are returned before anything is enqueued.  Device-side faults
+ *     of the numerics (non-finite values) are recorded in a status word read
+ *     by nadmm_get_status.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *   - Every function returning nadmm_status sets a thread-local message
+ *     (nadmm_last_error) on failure.
+ */
+#ifndef NADMM_H
+#define NADMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum nadmm_status {
+  NADMM_OK = 0,
+  NADMM_ERR_INVALID_ARG = 1,      /* null pointer, bad parameter value         */
+  NADMM_ERR_UNSUPPORTED_SIZE = 2, /* dim < 4, nx % 4, ny % 2, prime factor not
+                                     in {2,3,5,7}, or plane beyond shared mem  */
+  NADMM_ERR_ALIGNMENT = 3,        /* device pointer not 16-byte aligned        */
+  NADMM_ERR_NO_WORKSPACE = 4,     /* workspace missing or too small            */
+  NADMM_ERR_CUDA = 5,             /* a CUDA runtime call failed                */
+  NADMM_ERR_NONFINITE = 6         /* device status: NaN/Inf met in a bound step */
+} nadmm_status;
+
+/* flags */
+#define NADMM_FLAG_NO_GRAPH 1u    /* launch kernels directly instead of replaying
+                                     a captured CUDA graph                      */
+
+typedef struct nadmm_config {
+  int32_t nx, ny, nz;         /* grid (M, N, H); see NADMM_ERR_UNSUPPORTED_SIZE */
+  int32_t order_n;            /* regulariser order n, 1..8 (Eq. 2)            */
+  float lambda;               /* regularisation weight lambda >= 0 (Eq. 2)    */
+  float theta;                /* ADMM penalty theta > 0 (Eq. 4)               */
+  int32_t outer_iters;        /* compositions, >= 1 (Eq. 1 with N = 1)        */
+  int32_t inner_iters;        /* ADMM iterations per composition, >= 1 (Eq. 5)*/
+  int32_t data_term;          /* s: 2 (L2, Sherman-Morrison) or 1 (L1)        */
+  float eps;                  /* s = 1 denominator guard, > 0 (after Eq. 6)   */
+  float bound_kappa;          /* max ||D v||_inf per step, > 0 or INFINITY    */
+  float bound_delta;          /* max |v|_inf per step (voxels), > 0 or INFINITY */
+  uint32_t flags;             /* NADMM_FLAG_*                                 */
+} nadmm_config;
+
+typedef struct nadmm_context* nadmm_handle;
+
+/* Fill `cfg` with defaults for an nx x ny x nz grid: n = 2, lambda = 10,
+ * theta = 0.1, 10 outer x 10 inner iterations, s = 2, eps = 1e-6,
+ * kappa = 0.5, delta = 1.0, flags = 0.  Host only. */
+void nadmm_config_init(nadmm_config* cfg, int32_t nx, int32_t ny, int32_t nz);
+
+/* Validate `cfg` and create a handle (host memory only; no CUDA call).
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE.  *out is NULL on failure. */
+nadmm_status nadmm_create(const nadmm_config* cfg, nadmm_handle* out);
+
+/* Release the handle and any CUDA graph/stream it created.  NULL is a no-op.
+ * The workspace is the caller's and is not freed. */
+void nadmm_destroy(nadmm_handle h);
+
+/* Bytes of device workspace the handle needs (host only). */
+nadmm_status nadmm_workspace_size(nadmm_handle h, size_t* bytes);
+
+/* Attach a caller-owned device workspace of at least nadmm_workspace_size
+ * bytes, 256-byte aligned, on the current device.  Uploads the FFT twiddle
+ * and symbol tables into it (synchronous copy).  The memory must stay valid
+ * until the handle is destroyed or another workspace is attached.
+ * Errors: INVALID_ARG, ALIGNMENT, NO_WORKSPACE, CUDA. */
+nadmm_status nadmm_set_workspace(nadmm_handle h, void* dev_ptr, size_t bytes);
+
+/* Change lambda and theta (Eq. 2, Eq. 4) for later calls.  Host only. */
+nadmm_status nadmm_set_params(nadmm_handle h, float lambda, float theta);
+
+/* Full registration (Sec. 2 outer loop around Eq. 5/6):
+ *   fixed  = I0 (target), device [nz][ny][nx];
+ *   moving = I1 (source), device [nz][ny][nx];
+ *   u_out  = displacement u with I1 o (Id + u) ~ I0, device [3][nz][ny][nx].
+ * Runs outer_iters x (inner_iters ADMM iterations + bound + compose +
+ * re-warp) as one CUDA-graph replay on `stream` (or direct launches with
+ * NADMM_FLAG_NO_GRAPH).  Inputs are read-only; u_out is overwritten.
+ * Errors: INVALID_ARG, ALIGNMENT, NO_WORKSPACE, CUDA. */
+nadmm_status nadmm_register(nadmm_handle h, const float* fixed, const float* moving,
+                            float* u_out, void* stream);
+
+/* Same as nadmm_register with HOST buffers: copies fixed/moving host->device
+ * into the workspace, registers, and copies u back device->host, all
+ * enqueued on `stream`; returns after the stream has completed the copy of
+ * u_out (pinned host memory makes the copies asynchronous DMA). */
+nadmm_status nadmm_register_host(nadmm_handle h, const float* fixed_host,
+                                 const float* moving_host, float* u_out_host, void* stream);
+
+/* Synchronise `stream`, read and clear the device status word.
+ * Returns NADMM_OK or NADMM_ERR_NONFINITE (or CUDA on a runtime error). */
+nadmm_status nadmm_get_status(nadmm_handle h, void* stream);
+
+/* Thread-local description of the last failure of this thread. */
+const char* nadmm_last_error(void);
+
+/* Static name of a status code. */
+const char* nadmm_status_string(nadmm_status s);
+
+/* ---------------------------------------------------------------------
+ * Step-level entry points: one part of the path each, on device buffers of
+ * the handle's grid, using the handle's workspace as scratch.  They run the
+ * same kernels as nadmm_register.
+ * --------------------------------------------------------------------- */
+
+/* Regulariser step alone (Eq. 5 line 2 solved by Eq. 6 last line):
+ *   w = F^-1[ F(y) / (1 + (lambda/theta) K^n) ] per component,
+ * y, w device [3][nz][ny][nx]; w may alias y. */
+nadmm_status nadmm_spectral_solve(nadmm_handle h, const float* y, float* w, void* stream);
+
+/* ADMM iterations k .. k+steps-1 of Eq. 5 for the linearisation (J, c):
+ *   J device [3][nz][ny][nx] (= grad I1w), c device [nz][ny][nx] (= I1w - I0);
+ *   w_km1, w_km2, b_km1, b_km2: state after iteration k-1, device
+ *   [3][nz][ny][nx] (w^{k-1}, w^{k-2}, b^{k-1}, b^{k-2}); ignored when k = 0
+ *   (w_hat^0 = b_hat^0 = 0), and w_km2/b_km2 ignored when k = 1 (beta_0 = 0);
+ *   w_out, b_out: device [3][nz][ny][nx], receive w^{k+steps-1}, b^{k+steps-1}.
+ * Uses the Nesterov factors beta_{k-1} = (alpha^{k-1} - 1)/alpha^k.
+ * Output buffers must not alias inputs.  k >= 0, steps >= 1. */
+nadmm_status nadmm_admm_run(nadmm_handle h, const float* J, const float* c,
+                            const float* w_km1, const float* w_km2,
+                            const float* b_km1, const float* b_km2,
+                            int32_t k, int32_t steps, float* w_out, float* b_out,
+                            void* stream);
+
+/* Re-warp and re-linearise (Sec. 2, text after Eq. 2; Eq. 2's rho):
+ *   I1w = I1 o (Id + u) (trilinear), J = grad I1w, c = I1w - I0.
+ * fixed, moving device [nz][ny][nx]; u device [3][nz][ny][nx];
+ * J device [3][nz][ny][nx]; c device [nz][ny][nx]; I1w_out device
+ * [nz][ny][nx] or NULL.  Outputs must not alias inputs. */
+nadmm_status nadmm_linearise(nadmm_handle h, const float* fixed, const float* moving,
+                             const float* u, float* J, float* c, float* I1w_out,
+                             void* stream);
+
+/* Bound and compose (Sec. 2, Eq. 1 with N = 1):
+ *   s = min(1, kappa / max ||D w||_inf, delta / max |w|_inf),
+ *   u_out(x) = s w(x) + u_in(x + s w(x)).
+ * w, u_in, u_out device [3][nz][ny][nx] (u_out must not alias u_in or w);
+ * scale_out: device float receiving s, or NULL. */
+nadmm_status nadmm_bound_compose(nadmm_handle h, const float* w, const float* u_in,
+                                 float* u_out, float* scale_out, void* stream);
+
+/* Jacobian determinant det(I + D u) with central differences (Sec. 4,
+ * "Quantitative results"): det device [nz][ny][nx] or NULL;
+ * nonpositive device uint32 receiving the count of det <= 0, or NULL. */
+nadmm_status nadmm_jacobian_det(nadmm_handle h, const float* u, float* det,
+                                uint32_t* nonpositive, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Measurement
+ * --------------------------------------------------------------------- */
+
+/* Kernel classes reported by nadmm_register_profiled. */
+#define NADMM_KC_PLANE_FIRST   0  /* plane pass, k = 0 (no state read)          */
+#define NADMM_KC_PLANE_K1      1  /* plane pass, k = 1 (beta_0 = 0)             */
+#define NADMM_KC_PLANE         2  /* plane pass, k >= 2 (full Nesterov step)    */
+#define NADMM_KC_PLANE_FINAL   3  /* plane pass, final inverse x-DFT -> w^K     */
+#define NADMM_KC_PENCIL        4  /* pencil pass (y/z DFTs, symbol, inverses)   */
+#define NADMM_KC_WARP          5  /* trilinear re-warp of I1                    */
+#define NADMM_KC_GRAD          6  /* gradient + residual                        */
+#define NADMM_KC_BOUND         7  /* velocity bound reduction                   */
+#define NADMM_KC_COMPOSE       8  /* composition u <- s w + u o (Id + s w)      */
+#define NADMM_KC_COUNT         9
+
+/* nadmm_register with direct launches on `stream`, a CUDA event recorded on
+ * that stream before and after every kernel, and a stream synchronisation
+ * at the end.  kernel_ms[NADMM_KC_COUNT] (host) receives the summed device
+ * time of each kernel class, launches[NADMM_KC_COUNT] (host) the number of
+ * launches.  Output u_out is the same as nadmm_register's. */
+nadmm_status nadmm_register_profiled(nadmm_handle h, const float* fixed, const float* moving,
+                                     float* u_out, void* stream, float* kernel_ms,
+                                     int32_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NADMM_H */

@@ -1,0 +1,295 @@
+// In-place mixed-radix FFT building blocks for lines held in shared memory.
+//
+// The regulariser step of the method (Eq. 6, last line) is a division in the
+// spectrum of the 3D DFT.  Because the symbol 1/(1 + gamma K^n) is applied
+// point-wise, the forward transform may leave its output in any known order:
+// the forward pass is a decimation-in-frequency (DIF) FFT that stores each
+// stage's outputs back into the positions it read (no reordering), so its
+// result is in mixed-radix digit-reversed order; the inverse is the exact
+// stage-by-stage inverse (decimation in time, conjugate twiddles, stages in
+// reverse order), which takes that order back to natural order.  No
+// transposition or bit-reversal pass is ever made.
+//
+// Stage i (1-based) of a length-N transform with radices r_1..r_S works on
+// blocks of length L_i = N / (r_1...r_{i-1}); with m_i = L_i / r_i it reads
+// x[n1 + m_i j] (j < r_i) of each block, forms the r_i-point DFT over j,
+// multiplies output k by w_{L_i}^{n1 k} and stores it at n1 + m_i k.  The
+// frequency stored at position p = sum_i d_i m_i is k = sum_i d_i r_1..r_{i-1}.
+//
+// Every function here is __host__ __device__ and takes (tid, nthr) so that a
+// block-level loop is plain C++; the kernels separate phases with barriers.
+#pragma once
+#include <cuda_runtime.h>
+
+#if defined(__CUDACC__)
+#define NADMM_HD __host__ __device__ __forceinline__
+#else
+#define NADMM_HD inline
+#endif
+
+namespace nadmm {
+
+constexpr int kMaxStages = 5;
+
+// Radix plan of one axis, passed to kernels by value.
+struct AxisPlan {
+  int n;                     // transform length
+  int nst;                   // number of stages
+  int radix[kMaxStages];     // r_i
+  int L[kMaxStages];         // block length at stage i
+  int m[kMaxStages];         // L_i / r_i
+  int tw_off[kMaxStages];    // offset of stage i's twiddles in the axis table
+};
+
+NADMM_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+NADMM_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+NADMM_HD float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+NADMM_HD float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+NADMM_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+NADMM_HD float2 rot90(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// ----------------------------------------------------------------- codelets
+// Forward: X_k = sum_j x_j exp(-2 pi i jk/R); inverse uses exp(+2 pi i jk/R)
+// and is unnormalised.
+template <bool INV>
+NADMM_HD void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV>
+NADMM_HD void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  float2 t0 = cadd(x0, x2), t1 = csub(x0, x2);
+  float2 t2 = cadd(x1, x3), t3 = rot90<INV>(csub(x1, x3));
+  x0 = cadd(t0, t2);
+  x2 = csub(t0, t2);
+  x1 = cadd(t1, t3);
+  x3 = csub(t1, t3);
+}
+
+// cos/sin of 2 pi m / 16 for m = 0..3 (the rest follow by symmetry)
+struct C16 {
+  static constexpr float c1 = 0.92387953251128674f;  // cos(pi/8)
+  static constexpr float s1 = 0.38268343236508978f;  // sin(pi/8)
+  static constexpr float h = 0.70710678118654752f;   // cos(pi/4)
+};
+
+// multiply by w_8^k (k = 0..3), forward w = exp(-i pi/4)
+template <bool INV, int K>
+NADMM_HD float2 tw8(float2 a) {
+  if (K == 0) return a;
+  if (K == 2) return rot90<INV>(a);
+  const float h = C16::h;
+  if (K == 1) {  // (1 - i)/sqrt2 forward, (1 + i)/sqrt2 inverse
+    return INV ? make_float2(h * (a.x - a.y), h * (a.x + a.y))
+               : make_float2(h * (a.x + a.y), h * (a.y - a.x));
+  }
+  // K == 3: (-1 - i)/sqrt2 forward, (-1 + i)/sqrt2 inverse
+  return INV ? make_float2(-h * (a.x + a.y), h * (a.x - a.y))
+             : make_float2(h * (a.y - a.x), -h * (a.x + a.y));
+}
+
+template <bool INV>
+NADMM_HD void dft8(float2 (&x)[8]) {
+  // even/odd split: E = DFT4(x0,x2,x4,x6), O = DFT4(x1,x3,x5,x7)
+  float2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+  float2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  o1 = tw8<INV, 1>(o1);
+  o2 = tw8<INV, 2>(o2);
+  o3 = tw8<INV, 3>(o3);
+  x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
+  x[1] = cadd(e1, o1); x[5] = csub(e1, o1);
+  x[2] = cadd(e2, o2); x[6] = csub(e2, o2);
+  x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
+}
+
+// multiply by w_16^m for m in [0, 9]
+template <bool INV>
+NADMM_HD float2 tw16(float2 a, int m) {
+  float c, s;  // exp(-2 pi i m/16) = c - i s  (forward)
+  switch (m) {
+    case 0: return a;
+    case 1: c = C16::c1; s = C16::s1; break;
+    case 2: c = C16::h; s = C16::h; break;
+    case 3: c = C16::s1; s = C16::c1; break;
+    case 4: return rot90<INV>(a);
+    case 6: c = -C16::h; s = C16::h; break;
+    case 9: c = -C16::c1; s = -C16::s1; break;
+    default: c = 1.f; s = 0.f; break;
+  }
+  float sg = INV ? -s : s;  // forward multiplies by (c - i s)
+  return make_float2(a.x * c + a.y * sg, a.y * c - a.x * sg);
+}
+
+template <bool INV>
+NADMM_HD void dft16(float2 (&x)[16]) {
+  // 16 = 4 x 4: inner DFT4 over n1 of x[4 n1 + n2], twiddle w16^{n2 k1},
+  // outer DFT4 over n2; output index k1 + 4 k2.
+  float2 y[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    float2 a = x[n2], b = x[4 + n2], c = x[8 + n2], d = x[12 + n2];
+    dft4<INV>(a, b, c, d);
+    y[0 * 4 + n2] = a;
+    y[1 * 4 + n2] = tw16<INV>(b, n2);
+    y[2 * 4 + n2] = tw16<INV>(c, 2 * n2);
+    y[3 * 4 + n2] = tw16<INV>(d, 3 * n2);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 a = y[k1 * 4 + 0], b = y[k1 * 4 + 1], c = y[k1 * 4 + 2], d = y[k1 * 4 + 3];
+    dft4<INV>(a, b, c, d);
+    x[k1] = a;
+    x[k1 + 4] = b;
+    x[k1 + 8] = c;
+    x[k1 + 12] = d;
+  }
+}
+
+// odd prime radices: cos/sin(2 pi m/R), m = 1..(R-1)/2
+template <int R> struct OddTab;
+template <> struct OddTab<3> {
+  NADMM_HD static float c(int m) { (void)m; return -0.5f; }
+  NADMM_HD static float s(int m) { (void)m; return 0.86602540378443865f; }
+};
+template <> struct OddTab<5> {
+  NADMM_HD static float c(int m) { return m == 1 ? 0.30901699437494742f : -0.80901699437494742f; }
+  NADMM_HD static float s(int m) { return m == 1 ? 0.95105651629515357f : 0.58778525229247313f; }
+};
+template <> struct OddTab<7> {
+  NADMM_HD static float c(int m) {
+    return m == 1 ? 0.62348980185873353f : (m == 2 ? -0.22252093395631440f : -0.90096886790241913f);
+  }
+  NADMM_HD static float s(int m) {
+    return m == 1 ? 0.78183148246802981f : (m == 2 ? 0.97492791218182361f : 0.43388373911755812f);
+  }
+};
+
+// cos(2 pi q/R) and sin(2 pi q/R) for any integer q, from the half table
+template <int R>
+NADMM_HD void odd_cs(int q, float& c, float& s) {
+  q %= R;
+  if (q == 0) { c = 1.f; s = 0.f; return; }
+  if (q <= (R - 1) / 2) { c = OddTab<R>::c(q); s = OddTab<R>::s(q); return; }
+  c = OddTab<R>::c(R - q);
+  s = -OddTab<R>::s(R - q);
+}
+
+template <int R, bool INV>
+NADMM_HD void dft_odd(float2 (&x)[R]) {
+  constexpr int H = (R - 1) / 2;
+  float2 a[H], d[H];
+#pragma unroll
+  for (int j = 1; j <= H; ++j) {
+    a[j - 1] = cadd(x[j], x[R - j]);
+    d[j - 1] = csub(x[j], x[R - j]);
+  }
+  float2 x0 = x[0];
+  float2 sum = x0;
+#pragma unroll
+  for (int j = 0; j < H; ++j) sum = cadd(sum, a[j]);
+#pragma unroll
+  for (int k = 1; k <= H; ++k) {
+    float2 P = x0, Q = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 1; j <= H; ++j) {
+      float c, s;
+      odd_cs<R>(j * k, c, s);
+      P = cadd(P, cscale(a[j - 1], c));
+      Q = cadd(Q, cscale(d[j - 1], s));
+    }
+    // forward: X_k = P - i Q, X_{R-k} = P + i Q
+    float2 iQ = rot90<INV>(Q);  // -iQ forward, +iQ inverse
+    x[k] = cadd(P, iQ);
+    x[R - k] = csub(P, iQ);
+  }
+  x[0] = sum;
+}
+
+template <int R, bool INV>
+NADMM_HD void dft(float2 (&x)[R]) {
+  if constexpr (R == 2) {
+    dft2<INV>(x[0], x[1]);
+  } else if constexpr (R == 4) {
+    dft4<INV>(x[0], x[1], x[2], x[3]);
+  } else if constexpr (R == 8) {
+    dft8<INV>(x);
+  } else if constexpr (R == 16) {
+    dft16<INV>(x);
+  } else {
+    dft_odd<R, INV>(x);
+  }
+}
+
+// One radix-R butterfly of a stage: positions base[j * step], j < R.
+// Forward: DFT then twiddle w_L^{n1 k}; inverse: conjugate twiddle then
+// inverse DFT.  tw points at the stage table [(k-1) * m + n1].
+template <int R, bool INV>
+NADMM_HD void butterfly(float2* base, int step, const float2* tw, int m, int n1) {
+  float2 x[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) x[j] = base[j * step];
+  if (!INV) {
+    dft<R, false>(x);
+    if (m > 1) {
+#pragma unroll
+      for (int k = 1; k < R; ++k) x[k] = cmul(x[k], tw[(k - 1) * m + n1]);
+    }
+  } else {
+    if (m > 1) {
+#pragma unroll
+      for (int k = 1; k < R; ++k) x[k] = cmulc(x[k], tw[(k - 1) * m + n1]);
+    }
+    dft<R, true>(x);
+  }
+#pragma unroll
+  for (int j = 0; j < R; ++j) base[j * step] = x[j];
+}
+
+// All butterflies of stage s over a batch of `nlines` lines: element e of
+// line l lives at buf[l * ls + e * es].  Work item g -> (line fastest, then
+// n1, then block) so that a warp's lanes sit on different lines.
+template <int R, bool INV>
+NADMM_HD void stage_loop(float2* buf, int nlines, int es, int ls, int L, int m,
+                         const float2* tw, int nblk, int tid, int nthr) {
+  const int total = nlines * nblk * m;
+  const int step = m * es;
+  for (int g = tid; g < total; g += nthr) {
+    int line = g % nlines;
+    int q = g / nlines;
+    int n1 = q % m;
+    int blk = q / m;
+    float2* base = buf + line * ls + (blk * L + n1) * es;
+    butterfly<R, INV>(base, step, tw, m, n1);
+  }
+}
+
+// Stage s of plan p (forward or inverse); tw_axis is the axis table.
+template <bool INV>
+NADMM_HD void fft_stage(const AxisPlan& p, int s, float2* buf, int nlines, int es, int ls,
+                        const float2* tw_axis, int tid, int nthr) {
+  const int L = p.L[s], m = p.m[s], nblk = p.n / L;
+  const float2* tw = tw_axis + p.tw_off[s];
+  switch (p.radix[s]) {
+    case 2: stage_loop<2, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
+    case 3: stage_loop<3, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
+    case 4: stage_loop<4, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
+    case 5: stage_loop<5, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
+    case 7: stage_loop<7, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
+    case 8: stage_loop<8, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
+    default: stage_loop<16, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
+  }
+}
+
+}  // namespace nadmm

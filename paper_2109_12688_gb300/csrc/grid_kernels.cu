@@ -1,0 +1,232 @@
+// Outer diffeomorphic step (Sec. 2, Eq. 1 with N = 1) and grid utilities:
+//   bound the velocity, compose phi <- phi o (Id + v), re-warp the moving
+//   image by trilinear interpolation and recompute its gradient and the
+//   residual that linearise the data term of Eq. 2 for the next ADMM solve.
+// Sampling clamps coordinates to [0, dim - 1]; gradients are central
+// differences with clamped indices, (f[i+1] - f[i-1]) / 2.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "nadmm_internal.h"
+
+namespace nadmm {
+
+constexpr int kGridThreads = 256;
+
+__device__ __forceinline__ float trilerp(const float* __restrict__ f, Dims d, float px, float py,
+                                         float pz) {
+  px = fminf(fmaxf(px, 0.0f), (float)(d.nx - 1));
+  py = fminf(fmaxf(py, 0.0f), (float)(d.ny - 1));
+  pz = fminf(fmaxf(pz, 0.0f), (float)(d.nz - 1));
+  int ix = min((int)floorf(px), d.nx - 2);
+  int iy = min((int)floorf(py), d.ny - 2);
+  int iz = min((int)floorf(pz), d.nz - 2);
+  float fx = px - (float)ix, fy = py - (float)iy, fz = pz - (float)iz;
+  const size_t sx = 1, sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
+  const float* p = f + (size_t)iz * sz + (size_t)iy * sy + ix;
+  float c000 = __ldg(p), c001 = __ldg(p + sx);
+  float c010 = __ldg(p + sy), c011 = __ldg(p + sy + sx);
+  float c100 = __ldg(p + sz), c101 = __ldg(p + sz + sx);
+  float c110 = __ldg(p + sz + sy), c111 = __ldg(p + sz + sy + sx);
+  float c00 = c000 + fx * (c001 - c000);
+  float c01 = c010 + fx * (c011 - c010);
+  float c10 = c100 + fx * (c101 - c100);
+  float c11 = c110 + fx * (c111 - c110);
+  float c0 = c00 + fy * (c01 - c00);
+  float c1 = c10 + fy * (c11 - c10);
+  return c0 + fz * (c1 - c0);
+}
+
+__device__ __forceinline__ void vox_coords(size_t i, Dims d, int& x, int& y, int& z) {
+  x = (int)(i % d.nx);
+  size_t r = i / d.nx;
+  y = (int)(r % d.ny);
+  z = (int)(r / d.ny);
+}
+
+// I1w(x) = I1(x + u(x))
+__global__ void __launch_bounds__(kGridThreads) k_warp(Dims d, const float* __restrict__ I1,
+                                                       const float* __restrict__ u,
+                                                       float* __restrict__ I1w) {
+  const size_t V = (size_t)d.nx * d.ny * d.nz;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    vox_coords(i, d, x, y, z);
+    I1w[i] = trilerp(I1, d, (float)x + u[i], (float)y + u[V + i], (float)z + u[2 * V + i]);
+  }
+}
+
+// J = grad I1w (clamped central differences), c = I1w - I0
+__global__ void __launch_bounds__(kGridThreads) k_grad_residual(Dims d,
+                                                                const float* __restrict__ I1w,
+                                                                const float* __restrict__ I0,
+                                                                float* __restrict__ J,
+                                                                float* __restrict__ c) {
+  const size_t V = (size_t)d.nx * d.ny * d.nz;
+  const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    vox_coords(i, d, x, y, z);
+    size_t xp = i + (x + 1 < d.nx ? 1 : 0), xm = i - (x > 0 ? 1 : 0);
+    size_t yp = i + (y + 1 < d.ny ? sy : 0), ym = i - (y > 0 ? sy : 0);
+    size_t zp = i + (z + 1 < d.nz ? sz : 0), zm = i - (z > 0 ? sz : 0);
+    J[i] = 0.5f * (__ldg(I1w + xp) - __ldg(I1w + xm));
+    J[V + i] = 0.5f * (__ldg(I1w + yp) - __ldg(I1w + ym));
+    J[2 * V + i] = 0.5f * (__ldg(I1w + zp) - __ldg(I1w + zm));
+    c[i] = __ldg(I1w + i) - __ldg(I0 + i);
+  }
+}
+
+// Per-voxel |w|_inf and ||D w||_inf (max absolute row sum of the Jacobian);
+// grid-wide max through atomicMax on the float bit patterns (non-negative
+// floats order like their bits; NaN bits sort above +inf).
+__global__ void __launch_bounds__(kGridThreads) k_bound_reduce(Dims d, const float* __restrict__ w,
+                                                               unsigned* red) {
+  const size_t V = (size_t)d.nx * d.ny * d.nz;
+  const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
+  float mabs = 0.0f, mjac = 0.0f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    vox_coords(i, d, x, y, z);
+    size_t xp = i + (x + 1 < d.nx ? 1 : 0), xm = i - (x > 0 ? 1 : 0);
+    size_t yp = i + (y + 1 < d.ny ? sy : 0), ym = i - (y > 0 ? sy : 0);
+    size_t zp = i + (z + 1 < d.nz ? sz : 0), zm = i - (z > 0 ? sz : 0);
+    for (int comp = 0; comp < 3; ++comp) {
+      const float* f = w + comp * V;
+      float a = fabsf(__ldg(f + i));
+      float row = fabsf(0.5f * (__ldg(f + xp) - __ldg(f + xm))) +
+                  fabsf(0.5f * (__ldg(f + yp) - __ldg(f + ym))) +
+                  fabsf(0.5f * (__ldg(f + zp) - __ldg(f + zm)));
+      // fmaxf drops NaN; keep it visible through the bit-pattern max instead
+      mabs = (a != a || a > mabs) ? a : mabs;
+      mjac = (row != row || row > mjac) ? row : mjac;
+    }
+  }
+  unsigned ua = __float_as_uint(mabs), uj = __float_as_uint(mjac);
+  for (int off = 16; off > 0; off >>= 1) {
+    ua = max(ua, __shfl_xor_sync(0xffffffffu, ua, off));
+    uj = max(uj, __shfl_xor_sync(0xffffffffu, uj, off));
+  }
+  __shared__ unsigned sa[kGridThreads / 32], sj[kGridThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { sa[wid] = ua; sj[wid] = uj; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) { ua = max(ua, sa[k]); uj = max(uj, sj[k]); }
+    atomicMax(red, ua);
+    atomicMax(red + 1, uj);
+  }
+}
+
+__device__ __forceinline__ float bound_factor(const unsigned* red, float kappa, float delta,
+                                              unsigned* status) {
+  float mabs = __uint_as_float(red[0]);
+  float mjac = __uint_as_float(red[1]);
+  if (!isfinite(mabs) || !isfinite(mjac)) {
+    if (status) atomicOr(status, 1u);
+    return 0.0f;
+  }
+  float s = 1.0f;
+  if (isfinite(kappa) && mjac > 0.0f) s = fminf(s, kappa / mjac);
+  if (isfinite(delta) && mabs > 0.0f) s = fminf(s, delta / mabs);
+  return s;
+}
+
+// u_out(x) = v(x) + u_in(x + v(x)), v = s w
+__global__ void __launch_bounds__(kGridThreads) k_compose(Dims d, const float* __restrict__ w,
+                                                          const float* __restrict__ u_in,
+                                                          float* __restrict__ u_out,
+                                                          const unsigned* red, float kappa,
+                                                          float delta, unsigned* status,
+                                                          float* scale_out) {
+  const size_t V = (size_t)d.nx * d.ny * d.nz;
+  const float s = bound_factor(red, kappa, delta,
+                               (blockIdx.x == 0 && threadIdx.x == 0) ? status : nullptr);
+  if (scale_out != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *scale_out = s;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    vox_coords(i, d, x, y, z);
+    float vx = s * w[i], vy = s * w[V + i], vz = s * w[2 * V + i];
+    float px = (float)x + vx, py = (float)y + vy, pz = (float)z + vz;
+    u_out[i] = vx + trilerp(u_in, d, px, py, pz);
+    u_out[V + i] = vy + trilerp(u_in + V, d, px, py, pz);
+    u_out[2 * V + i] = vz + trilerp(u_in + 2 * V, d, px, py, pz);
+  }
+}
+
+// det(I + D u) per voxel, count of det <= 0
+__global__ void __launch_bounds__(kGridThreads) k_jacobian(Dims d, const float* __restrict__ u,
+                                                           float* __restrict__ det,
+                                                           unsigned* count) {
+  const size_t V = (size_t)d.nx * d.ny * d.nz;
+  const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
+  unsigned local = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, z;
+    vox_coords(i, d, x, y, z);
+    size_t xp = i + (x + 1 < d.nx ? 1 : 0), xm = i - (x > 0 ? 1 : 0);
+    size_t yp = i + (y + 1 < d.ny ? sy : 0), ym = i - (y > 0 ? sy : 0);
+    size_t zp = i + (z + 1 < d.nz ? sz : 0), zm = i - (z > 0 ? sz : 0);
+    float A[3][3];
+    for (int comp = 0; comp < 3; ++comp) {
+      const float* f = u + comp * V;
+      A[comp][0] = 0.5f * (__ldg(f + xp) - __ldg(f + xm));
+      A[comp][1] = 0.5f * (__ldg(f + yp) - __ldg(f + ym));
+      A[comp][2] = 0.5f * (__ldg(f + zp) - __ldg(f + zm));
+      A[comp][comp] += 1.0f;
+    }
+    float dt = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+               A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+               A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    if (det != nullptr) det[i] = dt;
+    if (!(dt > 0.0f)) ++local;
+  }
+  if (count != nullptr) {
+    for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+  }
+}
+
+static unsigned grid_for(size_t V) {
+  size_t b = (V + kGridThreads - 1) / kGridThreads;
+  const size_t cap = 152 * 16;  // grid-stride beyond 16 CTAs per SM
+  return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+static size_t vol(Dims d) { return (size_t)d.nx * d.ny * d.nz; }
+
+cudaError_t launch_warp(Dims d, const float* I1, const float* u, float* I1w, cudaStream_t s) {
+  k_warp<<<grid_for(vol(d)), kGridThreads, 0, s>>>(d, I1, u, I1w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_residual(Dims d, const float* I1w, const float* I0, float* J, float* c,
+                                 cudaStream_t s) {
+  k_grad_residual<<<grid_for(vol(d)), kGridThreads, 0, s>>>(d, I1w, I0, J, c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bound_reduce(Dims d, const float* w, unsigned* red, cudaStream_t s) {
+  k_bound_reduce<<<grid_for(vol(d)), kGridThreads, 0, s>>>(d, w, red);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compose(Dims d, const float* w, const float* u_in, float* u_out,
+                           const unsigned* red, float kappa, float delta, unsigned* status,
+                           float* scale_out, cudaStream_t s) {
+  k_compose<<<grid_for(vol(d)), kGridThreads, 0, s>>>(d, w, u_in, u_out, red, kappa, delta, status,
+                                                       scale_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobian(Dims d, const float* u, float* det, unsigned* count, cudaStream_t s) {
+  k_jacobian<<<grid_for(vol(d)), kGridThreads, 0, s>>>(d, u, det, count);
+  return cudaGetLastError();
+}
+
+}  // namespace nadmm

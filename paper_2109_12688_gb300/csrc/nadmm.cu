@@ -1,0 +1,653 @@
+// C ABI (include/nadmm.h): validation, workspace layout, FFT tables, the
+// outer/inner loop schedule and its CUDA-graph capture.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nadmm.h"
+#include "nadmm_internal.h"
+#include "plan.h"
+
+using namespace nadmm;
+
+namespace {
+
+thread_local std::string g_err;
+
+nadmm_status fail(nadmm_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+nadmm_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(NADMM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+struct nadmm_context {
+  nadmm_config cfg;
+  AxisPlan px, py, pz;
+  std::vector<float2> twx, twy, twz;
+  std::vector<int> posx;
+  std::vector<float> Kx, Ky, Kz;
+  std::vector<float> beta;   // beta_0 .. beta_{K-1}
+  int R = 0, pitch_x = 0, pitch_y = 0;
+  size_t V = 0, nkx = 0;
+  size_t plane_smem = 0, pencil_smem = 0;
+  // workspace layout (byte offsets)
+  size_t o_spec, o_y, o_wp, o_bp, o_J, o_c, o_I1w, o_ut, o_io_f, o_io_m, o_io_u, o_red, o_twx,
+      o_twy, o_twz, o_posx, o_Kx, o_Ky, o_Kz, total;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool kernels_configured = false;
+  // graph cache
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t cap = nullptr;
+
+  template <class T>
+  T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+};
+
+namespace {
+
+bool good_factors(int n) {
+  for (int q : {2, 3, 5, 7})
+    while (n % q == 0) n /= q;
+  return n == 1;
+}
+
+void invalidate_graph(nadmm_context* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+  h->gkey[0] = h->gkey[1] = h->gkey[2] = nullptr;
+}
+
+nadmm_status validate(const nadmm_config* c) {
+  if (!c) return fail(NADMM_ERR_INVALID_ARG, "config is NULL");
+  if (c->nx < 4 || c->ny < 4 || c->nz < 4)
+    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "every dimension must be >= 4");
+  if (c->nx % 4 != 0) return fail(NADMM_ERR_UNSUPPORTED_SIZE, "nx must be a multiple of 4");
+  if (c->ny % 2 != 0) return fail(NADMM_ERR_UNSUPPORTED_SIZE, "ny must be even");
+  if (!good_factors(c->nx) || !good_factors(c->ny) || !good_factors(c->nz))
+    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "dimensions must factor into 2, 3, 5, 7");
+  if (c->order_n < 1 || c->order_n > 8) return fail(NADMM_ERR_INVALID_ARG, "order_n must be in 1..8");
+  if (!(c->lambda >= 0.0f) || !std::isfinite(c->lambda))
+    return fail(NADMM_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+  if (!(c->theta > 0.0f) || !std::isfinite(c->theta))
+    return fail(NADMM_ERR_INVALID_ARG, "theta must be finite and > 0");
+  if (c->outer_iters < 1 || c->inner_iters < 1)
+    return fail(NADMM_ERR_INVALID_ARG, "iteration counts must be >= 1");
+  if (c->data_term != 1 && c->data_term != 2)
+    return fail(NADMM_ERR_INVALID_ARG, "data_term must be 1 or 2");
+  if (!(c->eps > 0.0f) || !std::isfinite(c->eps)) return fail(NADMM_ERR_INVALID_ARG, "eps must be > 0");
+  if (!(c->bound_kappa > 0.0f) || !(c->bound_delta > 0.0f))
+    return fail(NADMM_ERR_INVALID_ARG, "bound_kappa and bound_delta must be > 0 (INFINITY disables)");
+  if (c->flags & ~NADMM_FLAG_NO_GRAPH) return fail(NADMM_ERR_INVALID_ARG, "unknown flag bits");
+  return NADMM_OK;
+}
+
+void compute_beta(nadmm_context* h) {
+  // Eq. 5: alpha^0 = 1, alpha^{k+1} = (1 + sqrt(1 + 4 alpha_k^2)) / 2,
+  // beta_k = (alpha^k - 1) / alpha^{k+1}; evaluated in double on the host.
+  int K = h->cfg.inner_iters + 1;
+  h->beta.assign(K, 0.0f);
+  double a = 1.0;
+  for (int k = 0; k < K; ++k) {
+    double an = (1.0 + std::sqrt(1.0 + 4.0 * a * a)) / 2.0;
+    h->beta[k] = (float)((a - 1.0) / an);
+    a = an;
+  }
+}
+
+float beta_for(const nadmm_context* h, int k) {  // factor used to form w_hat^k
+  if (k <= 0) return 0.0f;
+  if (k - 1 < (int)h->beta.size()) return h->beta[k - 1];
+  double a = 1.0, b = 0.0;
+  for (int i = 0; i < k; ++i) {
+    double an = (1.0 + std::sqrt(1.0 + 4.0 * a * a)) / 2.0;
+    b = (a - 1.0) / an;
+    a = an;
+  }
+  return (float)b;
+}
+
+PlaneArgs plane_args(const nadmm_context* h) {
+  PlaneArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.spec = h->at<float2>(h->o_spec);
+  a.y = h->at<float>(h->o_y);
+  a.wp = h->at<float>(h->o_wp);
+  a.bp = h->at<float>(h->o_bp);
+  a.J = h->at<float>(h->o_J);
+  a.c = h->at<float>(h->o_c);
+  a.twx = h->at<float2>(h->o_twx);
+  a.posx = h->at<int>(h->o_posx);
+  a.px = h->px;
+  a.nx = h->cfg.nx;
+  a.ny = h->cfg.ny;
+  a.nz = h->cfg.nz;
+  a.nkx = (int)h->nkx;
+  a.R = h->R;
+  a.pitch = h->pitch_x;
+  a.theta = h->cfg.theta;
+  a.eps = h->cfg.eps;
+  a.data_term = h->cfg.data_term;
+  return a;
+}
+
+PencilArgs pencil_args(const nadmm_context* h) {
+  PencilArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.spec = h->at<float2>(h->o_spec);
+  a.twy = h->at<float2>(h->o_twy);
+  a.twz = h->at<float2>(h->o_twz);
+  a.Kx = h->at<float>(h->o_Kx);
+  a.Ky = h->at<float>(h->o_Ky);
+  a.Kz = h->at<float>(h->o_Kz);
+  a.py = h->py;
+  a.pz = h->pz;
+  a.ny = h->cfg.ny;
+  a.nz = h->cfg.nz;
+  a.nkx = (int)h->nkx;
+  a.pitch = h->pitch_y;
+  a.order_n = h->cfg.order_n;
+  a.gamma = h->cfg.lambda / h->cfg.theta;
+  a.scale = (float)(1.0 / ((double)h->cfg.nx * h->cfg.ny * h->cfg.nz));
+  return a;
+}
+
+Dims dims_of(const nadmm_context* h) { return Dims{h->cfg.nx, h->cfg.ny, h->cfg.nz}; }
+
+#define TRY(expr)                                  \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return e_;              \
+  } while (0)
+
+// Optional per-kernel timing: events recorded on the launch stream around
+// every kernel of a direct-launch run (never active during graph capture).
+struct Profiler {
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  cudaError_t begin(int kc, cudaStream_t s, cudaEvent_t& start) {
+    TRY(cudaEventCreate(&start));
+    cudaError_t e = cudaEventRecord(start, s);
+    if (e != cudaSuccess) cudaEventDestroy(start);
+    return e;
+  }
+  cudaError_t end(int kc, cudaStream_t s, cudaEvent_t start) {
+    cudaEvent_t stop;
+    TRY(cudaEventCreate(&stop));
+    cudaError_t e = cudaEventRecord(stop, s);
+    marks.push_back({kc, {start, stop}});
+    return e;
+  }
+  void release() {
+    for (auto& m : marks) {
+      cudaEventDestroy(m.second.first);
+      cudaEventDestroy(m.second.second);
+    }
+    marks.clear();
+  }
+};
+thread_local Profiler* g_prof = nullptr;
+
+// Launch `expr` as kernel class kc, bracketed by events when profiling.
+#define KLAUNCH(kc, s, expr)                          \
+  do {                                                \
+    cudaEvent_t st_ = nullptr;                        \
+    if (g_prof) TRY(g_prof->begin((kc), (s), st_));   \
+    TRY(expr);                                        \
+    if (g_prof) TRY(g_prof->end((kc), (s), st_));     \
+  } while (0)
+
+// ADMM iterations k0 .. k0+steps-1 starting from `first` (plane pass that
+// starts iteration k0), then the final inverse transform into w_out/b_out.
+cudaError_t enqueue_inner(nadmm_context* h, PlaneArgs first, int in_first, bool prev_first, int k0,
+                          int steps, const float* J, const float* c, float* w_out, float* b_out,
+                          cudaStream_t s) {
+  first.J = J;
+  first.c = c;
+  first.beta = beta_for(h, k0);
+  KLAUNCH(in_first == IN_NONE ? NADMM_KC_PLANE_FIRST : (prev_first ? NADMM_KC_PLANE : NADMM_KC_PLANE_K1),
+          s, launch_plane(in_first, prev_first, true, first, s));
+  PencilArgs pa = pencil_args(h);
+  PlaneArgs a = plane_args(h);
+  a.J = J;
+  a.c = c;
+  for (int k = k0 + 1; k < k0 + steps; ++k) {
+    KLAUNCH(NADMM_KC_PENCIL, s, launch_pencil(pa, s));
+    a.beta = beta_for(h, k);
+    KLAUNCH(k >= 2 ? NADMM_KC_PLANE : NADMM_KC_PLANE_K1, s, launch_plane(IN_SPEC, k >= 2, true, a, s));
+  }
+  KLAUNCH(NADMM_KC_PENCIL, s, launch_pencil(pa, s));
+  PlaneArgs fin = plane_args(h);
+  fin.w_out = w_out;
+  fin.b_out = b_out;
+  if (b_out == nullptr) fin.y = nullptr;  // b^{K-1} not wanted: skip reading y
+  KLAUNCH(NADMM_KC_PLANE_FINAL, s, launch_plane(IN_SPEC, false, false, fin, s));
+  return cudaSuccess;
+}
+
+cudaError_t enqueue_register(nadmm_context* h, const float* I0, const float* I1, float* u_out,
+                             cudaStream_t s) {
+  const Dims d = dims_of(h);
+  const size_t V = h->V;
+  const int O = h->cfg.outer_iters, K = h->cfg.inner_iters;
+  float* ut = h->at<float>(h->o_ut);
+  float* I1w = h->at<float>(h->o_I1w);
+  float* J = h->at<float>(h->o_J);
+  float* c = h->at<float>(h->o_c);
+  float* vbuf = h->at<float>(h->o_wp);  // velocity w^K reuses the w state slot
+  unsigned* red = h->at<unsigned>(h->o_red);
+  // u ping-pongs between u_out and ut so that the last compose lands in u_out
+  auto dst_of = [&](int o) { return ((O - 1 - o) % 2 == 0) ? u_out : ut; };
+  float* u_cur = (dst_of(0) == u_out) ? ut : u_out;
+  TRY(cudaMemsetAsync(red, 0, 4 * sizeof(unsigned), s));  // red[0..1], status red[2]
+  TRY(cudaMemsetAsync(u_cur, 0, 3 * V * sizeof(float), s));
+  KLAUNCH(NADMM_KC_WARP, s, launch_warp(d, I1, u_cur, I1w, s));
+  KLAUNCH(NADMM_KC_GRAD, s, launch_grad_residual(d, I1w, I0, J, c, s));
+  for (int o = 0; o < O; ++o) {
+    PlaneArgs first = plane_args(h);
+    TRY(enqueue_inner(h, first, IN_NONE, false, 0, K, J, c, vbuf, nullptr, s));
+    TRY(cudaMemsetAsync(red, 0, 2 * sizeof(unsigned), s));
+    KLAUNCH(NADMM_KC_BOUND, s, launch_bound_reduce(d, vbuf, red, s));
+    float* u_new = dst_of(o);
+    KLAUNCH(NADMM_KC_COMPOSE, s,
+            launch_compose(d, vbuf, u_cur, u_new, red, h->cfg.bound_kappa, h->cfg.bound_delta,
+                           red + 2, nullptr, s));
+    u_cur = u_new;
+    if (o + 1 < O) {
+      KLAUNCH(NADMM_KC_WARP, s, launch_warp(d, I1, u_cur, I1w, s));
+      KLAUNCH(NADMM_KC_GRAD, s, launch_grad_residual(d, I1w, I0, J, c, s));
+    }
+  }
+  return cudaSuccess;
+}
+
+nadmm_status need_ws(const nadmm_context* h) {
+  if (!h) return fail(NADMM_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->ws) return fail(NADMM_ERR_NO_WORKSPACE, "no workspace attached (nadmm_set_workspace)");
+  return NADMM_OK;
+}
+
+nadmm_status check_dev_ptrs(std::initializer_list<const void*> ptrs) {
+  for (const void* p : ptrs) {
+    if (!p) return fail(NADMM_ERR_INVALID_ARG, "device pointer is NULL");
+    if (!aligned16(p)) return fail(NADMM_ERR_ALIGNMENT, "device pointer not 16-byte aligned");
+  }
+  return NADMM_OK;
+}
+
+nadmm_status run_register(nadmm_context* h, const float* I0, const float* I1, float* u_out,
+                          cudaStream_t stream) {
+  if (h->cfg.flags & NADMM_FLAG_NO_GRAPH) {
+    cudaError_t e = enqueue_register(h, I0, I1, u_out, stream);
+    return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_register");
+  }
+  if (!h->gexec || h->gkey[0] != I0 || h->gkey[1] != I1 || h->gkey[2] != u_out) {
+    invalidate_graph(h);
+    cudaError_t e;
+    if (!h->cap) {
+      e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    cudaError_t le = enqueue_register(h, I0, I1, u_out, h->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->cap, &g);
+    if (le != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(le, "capture of nadmm_register");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      h->gexec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    h->gkey[0] = I0;
+    h->gkey[1] = I1;
+    h->gkey[2] = u_out;
+  }
+  cudaError_t e = cudaGraphLaunch(h->gexec, stream);
+  return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+void nadmm_config_init(nadmm_config* c, int32_t nx, int32_t ny, int32_t nz) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->nx = nx;
+  c->ny = ny;
+  c->nz = nz;
+  c->order_n = 2;
+  c->lambda = 10.0f;
+  c->theta = 0.1f;
+  c->outer_iters = 10;
+  c->inner_iters = 10;
+  c->data_term = 2;
+  c->eps = 1e-6f;
+  c->bound_kappa = 0.5f;
+  c->bound_delta = 1.0f;
+  c->flags = 0;
+}
+
+const char* nadmm_last_error(void) { return g_err.c_str(); }
+
+const char* nadmm_status_string(nadmm_status s) {
+  switch (s) {
+    case NADMM_OK: return "NADMM_OK";
+    case NADMM_ERR_INVALID_ARG: return "NADMM_ERR_INVALID_ARG";
+    case NADMM_ERR_UNSUPPORTED_SIZE: return "NADMM_ERR_UNSUPPORTED_SIZE";
+    case NADMM_ERR_ALIGNMENT: return "NADMM_ERR_ALIGNMENT";
+    case NADMM_ERR_NO_WORKSPACE: return "NADMM_ERR_NO_WORKSPACE";
+    case NADMM_ERR_CUDA: return "NADMM_ERR_CUDA";
+    case NADMM_ERR_NONFINITE: return "NADMM_ERR_NONFINITE";
+  }
+  return "unknown nadmm_status";
+}
+
+nadmm_status nadmm_create(const nadmm_config* cfg, nadmm_handle* out) {
+  if (!out) return fail(NADMM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  nadmm_status st = validate(cfg);
+  if (st != NADMM_OK) return st;
+  nadmm_context* h = new nadmm_context();
+  h->cfg = *cfg;
+  if (!factor_axis(cfg->nx, h->px) || !factor_axis(cfg->ny, h->py) || !factor_axis(cfg->nz, h->pz)) {
+    delete h;
+    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "no radix plan for these dimensions");
+  }
+  h->V = (size_t)cfg->nx * cfg->ny * cfg->nz;
+  h->nkx = (size_t)cfg->nx / 2 + 1;
+  h->R = (cfg->ny % 16 == 0) ? 16 : (cfg->ny % 8 == 0) ? 8 : (cfg->ny % 4 == 0) ? 4 : 2;
+  h->pitch_x = cfg->nx + 1;
+  h->pitch_y = cfg->ny + 1;
+  h->plane_smem = plane_smem_bytes(h->R, h->pitch_x);
+  h->pencil_smem = pencil_smem_bytes(cfg->ny, cfg->nz, h->pitch_y);
+  if (h->pencil_smem > 227 * 1024 || h->plane_smem > 227 * 1024) {
+    delete h;
+    return fail(NADMM_ERR_UNSUPPORTED_SIZE,
+                "a (ny x nz) spectrum plane exceeds the 227 KB of shared memory per CTA");
+  }
+  h->twx = axis_twiddles(h->px);
+  h->twy = axis_twiddles(h->py);
+  h->twz = axis_twiddles(h->pz);
+  h->posx = pos_table(h->px);
+  h->Kx = symbol_natural(cfg->nx, (int)h->nkx);
+  h->Ky = symbol_by_position(h->py);
+  h->Kz = symbol_by_position(h->pz);
+  compute_beta(h);
+  // workspace layout
+  const size_t V = h->V;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o = align_up(o + bytes);
+    return r;
+  };
+  h->o_spec = take(3 * h->nkx * cfg->ny * cfg->nz * sizeof(float2));
+  h->o_y = take(3 * V * sizeof(float));
+  h->o_wp = take(3 * V * sizeof(float));
+  h->o_bp = take(3 * V * sizeof(float));
+  h->o_J = take(3 * V * sizeof(float));
+  h->o_c = take(V * sizeof(float));
+  h->o_I1w = take(V * sizeof(float));
+  h->o_ut = take(3 * V * sizeof(float));
+  h->o_io_f = take(V * sizeof(float));
+  h->o_io_m = take(V * sizeof(float));
+  h->o_io_u = take(3 * V * sizeof(float));
+  h->o_red = take(4 * sizeof(unsigned));
+  h->o_twx = take(h->twx.size() * sizeof(float2));
+  h->o_twy = take(h->twy.size() * sizeof(float2));
+  h->o_twz = take(h->twz.size() * sizeof(float2));
+  h->o_posx = take(h->posx.size() * sizeof(int));
+  h->o_Kx = take(h->Kx.size() * sizeof(float));
+  h->o_Ky = take(h->Ky.size() * sizeof(float));
+  h->o_Kz = take(h->Kz.size() * sizeof(float));
+  h->total = o;
+  *out = h;
+  return NADMM_OK;
+}
+
+void nadmm_destroy(nadmm_handle h) {
+  if (!h) return;
+  invalidate_graph(h);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+}
+
+nadmm_status nadmm_workspace_size(nadmm_handle h, size_t* bytes) {
+  if (!h || !bytes) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
+  *bytes = h->total;
+  return NADMM_OK;
+}
+
+nadmm_status nadmm_set_workspace(nadmm_handle h, void* dev_ptr, size_t bytes) {
+  if (!h || !dev_ptr) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
+  if (((uintptr_t)dev_ptr % kAlign) != 0)
+    return fail(NADMM_ERR_ALIGNMENT, "workspace must be 256-byte aligned");
+  if (bytes < h->total) return fail(NADMM_ERR_NO_WORKSPACE, "workspace smaller than nadmm_workspace_size");
+  invalidate_graph(h);
+  h->ws = static_cast<char*>(dev_ptr);
+  h->ws_bytes = bytes;
+  cudaError_t e;
+  if (!h->kernels_configured) {
+    e = configure_admm_kernels(h->plane_smem, h->pencil_smem);
+    if (e != cudaSuccess) {
+      h->ws = nullptr;
+      return cuda_fail(e, "cudaFuncSetAttribute");
+    }
+    h->kernels_configured = true;
+  }
+  struct Up { size_t off; const void* src; size_t n; } ups[] = {
+      {h->o_twx, h->twx.data(), h->twx.size() * sizeof(float2)},
+      {h->o_twy, h->twy.data(), h->twy.size() * sizeof(float2)},
+      {h->o_twz, h->twz.data(), h->twz.size() * sizeof(float2)},
+      {h->o_posx, h->posx.data(), h->posx.size() * sizeof(int)},
+      {h->o_Kx, h->Kx.data(), h->Kx.size() * sizeof(float)},
+      {h->o_Ky, h->Ky.data(), h->Ky.size() * sizeof(float)},
+      {h->o_Kz, h->Kz.data(), h->Kz.size() * sizeof(float)},
+  };
+  for (const Up& u : ups) {
+    e = cudaMemcpy(h->ws + u.off, u.src, u.n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      h->ws = nullptr;
+      return cuda_fail(e, "upload of FFT tables");
+    }
+  }
+  e = cudaMemset(h->ws + h->o_red, 0, 4 * sizeof(unsigned));
+  if (e != cudaSuccess) {
+    h->ws = nullptr;
+    return cuda_fail(e, "cudaMemset");
+  }
+  return NADMM_OK;
+}
+
+nadmm_status nadmm_set_params(nadmm_handle h, float lambda, float theta) {
+  if (!h) return fail(NADMM_ERR_INVALID_ARG, "handle is NULL");
+  nadmm_config c = h->cfg;
+  c.lambda = lambda;
+  c.theta = theta;
+  nadmm_status st = validate(&c);
+  if (st != NADMM_OK) return st;
+  h->cfg = c;
+  invalidate_graph(h);
+  return NADMM_OK;
+}
+
+nadmm_status nadmm_register(nadmm_handle h, const float* fixed, const float* moving, float* u_out,
+                            void* stream) {
+  nadmm_status st = need_ws(h);
+  if (st != NADMM_OK) return st;
+  if ((st = check_dev_ptrs({fixed, moving, u_out})) != NADMM_OK) return st;
+  return run_register(h, fixed, moving, u_out, (cudaStream_t)stream);
+}
+
+nadmm_status nadmm_register_host(nadmm_handle h, const float* fixed_host, const float* moving_host,
+                                 float* u_out_host, void* stream) {
+  nadmm_status st = need_ws(h);
+  if (st != NADMM_OK) return st;
+  if (!fixed_host || !moving_host || !u_out_host) return fail(NADMM_ERR_INVALID_ARG, "NULL host buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  float* f = h->at<float>(h->o_io_f);
+  float* m = h->at<float>(h->o_io_m);
+  float* u = h->at<float>(h->o_io_u);
+  const size_t V = h->V;
+  cudaError_t e = cudaMemcpyAsync(f, fixed_host, V * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m, moving_host, V * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+  if ((st = run_register(h, f, m, u, s)) != NADMM_OK) return st;
+  e = cudaMemcpyAsync(u_out_host, u, 3 * V * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "device-to-host copy");
+}
+
+nadmm_status nadmm_register_profiled(nadmm_handle h, const float* fixed, const float* moving,
+                                     float* u_out, void* stream, float* kernel_ms,
+                                     int32_t* launches) {
+  nadmm_status st = need_ws(h);
+  if (st != NADMM_OK) return st;
+  if ((st = check_dev_ptrs({fixed, moving, u_out})) != NADMM_OK) return st;
+  if (!kernel_ms || !launches) return fail(NADMM_ERR_INVALID_ARG, "NULL output array");
+  cudaStream_t s = (cudaStream_t)stream;
+  Profiler prof;
+  g_prof = &prof;
+  cudaError_t e = enqueue_register(h, fixed, moving, u_out, s);
+  g_prof = nullptr;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  for (int i = 0; i < NADMM_KC_COUNT; ++i) {
+    kernel_ms[i] = 0.0f;
+    launches[i] = 0;
+  }
+  if (e == cudaSuccess) {
+    for (auto& m : prof.marks) {
+      float ms = 0.0f;
+      e = cudaEventElapsedTime(&ms, m.second.first, m.second.second);
+      if (e != cudaSuccess) break;
+      kernel_ms[m.first] += ms;
+      launches[m.first] += 1;
+    }
+  }
+  prof.release();
+  return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_register_profiled");
+}
+
+nadmm_status nadmm_get_status(nadmm_handle h, void* stream) {
+  nadmm_status st = need_ws(h);
+  if (st != NADMM_OK) return st;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  unsigned word = 0;
+  unsigned* dev = h->at<unsigned>(h->o_red) + 2;
+  e = cudaMemcpy(&word, dev, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(dev, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (word & 1u) return fail(NADMM_ERR_NONFINITE, "non-finite velocity met in the bound step");
+  return NADMM_OK;
+}
+
+nadmm_status nadmm_spectral_solve(nadmm_handle h, const float* y, float* w, void* stream) {
+  nadmm_status st = need_ws(h);
+  if (st != NADMM_OK) return st;
+  if ((st = check_dev_ptrs({y, w})) != NADMM_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  PlaneArgs a = plane_args(h);
+  a.y = nullptr;
+  a.w_in = y;
+  cudaError_t e = launch_plane(IN_FIELD, false, true, a, s);
+  if (e == cudaSuccess) e = launch_pencil(pencil_args(h), s);
+  if (e == cudaSuccess) {
+    PlaneArgs f = plane_args(h);
+    f.y = nullptr;
+    f.w_out = w;
+    f.b_out = nullptr;
+    e = launch_plane(IN_SPEC, false, false, f, s);
+  }
+  return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_spectral_solve");
+}
+
+nadmm_status nadmm_admm_run(nadmm_handle h, const float* J, const float* c, const float* w_km1,
+                            const float* w_km2, const float* b_km1, const float* b_km2, int32_t k,
+                            int32_t steps, float* w_out, float* b_out, void* stream) {
+  nadmm_status st = need_ws(h);
+  if (st != NADMM_OK) return st;
+  if (k < 0 || steps < 1) return fail(NADMM_ERR_INVALID_ARG, "need k >= 0 and steps >= 1");
+  if ((st = check_dev_ptrs({J, c, w_out, b_out})) != NADMM_OK) return st;
+  if (k >= 1 && (st = check_dev_ptrs({w_km1, b_km1})) != NADMM_OK) return st;
+  if (k >= 2 && (st = check_dev_ptrs({w_km2, b_km2})) != NADMM_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  PlaneArgs first = plane_args(h);
+  int in_mode = IN_NONE;
+  bool prev = false;
+  if (k >= 1) {
+    in_mode = IN_STATE;
+    first.w_in = w_km1;
+    first.b_in = b_km1;
+    if (k >= 2) {
+      prev = true;
+      first.wprev_in = w_km2;
+      first.bprev_in = b_km2;
+    }
+  }
+  cudaError_t e = enqueue_inner(h, first, in_mode, prev, k, steps, J, c, w_out, b_out, s);
+  return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_admm_run");
+}
+
+nadmm_status nadmm_linearise(nadmm_handle h, const float* fixed, const float* moving, const float* u,
+                             float* J, float* c, float* I1w_out, void* stream) {
+  nadmm_status st = need_ws(h);
+  if (st != NADMM_OK) return st;
+  if ((st = check_dev_ptrs({fixed, moving, u, J, c})) != NADMM_OK) return st;
+  if (I1w_out && !aligned16(I1w_out)) return fail(NADMM_ERR_ALIGNMENT, "I1w_out not 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  float* I1w = I1w_out ? I1w_out : h->at<float>(h->o_I1w);
+  cudaError_t e = launch_warp(dims_of(h), moving, u, I1w, s);
+  if (e == cudaSuccess) e = launch_grad_residual(dims_of(h), I1w, fixed, J, c, s);
+  return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_linearise");
+}
+
+nadmm_status nadmm_bound_compose(nadmm_handle h, const float* w, const float* u_in, float* u_out,
+                                 float* scale_out, void* stream) {
+  nadmm_status st = need_ws(h);
+  if (st != NADMM_OK) return st;
+  if ((st = check_dev_ptrs({w, u_in, u_out})) != NADMM_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* red = h->at<unsigned>(h->o_red);
+  cudaError_t e = cudaMemsetAsync(red, 0, 2 * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = launch_bound_reduce(dims_of(h), w, red, s);
+  if (e == cudaSuccess)
+    e = launch_compose(dims_of(h), w, u_in, u_out, red, h->cfg.bound_kappa, h->cfg.bound_delta,
+                       red + 2, scale_out, s);
+  return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_bound_compose");
+}
+
+nadmm_status nadmm_jacobian_det(nadmm_handle h, const float* u, float* det, uint32_t* nonpositive,
+                                void* stream) {
+  if (!h) return fail(NADMM_ERR_INVALID_ARG, "handle is NULL");
+  if (nadmm_status st = check_dev_ptrs({u}); st != NADMM_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (nonpositive) e = cudaMemsetAsync(nonpositive, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = launch_jacobian(dims_of(h), u, det, nonpositive, s);
+  return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_jacobian_det");
+}
+
+}  // extern "C"

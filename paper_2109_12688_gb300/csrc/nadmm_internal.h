@@ -1,0 +1,87 @@
+// Internal interfaces between the host orchestration (nadmm.cu) and the
+// kernel translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_device.cuh"
+
+namespace nadmm {
+
+// ---------------------------------------------------------------- ADMM passes
+// Where the "plane pass" takes w^{k-1}, b^{k-1} from.
+enum InMode : int {
+  IN_NONE = 0,   // k = 0: w_hat^0 = b_hat^0 = 0
+  IN_SPEC = 1,   // inverse x-transform of the filtered spectrum; b = y - w
+  IN_STATE = 2,  // explicit real-space state buffers (step-level entry point)
+  IN_FIELD = 3,  // plain forward transform of a real field (spectral solve)
+};
+
+// Plane pass: one CTA owns R rows (y0..y0+R-1) of one z-plane, all three
+// components.  It finishes iteration k-1 (inverse x-DFT, dual update) and
+// starts iteration k (Nesterov extrapolation, closed-form v-step, forward
+// x-DFT), so the 3D transform needs only this pass and the pencil pass.
+struct PlaneArgs {
+  float2* spec;            // [3][nkx][nz][ny] half spectrum (in/out)
+  float* y;                // [3][V] y = v + b_hat of the current iteration (in/out) or null
+  float* wp;               // [3][V] w state slot (in: w^{k-2}, out: w^{k-1})
+  float* bp;               // [3][V] b state slot
+  const float* J;          // [3][V]
+  const float* c;          // [V]
+  const float* w_in;       // IN_STATE: w^{k-1};  IN_FIELD: the field
+  const float* b_in;       // IN_STATE: b^{k-1}
+  const float* wprev_in;   // IN_STATE: w^{k-2}
+  const float* bprev_in;   // IN_STATE: b^{k-2}
+  float* w_out;            // no-step variant: receives w^{k-1}
+  float* b_out;            // no-step variant: receives b^{k-1} (or null)
+  const float2* twx;       // x-axis stage twiddles
+  const int* posx;         // position of frequency kx after the forward x-DFT
+  AxisPlan px;
+  int nx, ny, nz, nkx;     // nkx = nx/2 + 1
+  int R;                   // rows per CTA (even, divides ny)
+  int pitch;               // shared-memory line pitch (odd, >= nx)
+  float beta;              // beta_{k-1}
+  float theta, eps;
+  int data_term;           // 1 or 2
+};
+
+// Pencil pass: one CTA owns one (component, kx) plane of the half spectrum,
+// [nz][ny] contiguous: forward y- and z-DFTs, the inverse-symbol multiply of
+// Eq. 6, inverse z- and y-DFTs.
+struct PencilArgs {
+  float2* spec;            // [3][nkx][nz][ny] (in/out)
+  const float2* twy;
+  const float2* twz;
+  const float* Kx;         // [nkx] 4 sin^2(pi kx / nx)
+  const float* Ky;         // [ny] 4 sin^2(pi ky / ny) by position
+  const float* Kz;         // [nz] 4 sin^2(pi kz / nz) by position
+  AxisPlan py, pz;
+  int ny, nz, nkx;
+  int pitch;               // shared-memory row pitch (odd, >= ny)
+  int order_n;
+  float gamma;             // lambda / theta
+  float scale;             // 1 / (nx ny nz)
+};
+
+// mode = InMode * 4 + prev * 2 + step
+cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, cudaStream_t s);
+cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s);
+size_t plane_smem_bytes(int R, int pitch);
+size_t pencil_smem_bytes(int ny, int nz, int pitch);
+cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem);
+
+// ---------------------------------------------------------------- grid ops
+struct Dims { int nx, ny, nz; };
+
+cudaError_t launch_warp(Dims d, const float* I1, const float* u, float* I1w, cudaStream_t s);
+cudaError_t launch_grad_residual(Dims d, const float* I1w, const float* I0, float* J, float* c,
+                                 cudaStream_t s);
+// red[0] = bits of max |w|_inf, red[1] = bits of max ||Dw||_inf (must start at 0)
+cudaError_t launch_bound_reduce(Dims d, const float* w, unsigned* red, cudaStream_t s);
+// s from red; u_out = s w + u_in(x + s w); status |= 1 on non-finite maxima
+cudaError_t launch_compose(Dims d, const float* w, const float* u_in, float* u_out,
+                           const unsigned* red, float kappa, float delta, unsigned* status,
+                           float* scale_out, cudaStream_t s);
+cudaError_t launch_jacobian(Dims d, const float* u, float* det, unsigned* count, cudaStream_t s);
+
+}  // namespace nadmm

@@ -1,0 +1,101 @@
+// Host-side FFT plans and tables for the spectral regulariser step (Eq. 6).
+// Twiddles are evaluated in double precision with the host C library and
+// rounded once to float.
+#pragma once
+#include <cmath>
+#include <vector>
+
+#include "fft_device.cuh"
+
+namespace nadmm {
+
+// Radices supported by the shared-memory stages, largest first.
+inline bool factor_axis(int n, AxisPlan& p) {
+  if (n < 2) return false;
+  int rem = n, ns = 0;
+  int rad[16];
+  // power-of-two part in radix-16/8/4/2 stages, then odd primes
+  while (rem % 16 == 0) { rad[ns++] = 16; rem /= 16; }
+  if (rem % 8 == 0) { rad[ns++] = 8; rem /= 8; }
+  if (rem % 4 == 0) { rad[ns++] = 4; rem /= 4; }
+  if (rem % 2 == 0) { rad[ns++] = 2; rem /= 2; }
+  for (int q : {3, 5, 7}) {
+    while (rem % q == 0) {
+      if (ns >= 16) return false;
+      rad[ns++] = q;
+      rem /= q;
+    }
+  }
+  if (rem != 1 || ns > kMaxStages) return false;
+  p.n = n;
+  p.nst = ns;
+  int L = n, off = 0;
+  for (int i = 0; i < ns; ++i) {
+    p.radix[i] = rad[i];
+    p.L[i] = L;
+    p.m[i] = L / rad[i];
+    p.tw_off[i] = off;
+    if (p.m[i] > 1) off += (rad[i] - 1) * p.m[i];
+    L /= rad[i];
+  }
+  for (int i = ns; i < kMaxStages; ++i) { p.radix[i] = 1; p.L[i] = 1; p.m[i] = 1; p.tw_off[i] = off; }
+  return true;
+}
+
+// Stage twiddles: stage i holds w_{L_i}^{n1 k} at [(k-1) m_i + n1].
+inline std::vector<float2> axis_twiddles(const AxisPlan& p) {
+  std::vector<float2> tw;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int i = 0; i < p.nst; ++i) {
+    if (p.m[i] <= 1) continue;
+    for (int k = 1; k < p.radix[i]; ++k)
+      for (int n1 = 0; n1 < p.m[i]; ++n1) {
+        long long e = (long long)n1 * k % p.L[i];
+        double a = -two_pi * (double)e / (double)p.L[i];
+        tw.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+      }
+  }
+  if (tw.empty()) tw.push_back(make_float2(1.f, 0.f));
+  return tw;
+}
+
+// Position holding frequency k after the forward transform.
+inline int freq_to_pos(const AxisPlan& p, int k) {
+  int pos = 0;
+  for (int i = 0; i < p.nst; ++i) {
+    int d = k % p.radix[i];
+    k /= p.radix[i];
+    pos += d * p.m[i];
+  }
+  return pos;
+}
+
+inline std::vector<int> pos_table(const AxisPlan& p) {
+  std::vector<int> t(p.n);
+  for (int k = 0; k < p.n; ++k) t[k] = freq_to_pos(p, k);
+  return t;
+}
+
+// 4 sin^2(pi k / n) stored at the position that holds frequency k, i.e. the
+// per-axis term of K = 2 (3 - cos - cos - cos) (text after Eq. 6).
+inline std::vector<float> symbol_by_position(const AxisPlan& p) {
+  std::vector<float> t(p.n);
+  const double pi = 3.14159265358979323846264338328;
+  for (int k = 0; k < p.n; ++k) {
+    double s = std::sin(pi * (double)k / (double)p.n);
+    t[freq_to_pos(p, k)] = (float)(4.0 * s * s);
+  }
+  return t;
+}
+
+inline std::vector<float> symbol_natural(int n, int count) {
+  std::vector<float> t(count);
+  const double pi = 3.14159265358979323846264338328;
+  for (int k = 0; k < count; ++k) {
+    double s = std::sin(pi * (double)k / (double)n);
+    t[k] = (float)(4.0 * s * s);
+  }
+  return t;
+}
+
+}  // namespace nadmm

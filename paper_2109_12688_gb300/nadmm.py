@@ -1,0 +1,253 @@
+"""Thin ctypes binding of ``libnadmm.so`` (C ABI declared in include/nadmm.h).
+
+Functions carry the C names and only marshal arguments: torch tensors (or raw
+integer addresses) become pointers, torch streams become ``cudaStream_t``.
+Every step of the registration runs in the library's CUDA kernels; if the
+library is missing this module raises instead of computing anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libnadmm.so")
+
+NADMM_OK = 0
+NADMM_ERR_INVALID_ARG = 1
+NADMM_ERR_UNSUPPORTED_SIZE = 2
+NADMM_ERR_ALIGNMENT = 3
+NADMM_ERR_NO_WORKSPACE = 4
+NADMM_ERR_CUDA = 5
+NADMM_ERR_NONFINITE = 6
+NADMM_FLAG_NO_GRAPH = 1
+
+KERNEL_CLASSES = ("plane_first", "plane_k1", "plane", "plane_final", "pencil", "warp", "grad",
+                  "bound", "compose")
+
+
+class NadmmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class nadmm_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("order_n", ctypes.c_int32), ("lambda_", ctypes.c_float),
+                ("theta", ctypes.c_float), ("outer_iters", ctypes.c_int32),
+                ("inner_iters", ctypes.c_int32), ("data_term", ctypes.c_int32),
+                ("eps", ctypes.c_float), ("bound_kappa", ctypes.c_float),
+                ("bound_delta", ctypes.c_float), ("flags", ctypes.c_uint32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_SIGS = {
+    "nadmm_config_init": (None, [ctypes.POINTER(nadmm_config), ctypes.c_int32, ctypes.c_int32,
+                                 ctypes.c_int32]),
+    "nadmm_create": (ctypes.c_int, [ctypes.POINTER(nadmm_config), ctypes.POINTER(_P)]),
+    "nadmm_destroy": (None, [_P]),
+    "nadmm_workspace_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "nadmm_set_workspace": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "nadmm_set_params": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float]),
+    "nadmm_register": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "nadmm_register_host": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "nadmm_get_status": (ctypes.c_int, [_P, _P]),
+    "nadmm_last_error": (ctypes.c_char_p, []),
+    "nadmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "nadmm_spectral_solve": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nadmm_admm_run": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
+                                      _P, _P, _P]),
+    "nadmm_linearise": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "nadmm_bound_compose": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "nadmm_jacobian_det": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "nadmm_register_profiled": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_float),
+                                               ctypes.POINTER(ctypes.c_int32)]),
+}
+
+
+def load(path: str | None = None):
+    """Load libnadmm.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build(); "
+                          "there is no fallback implementation")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != NADMM_OK:
+        lib = load()
+        raise NadmmError(status, lib.nadmm_last_error().decode())
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ---------------------------------------------------------------- C names
+def nadmm_config_init(nx, ny, nz):
+    cfg = nadmm_config()
+    load().nadmm_config_init(ctypes.byref(cfg), nx, ny, nz)
+    return cfg
+
+
+def nadmm_create(cfg):
+    h = _P()
+    _check(load().nadmm_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def nadmm_destroy(h):
+    load().nadmm_destroy(h)
+
+
+def nadmm_workspace_size(h):
+    n = ctypes.c_size_t()
+    _check(load().nadmm_workspace_size(h, ctypes.byref(n)))
+    return n.value
+
+
+def nadmm_set_workspace(h, ws, nbytes):
+    _check(load().nadmm_set_workspace(h, _ptr(ws), nbytes))
+
+
+def nadmm_set_params(h, lam, theta):
+    _check(load().nadmm_set_params(h, lam, theta))
+
+
+def nadmm_register(h, fixed, moving, u_out, stream=None):
+    _check(load().nadmm_register(h, _ptr(fixed), _ptr(moving), _ptr(u_out), _stream(stream)))
+
+
+def nadmm_register_host(h, fixed_host, moving_host, u_out_host, stream=None):
+    _check(load().nadmm_register_host(h, _ptr(fixed_host), _ptr(moving_host), _ptr(u_out_host),
+                                      _stream(stream)))
+
+
+def nadmm_register_profiled(h, fixed, moving, u_out, stream=None):
+    ms = (ctypes.c_float * len(KERNEL_CLASSES))()
+    n = (ctypes.c_int32 * len(KERNEL_CLASSES))()
+    _check(load().nadmm_register_profiled(h, _ptr(fixed), _ptr(moving), _ptr(u_out),
+                                          _stream(stream), ms, n))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def nadmm_get_status(h, stream=None):
+    return load().nadmm_get_status(h, _stream(stream))
+
+
+def nadmm_last_error():
+    return load().nadmm_last_error().decode()
+
+
+def nadmm_status_string(status):
+    return load().nadmm_status_string(status).decode()
+
+
+def nadmm_spectral_solve(h, y, w, stream=None):
+    _check(load().nadmm_spectral_solve(h, _ptr(y), _ptr(w), _stream(stream)))
+
+
+def nadmm_admm_run(h, J, c, w_km1, w_km2, b_km1, b_km2, k, steps, w_out, b_out, stream=None):
+    _check(load().nadmm_admm_run(h, _ptr(J), _ptr(c), _ptr(w_km1), _ptr(w_km2), _ptr(b_km1),
+                                 _ptr(b_km2), k, steps, _ptr(w_out), _ptr(b_out), _stream(stream)))
+
+
+def nadmm_linearise(h, fixed, moving, u, J, c, I1w_out=None, stream=None):
+    _check(load().nadmm_linearise(h, _ptr(fixed), _ptr(moving), _ptr(u), _ptr(J), _ptr(c),
+                                  _ptr(I1w_out), _stream(stream)))
+
+
+def nadmm_bound_compose(h, w, u_in, u_out, scale_out=None, stream=None):
+    _check(load().nadmm_bound_compose(h, _ptr(w), _ptr(u_in), _ptr(u_out), _ptr(scale_out),
+                                      _stream(stream)))
+
+
+def nadmm_jacobian_det(h, u, det=None, nonpositive=None, stream=None):
+    _check(load().nadmm_jacobian_det(h, _ptr(u), _ptr(det), _ptr(nonpositive), _stream(stream)))
+
+
+# ---------------------------------------------------------------- convenience
+def make_config(dims, order_n=2, lam=10.0, theta=0.1, outer=10, inner=10, data_term=2,
+                eps=1e-6, kappa=0.5, delta=1.0, flags=0):
+    """nadmm_config for dims = (nx, ny, nz); kappa/delta may be math.inf."""
+    nx, ny, nz = dims
+    cfg = nadmm_config_init(nx, ny, nz)
+    cfg.order_n = order_n
+    cfg.lambda_ = lam
+    cfg.theta = theta
+    cfg.outer_iters = outer
+    cfg.inner_iters = inner
+    cfg.data_term = data_term
+    cfg.eps = eps
+    cfg.bound_kappa = kappa if math.isfinite(kappa) else float("inf")
+    cfg.bound_delta = delta if math.isfinite(delta) else float("inf")
+    cfg.flags = flags
+    return cfg
+
+
+class Registration:
+    """A handle plus a torch-allocated device workspace (PyTorch is used for
+    device memory only)."""
+
+    def __init__(self, dims, device="cuda", **kw):
+        import torch
+        self.dims = tuple(dims)
+        self.cfg = make_config(self.dims, **kw)
+        self.handle = nadmm_create(self.cfg)
+        nbytes = nadmm_workspace_size(self.handle)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        nadmm_set_workspace(self.handle, self._ws_ptr, nbytes)
+
+    def register(self, fixed, moving, u_out=None, stream=None):
+        import torch
+        nx, ny, nz = self.dims
+        if u_out is None:
+            u_out = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=fixed.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(fixed.device)
+        nadmm_register(self.handle, fixed, moving, u_out, stream)
+        return u_out
+
+    def close(self):
+        if self.handle:
+            nadmm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

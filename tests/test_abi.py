@@ -1,0 +1,115 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol
+declared in include/nadmm.h, and its host-side validation behaves as
+documented.  No call here touches a CUDA device."""
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2109_12688_gb300 import nadmm
+    return nadmm
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "nadmm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nadmm_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 17
+    so = lib.load()
+    for n in names:
+        assert hasattr(so, n), n
+    # and the binding exposes the same names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_config_defaults(lib):
+    cfg = lib.nadmm_config_init(128, 128, 96)
+    assert (cfg.nx, cfg.ny, cfg.nz) == (128, 128, 96)
+    assert cfg.order_n == 2 and cfg.data_term == 2
+    assert cfg.lambda_ == pytest.approx(10.0) and cfg.theta == pytest.approx(0.1)
+    assert cfg.outer_iters == 10 and cfg.inner_iters == 10
+    assert cfg.bound_kappa == pytest.approx(0.5) and cfg.bound_delta == pytest.approx(1.0)
+
+
+@pytest.mark.parametrize("dims", [(128, 128, 96), (32, 32, 24), (160, 160, 112), (96, 96, 64),
+                                  (20, 12, 14), (4, 4, 4), (12, 6, 7)])
+def test_create_and_workspace_size(lib, dims):
+    h = lib.nadmm_create(lib.make_config(dims))
+    nx, ny, nz = dims
+    V = nx * ny * nz
+    ws = lib.nadmm_workspace_size(h)
+    # half spectrum + 6 vector fields + 4 scalar fields, plus small tables
+    expect = 3 * (nx // 2 + 1) * ny * nz * 8 + (6 * 3 + 4) * V * 4
+    assert expect <= ws <= expect + 64 * 1024
+    lib.nadmm_destroy(h)
+
+
+@pytest.mark.parametrize("dims,why", [((3, 8, 8), "dimension"), ((10, 8, 8), "multiple of 4"),
+                                      ((8, 7, 8), "even"), ((44, 8, 8), "factor"),
+                                      ((8, 8, 13), "factor"), ((256, 256, 192), "shared")])
+def test_unsupported_sizes_are_rejected(lib, dims, why):
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_create(lib.make_config(dims))
+    assert e.value.status == lib.NADMM_ERR_UNSUPPORTED_SIZE
+    assert why in str(e.value)
+
+
+@pytest.mark.parametrize("field,value", [("order_n", 0), ("order_n", 9), ("theta", 0.0),
+                                         ("theta", -1.0), ("lambda_", -0.5),
+                                         ("lambda_", float("nan")), ("outer_iters", 0),
+                                         ("inner_iters", 0), ("data_term", 3), ("eps", 0.0),
+                                         ("bound_kappa", 0.0), ("bound_delta", -1.0),
+                                         ("flags", 8)])
+def test_bad_parameters_are_rejected(lib, field, value):
+    cfg = lib.make_config((32, 32, 24))
+    setattr(cfg, field, value)
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_create(cfg)
+    assert e.value.status == lib.NADMM_ERR_INVALID_ARG
+
+
+def test_infinite_bounds_allowed(lib):
+    h = lib.nadmm_create(lib.make_config((32, 32, 24), kappa=math.inf, delta=math.inf))
+    lib.nadmm_destroy(h)
+
+
+def test_calls_without_workspace_fail_before_any_device_work(lib):
+    h = lib.nadmm_create(lib.make_config((32, 32, 24)))
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_register(h, 256, 512, 768)
+    assert e.value.status == lib.NADMM_ERR_NO_WORKSPACE
+    for fn, args in ((lib.nadmm_spectral_solve, (256, 512)),
+                     (lib.nadmm_bound_compose, (256, 512, 768))):
+        with pytest.raises(lib.NadmmError) as e:
+            fn(h, *args)
+        assert e.value.status == lib.NADMM_ERR_NO_WORKSPACE
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_set_workspace(h, 1000, 1 << 30)
+    assert e.value.status == lib.NADMM_ERR_ALIGNMENT
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_set_workspace(h, 4096, 16)
+    assert e.value.status == lib.NADMM_ERR_NO_WORKSPACE
+    with pytest.raises(lib.NadmmError):
+        lib.nadmm_set_params(h, 1.0, 0.0)
+    lib.nadmm_set_params(h, 1.0, 0.5)
+    lib.nadmm_destroy(h)
+    lib.nadmm_destroy(None)
+
+
+def test_status_strings(lib):
+    assert lib.nadmm_status_string(0) == "NADMM_OK"
+    assert lib.nadmm_status_string(lib.NADMM_ERR_NONFINITE) == "NADMM_ERR_NONFINITE"
+    assert "unknown" in lib.nadmm_status_string(99)
