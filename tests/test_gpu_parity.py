@@ -49,6 +49,15 @@ def rel_l2(a, b):
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-30))
 
 
+def position_tol(dims, f):
+    """Bound for sampling f at x + u computed in FP32: the position carries a
+    rounding error <= ulp(max dim) / 2 = 2^-24 * 2^ceil(log2(max dim)), times
+    the largest neighbour difference of f, doubled, plus FP32 arithmetic."""
+    f = np.asarray(f, np.float64)
+    slope = max(np.abs(np.diff(f, axis=a)).max() for a in range(f.ndim))
+    return 2.0 * 2.0 ** -24 * 2.0 ** math.ceil(math.log2(max(dims))) * slope + 1e-6
+
+
 def smooth_field(dims, seed, amp):
     v = synth.random_velocity(dims, np.random.default_rng(seed), max_amp=amp)
     return v.astype(np.float32)
@@ -146,9 +155,10 @@ def test_linearise(lib, dims):
     lib.nadmm_linearise(reg.handle, dev(p["fixed"]), dev(p["moving"]), dev(u), J, c, I1w,
                         torch.cuda.current_stream())
     J_ref, c_ref, I1w_ref = O.linearise(p["fixed"], p["moving"], u.astype(np.float64))
-    assert np.abs(host(I1w) - I1w_ref).max() <= 2e-6
-    assert np.abs(host(c) - c_ref).max() <= 2e-6
-    assert np.abs(host(J) - J_ref).max() <= 2e-6
+    tol = position_tol(dims, p["moving"])
+    assert np.abs(host(I1w) - I1w_ref).max() <= tol
+    assert np.abs(host(c) - c_ref).max() <= tol
+    assert np.abs(host(J) - J_ref).max() <= tol
 
 
 @pytest.mark.parametrize("kappa,delta", [(0.5, 1.0), (math.inf, math.inf), (0.05, 0.3)])
@@ -163,7 +173,8 @@ def test_bound_compose(lib, kappa, delta):
     s_ref, _, _ = O.bound_scale(w.astype(np.float64), kappa, delta)
     assert float(host(sc)[0]) == pytest.approx(s_ref, rel=1e-6)
     ref = O.compose(u.astype(np.float64), s_ref * w.astype(np.float64))
-    assert np.abs(host(u_out) - ref).max() <= 5e-6
+    tol = max(position_tol(dims, u[i]) for i in range(3)) + 1e-6 * np.abs(w).max()
+    assert np.abs(host(u_out) - ref).max() <= tol
 
 
 def test_jacobian_det(lib):
