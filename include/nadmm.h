@@ -184,6 +184,33 @@ nadmm_status nadmm_bound_compose(nadmm_handle h, const float* w, const float* u_
 nadmm_status nadmm_jacobian_det(nadmm_handle h, const float* u, float* det,
                                 uint32_t* nonpositive, void* stream);
 
+/* Regulariser solve that allocates nothing.  The paper has no counterpart:
+ * this entry exists for callers that may not allocate device memory -- a
+ * library running inside an application or framework that owns every device
+ * allocation through its own pool, or a latency-critical caller that cannot
+ * risk the device synchronisation cudaMalloc/cudaFree may cause.
+ *
+ * Computes the same result as nadmm_spectral_solve for an nx x ny x nz grid,
+ * order n, lambda and theta (same limits as nadmm_create), without a handle
+ * or workspace: y, w device [3][nz][ny][nx] fp32, 16-byte aligned, w may
+ * alias y.  The scratch (half spectrum + FFT tables) lives in one static
+ * device array of 24 MiB (25165824 bytes) that every GPU loading the library
+ * holds until the process exits; grids needing more, i.e. when
+ * 3 (nx/2+1) ny nz 8 bytes plus a few KB of tables exceed it, are rejected
+ * with NADMM_ERR_UNSUPPORTED_SIZE before any device work.  No cudaMalloc,
+ * cudaFree or other allocating call is made.
+ *
+ * The first call on a device performs a one-time set-up on that device (it
+ * looks up the array's device address with cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Every call shares the one array and
+ * it keeps the last call's contents (nothing in it needs clearing: each call
+ * writes every byte it later reads), so calls whose device work overlaps --
+ * on different streams or from different threads -- race and must be
+ * serialised by the caller. */
+nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, int32_t order_n,
+                                          float lambda, float theta, const float* y, float* w,
+                                          void* stream);
+
 /* ---------------------------------------------------------------------
  * Measurement
  * --------------------------------------------------------------------- */

@@ -651,3 +651,8 @@ nadmm_status nadmm_jacobian_det(nadmm_handle h, const float* u, float* det, uint
 }
 
 }  // extern "C"
+
+namespace nadmm {
+// Lets other translation units of the library report through nadmm_last_error.
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace nadmm

@@ -63,6 +63,9 @@ _SIGS = {
     "nadmm_linearise": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "nadmm_bound_compose": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "nadmm_jacobian_det": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "nadmm_spectral_solve_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
+                                                     ctypes.c_int32, ctypes.c_int32,
+                                                     ctypes.c_float, ctypes.c_float, _P, _P, _P]),
     "nadmm_register_profiled": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_float),
                                                ctypes.POINTER(ctypes.c_int32)]),
 }
@@ -176,6 +179,11 @@ def nadmm_status_string(status):
 
 def nadmm_spectral_solve(h, y, w, stream=None):
     _check(load().nadmm_spectral_solve(h, _ptr(y), _ptr(w), _stream(stream)))
+
+
+def nadmm_spectral_solve_noalloc(nx, ny, nz, order_n, lam, theta, y, w, stream=None):
+    _check(load().nadmm_spectral_solve_noalloc(nx, ny, nz, order_n, lam, theta, _ptr(y), _ptr(w),
+                                               _stream(stream)))
 
 
 def nadmm_admm_run(h, J, c, w_km1, w_km2, b_km1, b_km2, k, steps, w_out, b_out, stream=None):
