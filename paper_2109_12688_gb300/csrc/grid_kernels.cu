@@ -13,6 +13,12 @@ namespace nadmm {
 
 constexpr int kGridThreads = 256;
 
+// (1 - t) a + t b, exact at t = 0 and t = 1 (a sample on a grid point, or
+// clamped to the last one, returns the grid value itself)
+__device__ __forceinline__ float lerp(float a, float b, float t) {
+  return fmaf(t, b, fmaf(-t, a, a));
+}
+
 __device__ __forceinline__ float trilerp(const float* __restrict__ f, Dims d, float px, float py,
                                          float pz) {
   px = fminf(fmaxf(px, 0.0f), (float)(d.nx - 1));
@@ -28,13 +34,13 @@ __device__ __forceinline__ float trilerp(const float* __restrict__ f, Dims d, fl
   float c010 = __ldg(p + sy), c011 = __ldg(p + sy + sx);
   float c100 = __ldg(p + sz), c101 = __ldg(p + sz + sx);
   float c110 = __ldg(p + sz + sy), c111 = __ldg(p + sz + sy + sx);
-  float c00 = c000 + fx * (c001 - c000);
-  float c01 = c010 + fx * (c011 - c010);
-  float c10 = c100 + fx * (c101 - c100);
-  float c11 = c110 + fx * (c111 - c110);
-  float c0 = c00 + fy * (c01 - c00);
-  float c1 = c10 + fy * (c11 - c10);
-  return c0 + fz * (c1 - c0);
+  float c00 = lerp(c000, c001, fx);
+  float c01 = lerp(c010, c011, fx);
+  float c10 = lerp(c100, c101, fx);
+  float c11 = lerp(c110, c111, fx);
+  float c0 = lerp(c00, c01, fy);
+  float c1 = lerp(c10, c11, fy);
+  return lerp(c0, c1, fz);
 }
 
 __device__ __forceinline__ void vox_coords(size_t i, Dims d, int& x, int& y, int& z) {
