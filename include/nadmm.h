@@ -59,7 +59,9 @@ typedef enum nadmm_status {
   NADMM_ERR_ALIGNMENT = 3,        /* device pointer not 16-byte aligned        */
   NADMM_ERR_NO_WORKSPACE = 4,     /* workspace missing or too small            */
   NADMM_ERR_CUDA = 5,             /* a CUDA runtime call failed                */
-  NADMM_ERR_NONFINITE = 6         /* device status: NaN/Inf met in a bound step */
+  NADMM_ERR_NONFINITE = 6,        /* device status: NaN/Inf met in a bound step */
+  NADMM_ERR_TIMEOUT = 7           /* device status: a kernel's bounded wait for its
+                                     own bulk copies expired; the kernel returned */
 } nadmm_status;
 
 /* flags */
@@ -127,7 +129,8 @@ nadmm_status nadmm_register_host(nadmm_handle h, const float* fixed_host,
                                  const float* moving_host, float* u_out_host, void* stream);
 
 /* Synchronise `stream`, read and clear the device status word.
- * Returns NADMM_OK or NADMM_ERR_NONFINITE (or CUDA on a runtime error). */
+ * Returns NADMM_OK, NADMM_ERR_TIMEOUT or NADMM_ERR_NONFINITE (or CUDA on a
+ * runtime error). */
 nadmm_status nadmm_get_status(nadmm_handle h, void* stream);
 
 /* Thread-local description of the last failure of this thread. */

@@ -13,8 +13,14 @@
 //       forward y- and z-DFTs, multiply by 1/(1 + gamma K^n) / (nx ny nz),
 //       inverse z- and y-DFTs                             (Eq. 5 line 2, Eq. 6)
 // so the w-step's 3D transform pair costs two global passes and no
-// transpose kernels.  The phase functions below are plain C++ over
-// (tid, nthr); kernels separate them with barriers.
+// transpose kernels.
+//
+// Data movement: the plane pass brings its real-space tiles (y, the w/b state,
+// J, c) into shared memory with TMA bulk copies issued at kernel start, so
+// they stream in while the spectrum is gathered and inverse-transformed; the
+// pencil pass moves its whole (ny x nz) plane in and out with bulk copies.
+// Every mbarrier wait is bounded: on expiry the kernel records a status bit
+// and returns instead of spinning.
 #include <cuda_runtime.h>
 
 #include "fft_device.cuh"
@@ -43,86 +49,194 @@ NADMM_HD void v_step(int data_term, float theta, float eps, const float (&J)[3],
   v[2] = u[2] - f * J[2];
 }
 
+// ---------------------------------------------------------------- TMA / mbarrier
+#if defined(__CUDA_ARCH__)
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// global -> shared bulk copy completing on `bar` (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// shared -> global bulk copy in the thread's bulk group
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// try_wait suspends for a hardware-bounded time per attempt; the attempt
+// count bounds the whole wait well under a second of a stuck copy.
+constexpr int kWaitAttempts = 1 << 20;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < kWaitAttempts; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+#endif
+
 // ---------------------------------------------------------------- plane pass
+// Shared-memory staging of the real-space tiles: slot s holds R rows x nx.
+struct FieldMap {
+  int y, w, b, wp, bp, J, c, n;
+};
+
+template <int IN, bool PREV, bool STEP>
+NADMM_HD constexpr FieldMap field_map() {
+  FieldMap f{-1, -1, -1, -1, -1, -1, -1, 0};
+  int n = 0;
+  if (IN == IN_SPEC && STEP) { f.y = n; n += 3; }
+  if (IN == IN_STATE || IN == IN_FIELD) { f.w = n; n += 3; }
+  if (IN == IN_STATE) { f.b = n; n += 3; }
+  if (STEP && PREV) { f.wp = n; n += 3; f.bp = n; n += 3; }
+  if (STEP && IN != IN_FIELD) { f.J = n; n += 3; f.c = n; n += 1; }
+  f.n = n;
+  return f;
+}
+
+constexpr int kGatherItems = 8;   // spectrum values per thread held in flight
+constexpr int kPlaneThreads = 256;
+constexpr int kPencilThreads = 384;
+
 // Lines: line l = comp * (R/2) + r holds rows (y0 + r) [real part] and
 // (y0 + r + R/2) [imaginary part] of component comp, at pitch a.pitch.
 
 // Half spectrum (A, B of the two rows) -> full complex line Z = A + iB.
-NADMM_HD void plane_gather(const PlaneArgs& a, float2* lines, int z, int y0, int tid, int nthr) {
+// All loads of a thread are issued before its first shared-memory store.
+NADMM_HD void plane_gather(const PlaneArgs& a, float2* lines, const int* pos, int z, int y0,
+                           int tid, int nthr) {
   const int h = a.R / 2;
   const int total = 3 * a.nkx * h;
-  for (int g = tid; g < total; g += nthr) {
-    int r = g % h;
-    int rest = g / h;
-    int kx = rest % a.nkx;
-    int comp = rest / a.nkx;
-    const float2* src = a.spec + ((size_t)(comp * a.nkx + kx) * a.nz + z) * a.ny + y0 + r;
-    float2 A = src[0];
-    float2 B = src[h];
-    float2* line = lines + (comp * h + r) * a.pitch;
-    if (kx == 0 || 2 * kx == a.nx) {
-      line[a.posx[kx]] = make_float2(A.x, B.x);
-    } else {
-      line[a.posx[kx]] = make_float2(A.x - B.y, A.y + B.x);
-      line[a.posx[a.nx - kx]] = make_float2(A.x + B.y, B.x - A.y);
+  float2 A[kGatherItems], B[kGatherItems];
+#pragma unroll
+  for (int it = 0; it < kGatherItems; ++it) {
+    const int g = tid + it * nthr;
+    if (g < total) {
+      const int rest = (int)fdiv((uint32_t)g, a.half_div);
+      const int r = g - rest * h;
+      const int comp = (int)fdiv((uint32_t)rest, a.nkx_div);
+      const int kx = rest - comp * a.nkx;
+      const float2* src = a.spec + ((size_t)(comp * a.nkx + kx) * a.nz + z) * a.ny + y0 + r;
+      A[it] = src[0];
+      B[it] = src[h];
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < kGatherItems; ++it) {
+    const int g = tid + it * nthr;
+    if (g < total) {
+      const int rest = (int)fdiv((uint32_t)g, a.half_div);
+      const int r = g - rest * h;
+      const int comp = (int)fdiv((uint32_t)rest, a.nkx_div);
+      const int kx = rest - comp * a.nkx;
+      float2* line = lines + (comp * h + r) * a.pitch;
+      const float2 Av = A[it], Bv = B[it];
+      if (kx == 0 || 2 * kx == a.nx) {
+        line[pos[kx]] = make_float2(Av.x, Bv.x);
+      } else {
+        line[pos[kx]] = make_float2(Av.x - Bv.y, Av.y + Bv.x);
+        line[pos[a.nx - kx]] = make_float2(Av.x + Bv.y, Bv.x - Av.y);
+      }
     }
   }
 }
 
 // Full complex line Z -> half spectra A = (Z_k + conj Z_{N-k})/2,
 // B = (Z_k - conj Z_{N-k})/(2i) of the two real rows.
-NADMM_HD void plane_scatter(const PlaneArgs& a, const float2* lines, int z, int y0, int tid,
-                            int nthr) {
+NADMM_HD void plane_scatter(const PlaneArgs& a, const float2* lines, const int* pos, int z, int y0,
+                            int tid, int nthr) {
   const int h = a.R / 2;
   const int total = 3 * a.nkx * h;
   for (int g = tid; g < total; g += nthr) {
-    int r = g % h;
-    int rest = g / h;
-    int kx = rest % a.nkx;
-    int comp = rest / a.nkx;
+    const int rest = (int)fdiv((uint32_t)g, a.half_div);
+    const int r = g - rest * h;
+    const int comp = (int)fdiv((uint32_t)rest, a.nkx_div);
+    const int kx = rest - comp * a.nkx;
     const float2* line = lines + (comp * h + r) * a.pitch;
-    float2 Zk = line[a.posx[kx]];
-    float2 Zm = line[a.posx[kx == 0 ? 0 : a.nx - kx]];
+    const float2 Zk = line[pos[kx]];
+    const float2 Zm = line[pos[kx == 0 ? 0 : a.nx - kx]];
     float2* dst = a.spec + ((size_t)(comp * a.nkx + kx) * a.nz + z) * a.ny + y0 + r;
     dst[0] = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
     dst[h] = make_float2(0.5f * (Zk.y + Zm.y), 0.5f * (Zm.x - Zk.x));
   }
 }
 
+// Point-wise part of the iteration on staged tiles (fld) and lines.
 template <int IN, bool PREV, bool STEP>
-NADMM_HD void plane_pointwise(const PlaneArgs& a, float2* lines, int z, int y0, int tid,
-                              int nthr) {
+NADMM_HD void plane_pointwise(const PlaneArgs& a, const float* fld, float2* lines, int z, int y0,
+                              int tid, int nthr) {
+  constexpr FieldMap F = field_map<IN, PREV, STEP>();
   const int h = a.R / 2;
+  const int tile = a.R * a.nx;
   const size_t V = (size_t)a.nx * a.ny * a.nz;
   const int total = h * a.nx;
   for (int g = tid; g < total; g += nthr) {
-    int x = g % a.nx;
-    int r = g / a.nx;
+    const int r = (int)fdiv((uint32_t)g, a.nx_div);
+    const int x = g - r * a.nx;
     float ynew[2][3];
     for (int half = 0; half < 2; ++half) {
-      const size_t vox = ((size_t)z * a.ny + (y0 + r + half * h)) * a.nx + x;
+      const int row = r + half * h;
+      const int so = row * a.nx + x;  // offset inside a staged tile
+      const size_t vox = ((size_t)z * a.ny + (y0 + row)) * a.nx + x;
       float wk1[3], bk1[3], wh[3], bh[3];
+#pragma unroll
       for (int comp = 0; comp < 3; ++comp) {
         const size_t i = comp * V + vox;
         if (IN == IN_SPEC) {
-          float2 l = lines[(comp * h + r) * a.pitch + x];
+          const float2 l = lines[(comp * h + r) * a.pitch + x];
           wk1[comp] = half ? l.y : l.x;
-          bk1[comp] = (a.y != nullptr) ? a.y[i] - wk1[comp] : 0.0f;
+          if (STEP)
+            bk1[comp] = fld[(F.y + comp) * tile + so] - wk1[comp];
+          else
+            bk1[comp] = (a.b_out != nullptr) ? a.y[i] - wk1[comp] : 0.0f;
         } else if (IN == IN_STATE) {
-          wk1[comp] = a.w_in[i];
-          bk1[comp] = a.b_in[i];
+          wk1[comp] = fld[(F.w + comp) * tile + so];
+          bk1[comp] = fld[(F.b + comp) * tile + so];
         } else if (IN == IN_FIELD) {
-          wk1[comp] = a.w_in[i];
+          wk1[comp] = fld[(F.w + comp) * tile + so];
           bk1[comp] = 0.0f;
         } else {
           wk1[comp] = 0.0f;
           bk1[comp] = 0.0f;
         }
         if (STEP && PREV) {
-          const float* wsrc = (IN == IN_STATE) ? a.wprev_in : a.wp;
-          const float* bsrc = (IN == IN_STATE) ? a.bprev_in : a.bp;
-          wh[comp] = wk1[comp] + a.beta * (wk1[comp] - wsrc[i]);
-          bh[comp] = bk1[comp] + a.beta * (bk1[comp] - bsrc[i]);
+          wh[comp] = wk1[comp] + a.beta * (wk1[comp] - fld[(F.wp + comp) * tile + so]);
+          bh[comp] = bk1[comp] + a.beta * (bk1[comp] - fld[(F.bp + comp) * tile + so]);
         } else {
           wh[comp] = wk1[comp];
           bh[comp] = bk1[comp];
@@ -137,14 +251,17 @@ NADMM_HD void plane_pointwise(const PlaneArgs& a, float2* lines, int z, int y0, 
       }
       if (STEP) {
         if (IN == IN_FIELD) {
+#pragma unroll
           for (int comp = 0; comp < 3; ++comp) ynew[half][comp] = wk1[comp];
         } else {
           float Jv[3], u[3], v[3];
+#pragma unroll
           for (int comp = 0; comp < 3; ++comp) {
-            Jv[comp] = a.J[comp * V + vox];
+            Jv[comp] = fld[(F.J + comp) * tile + so];
             u[comp] = wh[comp] - bh[comp];
           }
-          v_step(a.data_term, a.theta, a.eps, Jv, a.c[vox], u, v);
+          v_step(a.data_term, a.theta, a.eps, Jv, fld[F.c * tile + so], u, v);
+#pragma unroll
           for (int comp = 0; comp < 3; ++comp) {
             ynew[half][comp] = v[comp] + bh[comp];
             if (a.y != nullptr) a.y[comp * V + vox] = ynew[half][comp];
@@ -153,106 +270,279 @@ NADMM_HD void plane_pointwise(const PlaneArgs& a, float2* lines, int z, int y0, 
       }
     }
     if (STEP) {
+#pragma unroll
       for (int comp = 0; comp < 3; ++comp)
         lines[(comp * h + r) * a.pitch + x] = make_float2(ynew[0][comp], ynew[1][comp]);
     }
   }
 }
 
-#if defined(__CUDACC__)
-#define NADMM_SYNC() __syncthreads()
-#else
-#define NADMM_SYNC()
+// Shared-memory layout of the plane pass (byte offsets).
+struct PlaneSmem {
+  size_t fld, lines, tw, pos, total;
+};
+
+NADMM_HD PlaneSmem plane_layout(const PlaneArgs& a, int nfields) {
+  PlaneSmem L;
+  size_t o = 16;  // mbarrier
+  L.fld = o;
+  o += (size_t)nfields * a.R * a.nx * sizeof(float);
+  o = (o + 15) & ~(size_t)15;
+  L.lines = o;
+  o += (size_t)3 * (a.R / 2) * a.pitch * sizeof(float2);
+  L.tw = o;
+  o += (size_t)a.px.tw_count * sizeof(float2);
+  L.pos = o;
+  o += (size_t)a.nx * sizeof(int);
+  L.total = (o + 15) & ~(size_t)15;
+  return L;
+}
+
+#if defined(__CUDA_ARCH__)
+template <int IN, bool PREV, bool STEP>
+__device__ __forceinline__ const float* field_src(const PlaneArgs& a, int slot) {
+  constexpr FieldMap F = field_map<IN, PREV, STEP>();
+  const size_t V = (size_t)a.nx * a.ny * a.nz;
+  auto in_range = [](int s, int base, int cnt) { return base >= 0 && s >= base && s < base + cnt; };
+  if (in_range(slot, F.y, 3)) return a.y + (slot - F.y) * V;
+  if (in_range(slot, F.w, 3)) return a.w_in + (slot - F.w) * V;
+  if (in_range(slot, F.b, 3)) return a.b_in + (slot - F.b) * V;
+  if (in_range(slot, F.wp, 3)) return (IN == IN_STATE ? a.wprev_in : a.wp) + (slot - F.wp) * V;
+  if (in_range(slot, F.bp, 3)) return (IN == IN_STATE ? a.bprev_in : a.bp) + (slot - F.bp) * V;
+  if (in_range(slot, F.J, 3)) return a.J + (slot - F.J) * V;
+  return a.c;
+}
 #endif
 
-constexpr int kPlaneThreads = 256;
-constexpr int kPencilThreads = 512;
-
 template <int IN, bool PREV, bool STEP>
-__global__ void __launch_bounds__(kPlaneThreads) k_plane(PlaneArgs a) {
-  extern __shared__ float2 lines[];
+__global__ void __launch_bounds__(kPlaneThreads, 2) k_plane(PlaneArgs a) {
+#if defined(__CUDA_ARCH__)
+  constexpr FieldMap F = field_map<IN, PREV, STEP>();
+  extern __shared__ __align__(128) unsigned char smem[];
+  const PlaneSmem L = plane_layout(a, F.n);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  float* fld = reinterpret_cast<float*>(smem + L.fld);
+  float2* lines = reinterpret_cast<float2*>(smem + L.lines);
+  float2* tw = reinterpret_cast<float2*>(smem + L.tw);
+  int* pos = reinterpret_cast<int*>(smem + L.pos);
   const int tiles_y = a.ny / a.R;
-  const int z = blockIdx.x / tiles_y;
-  const int y0 = (blockIdx.x % tiles_y) * a.R;
+  const int z = (int)fdiv(blockIdx.x, a.tiles_div);
+  const int y0 = (blockIdx.x - z * tiles_y) * a.R;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int nlines = 3 * (a.R / 2);
+
+  if (F.n > 0) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid < 32) {
+      const uint32_t tile_bytes = (uint32_t)(a.R * a.nx * sizeof(float));
+      if (tid == 0) mbar_expect_tx(bar, tile_bytes * F.n);
+      __syncwarp();
+      const size_t off = ((size_t)z * a.ny + y0) * a.nx;
+      for (int s = tid; s < F.n; s += 32)
+        bulk_load(fld + (size_t)s * a.R * a.nx, field_src<IN, PREV, STEP>(a, s) + off, tile_bytes,
+                  bar);
+    }
+  }
+  for (int i = tid; i < a.px.tw_count; i += nthr) tw[i] = a.twx[i];
+  for (int i = tid; i < a.nx; i += nthr) pos[i] = a.posx[i];
+  __syncthreads();
   if (IN == IN_SPEC) {
-    plane_gather(a, lines, z, y0, tid, nthr);
-    NADMM_SYNC();
+    plane_gather(a, lines, pos, z, y0, tid, nthr);
+    __syncthreads();
     for (int s = a.px.nst - 1; s >= 0; --s) {
-      fft_stage<true>(a.px, s, lines, nlines, 1, a.pitch, a.twx, tid, nthr);
-      NADMM_SYNC();
+      fft_stage<true>(a.px, s, lines, nlines, a.lines_div, 1, a.pitch, tw, tid, nthr);
+      __syncthreads();
     }
   }
-  plane_pointwise<IN, PREV, STEP>(a, lines, z, y0, tid, nthr);
+  if (F.n > 0) {
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0));
+    if (!ok) {
+      if (tid == 0 && a.status != nullptr) atomicOr(a.status, kStatusTimeout);
+      mbar_wait_bounded(bar, 0);  // let copies still in flight land before exit
+      return;
+    }
+  }
+  plane_pointwise<IN, PREV, STEP>(a, fld, lines, z, y0, tid, nthr);
   if (STEP) {
-    NADMM_SYNC();
+    __syncthreads();
     for (int s = 0; s < a.px.nst; ++s) {
-      fft_stage<false>(a.px, s, lines, nlines, 1, a.pitch, a.twx, tid, nthr);
-      NADMM_SYNC();
+      fft_stage<false>(a.px, s, lines, nlines, a.lines_div, 1, a.pitch, tw, tid, nthr);
+      __syncthreads();
     }
-    plane_scatter(a, lines, z, y0, tid, nthr);
+    plane_scatter(a, lines, pos, z, y0, tid, nthr);
   }
+#endif
 }
 
 // ---------------------------------------------------------------- pencil pass
-NADMM_HD void pencil_symbol(const PencilArgs& a, float2* sm, int kx, int tid, int nthr) {
-  const int total = a.ny * a.nz;
-  const float kxv = a.Kx[kx];
-  for (int g = tid; g < total; g += nthr) {
-    int yy = g % a.ny;
-    int zz = g / a.ny;
-    float K = kxv + a.Ky[yy] + a.Kz[zz];
+// Gain 1/(1 + gamma K^n)/(nx ny nz) at (kx, y position `line`, z position).
+struct PencilFilter {
+  const float* Ky;
+  const float* Kz;
+  float kx_term, gamma, scale;
+  int order;
+  NADMM_HD float operator()(int line, int zpos) const {
+    const float K = kx_term + Ky[line] + Kz[zpos];
     float Kn = K;
-    for (int i = 1; i < a.order_n; ++i) Kn *= K;
-    float S = a.scale / (1.0f + a.gamma * Kn);
-    float2& e = sm[zz * a.pitch + yy];
-    e = cscale(e, S);
+    for (int i = 1; i < order; ++i) Kn *= K;
+    return scale / (1.0f + gamma * Kn);
   }
+};
+
+struct PencilSmem {
+  size_t plane, twy, twz, ky, kz, total;
+};
+
+NADMM_HD PencilSmem pencil_layout(const PencilArgs& a) {
+  PencilSmem L;
+  size_t o = 16;  // mbarrier
+  L.plane = o;
+  o += (size_t)a.nz * a.pitch * sizeof(float2);
+  L.twy = o;
+  o += (size_t)a.py.tw_count * sizeof(float2);
+  L.twz = o;
+  o += (size_t)a.pz.tw_count * sizeof(float2);
+  L.ky = o;
+  o += (size_t)a.ny * sizeof(float);
+  L.kz = o;
+  o += (size_t)a.nz * sizeof(float);
+  L.total = (o + 15) & ~(size_t)15;
+  return L;
 }
 
-__global__ void __launch_bounds__(kPencilThreads) k_pencil(PencilArgs a) {
-  extern __shared__ float2 sm[];
-  const int plane = blockIdx.x;
-  const int kx = plane % a.nkx;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  float2* g = a.spec + (size_t)plane * a.ny * a.nz;
-  const int total = a.ny * a.nz;
-  for (int i = tid; i < total; i += nthr) {
-    int yy = i % a.ny, zz = i / a.ny;
-    sm[zz * a.pitch + yy] = g[i];
-  }
-  __syncthreads();
+// The transform of one (component, kx) plane held at `sm` [nz][pitch].
+NADMM_HD void pencil_transform(const PencilArgs& a, float2* sm, const float2* twy, const float2* twz,
+                               const float* Ky, const float* Kz, int kx, int tid, int nthr,
+                               bool sync_between) {
+#if defined(__CUDA_ARCH__)
+#define NADMM_PSYNC() \
+  if (sync_between) __syncthreads()
+#else
+#define NADMM_PSYNC() (void)sync_between
+#endif
+  // forward y-DFT of every z-row (lines = z rows, elements contiguous)
   for (int s = 0; s < a.py.nst; ++s) {
-    fft_stage<false>(a.py, s, sm, a.nz, 1, a.pitch, a.twy, tid, nthr);
-    __syncthreads();
+    fft_stage<false>(a.py, s, sm, a.nz, a.nz_div, 1, a.pitch, twy, tid, nthr);
+    NADMM_PSYNC();
   }
-  for (int s = 0; s < a.pz.nst; ++s) {
-    fft_stage<false>(a.pz, s, sm, a.ny, a.pitch, 1, a.twz, tid, nthr);
-    __syncthreads();
+  // forward z-DFT of every y-column except its last stage
+  for (int s = 0; s + 1 < a.pz.nst; ++s) {
+    fft_stage<false>(a.pz, s, sm, a.ny, a.ny_div, a.pitch, 1, twz, tid, nthr);
+    NADMM_PSYNC();
   }
-  pencil_symbol(a, sm, kx, tid, nthr);
-  __syncthreads();
-  for (int s = a.pz.nst - 1; s >= 0; --s) {
-    fft_stage<true>(a.pz, s, sm, a.ny, a.pitch, 1, a.twz, tid, nthr);
-    __syncthreads();
+  // last forward z stage, inverse-symbol multiply, first inverse z stage
+  // Kx is indexed by the natural frequency kx < nkx (the x-transform is
+  // scattered in natural order); Ky, Kz by position
+  const PencilFilter filt{Ky, Kz, a.Kx[kx], a.gamma, a.scale, a.order_n};
+  fft_filter_last(a.pz, sm, a.ny, a.ny_div, a.pitch, 1, filt, tid, nthr);
+  NADMM_PSYNC();
+  for (int s = a.pz.nst - 2; s >= 0; --s) {
+    fft_stage<true>(a.pz, s, sm, a.ny, a.ny_div, a.pitch, 1, twz, tid, nthr);
+    NADMM_PSYNC();
   }
   for (int s = a.py.nst - 1; s >= 0; --s) {
-    fft_stage<true>(a.py, s, sm, a.nz, 1, a.pitch, a.twy, tid, nthr);
-    __syncthreads();
+    fft_stage<true>(a.py, s, sm, a.nz, a.nz_div, 1, a.pitch, twy, tid, nthr);
+    NADMM_PSYNC();
   }
-  for (int i = tid; i < total; i += nthr) {
-    int yy = i % a.ny, zz = i / a.ny;
-    g[i] = sm[zz * a.pitch + yy];
+#undef NADMM_PSYNC
+}
+
+
+__global__ void __launch_bounds__(kPencilThreads, 2) k_pencil(PencilArgs a) {
+#if defined(__CUDA_ARCH__)
+  extern __shared__ __align__(128) unsigned char smem[];
+  const PencilSmem L = pencil_layout(a);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  float2* sm = reinterpret_cast<float2*>(smem + L.plane);
+  float2* twy = reinterpret_cast<float2*>(smem + L.twy);
+  float2* twz = reinterpret_cast<float2*>(smem + L.twz);
+  float* Ky = reinterpret_cast<float*>(smem + L.ky);
+  float* Kz = reinterpret_cast<float*>(smem + L.kz);
+  const int plane = blockIdx.x;
+  const int kx = plane - (int)fdiv((uint32_t)plane, a.nkx_div) * a.nkx;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  float2* g = a.spec + (size_t)plane * a.ny * a.nz;
+  const uint32_t row_bytes = (uint32_t)(a.ny * sizeof(float2));
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
   }
+  __syncthreads();
+  if (tid < 32) {
+    if (tid == 0) mbar_expect_tx(bar, row_bytes * a.nz);
+    __syncwarp();
+    for (int zz = tid; zz < a.nz; zz += 32)
+      bulk_load(sm + (size_t)zz * a.pitch, g + (size_t)zz * a.ny, row_bytes, bar);
+  }
+  for (int i = tid; i < a.py.tw_count; i += nthr) twy[i] = a.twy[i];
+  for (int i = tid; i < a.pz.tw_count; i += nthr) twz[i] = a.twz[i];
+  for (int i = tid; i < a.ny; i += nthr) Ky[i] = a.Ky[i];
+  for (int i = tid; i < a.nz; i += nthr) Kz[i] = a.Kz[i];
+  const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0));
+  if (!ok) {
+    if (tid == 0 && a.status != nullptr) atomicOr(a.status, kStatusTimeout);
+    mbar_wait_bounded(bar, 0);
+    return;
+  }
+  pencil_transform(a, sm, twy, twz, Ky, Kz, kx, tid, nthr, true);
+  // make the generic-proxy writes visible to the bulk-copy engine, then store
+  fence_proxy_async();
+  __syncthreads();
+  if (tid < 32) {
+    for (int zz = tid; zz < a.nz; zz += 32)
+      bulk_store(g + (size_t)zz * a.ny, sm + (size_t)zz * a.pitch, row_bytes);
+    bulk_commit();
+    bulk_wait_read();
+  }
+#endif
 }
 
 // ---------------------------------------------------------------- launchers
-size_t plane_smem_bytes(int R, int pitch) { return (size_t)3 * (R / 2) * pitch * sizeof(float2); }
-size_t pencil_smem_bytes(int ny, int nz, int pitch) {
-  (void)ny;
-  return (size_t)nz * pitch * sizeof(float2);
+int rows_per_tile(int ny) { return (ny % 8 == 0) ? 8 : (ny % 4 == 0) ? 4 : 2; }
+
+void finish_plane_args(PlaneArgs& a) {
+  a.nkx = a.nx / 2 + 1;
+  a.R = rows_per_tile(a.ny);
+  a.pitch = a.nx + 1;
+  a.nx_div = make_fastdiv((uint32_t)a.nx);
+  a.lines_div = make_fastdiv((uint32_t)(3 * (a.R / 2)));
+  a.half_div = make_fastdiv((uint32_t)(a.R / 2));
+  a.nkx_div = make_fastdiv((uint32_t)a.nkx);
+  a.tiles_div = make_fastdiv((uint32_t)(a.ny / a.R));
 }
+
+void finish_pencil_args(PencilArgs& a) {
+  a.pitch = a.ny + 2;
+  a.ny_div = make_fastdiv((uint32_t)a.ny);
+  a.nz_div = make_fastdiv((uint32_t)a.nz);
+  a.nkx_div = make_fastdiv((uint32_t)a.nkx);
+}
+
+static int field_count(int in_mode, bool prev, bool step) {
+  switch (in_mode * 4 + (prev ? 2 : 0) + (step ? 1 : 0)) {
+    case IN_NONE * 4 + 1: return field_map<IN_NONE, false, true>().n;
+    case IN_SPEC * 4 + 1: return field_map<IN_SPEC, false, true>().n;
+    case IN_SPEC * 4 + 3: return field_map<IN_SPEC, true, true>().n;
+    case IN_SPEC * 4 + 0: return field_map<IN_SPEC, false, false>().n;
+    case IN_STATE * 4 + 1: return field_map<IN_STATE, false, true>().n;
+    case IN_STATE * 4 + 3: return field_map<IN_STATE, true, true>().n;
+    case IN_FIELD * 4 + 1: return field_map<IN_FIELD, false, true>().n;
+  }
+  return 0;
+}
+
+size_t plane_smem_bytes(const PlaneArgs& a, int in_mode, bool prev, bool step) {
+  return plane_layout(a, field_count(in_mode, prev, step)).total;
+}
+
+size_t plane_smem_max(const PlaneArgs& a) { return plane_layout(a, 16).total; }
+
+size_t pencil_smem_bytes(const PencilArgs& a) { return pencil_layout(a).total; }
 
 template <int IN, bool PREV, bool STEP>
 static cudaError_t set_plane_attr(size_t smem) {
@@ -275,9 +565,8 @@ cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem) {
 
 cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, cudaStream_t s) {
   dim3 grid((unsigned)((a.ny / a.R) * a.nz));
-  size_t smem = plane_smem_bytes(a.R, a.pitch);
-  int key = in_mode * 4 + (prev ? 2 : 0) + (step ? 1 : 0);
-  switch (key) {
+  const size_t smem = plane_smem_bytes(a, in_mode, prev, step);
+  switch (in_mode * 4 + (prev ? 2 : 0) + (step ? 1 : 0)) {
     case IN_NONE * 4 + 1: k_plane<IN_NONE, false, true><<<grid, kPlaneThreads, smem, s>>>(a); break;
     case IN_SPEC * 4 + 1: k_plane<IN_SPEC, false, true><<<grid, kPlaneThreads, smem, s>>>(a); break;
     case IN_SPEC * 4 + 3: k_plane<IN_SPEC, true, true><<<grid, kPlaneThreads, smem, s>>>(a); break;
@@ -292,7 +581,7 @@ cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, 
 
 cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s) {
   dim3 grid((unsigned)(3 * a.nkx));
-  k_pencil<<<grid, kPencilThreads, pencil_smem_bytes(a.ny, a.nz, a.pitch), s>>>(a);
+  k_pencil<<<grid, kPencilThreads, pencil_smem_bytes(a), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@
 // block-level loop is plain C++; the kernels separate phases with barriers.
 #pragma once
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #if defined(__CUDACC__)
 #define NADMM_HD __host__ __device__ __forceinline__
@@ -31,6 +32,39 @@ namespace nadmm {
 
 constexpr int kMaxStages = 5;
 
+// Division by a runtime-invariant divisor d >= 1 for 0 <= n < 2^31, by the
+// round-up multiplier method (Granlund & Montgomery, "Division by invariant
+// integers using multiplication", 1994): with l = ceil(log2 d), p = 31 + l,
+// mul = ceil(2^p / d), q = floor(n * mul / 2^p).
+struct FastDiv {
+  uint32_t d, mul, shift;  // shift = p - 32 (unused when d == 1)
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  if (d <= 1) {
+    f.mul = 0;
+    f.shift = 0;
+    return f;
+  }
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  uint64_t p2 = 1ull << (31 + l);
+  f.mul = (uint32_t)((p2 + d - 1) / d);
+  f.shift = l - 1;
+  return f;
+}
+
+NADMM_HD uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  if (f.d <= 1) return n;
+#if defined(__CUDA_ARCH__)
+  return __umulhi(n, f.mul) >> f.shift;
+#else
+  return (uint32_t)(((uint64_t)n * f.mul) >> 32) >> f.shift;
+#endif
+}
+
 // Radix plan of one axis, passed to kernels by value.
 struct AxisPlan {
   int n;                     // transform length
@@ -39,6 +73,8 @@ struct AxisPlan {
   int L[kMaxStages];         // block length at stage i
   int m[kMaxStages];         // L_i / r_i
   int tw_off[kMaxStages];    // offset of stage i's twiddles in the axis table
+  int tw_count;              // entries in the axis table
+  FastDiv mdiv[kMaxStages];  // division by m_i
 };
 
 NADMM_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -217,6 +253,93 @@ NADMM_HD void dft_odd(float2 (&x)[R]) {
   x[0] = sum;
 }
 
+// cos/sin(2 pi m / R) for m = 0..6, R in {6, 9, 10, 12}: the internal
+// twiddles of the composite codelets (m = n2 k1 never exceeds 6 there).
+template <int R> struct CompTab;
+template <> struct CompTab<6> {
+  NADMM_HD static float c(int m) {
+    const float t[7] = {1.f, 0.5f, -0.5f, -1.f, -0.5f, 0.5f, 1.f};
+    return t[m];
+  }
+  NADMM_HD static float s(int m) {
+    const float t[7] = {0.f, 0.86602540378443865f, 0.86602540378443865f, 0.f,
+                        -0.86602540378443865f, -0.86602540378443865f, 0.f};
+    return t[m];
+  }
+};
+template <> struct CompTab<9> {
+  NADMM_HD static float c(int m) {
+    const float t[7] = {1.f, 0.76604444311897801f, 0.17364817766693041f, -0.5f,
+                        -0.93969262078590832f, -0.93969262078590843f, -0.5f};
+    return t[m];
+  }
+  NADMM_HD static float s(int m) {
+    const float t[7] = {0.f, 0.64278760968653925f, 0.98480775301220802f, 0.86602540378443865f,
+                        0.34202014332566888f, -0.34202014332566866f, -0.86602540378443865f};
+    return t[m];
+  }
+};
+template <> struct CompTab<10> {
+  NADMM_HD static float c(int m) {
+    const float t[7] = {1.f, 0.80901699437494745f, 0.30901699437494745f, -0.30901699437494734f,
+                        -0.80901699437494734f, -1.f, -0.80901699437494756f};
+    return t[m];
+  }
+  NADMM_HD static float s(int m) {
+    const float t[7] = {0.f, 0.58778525229247314f, 0.95105651629515353f, 0.95105651629515364f,
+                        0.58778525229247325f, 0.f, -0.58778525229247303f};
+    return t[m];
+  }
+};
+template <> struct CompTab<12> {
+  NADMM_HD static float c(int m) {
+    const float t[7] = {1.f, 0.86602540378443865f, 0.5f, 0.f, -0.5f, -0.86602540378443865f, -1.f};
+    return t[m];
+  }
+  NADMM_HD static float s(int m) {
+    const float t[7] = {0.f, 0.5f, 0.86602540378443865f, 1.f, 0.86602540378443865f, 0.5f, 0.f};
+    return t[m];
+  }
+};
+
+template <int R, bool INV>
+NADMM_HD void dft(float2 (&x)[R]);
+
+// R = A * B in registers: inner A-point DFTs over n1 of x[B n1 + n2],
+// twiddle w_R^{n2 k1}, outer B-point DFTs over n2; output X[k1 + A k2].
+template <int A, int B, bool INV>
+NADMM_HD void dft_composite(float2 (&x)[A * B]) {
+  constexpr int R = A * B;
+  float2 y[R];
+#pragma unroll
+  for (int n2 = 0; n2 < B; ++n2) {
+    float2 a[A];
+#pragma unroll
+    for (int n1 = 0; n1 < A; ++n1) a[n1] = x[B * n1 + n2];
+    dft<A, INV>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+      const int m = n2 * k1;
+      float2 v = a[k1];
+      if (m != 0) {
+        const float c = CompTab<R>::c(m), s = CompTab<R>::s(m);
+        const float sg = INV ? -s : s;
+        v = make_float2(v.x * c + v.y * sg, v.y * c - v.x * sg);
+      }
+      y[k1 * B + n2] = v;
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) {
+    float2 b[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) b[n2] = y[k1 * B + n2];
+    dft<B, INV>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) x[k1 + A * k2] = b[k2];
+  }
+}
+
 template <int R, bool INV>
 NADMM_HD void dft(float2 (&x)[R]) {
   if constexpr (R == 2) {
@@ -227,6 +350,14 @@ NADMM_HD void dft(float2 (&x)[R]) {
     dft8<INV>(x);
   } else if constexpr (R == 16) {
     dft16<INV>(x);
+  } else if constexpr (R == 6) {
+    dft_composite<3, 2, INV>(x);
+  } else if constexpr (R == 9) {
+    dft_composite<3, 3, INV>(x);
+  } else if constexpr (R == 10) {
+    dft_composite<5, 2, INV>(x);
+  } else if constexpr (R == 12) {
+    dft_composite<4, 3, INV>(x);
   } else {
     dft_odd<R, INV>(x);
   }
@@ -261,15 +392,15 @@ NADMM_HD void butterfly(float2* base, int step, const float2* tw, int m, int n1)
 // line l lives at buf[l * ls + e * es].  Work item g -> (line fastest, then
 // n1, then block) so that a warp's lanes sit on different lines.
 template <int R, bool INV>
-NADMM_HD void stage_loop(float2* buf, int nlines, int es, int ls, int L, int m,
-                         const float2* tw, int nblk, int tid, int nthr) {
+NADMM_HD void stage_loop(float2* buf, int nlines, const FastDiv& ldiv, int es, int ls, int L, int m,
+                         const FastDiv& mdiv, const float2* tw, int nblk, int tid, int nthr) {
   const int total = nlines * nblk * m;
   const int step = m * es;
   for (int g = tid; g < total; g += nthr) {
-    int line = g % nlines;
-    int q = g / nlines;
-    int n1 = q % m;
-    int blk = q / m;
+    const int q = (int)fdiv((uint32_t)g, ldiv);
+    const int line = g - q * nlines;
+    const int blk = (int)fdiv((uint32_t)q, mdiv);
+    const int n1 = q - blk * m;
     float2* base = buf + line * ls + (blk * L + n1) * es;
     butterfly<R, INV>(base, step, tw, m, n1);
   }
@@ -277,18 +408,66 @@ NADMM_HD void stage_loop(float2* buf, int nlines, int es, int ls, int L, int m,
 
 // Stage s of plan p (forward or inverse); tw_axis is the axis table.
 template <bool INV>
-NADMM_HD void fft_stage(const AxisPlan& p, int s, float2* buf, int nlines, int es, int ls,
-                        const float2* tw_axis, int tid, int nthr) {
+NADMM_HD void fft_stage(const AxisPlan& p, int s, float2* buf, int nlines, const FastDiv& ldiv,
+                        int es, int ls, const float2* tw_axis, int tid, int nthr) {
   const int L = p.L[s], m = p.m[s], nblk = p.n / L;
   const float2* tw = tw_axis + p.tw_off[s];
+  const FastDiv& md = p.mdiv[s];
   switch (p.radix[s]) {
-    case 2: stage_loop<2, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
-    case 3: stage_loop<3, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
-    case 4: stage_loop<4, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
-    case 5: stage_loop<5, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
-    case 7: stage_loop<7, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
-    case 8: stage_loop<8, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
-    default: stage_loop<16, INV>(buf, nlines, es, ls, L, m, tw, nblk, tid, nthr); break;
+    case 2: stage_loop<2, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
+    case 3: stage_loop<3, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
+    case 4: stage_loop<4, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
+    case 5: stage_loop<5, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
+    case 6: stage_loop<6, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
+    case 7: stage_loop<7, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
+    case 8: stage_loop<8, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
+    case 9: stage_loop<9, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
+    case 10: stage_loop<10, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
+    case 12: stage_loop<12, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
+    default: stage_loop<16, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
+  }
+}
+
+// Last forward stage (m = 1), point-wise multiply by the filter, and the
+// first inverse stage, fused in registers: each group of R consecutive
+// positions (step es) is transformed, scaled and transformed back.
+// filt(pos) returns the real gain for position pos of the line.
+template <int R, class Filt>
+NADMM_HD void filter_loop(float2* buf, int nlines, const FastDiv& ldiv, int es, int ls, int n,
+                          Filt filt, int tid, int nthr) {
+  const int nblk = n / R;
+  const int total = nlines * nblk;
+  for (int g = tid; g < total; g += nthr) {
+    const int blk = (int)fdiv((uint32_t)g, ldiv);
+    const int line = g - blk * nlines;
+    float2* base = buf + line * ls + blk * R * es;
+    float2 x[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) x[j] = base[j * es];
+    dft<R, false>(x);
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = cscale(x[k], filt(line, blk * R + k));
+    dft<R, true>(x);
+#pragma unroll
+    for (int j = 0; j < R; ++j) base[j * es] = x[j];
+  }
+}
+
+template <class Filt>
+NADMM_HD void fft_filter_last(const AxisPlan& p, float2* buf, int nlines, const FastDiv& ldiv,
+                              int es, int ls, Filt filt, int tid, int nthr) {
+  switch (p.radix[p.nst - 1]) {
+    case 2: filter_loop<2>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
+    case 3: filter_loop<3>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
+    case 4: filter_loop<4>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
+    case 5: filter_loop<5>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
+    case 6: filter_loop<6>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
+    case 7: filter_loop<7>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
+    case 8: filter_loop<8>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
+    case 9: filter_loop<9>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
+    case 10: filter_loop<10>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
+    case 12: filter_loop<12>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
+    default: filter_loop<16>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
   }
 }
 

@@ -41,7 +41,7 @@ struct nadmm_context {
   std::vector<int> posx;
   std::vector<float> Kx, Ky, Kz;
   std::vector<float> beta;   // beta_0 .. beta_{K-1}
-  int R = 0, pitch_x = 0, pitch_y = 0;
+  int R = 0;
   size_t V = 0, nkx = 0;
   size_t plane_smem = 0, pencil_smem = 0;
   // workspace layout (byte offsets)
@@ -138,11 +138,11 @@ PlaneArgs plane_args(const nadmm_context* h) {
   a.ny = h->cfg.ny;
   a.nz = h->cfg.nz;
   a.nkx = (int)h->nkx;
-  a.R = h->R;
-  a.pitch = h->pitch_x;
+  a.status = h->at<unsigned>(h->o_red) + 2;
   a.theta = h->cfg.theta;
   a.eps = h->cfg.eps;
   a.data_term = h->cfg.data_term;
+  finish_plane_args(a);
   return a;
 }
 
@@ -160,10 +160,11 @@ PencilArgs pencil_args(const nadmm_context* h) {
   a.ny = h->cfg.ny;
   a.nz = h->cfg.nz;
   a.nkx = (int)h->nkx;
-  a.pitch = h->pitch_y;
+  a.status = h->at<unsigned>(h->o_red) + 2;
   a.order_n = h->cfg.order_n;
   a.gamma = h->cfg.lambda / h->cfg.theta;
   a.scale = (float)(1.0 / ((double)h->cfg.nx * h->cfg.ny * h->cfg.nz));
+  finish_pencil_args(a);
   return a;
 }
 
@@ -360,6 +361,7 @@ const char* nadmm_status_string(nadmm_status s) {
     case NADMM_ERR_NO_WORKSPACE: return "NADMM_ERR_NO_WORKSPACE";
     case NADMM_ERR_CUDA: return "NADMM_ERR_CUDA";
     case NADMM_ERR_NONFINITE: return "NADMM_ERR_NONFINITE";
+    case NADMM_ERR_TIMEOUT: return "NADMM_ERR_TIMEOUT";
   }
   return "unknown nadmm_status";
 }
@@ -377,15 +379,34 @@ nadmm_status nadmm_create(const nadmm_config* cfg, nadmm_handle* out) {
   }
   h->V = (size_t)cfg->nx * cfg->ny * cfg->nz;
   h->nkx = (size_t)cfg->nx / 2 + 1;
-  h->R = (cfg->ny % 16 == 0) ? 16 : (cfg->ny % 8 == 0) ? 8 : (cfg->ny % 4 == 0) ? 4 : 2;
-  h->pitch_x = cfg->nx + 1;
-  h->pitch_y = cfg->ny + 1;
-  h->plane_smem = plane_smem_bytes(h->R, h->pitch_x);
-  h->pencil_smem = pencil_smem_bytes(cfg->ny, cfg->nz, h->pitch_y);
+  {
+    PlaneArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.nx = cfg->nx;
+    pa.ny = cfg->ny;
+    pa.nz = cfg->nz;
+    pa.px = h->px;
+    finish_plane_args(pa);
+    PencilArgs qa;
+    std::memset(&qa, 0, sizeof(qa));
+    qa.ny = cfg->ny;
+    qa.nz = cfg->nz;
+    qa.nkx = (int)h->nkx;
+    qa.py = h->py;
+    qa.pz = h->pz;
+    finish_pencil_args(qa);
+    h->R = pa.R;
+    h->plane_smem = plane_smem_max(pa);
+    h->pencil_smem = pencil_smem_bytes(qa);
+  }
   if (h->pencil_smem > 227 * 1024 || h->plane_smem > 227 * 1024) {
     delete h;
     return fail(NADMM_ERR_UNSUPPORTED_SIZE,
                 "a (ny x nz) spectrum plane exceeds the 227 KB of shared memory per CTA");
+  }
+  if (3 * (int)h->nkx * (h->R / 2) > kPlaneGatherCapacity) {
+    delete h;
+    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "nx too large for the plane pass gather");
   }
   h->twx = axis_twiddles(h->px);
   h->twy = axis_twiddles(h->py);
@@ -560,7 +581,10 @@ nadmm_status nadmm_get_status(nadmm_handle h, void* stream) {
   e = cudaMemcpy(&word, dev, sizeof(unsigned), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(dev, 0, sizeof(unsigned));
   if (e != cudaSuccess) return cuda_fail(e, "status read");
-  if (word & 1u) return fail(NADMM_ERR_NONFINITE, "non-finite velocity met in the bound step");
+  if (word & kStatusTimeout)
+    return fail(NADMM_ERR_TIMEOUT, "a kernel's bounded wait for its bulk copies expired");
+  if (word & kStatusNonfinite)
+    return fail(NADMM_ERR_NONFINITE, "non-finite velocity met in the bound step");
   return NADMM_OK;
 }
 

@@ -36,7 +36,13 @@ struct PlaneArgs {
   float* b_out;            // no-step variant: receives b^{k-1} (or null)
   const float2* twx;       // x-axis stage twiddles
   const int* posx;         // position of frequency kx after the forward x-DFT
+  unsigned* status;        // device status word (bit 1: a bounded wait expired) or null
   AxisPlan px;
+  FastDiv nx_div;          // division by nx
+  FastDiv lines_div;       // division by the line count 3 R / 2
+  FastDiv half_div;        // division by R / 2
+  FastDiv nkx_div;         // division by nkx
+  FastDiv tiles_div;       // division by ny / R
   int nx, ny, nz, nkx;     // nkx = nx/2 + 1
   int R;                   // rows per CTA (even, divides ny)
   int pitch;               // shared-memory line pitch (odd, >= nx)
@@ -55,19 +61,34 @@ struct PencilArgs {
   const float* Kx;         // [nkx] 4 sin^2(pi kx / nx)
   const float* Ky;         // [ny] 4 sin^2(pi ky / ny) by position
   const float* Kz;         // [nz] 4 sin^2(pi kz / nz) by position
+  unsigned* status;        // device status word (bit 1: a bounded wait expired) or null
   AxisPlan py, pz;
+  FastDiv ny_div, nz_div;  // line counts of the z- and y-transforms
+  FastDiv nkx_div;
   int ny, nz, nkx;
-  int pitch;               // shared-memory row pitch (odd, >= ny)
+  int pitch;               // shared-memory row pitch (even so rows stay 16-byte aligned)
   int order_n;
   float gamma;             // lambda / theta
   float scale;             // 1 / (nx ny nz)
 };
 
+// the plane pass holds at most this many spectrum values of its tile in flight
+constexpr int kPlaneGatherCapacity = 8 * 256;
+
+constexpr unsigned kStatusNonfinite = 1u;
+constexpr unsigned kStatusTimeout = 2u;
+
+// Fill the FastDiv fields and pitches of the pass arguments from the sizes.
+void finish_plane_args(PlaneArgs& a);
+void finish_pencil_args(PencilArgs& a);
+
 // mode = InMode * 4 + prev * 2 + step
 cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, cudaStream_t s);
 cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s);
-size_t plane_smem_bytes(int R, int pitch);
-size_t pencil_smem_bytes(int ny, int nz, int pitch);
+size_t plane_smem_bytes(const PlaneArgs& a, int in_mode, bool prev, bool step);
+size_t plane_smem_max(const PlaneArgs& a);
+size_t pencil_smem_bytes(const PencilArgs& a);
+int rows_per_tile(int ny);
 cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem);
 
 // ---------------------------------------------------------------- grid ops

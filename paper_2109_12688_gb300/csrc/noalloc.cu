@@ -182,13 +182,30 @@ extern "C" nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int
   AxisPlan px, py, pz;
   if (!factor_axis(nx, px) || !factor_axis(ny, py) || !factor_axis(nz, pz))
     return fail(NADMM_ERR_UNSUPPORTED_SIZE, "no radix plan for these dimensions");
-  const int R = (ny % 16 == 0) ? 16 : (ny % 8 == 0) ? 8 : (ny % 4 == 0) ? 4 : 2;
-  const int pitch_x = nx + 1, pitch_y = ny + 1;
-  const size_t plane_smem = plane_smem_bytes(R, pitch_x);
-  const size_t pencil_smem = pencil_smem_bytes(ny, nz, pitch_y);
-  if (plane_smem > 227 * 1024 || pencil_smem > 227 * 1024)
+  PlaneArgs a = {};
+  a.px = px;
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  a.theta = theta;
+  a.eps = 1e-6f;
+  a.data_term = 2;
+  finish_plane_args(a);
+  PencilArgs pa = {};
+  pa.py = py;
+  pa.pz = pz;
+  pa.ny = ny;
+  pa.nz = nz;
+  pa.nkx = nx / 2 + 1;
+  pa.order_n = order_n;
+  pa.gamma = lambda / theta;
+  pa.scale = (float)(1.0 / ((double)nx * ny * nz));
+  finish_pencil_args(pa);
+  if (plane_smem_max(a) > 227 * 1024 || pencil_smem_bytes(pa) > 227 * 1024)
     return fail(NADMM_ERR_UNSUPPORTED_SIZE,
                 "a (ny x nz) spectrum plane exceeds the 227 KB of shared memory per CTA");
+  if (3 * a.nkx * (a.R / 2) > kPlaneGatherCapacity)
+    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "nx too large for the plane pass gather");
   const StaticLayout L = layout_for(nx, ny, nz, px, py, pz);
   if (L.total > kStaticScratchBytes)
     return fail(NADMM_ERR_UNSUPPORTED_SIZE,
@@ -223,41 +240,20 @@ extern "C" nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "table fill");
 
-  PlaneArgs a = {};
   a.spec = reinterpret_cast<float2*>(base + L.spec);
   a.twx = twx;
   a.posx = posx;
-  a.px = px;
-  a.nx = nx;
-  a.ny = ny;
-  a.nz = nz;
-  a.nkx = nx / 2 + 1;
-  a.R = R;
-  a.pitch = pitch_x;
-  a.theta = theta;
-  a.eps = 1e-6f;
-  a.data_term = 2;
   PlaneArgs fwd = a;
   fwd.y = nullptr;
   fwd.w_in = y;
   e = launch_plane(IN_FIELD, false, true, fwd, s);
   if (e == cudaSuccess) {
-    PencilArgs pa = {};
     pa.spec = a.spec;
     pa.twy = twy;
     pa.twz = twz;
     pa.Kx = Kx;
     pa.Ky = Ky;
     pa.Kz = Kz;
-    pa.py = py;
-    pa.pz = pz;
-    pa.ny = ny;
-    pa.nz = nz;
-    pa.nkx = nx / 2 + 1;
-    pa.pitch = pitch_y;
-    pa.order_n = order_n;
-    pa.gamma = lambda / theta;
-    pa.scale = (float)(1.0 / ((double)nx * ny * nz));
     e = launch_pencil(pa, s);
   }
   if (e == cudaSuccess) {

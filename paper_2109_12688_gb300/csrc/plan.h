@@ -9,36 +9,49 @@
 
 namespace nadmm {
 
-// Radices supported by the shared-memory stages, largest first.
+// Radices with register codelets.  The plan uses the fewest stages (each
+// stage is one pass over shared memory), larger radices first on ties.
+constexpr int kRadices[] = {16, 12, 10, 9, 8, 7, 6, 5, 4, 3, 2};
+
+inline bool best_factors(int n, int depth, int* out, int& best_len, int* cur, int len) {
+  if (n == 1) {
+    if (len < best_len) {
+      best_len = len;
+      for (int i = 0; i < len; ++i) out[i] = cur[i];
+    }
+    return true;
+  }
+  if (len >= depth || len + 1 >= best_len) return false;
+  bool found = false;
+  for (int r : kRadices) {
+    if (n % r) continue;
+    cur[len] = r;
+    found |= best_factors(n / r, depth, out, best_len, cur, len + 1);
+  }
+  return found;
+}
+
 inline bool factor_axis(int n, AxisPlan& p) {
   if (n < 2) return false;
-  int rem = n, ns = 0;
-  int rad[16];
-  // power-of-two part in radix-16/8/4/2 stages, then odd primes
-  while (rem % 16 == 0) { rad[ns++] = 16; rem /= 16; }
-  if (rem % 8 == 0) { rad[ns++] = 8; rem /= 8; }
-  if (rem % 4 == 0) { rad[ns++] = 4; rem /= 4; }
-  if (rem % 2 == 0) { rad[ns++] = 2; rem /= 2; }
-  for (int q : {3, 5, 7}) {
-    while (rem % q == 0) {
-      if (ns >= 16) return false;
-      rad[ns++] = q;
-      rem /= q;
-    }
-  }
-  if (rem != 1 || ns > kMaxStages) return false;
+  int out[kMaxStages], cur[kMaxStages], best = kMaxStages + 1;
+  if (!best_factors(n, kMaxStages, out, best, cur, 0)) return false;
   p.n = n;
-  p.nst = ns;
+  p.nst = best;
   int L = n, off = 0;
-  for (int i = 0; i < ns; ++i) {
-    p.radix[i] = rad[i];
-    p.L[i] = L;
-    p.m[i] = L / rad[i];
-    p.tw_off[i] = off;
-    if (p.m[i] > 1) off += (rad[i] - 1) * p.m[i];
-    L /= rad[i];
+  for (int i = 0; i < kMaxStages; ++i) {
+    if (i < best) {
+      p.radix[i] = out[i];
+      p.L[i] = L;
+      p.m[i] = L / out[i];
+      p.tw_off[i] = off;
+      if (p.m[i] > 1) off += (out[i] - 1) * p.m[i];
+      L /= out[i];
+    } else {
+      p.radix[i] = 1; p.L[i] = 1; p.m[i] = 1; p.tw_off[i] = off;
+    }
+    p.mdiv[i] = make_fastdiv((uint32_t)p.m[i]);
   }
-  for (int i = ns; i < kMaxStages; ++i) { p.radix[i] = 1; p.L[i] = 1; p.m[i] = 1; p.tw_off[i] = off; }
+  p.tw_count = off > 0 ? off : 1;
   return true;
 }
 

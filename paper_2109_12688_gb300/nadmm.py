@@ -21,6 +21,7 @@ NADMM_ERR_ALIGNMENT = 3
 NADMM_ERR_NO_WORKSPACE = 4
 NADMM_ERR_CUDA = 5
 NADMM_ERR_NONFINITE = 6
+NADMM_ERR_TIMEOUT = 7
 NADMM_FLAG_NO_GRAPH = 1
 
 KERNEL_CLASSES = ("plane_first", "plane_k1", "plane", "plane_final", "pencil", "warp", "grad",
