@@ -315,7 +315,7 @@ __device__ __forceinline__ const float* field_src(const PlaneArgs& a, int slot) 
 #endif
 
 template <int IN, bool PREV, bool STEP>
-__global__ void __launch_bounds__(kPlaneThreads, 2) k_plane(PlaneArgs a) {
+__global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
 #if defined(__CUDA_ARCH__)
   constexpr FieldMap F = field_map<IN, PREV, STEP>();
   extern __shared__ __align__(128) unsigned char smem[];
@@ -331,6 +331,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 2) k_plane(PlaneArgs a) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int nlines = 3 * (a.R / 2);
 
+  // Prologue independent of the previous kernel (which writes only the
+  // spectrum): the real-space tiles were written two or more kernels back.
   if (F.n > 0) {
     if (tid == 0) {
       mbar_init(bar, 1);
@@ -350,6 +352,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 2) k_plane(PlaneArgs a) {
   for (int i = tid; i < a.px.tw_count; i += nthr) tw[i] = a.twx[i];
   for (int i = tid; i < a.nx; i += nthr) pos[i] = a.posx[i];
   __syncthreads();
+  pdl_wait();
+  pdl_trigger();
   if (IN == IN_SPEC) {
     plane_gather(a, lines, pos, z, y0, tid, nthr);
     __syncthreads();
@@ -378,8 +382,18 @@ __global__ void __launch_bounds__(kPlaneThreads, 2) k_plane(PlaneArgs a) {
 #endif
 }
 
-// ---------------------------------------------------------------- pencil pass
-// Gain 1/(1 + gamma K^n)/(nx ny nz) at (kx, y position `line`, z position).
+// ---------------------------------------------------------------- y / z passes
+// The pencil work of Eq. 6's 3D DFT on the half spectrum [3][nkx][nz][ny]:
+//   y-pass  (forward, then inverse after the z-pass): y-DFT of `yrows`
+//           consecutive (component, kx, z) rows per CTA;
+//   z-pass: for a (component, kx) plane and `zcols` consecutive y positions,
+//           forward z-DFT, multiply by 1/(1 + gamma K^n)/(nx ny nz), inverse
+//           z-DFT (last forward stage, filter and first inverse stage fused).
+// The spectrum stays L2-resident between them; each CTA is small, so the
+// grid covers every SM several times whatever the grid size.
+
+// Gain 1/(1 + gamma K^n)/(nx ny nz) for y position `line` of the tile and
+// z position `zpos` (Ky holds the tile's slice, Kz the whole axis).
 struct PencilFilter {
   const float* Ky;
   const float* Kz;
@@ -393,109 +407,152 @@ struct PencilFilter {
   }
 };
 
-struct PencilSmem {
-  size_t plane, twy, twz, ky, kz, total;
-};
+constexpr int kYThreads = 128;
+constexpr int kZThreads = 128;
 
-NADMM_HD PencilSmem pencil_layout(const PencilArgs& a) {
-  PencilSmem L;
-  size_t o = 16;  // mbarrier
-  L.plane = o;
-  o += (size_t)a.nz * a.pitch * sizeof(float2);
-  L.twy = o;
-  o += (size_t)a.py.tw_count * sizeof(float2);
-  L.twz = o;
-  o += (size_t)a.pz.tw_count * sizeof(float2);
-  L.ky = o;
-  o += (size_t)a.ny * sizeof(float);
-  L.kz = o;
-  o += (size_t)a.nz * sizeof(float);
-  L.total = (o + 15) & ~(size_t)15;
-  return L;
+NADMM_HD size_t ypass_smem(const PencilArgs& a) {
+  return 16 + (size_t)a.yrows * a.ypitch * sizeof(float2) + (size_t)a.py.tw_count * sizeof(float2);
 }
 
-// The transform of one (component, kx) plane held at `sm` [nz][pitch].
-NADMM_HD void pencil_transform(const PencilArgs& a, float2* sm, const float2* twy, const float2* twz,
-                               const float* Ky, const float* Kz, int kx, int tid, int nthr,
-                               bool sync_between) {
+NADMM_HD size_t zpass_smem(const PencilArgs& a) {
+  return 16 + (size_t)a.nz * a.zcols * sizeof(float2) + (size_t)a.pz.tw_count * sizeof(float2) +
+         (size_t)(a.nz + a.zcols) * sizeof(float) + 16;
+}
+
+// y-DFT (forward or inverse) of `nrows` rows held at `rows` with pitch ypitch.
+template <bool INV>
+NADMM_HD void ypass_transform(const PencilArgs& a, float2* rows, const float2* tw, int tid,
+                              int nthr, bool sync_between) {
 #if defined(__CUDA_ARCH__)
 #define NADMM_PSYNC() \
   if (sync_between) __syncthreads()
 #else
 #define NADMM_PSYNC() (void)sync_between
 #endif
-  // forward y-DFT of every z-row (lines = z rows, elements contiguous)
-  for (int s = 0; s < a.py.nst; ++s) {
-    fft_stage<false>(a.py, s, sm, a.nz, a.nz_div, 1, a.pitch, twy, tid, nthr);
-    NADMM_PSYNC();
+  if (!INV) {
+    for (int s = 0; s < a.py.nst; ++s) {
+      fft_stage<false>(a.py, s, rows, a.yrows, a.yrows_div, 1, a.ypitch, tw, tid, nthr);
+      NADMM_PSYNC();
+    }
+  } else {
+    for (int s = a.py.nst - 1; s >= 0; --s) {
+      fft_stage<true>(a.py, s, rows, a.yrows, a.yrows_div, 1, a.ypitch, tw, tid, nthr);
+      NADMM_PSYNC();
+    }
   }
-  // forward z-DFT of every y-column except its last stage
+#undef NADMM_PSYNC
+}
+
+// z-DFT, filter, inverse z-DFT of a [nz][zcols] tile (lines = y positions).
+NADMM_HD void zpass_transform(const PencilArgs& a, float2* tile, const float2* tw,
+                              const PencilFilter& filt, int tid, int nthr, bool sync_between) {
+#if defined(__CUDA_ARCH__)
+#define NADMM_PSYNC() \
+  if (sync_between) __syncthreads()
+#else
+#define NADMM_PSYNC() (void)sync_between
+#endif
   for (int s = 0; s + 1 < a.pz.nst; ++s) {
-    fft_stage<false>(a.pz, s, sm, a.ny, a.ny_div, a.pitch, 1, twz, tid, nthr);
+    fft_stage<false>(a.pz, s, tile, a.zcols, a.zcols_div, a.zcols, 1, tw, tid, nthr);
     NADMM_PSYNC();
   }
-  // last forward z stage, inverse-symbol multiply, first inverse z stage
-  // Kx is indexed by the natural frequency kx < nkx (the x-transform is
-  // scattered in natural order); Ky, Kz by position
-  const PencilFilter filt{Ky, Kz, a.Kx[kx], a.gamma, a.scale, a.order_n};
-  fft_filter_last(a.pz, sm, a.ny, a.ny_div, a.pitch, 1, filt, tid, nthr);
+  fft_filter_last(a.pz, tile, a.zcols, a.zcols_div, a.zcols, 1, filt, tid, nthr);
   NADMM_PSYNC();
   for (int s = a.pz.nst - 2; s >= 0; --s) {
-    fft_stage<true>(a.pz, s, sm, a.ny, a.ny_div, a.pitch, 1, twz, tid, nthr);
-    NADMM_PSYNC();
-  }
-  for (int s = a.py.nst - 1; s >= 0; --s) {
-    fft_stage<true>(a.py, s, sm, a.nz, a.nz_div, 1, a.pitch, twy, tid, nthr);
+    fft_stage<true>(a.pz, s, tile, a.zcols, a.zcols_div, a.zcols, 1, tw, tid, nthr);
     NADMM_PSYNC();
   }
 #undef NADMM_PSYNC
 }
 
-
-__global__ void __launch_bounds__(kPencilThreads, 2) k_pencil(PencilArgs a) {
+template <bool INV>
+__global__ void __launch_bounds__(kYThreads) k_ypass(PencilArgs a) {
 #if defined(__CUDA_ARCH__)
   extern __shared__ __align__(128) unsigned char smem[];
-  const PencilSmem L = pencil_layout(a);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  float2* sm = reinterpret_cast<float2*>(smem + L.plane);
-  float2* twy = reinterpret_cast<float2*>(smem + L.twy);
-  float2* twz = reinterpret_cast<float2*>(smem + L.twz);
-  float* Ky = reinterpret_cast<float*>(smem + L.ky);
-  float* Kz = reinterpret_cast<float*>(smem + L.kz);
-  const int plane = blockIdx.x;
-  const int kx = plane - (int)fdiv((uint32_t)plane, a.nkx_div) * a.nkx;
+  float2* rows = reinterpret_cast<float2*>(smem + 16);
+  float2* tw = rows + (size_t)a.yrows * a.ypitch;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  float2* g = a.spec + (size_t)plane * a.ny * a.nz;
+  float2* g = a.spec + (size_t)blockIdx.x * a.yrows * a.ny;
   const uint32_t row_bytes = (uint32_t)(a.ny * sizeof(float2));
-
+  for (int i = tid; i < a.py.tw_count; i += nthr) tw[i] = a.twy[i];
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
   }
   __syncthreads();
+  pdl_wait();  // the spectrum comes from the previous kernel
   if (tid < 32) {
-    if (tid == 0) mbar_expect_tx(bar, row_bytes * a.nz);
+    if (tid == 0) mbar_expect_tx(bar, row_bytes * a.yrows);
     __syncwarp();
-    for (int zz = tid; zz < a.nz; zz += 32)
-      bulk_load(sm + (size_t)zz * a.pitch, g + (size_t)zz * a.ny, row_bytes, bar);
+    for (int r = tid; r < a.yrows; r += 32)
+      bulk_load(rows + (size_t)r * a.ypitch, g + (size_t)r * a.ny, row_bytes, bar);
   }
-  for (int i = tid; i < a.py.tw_count; i += nthr) twy[i] = a.twy[i];
-  for (int i = tid; i < a.pz.tw_count; i += nthr) twz[i] = a.twz[i];
-  for (int i = tid; i < a.ny; i += nthr) Ky[i] = a.Ky[i];
-  for (int i = tid; i < a.nz; i += nthr) Kz[i] = a.Kz[i];
+  pdl_trigger();
   const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0));
   if (!ok) {
     if (tid == 0 && a.status != nullptr) atomicOr(a.status, kStatusTimeout);
     mbar_wait_bounded(bar, 0);
     return;
   }
-  pencil_transform(a, sm, twy, twz, Ky, Kz, kx, tid, nthr, true);
-  // make the generic-proxy writes visible to the bulk-copy engine, then store
+  ypass_transform<INV>(a, rows, tw, tid, nthr, true);
+  fence_proxy_async();
+  __syncthreads();
+  if (tid < 32) {
+    for (int r = tid; r < a.yrows; r += 32)
+      bulk_store(g + (size_t)r * a.ny, rows + (size_t)r * a.ypitch, row_bytes);
+    bulk_commit();
+    bulk_wait_read();
+  }
+#endif
+}
+
+__global__ void __launch_bounds__(kZThreads) k_zpass(PencilArgs a) {
+#if defined(__CUDA_ARCH__)
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  float2* tile = reinterpret_cast<float2*>(smem + 16);
+  float2* tw = tile + (size_t)a.nz * a.zcols;
+  float* Kz = reinterpret_cast<float*>(tw + a.pz.tw_count);
+  float* Ky = Kz + a.nz;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tiles = a.ny / a.zcols;
+  const int plane = (int)fdiv(blockIdx.x, a.ztiles_div);
+  const int y0 = (blockIdx.x - plane * tiles) * a.zcols;
+  const int kx = plane - (int)fdiv((uint32_t)plane, a.nkx_div) * a.nkx;
+  float2* g = a.spec + (size_t)plane * a.ny * a.nz + y0;
+  const uint32_t seg_bytes = (uint32_t)(a.zcols * sizeof(float2));
+  for (int i = tid; i < a.pz.tw_count; i += nthr) tw[i] = a.twz[i];
+  for (int i = tid; i < a.nz; i += nthr) Kz[i] = a.Kz[i];
+  for (int i = tid; i < a.zcols; i += nthr) Ky[i] = a.Ky[y0 + i];
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  pdl_wait();
+  if (tid < 32) {
+    if (tid == 0) mbar_expect_tx(bar, seg_bytes * a.nz);
+    __syncwarp();
+    for (int zz = tid; zz < a.nz; zz += 32)
+      bulk_load(tile + (size_t)zz * a.zcols, g + (size_t)zz * a.ny, seg_bytes, bar);
+  }
+  pdl_trigger();
+  const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0));
+  if (!ok) {
+    if (tid == 0 && a.status != nullptr) atomicOr(a.status, kStatusTimeout);
+    mbar_wait_bounded(bar, 0);
+    return;
+  }
+  // Kx by the natural frequency kx < nkx (the x-transform is scattered in
+  // natural order); Ky and Kz by position.
+  const PencilFilter filt{Ky, Kz, a.Kx[kx], a.gamma, a.scale, a.order_n};
+  zpass_transform(a, tile, tw, filt, tid, nthr, true);
   fence_proxy_async();
   __syncthreads();
   if (tid < 32) {
     for (int zz = tid; zz < a.nz; zz += 32)
-      bulk_store(g + (size_t)zz * a.ny, sm + (size_t)zz * a.pitch, row_bytes);
+      bulk_store(g + (size_t)zz * a.ny, tile + (size_t)zz * a.zcols, seg_bytes);
     bulk_commit();
     bulk_wait_read();
   }
@@ -517,9 +574,12 @@ void finish_plane_args(PlaneArgs& a) {
 }
 
 void finish_pencil_args(PencilArgs& a) {
-  a.pitch = a.ny + 2;
-  a.ny_div = make_fastdiv((uint32_t)a.ny);
-  a.nz_div = make_fastdiv((uint32_t)a.nz);
+  a.yrows = (a.nz % 16 == 0) ? 16 : (a.nz % 8 == 0) ? 8 : (a.nz % 4 == 0) ? 4 : (a.nz % 2 == 0) ? 2 : 1;
+  a.ypitch = a.ny + 2;  // even: row starts stay 16-byte aligned for bulk copies
+  a.zcols = (a.ny % 16 == 0) ? 16 : (a.ny % 8 == 0) ? 8 : (a.ny % 4 == 0) ? 4 : 2;
+  a.yrows_div = make_fastdiv((uint32_t)a.yrows);
+  a.zcols_div = make_fastdiv((uint32_t)a.zcols);
+  a.ztiles_div = make_fastdiv((uint32_t)(a.ny / a.zcols));
   a.nkx_div = make_fastdiv((uint32_t)a.nkx);
 }
 
@@ -542,7 +602,10 @@ size_t plane_smem_bytes(const PlaneArgs& a, int in_mode, bool prev, bool step) {
 
 size_t plane_smem_max(const PlaneArgs& a) { return plane_layout(a, 16).total; }
 
-size_t pencil_smem_bytes(const PencilArgs& a) { return pencil_layout(a).total; }
+size_t pencil_smem_bytes(const PencilArgs& a) {
+  const size_t y = ypass_smem(a), z = zpass_smem(a);
+  return y > z ? y : z;
+}
 
 template <int IN, bool PREV, bool STEP>
 static cudaError_t set_plane_attr(size_t smem) {
@@ -559,30 +622,39 @@ cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem) {
   if ((e = set_plane_attr<IN_STATE, false, true>(plane_smem)) != cudaSuccess) return e;
   if ((e = set_plane_attr<IN_STATE, true, true>(plane_smem)) != cudaSuccess) return e;
   if ((e = set_plane_attr<IN_FIELD, false, true>(plane_smem)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_pencil, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(k_ypass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pencil_smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_ypass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pencil_smem)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(k_zpass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)pencil_smem);
 }
 
 cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, cudaStream_t s) {
   dim3 grid((unsigned)((a.ny / a.R) * a.nz));
+  dim3 block(kPlaneThreads);
   const size_t smem = plane_smem_bytes(a, in_mode, prev, step);
   switch (in_mode * 4 + (prev ? 2 : 0) + (step ? 1 : 0)) {
-    case IN_NONE * 4 + 1: k_plane<IN_NONE, false, true><<<grid, kPlaneThreads, smem, s>>>(a); break;
-    case IN_SPEC * 4 + 1: k_plane<IN_SPEC, false, true><<<grid, kPlaneThreads, smem, s>>>(a); break;
-    case IN_SPEC * 4 + 3: k_plane<IN_SPEC, true, true><<<grid, kPlaneThreads, smem, s>>>(a); break;
-    case IN_SPEC * 4 + 0: k_plane<IN_SPEC, false, false><<<grid, kPlaneThreads, smem, s>>>(a); break;
-    case IN_STATE * 4 + 1: k_plane<IN_STATE, false, true><<<grid, kPlaneThreads, smem, s>>>(a); break;
-    case IN_STATE * 4 + 3: k_plane<IN_STATE, true, true><<<grid, kPlaneThreads, smem, s>>>(a); break;
-    case IN_FIELD * 4 + 1: k_plane<IN_FIELD, false, true><<<grid, kPlaneThreads, smem, s>>>(a); break;
-    default: return cudaErrorInvalidValue;
+    case IN_NONE * 4 + 1: return launch_pdl(k_plane<IN_NONE, false, true>, grid, block, smem, s, a);
+    case IN_SPEC * 4 + 1: return launch_pdl(k_plane<IN_SPEC, false, true>, grid, block, smem, s, a);
+    case IN_SPEC * 4 + 3: return launch_pdl(k_plane<IN_SPEC, true, true>, grid, block, smem, s, a);
+    case IN_SPEC * 4 + 0: return launch_pdl(k_plane<IN_SPEC, false, false>, grid, block, smem, s, a);
+    case IN_STATE * 4 + 1: return launch_pdl(k_plane<IN_STATE, false, true>, grid, block, smem, s, a);
+    case IN_STATE * 4 + 3: return launch_pdl(k_plane<IN_STATE, true, true>, grid, block, smem, s, a);
+    case IN_FIELD * 4 + 1: return launch_pdl(k_plane<IN_FIELD, false, true>, grid, block, smem, s, a);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s) {
-  dim3 grid((unsigned)(3 * a.nkx));
-  k_pencil<<<grid, kPencilThreads, pencil_smem_bytes(a), s>>>(a);
-  return cudaGetLastError();
+  const unsigned yblocks = (unsigned)(3 * a.nkx * a.nz / a.yrows);
+  const unsigned zblocks = (unsigned)(3 * a.nkx * (a.ny / a.zcols));
+  cudaError_t e = launch_pdl(k_ypass<false>, dim3(yblocks), dim3(kYThreads), ypass_smem(a), s, a);
+  if (e == cudaSuccess) e = launch_pdl(k_zpass, dim3(zblocks), dim3(kZThreads), zpass_smem(a), s, a);
+  if (e == cudaSuccess) e = launch_pdl(k_ypass<true>, dim3(yblocks), dim3(kYThreads), ypass_smem(a), s, a);
+  return e;
 }
 
 }  // namespace nadmm

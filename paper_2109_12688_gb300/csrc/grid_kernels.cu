@@ -50,11 +50,15 @@ __device__ __forceinline__ void vox_coords(size_t i, Dims d, int& x, int& y, int
   z = (int)(r / d.ny);
 }
 
-// I1w(x) = I1(x + u(x))
+// I1w(x) = I1(x + u(x)).  Also clears the bound reduction words of the next
+// outer step (the compose that read them has completed).
 __global__ void __launch_bounds__(kGridThreads) k_warp(Dims d, const float* __restrict__ I1,
                                                        const float* __restrict__ u,
-                                                       float* __restrict__ I1w) {
+                                                       float* __restrict__ I1w, unsigned* red) {
   const size_t V = (size_t)d.nx * d.ny * d.nz;
+  pdl_wait();
+  pdl_trigger();
+  if (red != nullptr && blockIdx.x == 0 && threadIdx.x < 2) red[threadIdx.x] = 0u;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
        i += (size_t)gridDim.x * blockDim.x) {
     int x, y, z;
@@ -69,6 +73,8 @@ __global__ void __launch_bounds__(kGridThreads) k_grad_residual(Dims d,
                                                                 const float* __restrict__ I0,
                                                                 float* __restrict__ J,
                                                                 float* __restrict__ c) {
+  pdl_wait();
+  pdl_trigger();
   const size_t V = (size_t)d.nx * d.ny * d.nz;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
@@ -90,6 +96,8 @@ __global__ void __launch_bounds__(kGridThreads) k_grad_residual(Dims d,
 // floats order like their bits; NaN bits sort above +inf).
 __global__ void __launch_bounds__(kGridThreads) k_bound_reduce(Dims d, const float* __restrict__ w,
                                                                unsigned* red) {
+  pdl_wait();
+  pdl_trigger();
   const size_t V = (size_t)d.nx * d.ny * d.nz;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   float mabs = 0.0f, mjac = 0.0f;
@@ -148,6 +156,8 @@ __global__ void __launch_bounds__(kGridThreads) k_compose(Dims d, const float* _
                                                           const unsigned* red, float kappa,
                                                           float delta, unsigned* status,
                                                           float* scale_out) {
+  pdl_wait();
+  pdl_trigger();
   const size_t V = (size_t)d.nx * d.ny * d.nz;
   const float s = bound_factor(red, kappa, delta,
                                (blockIdx.x == 0 && threadIdx.x == 0) ? status : nullptr);
@@ -168,6 +178,8 @@ __global__ void __launch_bounds__(kGridThreads) k_compose(Dims d, const float* _
 __global__ void __launch_bounds__(kGridThreads) k_jacobian(Dims d, const float* __restrict__ u,
                                                            float* __restrict__ det,
                                                            unsigned* count) {
+  pdl_wait();
+  pdl_trigger();
   const size_t V = (size_t)d.nx * d.ny * d.nz;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   unsigned local = 0;
@@ -206,33 +218,31 @@ static unsigned grid_for(size_t V) {
 
 static size_t vol(Dims d) { return (size_t)d.nx * d.ny * d.nz; }
 
-cudaError_t launch_warp(Dims d, const float* I1, const float* u, float* I1w, cudaStream_t s) {
-  k_warp<<<grid_for(vol(d)), kGridThreads, 0, s>>>(d, I1, u, I1w);
-  return cudaGetLastError();
+cudaError_t launch_warp(Dims d, const float* I1, const float* u, float* I1w, unsigned* red_reset,
+                        cudaStream_t s) {
+  return launch_pdl(k_warp, dim3(grid_for(vol(d))), dim3(kGridThreads), 0, s, d, I1, u, I1w,
+                    red_reset);
 }
 
 cudaError_t launch_grad_residual(Dims d, const float* I1w, const float* I0, float* J, float* c,
                                  cudaStream_t s) {
-  k_grad_residual<<<grid_for(vol(d)), kGridThreads, 0, s>>>(d, I1w, I0, J, c);
-  return cudaGetLastError();
+  return launch_pdl(k_grad_residual, dim3(grid_for(vol(d))), dim3(kGridThreads), 0, s, d, I1w, I0,
+                    J, c);
 }
 
 cudaError_t launch_bound_reduce(Dims d, const float* w, unsigned* red, cudaStream_t s) {
-  k_bound_reduce<<<grid_for(vol(d)), kGridThreads, 0, s>>>(d, w, red);
-  return cudaGetLastError();
+  return launch_pdl(k_bound_reduce, dim3(grid_for(vol(d))), dim3(kGridThreads), 0, s, d, w, red);
 }
 
 cudaError_t launch_compose(Dims d, const float* w, const float* u_in, float* u_out,
                            const unsigned* red, float kappa, float delta, unsigned* status,
                            float* scale_out, cudaStream_t s) {
-  k_compose<<<grid_for(vol(d)), kGridThreads, 0, s>>>(d, w, u_in, u_out, red, kappa, delta, status,
-                                                       scale_out);
-  return cudaGetLastError();
+  return launch_pdl(k_compose, dim3(grid_for(vol(d))), dim3(kGridThreads), 0, s, d, w, u_in, u_out,
+                    (const unsigned*)red, kappa, delta, status, scale_out);
 }
 
 cudaError_t launch_jacobian(Dims d, const float* u, float* det, unsigned* count, cudaStream_t s) {
-  k_jacobian<<<grid_for(vol(d)), kGridThreads, 0, s>>>(d, u, det, count);
-  return cudaGetLastError();
+  return launch_pdl(k_jacobian, dim3(grid_for(vol(d))), dim3(kGridThreads), 0, s, d, u, det, count);
 }
 
 }  // namespace nadmm

@@ -256,12 +256,12 @@ cudaError_t enqueue_register(nadmm_context* h, const float* I0, const float* I1,
   float* u_cur = (dst_of(0) == u_out) ? ut : u_out;
   TRY(cudaMemsetAsync(red, 0, 4 * sizeof(unsigned), s));  // red[0..1], status red[2]
   TRY(cudaMemsetAsync(u_cur, 0, 3 * V * sizeof(float), s));
-  KLAUNCH(NADMM_KC_WARP, s, launch_warp(d, I1, u_cur, I1w, s));
+  KLAUNCH(NADMM_KC_WARP, s, launch_warp(d, I1, u_cur, I1w, nullptr, s));
   KLAUNCH(NADMM_KC_GRAD, s, launch_grad_residual(d, I1w, I0, J, c, s));
   for (int o = 0; o < O; ++o) {
     PlaneArgs first = plane_args(h);
     TRY(enqueue_inner(h, first, IN_NONE, false, 0, K, J, c, vbuf, nullptr, s));
-    TRY(cudaMemsetAsync(red, 0, 2 * sizeof(unsigned), s));
+    // red[0..1] are zero here: cleared at the start, then by each re-warp
     KLAUNCH(NADMM_KC_BOUND, s, launch_bound_reduce(d, vbuf, red, s));
     float* u_new = dst_of(o);
     KLAUNCH(NADMM_KC_COMPOSE, s,
@@ -269,7 +269,7 @@ cudaError_t enqueue_register(nadmm_context* h, const float* I0, const float* I1,
                            red + 2, nullptr, s));
     u_cur = u_new;
     if (o + 1 < O) {
-      KLAUNCH(NADMM_KC_WARP, s, launch_warp(d, I1, u_cur, I1w, s));
+      KLAUNCH(NADMM_KC_WARP, s, launch_warp(d, I1, u_cur, I1w, red, s));
       KLAUNCH(NADMM_KC_GRAD, s, launch_grad_residual(d, I1w, I0, J, c, s));
     }
   }
@@ -402,7 +402,7 @@ nadmm_status nadmm_create(const nadmm_config* cfg, nadmm_handle* out) {
   if (h->pencil_smem > 227 * 1024 || h->plane_smem > 227 * 1024) {
     delete h;
     return fail(NADMM_ERR_UNSUPPORTED_SIZE,
-                "a (ny x nz) spectrum plane exceeds the 227 KB of shared memory per CTA");
+                "a pass's shared-memory tile exceeds the 227 KB per CTA (nx too large)");
   }
   if (3 * (int)h->nkx * (h->R / 2) > kPlaneGatherCapacity) {
     delete h;
@@ -643,7 +643,7 @@ nadmm_status nadmm_linearise(nadmm_handle h, const float* fixed, const float* mo
   if (I1w_out && !aligned16(I1w_out)) return fail(NADMM_ERR_ALIGNMENT, "I1w_out not 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   float* I1w = I1w_out ? I1w_out : h->at<float>(h->o_I1w);
-  cudaError_t e = launch_warp(dims_of(h), moving, u, I1w, s);
+  cudaError_t e = launch_warp(dims_of(h), moving, u, I1w, nullptr, s);
   if (e == cudaSuccess) e = launch_grad_residual(dims_of(h), I1w, fixed, J, c, s);
   return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_linearise");
 }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "fft_device.cuh"
 
 namespace nadmm {
@@ -51,9 +53,9 @@ struct PlaneArgs {
   int data_term;           // 1 or 2
 };
 
-// Pencil pass: one CTA owns one (component, kx) plane of the half spectrum,
-// [nz][ny] contiguous: forward y- and z-DFTs, the inverse-symbol multiply of
-// Eq. 6, inverse z- and y-DFTs.
+// Pencil work on the half spectrum: forward y-DFTs (y-pass), z-DFT with the
+// inverse-symbol multiply of Eq. 6 and inverse z-DFT (z-pass), inverse
+// y-DFTs (y-pass).
 struct PencilArgs {
   float2* spec;            // [3][nkx][nz][ny] (in/out)
   const float2* twy;
@@ -63,10 +65,11 @@ struct PencilArgs {
   const float* Kz;         // [nz] 4 sin^2(pi kz / nz) by position
   unsigned* status;        // device status word (bit 1: a bounded wait expired) or null
   AxisPlan py, pz;
-  FastDiv ny_div, nz_div;  // line counts of the z- and y-transforms
-  FastDiv nkx_div;
+  FastDiv yrows_div, zcols_div, ztiles_div, nkx_div;
   int ny, nz, nkx;
-  int pitch;               // shared-memory row pitch (even so rows stay 16-byte aligned)
+  int yrows;               // (component, kx, z) rows per y-pass CTA (divides nz)
+  int ypitch;              // y-pass shared-memory row pitch (even: 16-byte aligned rows)
+  int zcols;               // y positions per z-pass CTA (divides ny, even)
   int order_n;
   float gamma;             // lambda / theta
   float scale;             // 1 / (nx ny nz)
@@ -91,10 +94,47 @@ size_t pencil_smem_bytes(const PencilArgs& a);
 int rows_per_tile(int ny);
 cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem);
 
+// ---------------------------------------------------------------- launch helpers
+// Programmatic dependent launch: every kernel is launched with programmatic
+// stream serialisation, waits on the previous kernel with pdl_wait() before
+// touching its outputs, and lets the next kernel start (pdl_trigger) only
+// after that wait -- so a kernel's prologue never overlaps the kernel that
+// produced its inputs, only the one after it.
+#if defined(__CUDACC__)
+__device__ __forceinline__ void pdl_wait() {
+#if defined(__CUDA_ARCH__)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void pdl_trigger() {
+#if defined(__CUDA_ARCH__)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+#endif
+
 // ---------------------------------------------------------------- grid ops
 struct Dims { int nx, ny, nz; };
 
-cudaError_t launch_warp(Dims d, const float* I1, const float* u, float* I1w, cudaStream_t s);
+// red_reset (or null): two words zeroed for the next bound reduction
+cudaError_t launch_warp(Dims d, const float* I1, const float* u, float* I1w, unsigned* red_reset,
+                        cudaStream_t s);
 cudaError_t launch_grad_residual(Dims d, const float* I1w, const float* I0, float* J, float* c,
                                  cudaStream_t s);
 // red[0] = bits of max |w|_inf, red[1] = bits of max ||Dw||_inf (must start at 0)

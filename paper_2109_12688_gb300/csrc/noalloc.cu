@@ -203,7 +203,7 @@ extern "C" nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int
   finish_pencil_args(pa);
   if (plane_smem_max(a) > 227 * 1024 || pencil_smem_bytes(pa) > 227 * 1024)
     return fail(NADMM_ERR_UNSUPPORTED_SIZE,
-                "a (ny x nz) spectrum plane exceeds the 227 KB of shared memory per CTA");
+                "a pass's shared-memory tile exceeds the 227 KB per CTA (nx too large)");
   if (3 * a.nkx * (a.R / 2) > kPlaneGatherCapacity)
     return fail(NADMM_ERR_UNSUPPORTED_SIZE, "nx too large for the plane pass gather");
   const StaticLayout L = layout_for(nx, ny, nz, px, py, pz);

@@ -45,7 +45,7 @@ def test_config_defaults(lib):
 
 
 @pytest.mark.parametrize("dims", [(128, 128, 96), (32, 32, 24), (160, 160, 112), (96, 96, 64),
-                                  (20, 12, 14), (4, 4, 4), (12, 6, 7)])
+                                  (20, 12, 14), (4, 4, 4), (12, 6, 7), (256, 256, 192)])
 def test_create_and_workspace_size(lib, dims):
     h = lib.nadmm_create(lib.make_config(dims))
     nx, ny, nz = dims
@@ -59,7 +59,7 @@ def test_create_and_workspace_size(lib, dims):
 
 @pytest.mark.parametrize("dims,why", [((3, 8, 8), "dimension"), ((10, 8, 8), "multiple of 4"),
                                       ((8, 7, 8), "even"), ((44, 8, 8), "factor"),
-                                      ((8, 8, 13), "factor"), ((256, 256, 192), "shared")])
+                                      ((8, 8, 13), "factor"), ((512, 64, 64), "shared")])
 def test_unsupported_sizes_are_rejected(lib, dims, why):
     with pytest.raises(lib.NadmmError) as e:
         lib.nadmm_create(lib.make_config(dims))
