@@ -331,22 +331,26 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int nlines = 3 * (a.R / 2);
 
-  // Prologue independent of the previous kernel (which writes only the
-  // spectrum): the real-space tiles were written two or more kernels back.
+  // Within an ADMM loop the k >= 1 passes (IN_SPEC) read tiles written by the
+  // plane pass four kernels back, while the kernel just before them writes
+  // only the spectrum: their bulk loads are issued before waiting on it.
+  // Every other variant reads data of the immediately preceding kernel (the
+  // gradient kernel, or the caller's own work), so it loads after the wait.
+  constexpr bool kEarlyLoads = (IN == IN_SPEC);
+  const uint32_t tile_bytes = (uint32_t)(a.R * a.nx * sizeof(float));
+  const size_t tile_off = ((size_t)z * a.ny + y0) * a.nx;
   if (F.n > 0) {
     if (tid == 0) {
       mbar_init(bar, 1);
       fence_barrier_init();
     }
     __syncthreads();
-    if (tid < 32) {
-      const uint32_t tile_bytes = (uint32_t)(a.R * a.nx * sizeof(float));
+    if (kEarlyLoads && tid < 32) {
       if (tid == 0) mbar_expect_tx(bar, tile_bytes * F.n);
       __syncwarp();
-      const size_t off = ((size_t)z * a.ny + y0) * a.nx;
       for (int s = tid; s < F.n; s += 32)
-        bulk_load(fld + (size_t)s * a.R * a.nx, field_src<IN, PREV, STEP>(a, s) + off, tile_bytes,
-                  bar);
+        bulk_load(fld + (size_t)s * a.R * a.nx, field_src<IN, PREV, STEP>(a, s) + tile_off,
+                  tile_bytes, bar);
     }
   }
   for (int i = tid; i < a.px.tw_count; i += nthr) tw[i] = a.twx[i];
@@ -354,6 +358,13 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
   __syncthreads();
   pdl_wait();
   pdl_trigger();
+  if (F.n > 0 && !kEarlyLoads && tid < 32) {
+    if (tid == 0) mbar_expect_tx(bar, tile_bytes * F.n);
+    __syncwarp();
+    for (int s = tid; s < F.n; s += 32)
+      bulk_load(fld + (size_t)s * a.R * a.nx, field_src<IN, PREV, STEP>(a, s) + tile_off,
+                tile_bytes, bar);
+  }
   if (IN == IN_SPEC) {
     plane_gather(a, lines, pos, z, y0, tid, nthr);
     __syncthreads();
