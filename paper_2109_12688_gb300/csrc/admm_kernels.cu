@@ -84,6 +84,23 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t 
                "r"(smem_addr(src)), "r"(bytes)
                : "memory");
 }
+// 2D tiled TMA load of box {x, y} of `map` into shared memory (128-byte aligned)
+__device__ __forceinline__ void tensor_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                               uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+// 2D tiled TMA store of a shared-memory box to {x, y} of `map`
+__device__ __forceinline__ void tensor_store_2d(const CUtensorMap* map, int x, int y,
+                                                const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(smem_addr(src))
+               : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read() {
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
@@ -129,7 +146,7 @@ NADMM_HD constexpr FieldMap field_map() {
   return f;
 }
 
-constexpr int kGatherItems = 8;   // spectrum values per thread held in flight
+constexpr int kGatherItems = 4;   // spectrum values per thread held in flight per round
 constexpr int kPlaneThreads = 256;
 constexpr int kPencilThreads = 384;
 
@@ -142,35 +159,37 @@ NADMM_HD void plane_gather(const PlaneArgs& a, float2* lines, const int* pos, in
                            int tid, int nthr) {
   const int h = a.R / 2;
   const int total = 3 * a.nkx * h;
-  float2 A[kGatherItems], B[kGatherItems];
+  for (int base = 0; base < total; base += kGatherItems * nthr) {
+    float2 A[kGatherItems], B[kGatherItems];
 #pragma unroll
-  for (int it = 0; it < kGatherItems; ++it) {
-    const int g = tid + it * nthr;
-    if (g < total) {
-      const int rest = (int)fdiv((uint32_t)g, a.half_div);
-      const int r = g - rest * h;
-      const int comp = (int)fdiv((uint32_t)rest, a.nkx_div);
-      const int kx = rest - comp * a.nkx;
-      const float2* src = a.spec + ((size_t)(comp * a.nkx + kx) * a.nz + z) * a.ny + y0 + r;
-      A[it] = src[0];
-      B[it] = src[h];
+    for (int it = 0; it < kGatherItems; ++it) {
+      const int g = base + tid + it * nthr;
+      if (g < total) {
+        const int rest = (int)fdiv((uint32_t)g, a.half_div);
+        const int r = g - rest * h;
+        const int comp = (int)fdiv((uint32_t)rest, a.nkx_div);
+        const int kx = rest - comp * a.nkx;
+        const float2* src = a.spec + ((size_t)(comp * a.nkx + kx) * a.nz + z) * a.ny + y0 + r;
+        A[it] = src[0];
+        B[it] = src[h];
+      }
     }
-  }
 #pragma unroll
-  for (int it = 0; it < kGatherItems; ++it) {
-    const int g = tid + it * nthr;
-    if (g < total) {
-      const int rest = (int)fdiv((uint32_t)g, a.half_div);
-      const int r = g - rest * h;
-      const int comp = (int)fdiv((uint32_t)rest, a.nkx_div);
-      const int kx = rest - comp * a.nkx;
-      float2* line = lines + (comp * h + r) * a.pitch;
-      const float2 Av = A[it], Bv = B[it];
-      if (kx == 0 || 2 * kx == a.nx) {
-        line[pos[kx]] = make_float2(Av.x, Bv.x);
-      } else {
-        line[pos[kx]] = make_float2(Av.x - Bv.y, Av.y + Bv.x);
-        line[pos[a.nx - kx]] = make_float2(Av.x + Bv.y, Bv.x - Av.y);
+    for (int it = 0; it < kGatherItems; ++it) {
+      const int g = base + tid + it * nthr;
+      if (g < total) {
+        const int rest = (int)fdiv((uint32_t)g, a.half_div);
+        const int r = g - rest * h;
+        const int comp = (int)fdiv((uint32_t)rest, a.nkx_div);
+        const int kx = rest - comp * a.nkx;
+        float2* line = lines + (comp * h + r) * a.pitch;
+        const float2 Av = A[it], Bv = B[it];
+        if (kx == 0 || 2 * kx == a.nx) {
+          line[pos[kx]] = make_float2(Av.x, Bv.x);
+        } else {
+          line[pos[kx]] = make_float2(Av.x - Bv.y, Av.y + Bv.x);
+          line[pos[a.nx - kx]] = make_float2(Av.x + Bv.y, Bv.x - Av.y);
+        }
       }
     }
   }
@@ -414,7 +433,11 @@ struct PencilFilter {
     const float K = kx_term + Ky[line] + Kz[zpos];
     float Kn = K;
     for (int i = 1; i < order; ++i) Kn *= K;
+#if defined(__CUDA_ARCH__)
+    return __fdividef(scale, 1.0f + gamma * Kn);
+#else
     return scale / (1.0f + gamma * Kn);
+#endif
   }
 };
 
@@ -426,7 +449,7 @@ NADMM_HD size_t ypass_smem(const PencilArgs& a) {
 }
 
 NADMM_HD size_t zpass_smem(const PencilArgs& a) {
-  return 16 + (size_t)a.nz * a.zcols * sizeof(float2) + (size_t)a.pz.tw_count * sizeof(float2) +
+  return 16 + 128 + (size_t)a.nz * a.zcols * sizeof(float2) + (size_t)a.pz.tw_count * sizeof(float2) +
          (size_t)(a.nz + a.zcols) * sizeof(float) + 16;
 }
 
@@ -518,11 +541,14 @@ __global__ void __launch_bounds__(kYThreads) k_ypass(PencilArgs a) {
 #endif
 }
 
-__global__ void __launch_bounds__(kZThreads) k_zpass(PencilArgs a) {
+__global__ void __launch_bounds__(kZThreads) k_zpass(const __grid_constant__ PencilArgs a) {
 #if defined(__CUDA_ARCH__)
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  float2* tile = reinterpret_cast<float2*>(smem + 16);
+  // TMA box destination: round up to 128 bytes (the layout reserves the slack)
+  unsigned char* tile_p = smem + 16;
+  tile_p += (128u - (smem_addr(tile_p) & 127u)) & 127u;
+  float2* tile = reinterpret_cast<float2*>(tile_p);
   float2* tw = tile + (size_t)a.nz * a.zcols;
   float* Kz = reinterpret_cast<float*>(tw + a.pz.tw_count);
   float* Ky = Kz + a.nz;
@@ -531,8 +557,7 @@ __global__ void __launch_bounds__(kZThreads) k_zpass(PencilArgs a) {
   const int plane = (int)fdiv(blockIdx.x, a.ztiles_div);
   const int y0 = (blockIdx.x - plane * tiles) * a.zcols;
   const int kx = plane - (int)fdiv((uint32_t)plane, a.nkx_div) * a.nkx;
-  float2* g = a.spec + (size_t)plane * a.ny * a.nz + y0;
-  const uint32_t seg_bytes = (uint32_t)(a.zcols * sizeof(float2));
+  const int row0 = plane * a.nz;  // first row of this plane in the 2D view
   for (int i = tid; i < a.pz.tw_count; i += nthr) tw[i] = a.twz[i];
   for (int i = tid; i < a.nz; i += nthr) Kz[i] = a.Kz[i];
   for (int i = tid; i < a.zcols; i += nthr) Ky[i] = a.Ky[y0 + i];
@@ -542,11 +567,9 @@ __global__ void __launch_bounds__(kZThreads) k_zpass(PencilArgs a) {
   }
   __syncthreads();
   pdl_wait();
-  if (tid < 32) {
-    if (tid == 0) mbar_expect_tx(bar, seg_bytes * a.nz);
-    __syncwarp();
-    for (int zz = tid; zz < a.nz; zz += 32)
-      bulk_load(tile + (size_t)zz * a.zcols, g + (size_t)zz * a.ny, seg_bytes, bar);
+  if (tid == 0) {
+    mbar_expect_tx(bar, (uint32_t)(a.nz * a.zcols * sizeof(float2)));
+    tensor_load_2d(tile, &a.zmap, y0, row0, bar);
   }
   pdl_trigger();
   const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0));
@@ -561,9 +584,8 @@ __global__ void __launch_bounds__(kZThreads) k_zpass(PencilArgs a) {
   zpass_transform(a, tile, tw, filt, tid, nthr, true);
   fence_proxy_async();
   __syncthreads();
-  if (tid < 32) {
-    for (int zz = tid; zz < a.nz; zz += 32)
-      bulk_store(g + (size_t)zz * a.ny, tile + (size_t)zz * a.zcols, seg_bytes);
+  if (tid == 0) {
+    tensor_store_2d(&a.zmap, y0, row0, tile);
     bulk_commit();
     bulk_wait_read();
   }
@@ -592,6 +614,32 @@ void finish_pencil_args(PencilArgs& a) {
   a.zcols_div = make_fastdiv((uint32_t)a.zcols);
   a.ztiles_div = make_fastdiv((uint32_t)(a.ny / a.zcols));
   a.nkx_div = make_fastdiv((uint32_t)a.nkx);
+}
+
+cudaError_t encode_pencil_map(PencilArgs& a) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (encode == nullptr) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorSymbolNotFound;
+    encode = reinterpret_cast<EncodeFn>(fn);
+  }
+  // complex64 values as 8-byte elements: dims {ny, 3 nkx nz}, row stride ny * 8 bytes
+  const cuuint64_t dims[2] = {(cuuint64_t)a.ny, (cuuint64_t)3 * a.nkx * a.nz};
+  const cuuint64_t strides[1] = {(cuuint64_t)a.ny * sizeof(float2)};
+  const cuuint32_t box[2] = {(cuuint32_t)a.zcols, (cuuint32_t)a.nz};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(&a.zmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, a.spec, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 static int field_count(int in_mode, bool prev, bool step) {

@@ -50,6 +50,7 @@ struct nadmm_context {
   char* ws = nullptr;
   size_t ws_bytes = 0;
   bool kernels_configured = false;
+  CUtensorMap zmap;  // z-pass tensor map of the workspace spectrum
   // graph cache
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[3] = {nullptr, nullptr, nullptr};
@@ -165,6 +166,7 @@ PencilArgs pencil_args(const nadmm_context* h) {
   a.gamma = h->cfg.lambda / h->cfg.theta;
   a.scale = (float)(1.0 / ((double)h->cfg.nx * h->cfg.ny * h->cfg.nz));
   finish_pencil_args(a);
+  a.zmap = h->zmap;
   return a;
 }
 
@@ -404,9 +406,9 @@ nadmm_status nadmm_create(const nadmm_config* cfg, nadmm_handle* out) {
     return fail(NADMM_ERR_UNSUPPORTED_SIZE,
                 "a pass's shared-memory tile exceeds the 227 KB per CTA (nx too large)");
   }
-  if (3 * (int)h->nkx * (h->R / 2) > kPlaneGatherCapacity) {
+  if (cfg->nz > 256) {
     delete h;
-    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "nx too large for the plane pass gather");
+    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "nz must be <= 256 (one TMA box spans the z axis)");
   }
   h->twx = axis_twiddles(h->px);
   h->twy = axis_twiddles(h->py);
@@ -499,6 +501,13 @@ nadmm_status nadmm_set_workspace(nadmm_handle h, void* dev_ptr, size_t bytes) {
     h->ws = nullptr;
     return cuda_fail(e, "cudaMemset");
   }
+  PencilArgs pa = pencil_args(h);
+  e = encode_pencil_map(pa);
+  if (e != cudaSuccess) {
+    h->ws = nullptr;
+    return cuda_fail(e, "cuTensorMapEncodeTiled");
+  }
+  h->zmap = pa.zmap;
   return NADMM_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal interfaces between the host orchestration (nadmm.cu) and the
 // kernel translation units.  Not part of the public ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,6 +58,7 @@ struct PlaneArgs {
 // inverse-symbol multiply of Eq. 6 and inverse z-DFT (z-pass), inverse
 // y-DFTs (y-pass).
 struct PencilArgs {
+  CUtensorMap zmap;        // 2D view [3 nkx nz rows][ny] of the spectrum, box [nz][zcols]
   float2* spec;            // [3][nkx][nz][ny] (in/out)
   const float2* twy;
   const float2* twz;
@@ -75,15 +77,14 @@ struct PencilArgs {
   float scale;             // 1 / (nx ny nz)
 };
 
-// the plane pass holds at most this many spectrum values of its tile in flight
-constexpr int kPlaneGatherCapacity = 8 * 256;
-
 constexpr unsigned kStatusNonfinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;
 
 // Fill the FastDiv fields and pitches of the pass arguments from the sizes.
 void finish_plane_args(PlaneArgs& a);
 void finish_pencil_args(PencilArgs& a);
+// Encode a.zmap for a.spec (host only; needs finish_pencil_args first).
+cudaError_t encode_pencil_map(PencilArgs& a);
 
 // mode = InMode * 4 + prev * 2 + step
 cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, cudaStream_t s);

@@ -204,8 +204,7 @@ extern "C" nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int
   if (plane_smem_max(a) > 227 * 1024 || pencil_smem_bytes(pa) > 227 * 1024)
     return fail(NADMM_ERR_UNSUPPORTED_SIZE,
                 "a pass's shared-memory tile exceeds the 227 KB per CTA (nx too large)");
-  if (3 * a.nkx * (a.R / 2) > kPlaneGatherCapacity)
-    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "nx too large for the plane pass gather");
+  if (nz > 256) return fail(NADMM_ERR_UNSUPPORTED_SIZE, "nz must be <= 256");
   const StaticLayout L = layout_for(nx, ny, nz, px, py, pz);
   if (L.total > kStaticScratchBytes)
     return fail(NADMM_ERR_UNSUPPORTED_SIZE,
@@ -254,7 +253,8 @@ extern "C" nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int
     pa.Kx = Kx;
     pa.Ky = Ky;
     pa.Kz = Kz;
-    e = launch_pencil(pa, s);
+    e = encode_pencil_map(pa);
+    if (e == cudaSuccess) e = launch_pencil(pa, s);
   }
   if (e == cudaSuccess) {
     PlaneArgs fin = a;

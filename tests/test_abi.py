@@ -59,7 +59,8 @@ def test_create_and_workspace_size(lib, dims):
 
 @pytest.mark.parametrize("dims,why", [((3, 8, 8), "dimension"), ((10, 8, 8), "multiple of 4"),
                                       ((8, 7, 8), "even"), ((44, 8, 8), "factor"),
-                                      ((8, 8, 13), "factor"), ((512, 64, 64), "shared")])
+                                      ((8, 8, 13), "factor"), ((512, 64, 64), "shared"),
+                                      ((64, 64, 320), "nz must be")])
 def test_unsupported_sizes_are_rejected(lib, dims, why):
     with pytest.raises(lib.NadmmError) as e:
         lib.nadmm_create(lib.make_config(dims))
