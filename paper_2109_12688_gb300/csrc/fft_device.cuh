@@ -56,6 +56,25 @@ inline FastDiv make_fastdiv(uint32_t d) {
   return f;
 }
 
+#if defined(__CUDACC__)
+// Device-side construction (slow path for ragged tails only).
+__device__ __forceinline__ FastDiv make_fastdiv_dev(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  if (d <= 1) {
+    f.mul = 0;
+    f.shift = 0;
+    return f;
+  }
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  const unsigned long long p2 = 1ull << (31 + l);
+  f.mul = (uint32_t)((p2 + d - 1) / d);
+  f.shift = l - 1;
+  return f;
+}
+#endif
+
 NADMM_HD uint32_t fdiv(uint32_t n, const FastDiv& f) {
   if (f.d <= 1) return n;
 #if defined(__CUDA_ARCH__)

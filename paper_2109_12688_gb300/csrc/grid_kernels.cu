@@ -11,8 +11,6 @@
 
 namespace nadmm {
 
-constexpr int kGridThreads = 256;
-
 // (1 - t) a + t b, exact at t = 0 and t = 1 (a sample on a grid point, or
 // clamped to the last one, returns the grid value itself)
 __device__ __forceinline__ float lerp(float a, float b, float t) {
@@ -43,80 +41,80 @@ __device__ __forceinline__ float trilerp(const float* __restrict__ f, Dims d, fl
   return lerp(c0, c1, fz);
 }
 
-__device__ __forceinline__ void vox_coords(size_t i, Dims d, int& x, int& y, int& z) {
-  x = (int)(i % d.nx);
-  size_t r = i / d.nx;
-  y = (int)(r % d.ny);
-  z = (int)(r / d.ny);
-}
+// Block (32, 8) covers 32 x-consecutive voxels of 8 rows; grid (nx/32, ny/8,
+// z-slices).  Coordinates come from the block indices (no division).
+constexpr int kBX = 32, kBY = 8;
 
 // I1w(x) = I1(x + u(x)).  Also clears the bound reduction words of the next
 // outer step (the compose that read them has completed).
-__global__ void __launch_bounds__(kGridThreads) k_warp(Dims d, const float* __restrict__ I1,
-                                                       const float* __restrict__ u,
-                                                       float* __restrict__ I1w, unsigned* red) {
+__global__ void __launch_bounds__(kBX * kBY) k_warp(Dims d, const float* __restrict__ I1,
+                                                    const float* __restrict__ u,
+                                                    float* __restrict__ I1w, unsigned* red) {
   const size_t V = (size_t)d.nx * d.ny * d.nz;
   pdl_wait();
   pdl_trigger();
-  if (red != nullptr && blockIdx.x == 0 && threadIdx.x < 2) red[threadIdx.x] = 0u;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
-       i += (size_t)gridDim.x * blockDim.x) {
-    int x, y, z;
-    vox_coords(i, d, x, y, z);
-    I1w[i] = trilerp(I1, d, (float)x + u[i], (float)y + u[V + i], (float)z + u[2 * V + i]);
-  }
+  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
+  const int z = blockIdx.z;
+  if (red != nullptr && (blockIdx.x | blockIdx.y | blockIdx.z) == 0 && threadIdx.y == 0 &&
+      threadIdx.x < 2)
+    red[threadIdx.x] = 0u;
+  if (x >= d.nx || y >= d.ny) return;
+  const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
+  I1w[i] = trilerp(I1, d, (float)x + u[i], (float)y + u[V + i], (float)z + u[2 * V + i]);
 }
 
 // J = grad I1w (clamped central differences), c = I1w - I0
-__global__ void __launch_bounds__(kGridThreads) k_grad_residual(Dims d,
-                                                                const float* __restrict__ I1w,
-                                                                const float* __restrict__ I0,
-                                                                float* __restrict__ J,
-                                                                float* __restrict__ c) {
+__global__ void __launch_bounds__(kBX * kBY) k_grad_residual(Dims d,
+                                                             const float* __restrict__ I1w,
+                                                             const float* __restrict__ I0,
+                                                             float* __restrict__ J,
+                                                             float* __restrict__ c) {
   pdl_wait();
   pdl_trigger();
   const size_t V = (size_t)d.nx * d.ny * d.nz;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
-       i += (size_t)gridDim.x * blockDim.x) {
-    int x, y, z;
-    vox_coords(i, d, x, y, z);
-    size_t xp = i + (x + 1 < d.nx ? 1 : 0), xm = i - (x > 0 ? 1 : 0);
-    size_t yp = i + (y + 1 < d.ny ? sy : 0), ym = i - (y > 0 ? sy : 0);
-    size_t zp = i + (z + 1 < d.nz ? sz : 0), zm = i - (z > 0 ? sz : 0);
-    J[i] = 0.5f * (__ldg(I1w + xp) - __ldg(I1w + xm));
-    J[V + i] = 0.5f * (__ldg(I1w + yp) - __ldg(I1w + ym));
-    J[2 * V + i] = 0.5f * (__ldg(I1w + zp) - __ldg(I1w + zm));
-    c[i] = __ldg(I1w + i) - __ldg(I0 + i);
-  }
+  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= d.nx || y >= d.ny) return;
+  const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
+  const size_t xp = i + (x + 1 < d.nx ? 1 : 0), xm = i - (x > 0 ? 1 : 0);
+  const size_t yp = i + (y + 1 < d.ny ? sy : 0), ym = i - (y > 0 ? sy : 0);
+  const size_t zp = i + (z + 1 < d.nz ? sz : 0), zm = i - (z > 0 ? sz : 0);
+  J[i] = 0.5f * (__ldg(I1w + xp) - __ldg(I1w + xm));
+  J[V + i] = 0.5f * (__ldg(I1w + yp) - __ldg(I1w + ym));
+  J[2 * V + i] = 0.5f * (__ldg(I1w + zp) - __ldg(I1w + zm));
+  c[i] = __ldg(I1w + i) - __ldg(I0 + i);
 }
 
 // Per-voxel |w|_inf and ||D w||_inf (max absolute row sum of the Jacobian);
 // grid-wide max through atomicMax on the float bit patterns (non-negative
-// floats order like their bits; NaN bits sort above +inf).
-__global__ void __launch_bounds__(kGridThreads) k_bound_reduce(Dims d, const float* __restrict__ w,
-                                                               unsigned* red) {
+// floats order like their bits; NaN bits sort above +inf).  Each block
+// loops over the z-slices blockIdx.z, blockIdx.z + gridDim.z, ...
+__global__ void __launch_bounds__(kBX * kBY) k_bound_reduce(Dims d, const float* __restrict__ w,
+                                                            unsigned* red) {
   pdl_wait();
   pdl_trigger();
   const size_t V = (size_t)d.nx * d.ny * d.nz;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
+  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
   float mabs = 0.0f, mjac = 0.0f;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
-       i += (size_t)gridDim.x * blockDim.x) {
-    int x, y, z;
-    vox_coords(i, d, x, y, z);
-    size_t xp = i + (x + 1 < d.nx ? 1 : 0), xm = i - (x > 0 ? 1 : 0);
-    size_t yp = i + (y + 1 < d.ny ? sy : 0), ym = i - (y > 0 ? sy : 0);
-    size_t zp = i + (z + 1 < d.nz ? sz : 0), zm = i - (z > 0 ? sz : 0);
-    for (int comp = 0; comp < 3; ++comp) {
-      const float* f = w + comp * V;
-      float a = fabsf(__ldg(f + i));
-      float row = fabsf(0.5f * (__ldg(f + xp) - __ldg(f + xm))) +
-                  fabsf(0.5f * (__ldg(f + yp) - __ldg(f + ym))) +
-                  fabsf(0.5f * (__ldg(f + zp) - __ldg(f + zm)));
-      // fmaxf drops NaN; keep it visible through the bit-pattern max instead
-      mabs = (a != a || a > mabs) ? a : mabs;
-      mjac = (row != row || row > mjac) ? row : mjac;
+  if (x < d.nx && y < d.ny) {
+    for (int z = blockIdx.z; z < d.nz; z += gridDim.z) {
+      const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
+      const size_t xp = i + (x + 1 < d.nx ? 1 : 0), xm = i - (x > 0 ? 1 : 0);
+      const size_t yp = i + (y + 1 < d.ny ? sy : 0), ym = i - (y > 0 ? sy : 0);
+      const size_t zp = i + (z + 1 < d.nz ? sz : 0), zm = i - (z > 0 ? sz : 0);
+#pragma unroll
+      for (int comp = 0; comp < 3; ++comp) {
+        const float* f = w + comp * V;
+        const float a = fabsf(__ldg(f + i));
+        const float row = fabsf(0.5f * (__ldg(f + xp) - __ldg(f + xm))) +
+                          fabsf(0.5f * (__ldg(f + yp) - __ldg(f + ym))) +
+                          fabsf(0.5f * (__ldg(f + zp) - __ldg(f + zm)));
+        // fmaxf drops NaN; keep it visible through the bit-pattern max instead
+        mabs = (a != a || a > mabs) ? a : mabs;
+        mjac = (row != row || row > mjac) ? row : mjac;
+      }
     }
   }
   unsigned ua = __float_as_uint(mabs), uj = __float_as_uint(mjac);
@@ -124,12 +122,17 @@ __global__ void __launch_bounds__(kGridThreads) k_bound_reduce(Dims d, const flo
     ua = max(ua, __shfl_xor_sync(0xffffffffu, ua, off));
     uj = max(uj, __shfl_xor_sync(0xffffffffu, uj, off));
   }
-  __shared__ unsigned sa[kGridThreads / 32], sj[kGridThreads / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) { sa[wid] = ua; sj[wid] = uj; }
-  __syncthreads();
+  __shared__ unsigned sa[kBY], sj[kBY];
   if (threadIdx.x == 0) {
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) { ua = max(ua, sa[k]); uj = max(uj, sj[k]); }
+    sa[threadIdx.y] = ua;
+    sj[threadIdx.y] = uj;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    for (int k = 1; k < kBY; ++k) {
+      ua = max(ua, sa[k]);
+      uj = max(uj, sj[k]);
+    }
     atomicMax(red, ua);
     atomicMax(red + 1, uj);
   }
@@ -150,47 +153,47 @@ __device__ __forceinline__ float bound_factor(const unsigned* red, float kappa, 
 }
 
 // u_out(x) = v(x) + u_in(x + v(x)), v = s w
-__global__ void __launch_bounds__(kGridThreads) k_compose(Dims d, const float* __restrict__ w,
-                                                          const float* __restrict__ u_in,
-                                                          float* __restrict__ u_out,
-                                                          const unsigned* red, float kappa,
-                                                          float delta, unsigned* status,
-                                                          float* scale_out) {
+__global__ void __launch_bounds__(kBX * kBY) k_compose(Dims d, const float* __restrict__ w,
+                                                       const float* __restrict__ u_in,
+                                                       float* __restrict__ u_out,
+                                                       const unsigned* red, float kappa,
+                                                       float delta, unsigned* status,
+                                                       float* scale_out) {
   pdl_wait();
   pdl_trigger();
   const size_t V = (size_t)d.nx * d.ny * d.nz;
-  const float s = bound_factor(red, kappa, delta,
-                               (blockIdx.x == 0 && threadIdx.x == 0) ? status : nullptr);
-  if (scale_out != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *scale_out = s;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
-       i += (size_t)gridDim.x * blockDim.x) {
-    int x, y, z;
-    vox_coords(i, d, x, y, z);
-    float vx = s * w[i], vy = s * w[V + i], vz = s * w[2 * V + i];
-    float px = (float)x + vx, py = (float)y + vy, pz = (float)z + vz;
-    u_out[i] = vx + trilerp(u_in, d, px, py, pz);
-    u_out[V + i] = vy + trilerp(u_in + V, d, px, py, pz);
-    u_out[2 * V + i] = vz + trilerp(u_in + 2 * V, d, px, py, pz);
-  }
+  const bool first = (blockIdx.x | blockIdx.y | blockIdx.z) == 0 && threadIdx.x == 0 &&
+                     threadIdx.y == 0;
+  const float s = bound_factor(red, kappa, delta, first ? status : nullptr);
+  if (scale_out != nullptr && first) *scale_out = s;
+  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= d.nx || y >= d.ny) return;
+  const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
+  const float vx = s * w[i], vy = s * w[V + i], vz = s * w[2 * V + i];
+  const float px = (float)x + vx, py = (float)y + vy, pz = (float)z + vz;
+  u_out[i] = vx + trilerp(u_in, d, px, py, pz);
+  u_out[V + i] = vy + trilerp(u_in + V, d, px, py, pz);
+  u_out[2 * V + i] = vz + trilerp(u_in + 2 * V, d, px, py, pz);
 }
 
 // det(I + D u) per voxel, count of det <= 0
-__global__ void __launch_bounds__(kGridThreads) k_jacobian(Dims d, const float* __restrict__ u,
-                                                           float* __restrict__ det,
-                                                           unsigned* count) {
+__global__ void __launch_bounds__(kBX * kBY) k_jacobian(Dims d, const float* __restrict__ u,
+                                                        float* __restrict__ det, unsigned* count) {
   pdl_wait();
   pdl_trigger();
   const size_t V = (size_t)d.nx * d.ny * d.nz;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
+  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
+  const int z = blockIdx.z;
   unsigned local = 0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
-       i += (size_t)gridDim.x * blockDim.x) {
-    int x, y, z;
-    vox_coords(i, d, x, y, z);
-    size_t xp = i + (x + 1 < d.nx ? 1 : 0), xm = i - (x > 0 ? 1 : 0);
-    size_t yp = i + (y + 1 < d.ny ? sy : 0), ym = i - (y > 0 ? sy : 0);
-    size_t zp = i + (z + 1 < d.nz ? sz : 0), zm = i - (z > 0 ? sz : 0);
+  if (x < d.nx && y < d.ny) {
+    const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
+    const size_t xp = i + (x + 1 < d.nx ? 1 : 0), xm = i - (x > 0 ? 1 : 0);
+    const size_t yp = i + (y + 1 < d.ny ? sy : 0), ym = i - (y > 0 ? sy : 0);
+    const size_t zp = i + (z + 1 < d.nz ? sz : 0), zm = i - (z > 0 ? sz : 0);
     float A[3][3];
+#pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
       const float* f = u + comp * V;
       A[comp][0] = 0.5f * (__ldg(f + xp) - __ldg(f + xm));
@@ -198,51 +201,48 @@ __global__ void __launch_bounds__(kGridThreads) k_jacobian(Dims d, const float* 
       A[comp][2] = 0.5f * (__ldg(f + zp) - __ldg(f + zm));
       A[comp][comp] += 1.0f;
     }
-    float dt = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
-               A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
-               A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    const float dt = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                     A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                     A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
     if (det != nullptr) det[i] = dt;
-    if (!(dt > 0.0f)) ++local;
+    if (!(dt > 0.0f)) local = 1;
   }
   if (count != nullptr) {
     for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
-    if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+    if (threadIdx.x == 0 && local) atomicAdd(count, local);
   }
 }
 
-static unsigned grid_for(size_t V) {
-  size_t b = (V + kGridThreads - 1) / kGridThreads;
-  const size_t cap = 152 * 16;  // grid-stride beyond 16 CTAs per SM
-  return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
+static dim3 grid3(Dims d, int zslices) {
+  return dim3((unsigned)((d.nx + kBX - 1) / kBX), (unsigned)((d.ny + kBY - 1) / kBY),
+              (unsigned)zslices);
 }
-
-static size_t vol(Dims d) { return (size_t)d.nx * d.ny * d.nz; }
+static const dim3 kBlock(kBX, kBY);
 
 cudaError_t launch_warp(Dims d, const float* I1, const float* u, float* I1w, unsigned* red_reset,
                         cudaStream_t s) {
-  return launch_pdl(k_warp, dim3(grid_for(vol(d))), dim3(kGridThreads), 0, s, d, I1, u, I1w,
-                    red_reset);
+  return launch_pdl(k_warp, grid3(d, d.nz), kBlock, 0, s, d, I1, u, I1w, red_reset);
 }
 
 cudaError_t launch_grad_residual(Dims d, const float* I1w, const float* I0, float* J, float* c,
                                  cudaStream_t s) {
-  return launch_pdl(k_grad_residual, dim3(grid_for(vol(d))), dim3(kGridThreads), 0, s, d, I1w, I0,
-                    J, c);
+  return launch_pdl(k_grad_residual, grid3(d, d.nz), kBlock, 0, s, d, I1w, I0, J, c);
 }
 
 cudaError_t launch_bound_reduce(Dims d, const float* w, unsigned* red, cudaStream_t s) {
-  return launch_pdl(k_bound_reduce, dim3(grid_for(vol(d))), dim3(kGridThreads), 0, s, d, w, red);
+  // a few z-slices per block keep the number of atomics small
+  return launch_pdl(k_bound_reduce, grid3(d, d.nz < 8 ? d.nz : 8), kBlock, 0, s, d, w, red);
 }
 
 cudaError_t launch_compose(Dims d, const float* w, const float* u_in, float* u_out,
                            const unsigned* red, float kappa, float delta, unsigned* status,
                            float* scale_out, cudaStream_t s) {
-  return launch_pdl(k_compose, dim3(grid_for(vol(d))), dim3(kGridThreads), 0, s, d, w, u_in, u_out,
+  return launch_pdl(k_compose, grid3(d, d.nz), kBlock, 0, s, d, w, u_in, u_out,
                     (const unsigned*)red, kappa, delta, status, scale_out);
 }
 
 cudaError_t launch_jacobian(Dims d, const float* u, float* det, unsigned* count, cudaStream_t s) {
-  return launch_pdl(k_jacobian, dim3(grid_for(vol(d))), dim3(kGridThreads), 0, s, d, u, det, count);
+  return launch_pdl(k_jacobian, grid3(d, d.nz), kBlock, 0, s, d, u, det, count);
 }
 
 }  // namespace nadmm
