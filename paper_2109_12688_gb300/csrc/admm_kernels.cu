@@ -148,6 +148,7 @@ NADMM_HD constexpr FieldMap field_map() {
 
 constexpr int kGatherItems = 4;   // spectrum values per thread held in flight per round
 constexpr int kPlaneThreads = 256;
+constexpr int kPencilThreads = 384;
 
 // Lines: line l = comp * (R/2) + r holds rows (y0 + r) [real part] and
 // (y0 + r + R/2) [imaginary part] of component comp, at pitch a.pitch.
@@ -440,158 +441,154 @@ struct PencilFilter {
   }
 };
 
-constexpr int kYThreads = 128;  // 4 warps
+constexpr int kYThreads = 128;
 constexpr int kZThreads = 128;
-constexpr int kYWarpRows = 4;   // (component, kx, z) rows per warp in the y-pass
-constexpr int kChunk = 8;       // 16-byte loads per lane held in flight per round
-
-// Copy `n16` 16-byte words global -> shared (or back) within one warp, all
-// loads of a round issued before any store.  Row r of the shared side
-// starts at r * spitch16 words; row r of the global side at r * gpitch16.
-template <bool TO_SHARED>
-__device__ __forceinline__ void warp_copy_rows(float4* sh, int spitch16, float4* gl, int gpitch16,
-                                               int rows, int row16, int lane) {
-  const int total = rows * row16;
-  for (int base = 0; base < total; base += kChunk * 32) {
-    float4 v[kChunk];
-#pragma unroll
-    for (int it = 0; it < kChunk; ++it) {
-      const int g = base + lane + it * 32;
-      if (g < total) {
-        const int r = g / row16, c = g - (g / row16) * row16;
-        v[it] = TO_SHARED ? __ldcg(gl + (size_t)r * gpitch16 + c) : sh[r * spitch16 + c];
-      }
-    }
-#pragma unroll
-    for (int it = 0; it < kChunk; ++it) {
-      const int g = base + lane + it * 32;
-      if (g < total) {
-        const int r = g / row16, c = g - (g / row16) * row16;
-        if (TO_SHARED)
-          sh[r * spitch16 + c] = v[it];
-        else
-          __stcg(gl + (size_t)r * gpitch16 + c, v[it]);
-      }
-    }
-  }
-}
 
 NADMM_HD size_t ypass_smem(const PencilArgs& a) {
-  return (size_t)(kYThreads / 32) * kYWarpRows * a.ypitch * sizeof(float2) +
-         (size_t)a.py.tw_count * sizeof(float2);
+  return 16 + (size_t)a.yrows * a.ypitch * sizeof(float2) + (size_t)a.py.tw_count * sizeof(float2);
 }
 
 NADMM_HD size_t zpass_smem(const PencilArgs& a) {
-  return (size_t)(kZThreads / 32) * a.nz * a.zcols * sizeof(float2) +
-         (size_t)a.pz.tw_count * sizeof(float2) +
-         (size_t)(a.nz + (kZThreads / 32) * a.zcols) * sizeof(float);
+  return 16 + 128 + (size_t)a.nz * a.zcols * sizeof(float2) + (size_t)a.pz.tw_count * sizeof(float2) +
+         (size_t)(a.nz + a.zcols) * sizeof(float) + 16;
 }
 
-// y-DFT (forward or inverse) of `nrows` rows held at `rows` with pitch ypitch,
-// by the threads (tid, nthr) that own them.
+// y-DFT (forward or inverse) of `nrows` rows held at `rows` with pitch ypitch.
 template <bool INV>
-NADMM_HD void ypass_transform(const PencilArgs& a, float2* rows, int nrows, const FastDiv& rdiv,
-                              const float2* tw, int tid, int nthr) {
+NADMM_HD void ypass_transform(const PencilArgs& a, float2* rows, const float2* tw, int tid,
+                              int nthr, bool sync_between) {
+#if defined(__CUDA_ARCH__)
+#define NADMM_PSYNC() \
+  if (sync_between) __syncthreads()
+#else
+#define NADMM_PSYNC() (void)sync_between
+#endif
   if (!INV) {
     for (int s = 0; s < a.py.nst; ++s) {
-      fft_stage<false>(a.py, s, rows, nrows, rdiv, 1, a.ypitch, tw, tid, nthr);
-#if defined(__CUDA_ARCH__)
-      __syncwarp();
-#endif
+      fft_stage<false>(a.py, s, rows, a.yrows, a.yrows_div, 1, a.ypitch, tw, tid, nthr);
+      NADMM_PSYNC();
     }
   } else {
     for (int s = a.py.nst - 1; s >= 0; --s) {
-      fft_stage<true>(a.py, s, rows, nrows, rdiv, 1, a.ypitch, tw, tid, nthr);
-#if defined(__CUDA_ARCH__)
-      __syncwarp();
-#endif
+      fft_stage<true>(a.py, s, rows, a.yrows, a.yrows_div, 1, a.ypitch, tw, tid, nthr);
+      NADMM_PSYNC();
     }
   }
+#undef NADMM_PSYNC
 }
 
-// z-DFT, filter, inverse z-DFT of a [nz][ncols] tile (lines = y positions).
-NADMM_HD void zpass_transform(const PencilArgs& a, float2* tile, int ncols, const FastDiv& cdiv,
-                              const float2* tw, const PencilFilter& filt, int tid, int nthr) {
+// z-DFT, filter, inverse z-DFT of a [nz][zcols] tile (lines = y positions).
+NADMM_HD void zpass_transform(const PencilArgs& a, float2* tile, const float2* tw,
+                              const PencilFilter& filt, int tid, int nthr, bool sync_between) {
 #if defined(__CUDA_ARCH__)
-#define NADMM_WSYNC() __syncwarp()
+#define NADMM_PSYNC() \
+  if (sync_between) __syncthreads()
 #else
-#define NADMM_WSYNC()
+#define NADMM_PSYNC() (void)sync_between
 #endif
   for (int s = 0; s + 1 < a.pz.nst; ++s) {
-    fft_stage<false>(a.pz, s, tile, ncols, cdiv, ncols, 1, tw, tid, nthr);
-    NADMM_WSYNC();
+    fft_stage<false>(a.pz, s, tile, a.zcols, a.zcols_div, a.zcols, 1, tw, tid, nthr);
+    NADMM_PSYNC();
   }
-  fft_filter_last(a.pz, tile, ncols, cdiv, ncols, 1, filt, tid, nthr);
-  NADMM_WSYNC();
+  fft_filter_last(a.pz, tile, a.zcols, a.zcols_div, a.zcols, 1, filt, tid, nthr);
+  NADMM_PSYNC();
   for (int s = a.pz.nst - 2; s >= 0; --s) {
-    fft_stage<true>(a.pz, s, tile, ncols, cdiv, ncols, 1, tw, tid, nthr);
-    NADMM_WSYNC();
+    fft_stage<true>(a.pz, s, tile, a.zcols, a.zcols_div, a.zcols, 1, tw, tid, nthr);
+    NADMM_PSYNC();
   }
-#undef NADMM_WSYNC
+#undef NADMM_PSYNC
 }
 
-// Each warp transforms kYWarpRows consecutive rows of the [3 nkx nz][ny] view.
 template <bool INV>
-__global__ void __launch_bounds__(kYThreads) k_ypass(const __grid_constant__ PencilArgs a) {
+__global__ void __launch_bounds__(kYThreads) k_ypass(PencilArgs a) {
 #if defined(__CUDA_ARCH__)
   extern __shared__ __align__(128) unsigned char smem[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float2* tw = reinterpret_cast<float2*>(smem);
-  float2* rows = reinterpret_cast<float2*>(smem + ((size_t)a.py.tw_count * sizeof(float2) + 15) / 16 * 16) +
-                 (size_t)warp * kYWarpRows * a.ypitch;
-  for (int i = tid; i < a.py.tw_count; i += blockDim.x) tw[i] = a.twy[i];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  float2* rows = reinterpret_cast<float2*>(smem + 16);
+  float2* tw = rows + (size_t)a.yrows * a.ypitch;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  float2* g = a.spec + (size_t)blockIdx.x * a.yrows * a.ny;
+  const uint32_t row_bytes = (uint32_t)(a.ny * sizeof(float2));
+  for (int i = tid; i < a.py.tw_count; i += nthr) tw[i] = a.twy[i];
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
   __syncthreads();
   pdl_wait();  // the spectrum comes from the previous kernel
+  if (tid < 32) {
+    if (tid == 0) mbar_expect_tx(bar, row_bytes * a.yrows);
+    __syncwarp();
+    for (int r = tid; r < a.yrows; r += 32)
+      bulk_load(rows + (size_t)r * a.ypitch, g + (size_t)r * a.ny, row_bytes, bar);
+  }
   pdl_trigger();
-  const int total_rows = 3 * a.nkx * a.nz;
-  const int row0 = (blockIdx.x * (kYThreads / 32) + warp) * kYWarpRows;
-  if (row0 >= total_rows) return;
-  const int nrows = min(kYWarpRows, total_rows - row0);
-  const FastDiv rdiv = nrows == kYWarpRows ? a.ywarp_div : make_fastdiv_dev((uint32_t)nrows);
-  float4* g = reinterpret_cast<float4*>(a.spec + (size_t)row0 * a.ny);
-  const int row16 = a.ny / 2, sp16 = a.ypitch / 2;
-  warp_copy_rows<true>(reinterpret_cast<float4*>(rows), sp16, g, row16, nrows, row16, lane);
-  __syncwarp();
-  ypass_transform<INV>(a, rows, nrows, rdiv, tw, lane, 32);
-  warp_copy_rows<false>(reinterpret_cast<float4*>(rows), sp16, g, row16, nrows, row16, lane);
+  const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0));
+  if (!ok) {
+    if (tid == 0 && a.status != nullptr) atomicOr(a.status, kStatusTimeout);
+    mbar_wait_bounded(bar, 0);
+    return;
+  }
+  ypass_transform<INV>(a, rows, tw, tid, nthr, true);
+  fence_proxy_async();
+  __syncthreads();
+  if (tid < 32) {
+    for (int r = tid; r < a.yrows; r += 32)
+      bulk_store(g + (size_t)r * a.ny, rows + (size_t)r * a.ypitch, row_bytes);
+    bulk_commit();
+    bulk_wait_read();
+  }
 #endif
 }
 
-// Each warp filters a.zcols y positions of one (component, kx) plane; a CTA
-// covers 4 a.zcols consecutive positions (warps past ny exit).
 __global__ void __launch_bounds__(kZThreads) k_zpass(const __grid_constant__ PencilArgs a) {
 #if defined(__CUDA_ARCH__)
   extern __shared__ __align__(128) unsigned char smem[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int kWarps = kZThreads / 32;
-  const int zc = a.zcols;
-  float2* tiles = reinterpret_cast<float2*>(smem);
-  float2* tile = tiles + (size_t)warp * a.nz * zc;
-  float2* tw = tiles + (size_t)kWarps * a.nz * zc;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  // TMA box destination: round up to 128 bytes (the layout reserves the slack)
+  unsigned char* tile_p = smem + 16;
+  tile_p += (128u - (smem_addr(tile_p) & 127u)) & 127u;
+  float2* tile = reinterpret_cast<float2*>(tile_p);
+  float2* tw = tile + (size_t)a.nz * a.zcols;
   float* Kz = reinterpret_cast<float*>(tw + a.pz.tw_count);
-  float* Ky = Kz + a.nz;  // slice of the CTA's y positions
-  const int cta_cols = kWarps * zc;
-  const int tiles_per_plane = (a.ny + cta_cols - 1) / cta_cols;
+  float* Ky = Kz + a.nz;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tiles = a.ny / a.zcols;
   const int plane = (int)fdiv(blockIdx.x, a.ztiles_div);
-  const int yc = (blockIdx.x - plane * tiles_per_plane) * cta_cols;
+  const int y0 = (blockIdx.x - plane * tiles) * a.zcols;
   const int kx = plane - (int)fdiv((uint32_t)plane, a.nkx_div) * a.nkx;
-  for (int i = tid; i < a.pz.tw_count; i += blockDim.x) tw[i] = a.twz[i];
-  for (int i = tid; i < a.nz; i += blockDim.x) Kz[i] = a.Kz[i];
-  for (int i = tid; i < cta_cols && yc + i < a.ny; i += blockDim.x) Ky[i] = a.Ky[yc + i];
+  const int row0 = plane * a.nz;  // first row of this plane in the 2D view
+  for (int i = tid; i < a.pz.tw_count; i += nthr) tw[i] = a.twz[i];
+  for (int i = tid; i < a.nz; i += nthr) Kz[i] = a.Kz[i];
+  for (int i = tid; i < a.zcols; i += nthr) Ky[i] = a.Ky[y0 + i];
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
   __syncthreads();
   pdl_wait();
+  if (tid == 0) {
+    mbar_expect_tx(bar, (uint32_t)(a.nz * a.zcols * sizeof(float2)));
+    tensor_load_2d(tile, &a.zmap, y0, row0, bar);
+  }
   pdl_trigger();
-  const int y0 = yc + warp * zc;
-  if (y0 >= a.ny) return;
-  float4* g = reinterpret_cast<float4*>(a.spec + (size_t)plane * a.ny * a.nz + y0);
-  const int col16 = zc / 2;
-  warp_copy_rows<true>(reinterpret_cast<float4*>(tile), col16, g, a.ny / 2, a.nz, col16, lane);
-  __syncwarp();
+  const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0));
+  if (!ok) {
+    if (tid == 0 && a.status != nullptr) atomicOr(a.status, kStatusTimeout);
+    mbar_wait_bounded(bar, 0);
+    return;
+  }
   // Kx by the natural frequency kx < nkx (the x-transform is scattered in
   // natural order); Ky and Kz by position.
-  const PencilFilter filt{Ky + warp * zc, Kz, a.Kx[kx], a.gamma, a.scale, a.order_n};
-  zpass_transform(a, tile, zc, a.zcols_div, tw, filt, lane, 32);
-  warp_copy_rows<false>(reinterpret_cast<float4*>(tile), col16, g, a.ny / 2, a.nz, col16, lane);
+  const PencilFilter filt{Ky, Kz, a.Kx[kx], a.gamma, a.scale, a.order_n};
+  zpass_transform(a, tile, tw, filt, tid, nthr, true);
+  fence_proxy_async();
+  __syncthreads();
+  if (tid == 0) {
+    tensor_store_2d(&a.zmap, y0, row0, tile);
+    bulk_commit();
+    bulk_wait_read();
+  }
 #endif
 }
 
@@ -610,13 +607,12 @@ void finish_plane_args(PlaneArgs& a) {
 }
 
 void finish_pencil_args(PencilArgs& a) {
-  a.yrows = kYWarpRows;
-  a.ypitch = a.ny + 4;  // even (16-byte rows); == 4 mod 16 words spreads a half-warp's rows
-  a.zcols = (a.ny % 8 == 0) ? 8 : (a.ny % 4 == 0) ? 4 : 2;  // even: 16-byte copies
-  const int cta_cols = (kZThreads / 32) * a.zcols;
-  a.ywarp_div = make_fastdiv((uint32_t)kYWarpRows);
+  a.yrows = (a.nz % 16 == 0) ? 16 : (a.nz % 8 == 0) ? 8 : (a.nz % 4 == 0) ? 4 : (a.nz % 2 == 0) ? 2 : 1;
+  a.ypitch = a.ny + 2;  // even: row starts stay 16-byte aligned for bulk copies
+  a.zcols = (a.ny % 16 == 0) ? 16 : (a.ny % 8 == 0) ? 8 : (a.ny % 4 == 0) ? 4 : 2;
+  a.yrows_div = make_fastdiv((uint32_t)a.yrows);
   a.zcols_div = make_fastdiv((uint32_t)a.zcols);
-  a.ztiles_div = make_fastdiv((uint32_t)((a.ny + cta_cols - 1) / cta_cols));
+  a.ztiles_div = make_fastdiv((uint32_t)(a.ny / a.zcols));
   a.nkx_div = make_fastdiv((uint32_t)a.nkx);
 }
 
@@ -712,10 +708,8 @@ cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, 
 }
 
 cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s) {
-  const int rows_per_cta = (kYThreads / 32) * kYWarpRows;
-  const unsigned yblocks = (unsigned)((3 * a.nkx * a.nz + rows_per_cta - 1) / rows_per_cta);
-  const int cta_cols = (kZThreads / 32) * a.zcols;
-  const unsigned zblocks = (unsigned)(3 * a.nkx * ((a.ny + cta_cols - 1) / cta_cols));
+  const unsigned yblocks = (unsigned)(3 * a.nkx * a.nz / a.yrows);
+  const unsigned zblocks = (unsigned)(3 * a.nkx * (a.ny / a.zcols));
   cudaError_t e = launch_pdl(k_ypass<false>, dim3(yblocks), dim3(kYThreads), ypass_smem(a), s, a);
   if (e == cudaSuccess) e = launch_pdl(k_zpass, dim3(zblocks), dim3(kZThreads), zpass_smem(a), s, a);
   if (e == cudaSuccess) e = launch_pdl(k_ypass<true>, dim3(yblocks), dim3(kYThreads), ypass_smem(a), s, a);

@@ -67,11 +67,11 @@ struct PencilArgs {
   const float* Kz;         // [nz] 4 sin^2(pi kz / nz) by position
   unsigned* status;        // device status word (bit 1: a bounded wait expired) or null
   AxisPlan py, pz;
-  FastDiv ywarp_div, zcols_div, ztiles_div, nkx_div;
+  FastDiv yrows_div, zcols_div, ztiles_div, nkx_div;
   int ny, nz, nkx;
-  int yrows;               // (component, kx, z) rows per y-pass warp
+  int yrows;               // (component, kx, z) rows per y-pass CTA (divides nz)
   int ypitch;              // y-pass shared-memory row pitch (even: 16-byte aligned rows)
-  int zcols;               // y positions per z-pass warp
+  int zcols;               // y positions per z-pass CTA (divides ny, even)
   int order_n;
   float gamma;             // lambda / theta
   float scale;             // 1 / (nx ny nz)
@@ -85,7 +85,6 @@ void finish_plane_args(PlaneArgs& a);
 void finish_pencil_args(PencilArgs& a);
 // Encode a.zmap for a.spec (host only; needs finish_pencil_args first).
 cudaError_t encode_pencil_map(PencilArgs& a);
-
 
 // mode = InMode * 4 + prev * 2 + step
 cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, cudaStream_t s);
