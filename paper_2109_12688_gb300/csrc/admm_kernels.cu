@@ -148,7 +148,6 @@ NADMM_HD constexpr FieldMap field_map() {
 
 constexpr int kGatherItems = 4;   // spectrum values per thread held in flight per round
 constexpr int kPlaneThreads = 256;
-constexpr int kPencilThreads = 384;
 
 // Lines: line l = comp * (R/2) + r holds rows (y0 + r) [real part] and
 // (y0 + r + R/2) [imaginary part] of component comp, at pitch a.pitch.
@@ -710,9 +709,15 @@ cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, 
 cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s) {
   const unsigned yblocks = (unsigned)(3 * a.nkx * a.nz / a.yrows);
   const unsigned zblocks = (unsigned)(3 * a.nkx * (a.ny / a.zcols));
-  cudaError_t e = launch_pdl(k_ypass<false>, dim3(yblocks), dim3(kYThreads), ypass_smem(a), s, a);
-  if (e == cudaSuccess) e = launch_pdl(k_zpass, dim3(zblocks), dim3(kZThreads), zpass_smem(a), s, a);
-  if (e == cudaSuccess) e = launch_pdl(k_ypass<true>, dim3(yblocks), dim3(kYThreads), ypass_smem(a), s, a);
+  const bool ly = lane_y_supported(a), lz = lane_z_supported(a);
+  cudaError_t e = ly ? launch_lane_y(a, false, s)
+                     : launch_pdl(k_ypass<false>, dim3(yblocks), dim3(kYThreads), ypass_smem(a), s, a);
+  if (e == cudaSuccess)
+    e = lz ? launch_lane_z(a, s)
+           : launch_pdl(k_zpass, dim3(zblocks), dim3(kZThreads), zpass_smem(a), s, a);
+  if (e == cudaSuccess)
+    e = ly ? launch_lane_y(a, true, s)
+           : launch_pdl(k_ypass<true>, dim3(yblocks), dim3(kYThreads), ypass_smem(a), s, a);
   return e;
 }
 

@@ -321,6 +321,19 @@ template <> struct CompTab<12> {
   }
 };
 
+template <> struct CompTab<14> {
+  NADMM_HD static float c(int m) {
+    const float t[7] = {1.f, 0.90096886790241915f, 0.62348980185873359f, 0.22252093395631445f,
+                        -0.22252093395631434f, -0.62348980185873348f, -0.90096886790241903f};
+    return t[m];
+  }
+  NADMM_HD static float s(int m) {
+    const float t[7] = {0.f, 0.43388373911755812f, 0.7818314824680298f, 0.97492791218182362f,
+                        0.97492791218182362f, 0.78183148246802991f, 0.43388373911755823f};
+    return t[m];
+  }
+};
+
 template <int R, bool INV>
 NADMM_HD void dft(float2 (&x)[R]);
 
@@ -377,6 +390,8 @@ NADMM_HD void dft(float2 (&x)[R]) {
     dft_composite<5, 2, INV>(x);
   } else if constexpr (R == 12) {
     dft_composite<4, 3, INV>(x);
+  } else if constexpr (R == 14) {
+    dft_composite<7, 2, INV>(x);
   } else {
     dft_odd<R, INV>(x);
   }
@@ -443,6 +458,7 @@ NADMM_HD void fft_stage(const AxisPlan& p, int s, float2* buf, int nlines, const
     case 9: stage_loop<9, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
     case 10: stage_loop<10, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
     case 12: stage_loop<12, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
+    case 14: stage_loop<14, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
     default: stage_loop<16, INV>(buf, nlines, ldiv, es, ls, L, m, md, tw, nblk, tid, nthr); break;
   }
 }
@@ -486,6 +502,7 @@ NADMM_HD void fft_filter_last(const AxisPlan& p, float2* buf, int nlines, const 
     case 9: filter_loop<9>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
     case 10: filter_loop<10>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
     case 12: filter_loop<12>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
+    case 14: filter_loop<14>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
     default: filter_loop<16>(buf, nlines, ldiv, es, ls, p.n, filt, tid, nthr); break;
   }
 }

@@ -86,6 +86,12 @@ void finish_pencil_args(PencilArgs& a);
 // Encode a.zmap for a.spec (host only; needs finish_pencil_args first).
 cudaError_t encode_pencil_map(PencilArgs& a);
 
+// Lane-FFT y/z passes (lane_passes.cu) for two-stage plans [R1, R2 in {8, 16}].
+bool lane_y_supported(const PencilArgs& a);
+bool lane_z_supported(const PencilArgs& a);
+cudaError_t launch_lane_y(const PencilArgs& a, bool inv, cudaStream_t s);
+cudaError_t launch_lane_z(const PencilArgs& a, cudaStream_t s);
+
 // mode = InMode * 4 + prev * 2 + step
 cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, cudaStream_t s);
 cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s);

@@ -11,7 +11,21 @@ namespace nadmm {
 
 // Radices with register codelets.  The plan uses the fewest stages (each
 // stage is one pass over shared memory), larger radices first on ties.
-constexpr int kRadices[] = {16, 12, 10, 9, 8, 7, 6, 5, 4, 3, 2};
+constexpr int kRadices[] = {16, 14, 12, 10, 9, 8, 7, 6, 5, 4, 3, 2};
+
+// Lane-FFT plans: n = R1 * R2 with R2 in {8, 16} lanes per line and R1 values
+// per lane (a codelet radix); first stage R1, second stage R2.  Returns R2
+// (0 if n has no such split), trying R2 = 8 first.
+constexpr int kLaneR1[] = {3, 4, 6, 8, 9, 10, 12, 14, 16};
+
+inline int lane_split(int n) {
+  for (int r2 : {8, 16}) {
+    if (n % r2) continue;
+    for (int r1 : kLaneR1)
+      if (r1 == n / r2) return r2;
+  }
+  return 0;
+}
 
 inline bool best_factors(int n, int depth, int* out, int& best_len, int* cur, int len) {
   if (n == 1) {
@@ -31,10 +45,17 @@ inline bool best_factors(int n, int depth, int* out, int& best_len, int* cur, in
   return found;
 }
 
-inline bool factor_axis(int n, AxisPlan& p) {
+inline bool factor_axis(int n, AxisPlan& p, bool lane_plan = false) {
   if (n < 2) return false;
   int out[kMaxStages], cur[kMaxStages], best = kMaxStages + 1;
-  if (!best_factors(n, kMaxStages, out, best, cur, 0)) return false;
+  const int r2 = lane_plan ? lane_split(n) : 0;
+  if (r2) {
+    out[0] = n / r2;
+    out[1] = r2;
+    best = 2;
+  } else if (!best_factors(n, kMaxStages, out, best, cur, 0)) {
+    return false;
+  }
   p.n = n;
   p.nst = best;
   int L = n, off = 0;
