@@ -103,8 +103,15 @@ __global__ void __launch_bounds__(kLaneThreads) k_ylane(const __grid_constant__ 
   }
 }
 
+// Resident blocks requested per SM: the small shapes fit 64 registers.
 template <int R1, int R2>
-__global__ void __launch_bounds__(kLaneThreads) k_zlane(const __grid_constant__ PencilArgs a) {
+constexpr int zlane_min_blocks() {
+  return (R2 == 8 && R1 <= 12) ? 8 : 6;
+}
+
+template <int R1, int R2>
+__global__ void __launch_bounds__(kLaneThreads, zlane_min_blocks<R1, R2>())
+    k_zlane(const __grid_constant__ PencilArgs a) {
   constexpr int N = R1 * R2, CPW = 32 / R2;
   constexpr int P = N + (R2 == 8 ? 4 : 8);  // column pitch: a half-warp's columns on other banks
   extern __shared__ float2 sm_all[];
