@@ -24,7 +24,9 @@
 #include <cuda_runtime.h>
 
 #include "fft_device.cuh"
+#include "lane_fft.cuh"
 #include "nadmm_internal.h"
+#include "plan.h"
 
 namespace nadmm {
 
@@ -184,10 +186,10 @@ NADMM_HD void plane_gather(const PlaneArgs& a, float2* lines, const int* pos, in
         float2* line = lines + (comp * h + r) * a.pitch;
         const float2 Av = A[it], Bv = B[it];
         if (kx == 0 || 2 * kx == a.nx) {
-          line[pos[kx]] = make_float2(Av.x, Bv.x);
+          line[swz_rt(pos[kx], a.xlog2r2)] = make_float2(Av.x, Bv.x);
         } else {
-          line[pos[kx]] = make_float2(Av.x - Bv.y, Av.y + Bv.x);
-          line[pos[a.nx - kx]] = make_float2(Av.x + Bv.y, Bv.x - Av.y);
+          line[swz_rt(pos[kx], a.xlog2r2)] = make_float2(Av.x - Bv.y, Av.y + Bv.x);
+          line[swz_rt(pos[a.nx - kx], a.xlog2r2)] = make_float2(Av.x + Bv.y, Bv.x - Av.y);
         }
       }
     }
@@ -206,8 +208,8 @@ NADMM_HD void plane_scatter(const PlaneArgs& a, const float2* lines, const int* 
     const int comp = (int)fdiv((uint32_t)rest, a.nkx_div);
     const int kx = rest - comp * a.nkx;
     const float2* line = lines + (comp * h + r) * a.pitch;
-    const float2 Zk = line[pos[kx]];
-    const float2 Zm = line[pos[kx == 0 ? 0 : a.nx - kx]];
+    const float2 Zk = line[swz_rt(pos[kx], a.xlog2r2)];
+    const float2 Zm = line[swz_rt(pos[kx == 0 ? 0 : a.nx - kx], a.xlog2r2)];
     float2* dst = a.spec + ((size_t)(comp * a.nkx + kx) * a.nz + z) * a.ny + y0 + r;
     dst[0] = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
     dst[h] = make_float2(0.5f * (Zk.y + Zm.y), 0.5f * (Zm.x - Zk.x));
@@ -226,6 +228,7 @@ NADMM_HD void plane_pointwise(const PlaneArgs& a, const float* fld, float2* line
   for (int g = tid; g < total; g += nthr) {
     const int r = (int)fdiv((uint32_t)g, a.nx_div);
     const int x = g - r * a.nx;
+    const int xs = swz_rt(x, a.xlog2r2);  // position of x in the line buffer
     float ynew[2][3];
     for (int half = 0; half < 2; ++half) {
       const int row = r + half * h;
@@ -236,7 +239,7 @@ NADMM_HD void plane_pointwise(const PlaneArgs& a, const float* fld, float2* line
       for (int comp = 0; comp < 3; ++comp) {
         const size_t i = comp * V + vox;
         if (IN == IN_SPEC) {
-          const float2 l = lines[(comp * h + r) * a.pitch + x];
+          const float2 l = lines[(comp * h + r) * a.pitch + xs];
           wk1[comp] = half ? l.y : l.x;
           if (STEP)
             bk1[comp] = fld[(F.y + comp) * tile + so] - wk1[comp];
@@ -290,14 +293,14 @@ NADMM_HD void plane_pointwise(const PlaneArgs& a, const float* fld, float2* line
     if (STEP) {
 #pragma unroll
       for (int comp = 0; comp < 3; ++comp)
-        lines[(comp * h + r) * a.pitch + x] = make_float2(ynew[0][comp], ynew[1][comp]);
+        lines[(comp * h + r) * a.pitch + xs] = make_float2(ynew[0][comp], ynew[1][comp]);
     }
   }
 }
 
 // Shared-memory layout of the plane pass (byte offsets).
 struct PlaneSmem {
-  size_t fld, lines, tw, pos, total;
+  size_t fld, lines, total;
 };
 
 NADMM_HD PlaneSmem plane_layout(const PlaneArgs& a, int nfields) {
@@ -308,15 +311,23 @@ NADMM_HD PlaneSmem plane_layout(const PlaneArgs& a, int nfields) {
   o = (o + 15) & ~(size_t)15;
   L.lines = o;
   o += (size_t)3 * (a.R / 2) * a.pitch * sizeof(float2);
-  L.tw = o;
-  o += (size_t)a.px.tw_count * sizeof(float2);
-  L.pos = o;
-  o += (size_t)a.nx * sizeof(int);
   L.total = (o + 15) & ~(size_t)15;
   return L;
 }
 
 #if defined(__CUDA_ARCH__)
+// x-DFT of the CTA's lines by groups of xr2 lanes (lane FFT, swizzled lines).
+template <bool INV>
+__device__ __forceinline__ void plane_lane_fft(const PlaneArgs& a, float2* lines,
+                                               const float2* __restrict__ tw, int nlines, int tid) {
+  const int g = tid >> a.xlog2r2, l = tid & (a.xr2 - 1);
+  if (g < nlines) {
+    const int lane = tid & 31;
+    const unsigned gmask = ((a.xr2 == 32) ? 0xffffffffu : ((1u << a.xr2) - 1u)) << (lane & ~(a.xr2 - 1));
+    lane_line_fft_rt<INV>(a.xr1, a.xr2, lines + g * a.pitch, tw, l, gmask);
+  }
+}
+
 template <int IN, bool PREV, bool STEP>
 __device__ __forceinline__ const float* field_src(const PlaneArgs& a, int slot) {
   constexpr FieldMap F = field_map<IN, PREV, STEP>();
@@ -341,8 +352,9 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   float* fld = reinterpret_cast<float*>(smem + L.fld);
   float2* lines = reinterpret_cast<float2*>(smem + L.lines);
-  float2* tw = reinterpret_cast<float2*>(smem + L.tw);
-  int* pos = reinterpret_cast<int*>(smem + L.pos);
+  // the small x-axis tables are read through L1 where they are used
+  const float2* __restrict__ tw = a.twx;
+  const int* __restrict__ pos = a.posx;
   const int tiles_y = a.ny / a.R;
   const int z = (int)fdiv(blockIdx.x, a.tiles_div);
   const int y0 = (blockIdx.x - z * tiles_y) * a.R;
@@ -371,9 +383,6 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
                   tile_bytes, bar);
     }
   }
-  for (int i = tid; i < a.px.tw_count; i += nthr) tw[i] = a.twx[i];
-  for (int i = tid; i < a.nx; i += nthr) pos[i] = a.posx[i];
-  __syncthreads();
   pdl_wait();
   pdl_trigger();
   if (F.n > 0 && !kEarlyLoads && tid < 32) {
@@ -386,9 +395,14 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
   if (IN == IN_SPEC) {
     plane_gather(a, lines, pos, z, y0, tid, nthr);
     __syncthreads();
-    for (int s = a.px.nst - 1; s >= 0; --s) {
-      fft_stage<true>(a.px, s, lines, nlines, a.lines_div, 1, a.pitch, tw, tid, nthr);
+    if (a.xr2 != 0) {
+      plane_lane_fft<true>(a, lines, tw, nlines, tid);
       __syncthreads();
+    } else {
+      for (int s = a.px.nst - 1; s >= 0; --s) {
+        fft_stage<true>(a.px, s, lines, nlines, a.lines_div, 1, a.pitch, tw, tid, nthr);
+        __syncthreads();
+      }
     }
   }
   if (F.n > 0) {
@@ -402,9 +416,14 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
   plane_pointwise<IN, PREV, STEP>(a, fld, lines, z, y0, tid, nthr);
   if (STEP) {
     __syncthreads();
-    for (int s = 0; s < a.px.nst; ++s) {
-      fft_stage<false>(a.px, s, lines, nlines, a.lines_div, 1, a.pitch, tw, tid, nthr);
+    if (a.xr2 != 0) {
+      plane_lane_fft<false>(a, lines, tw, nlines, tid);
       __syncthreads();
+    } else {
+      for (int s = 0; s < a.px.nst; ++s) {
+        fft_stage<false>(a.px, s, lines, nlines, a.lines_div, 1, a.pitch, tw, tid, nthr);
+        __syncthreads();
+      }
     }
     plane_scatter(a, lines, pos, z, y0, tid, nthr);
   }
@@ -597,7 +616,19 @@ int rows_per_tile(int ny) { return (ny % 8 == 0) ? 8 : (ny % 4 == 0) ? 4 : 2; }
 void finish_plane_args(PlaneArgs& a) {
   a.nkx = a.nx / 2 + 1;
   a.R = rows_per_tile(a.ny);
-  a.pitch = a.nx + 1;
+  const AxisPlan& p = a.px;
+  const bool lane = p.nst == 2 && p.m[1] == 1 && lane_pair_supported(p.radix[0], p.radix[1]) &&
+                    3 * (a.R / 2) * p.radix[1] <= kPlaneThreads;
+  if (lane) {
+    a.xr1 = p.radix[0];
+    a.xr2 = p.radix[1];
+    a.xlog2r2 = (a.xr2 == 8) ? 3 : 4;
+    a.pitch = a.nx + 8;  // even; two 8-lane groups of a half-warp on different banks
+  } else {
+    a.xr1 = a.xr2 = 0;
+    a.xlog2r2 = -1;
+    a.pitch = a.nx + 1;  // odd: lanes on different lines hit different banks
+  }
   a.nx_div = make_fastdiv((uint32_t)a.nx);
   a.lines_div = make_fastdiv((uint32_t)(3 * (a.R / 2)));
   a.half_div = make_fastdiv((uint32_t)(a.R / 2));

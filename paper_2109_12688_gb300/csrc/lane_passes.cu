@@ -17,32 +17,13 @@
 #include <cuda_runtime.h>
 
 #include "fft_device.cuh"
+#include "lane_fft.cuh"
 #include "nadmm_internal.h"
+#include "plan.h"
 
 namespace nadmm {
 
 constexpr int kLaneThreads = 128;  // 4 independent warps
-
-// Position p of a line stored at p ^ ((p / R2) mod R2): rows of R2-blocks
-// are rotated so that both access patterns (lane l writing l + R2 k, a lane
-// reading a whole block) spread over the banks.
-template <int R2>
-__device__ __forceinline__ int swz(int p) {
-  return p ^ ((p / R2) & (R2 - 1));
-}
-
-template <int R1, int R2, bool INV>
-__device__ __forceinline__ void lane_stage1(float2 (&v)[R1], const float2* __restrict__ tw, int l) {
-  if (!INV) {
-    dft<R1, false>(v);
-#pragma unroll
-    for (int k = 1; k < R1; ++k) v[k] = cmul(v[k], __ldg(tw + (k - 1) * R2 + l));
-  } else {
-#pragma unroll
-    for (int k = 1; k < R1; ++k) v[k] = cmulc(v[k], __ldg(tw + (k - 1) * R2 + l));
-    dft<R1, true>(v);
-  }
-}
 
 template <int R1, int R2, bool INV>
 __global__ void __launch_bounds__(kLaneThreads) k_ylane(const __grid_constant__ PencilArgs a) {
@@ -191,12 +172,8 @@ cudaError_t launch_z(const PencilArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-#define NADMM_LANE_CASES(X) \
-  X(3, 8) X(4, 8) X(6, 8) X(8, 8) X(9, 8) X(10, 8) X(12, 8) X(14, 8) X(16, 8) \
-  X(3, 16) X(4, 16) X(6, 16) X(8, 16) X(9, 16) X(10, 16) X(12, 16) X(14, 16) X(16, 16)
-
 static bool is_lane_plan(const AxisPlan& p) {
-  return p.nst == 2 && (p.radix[1] == 8 || p.radix[1] == 16) && p.m[1] == 1;
+  return p.nst == 2 && p.m[1] == 1 && lane_pair_supported(p.radix[0], p.radix[1]);
 }
 
 bool lane_y_supported(const PencilArgs& a) { return is_lane_plan(a.py); }

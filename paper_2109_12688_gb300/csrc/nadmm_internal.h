@@ -48,7 +48,9 @@ struct PlaneArgs {
   FastDiv tiles_div;       // division by ny / R
   int nx, ny, nz, nkx;     // nkx = nx/2 + 1
   int R;                   // rows per CTA (even, divides ny)
-  int pitch;               // shared-memory line pitch (odd, >= nx)
+  int pitch;               // shared-memory line pitch (>= nx)
+  int xr1, xr2;            // lane-FFT plan of the x axis (xr2 = 0: shared-memory stages)
+  int xlog2r2;             // log2(xr2), or -1 (line positions not swizzled)
   float beta;              // beta_{k-1}
   float theta, eps;
   int data_term;           // 1 or 2

@@ -18,6 +18,14 @@ constexpr int kRadices[] = {16, 14, 12, 10, 9, 8, 7, 6, 5, 4, 3, 2};
 // (0 if n has no such split), trying R2 = 8 first.
 constexpr int kLaneR1[] = {3, 4, 6, 8, 9, 10, 12, 14, 16};
 
+// Whether a two-stage plan [r1, r2] has lane-FFT kernels.
+inline bool lane_pair_supported(int r1, int r2) {
+  if (r2 != 8 && r2 != 16) return false;
+  for (int r : kLaneR1)
+    if (r == r1) return true;
+  return false;
+}
+
 inline int lane_split(int n) {
   for (int r2 : {8, 16}) {
     if (n % r2) continue;
