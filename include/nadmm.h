@@ -140,6 +140,42 @@ const char* nadmm_last_error(void);
 const char* nadmm_status_string(nadmm_status s);
 
 /* ---------------------------------------------------------------------
+ * Batched registration: many independent pairs of different grid sizes
+ * (the paper registers each ED/ES pair on its own; Sec. 4 runs 220 pairs).
+ * --------------------------------------------------------------------- */
+
+/* Create a handle for npairs pairs: pair i has grid dims[3i], dims[3i+1],
+ * dims[3i+2] (nx, ny, nz) and every other setting from `base` (its nx, ny,
+ * nz are ignored).  Each grid is validated as by nadmm_create; the first
+ * failure is returned with "pair i: ..." in nadmm_last_error.  The pairs
+ * are spread over min(npairs, 4) lanes -- concurrent branches of one CUDA
+ * graph -- longest first, balancing voxel counts; pairs of one lane run one
+ * after another and share that lane's scratch, so the workspace is one
+ * state region per lane (its largest pair's) plus every pair's small
+ * tables.  Host only. */
+nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, const int32_t* dims,
+                                  nadmm_handle* out);
+
+/* Change the lane count (1 = all pairs in sequence) of a batched handle
+ * before its workspace is attached.  lanes > npairs is clamped to npairs.
+ * Errors: INVALID_ARG (not batched, lanes < 1, workspace already attached). */
+nadmm_status nadmm_batch_set_lanes(nadmm_handle h, int32_t lanes);
+
+/* Register every pair of a batched handle: fixed[i], moving[i] device
+ * [nz_i][ny_i][nx_i], u_out[i] device [3][nz_i][ny_i][nx_i] (host arrays of
+ * npairs device pointers each).  The same computation as nadmm_register on
+ * each pair, as one CUDA-graph replay on `stream` (re-captured when any
+ * pointer changes) or, with NADMM_FLAG_NO_GRAPH, direct launches of the
+ * pairs in order.  nadmm_get_status on the handle reports the first pair
+ * whose status word is set.  Only nadmm_register_batched,
+ * nadmm_get_status, nadmm_workspace_size, nadmm_set_workspace,
+ * nadmm_batch_set_lanes and nadmm_destroy accept a batched handle.
+ * Errors: INVALID_ARG, ALIGNMENT, NO_WORKSPACE, CUDA. */
+nadmm_status nadmm_register_batched(nadmm_handle h, const float* const* fixed,
+                                    const float* const* moving, float* const* u_out,
+                                    void* stream);
+
+/* ---------------------------------------------------------------------
  * Step-level entry points: one part of the path each, on device buffers of
  * the handle's grid, using the handle's workspace as scratch.  They run the
  * same kernels as nadmm_register.

@@ -2,7 +2,9 @@
 // outer/inner loop schedule and its CUDA-graph capture.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -28,6 +30,7 @@ nadmm_status cuda_fail(cudaError_t e, const char* where) {
 }
 
 constexpr size_t kAlign = 256;
+constexpr size_t kMaxSmem = 227 * 1024;  // opt-in dynamic shared memory per CTA
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -44,20 +47,35 @@ struct nadmm_context {
   int R = 0;
   size_t V = 0, nkx = 0;
   size_t plane_smem = 0, pencil_smem = 0;
-  // workspace layout (byte offsets)
-  size_t o_spec, o_y, o_wp, o_bp, o_J, o_c, o_I1w, o_ut, o_io_f, o_io_m, o_io_u, o_red, o_twx,
-      o_twy, o_twz, o_posx, o_Kx, o_Ky, o_Kz, total;
+  // Workspace: a state region (fields and spectrum, offsets o_spec..o_io_u
+  // from ws) and a table region (status/reduction words and FFT tables,
+  // offsets o_red..o_Kz from wt).  A single handle places the tables right
+  // after the state; the pairs of a batched handle that run one after
+  // another on the same lane share one state region and own their tables.
+  size_t o_spec, o_y, o_wp, o_bp, o_J, o_c, o_I1w, o_ut, o_io_f, o_io_m, o_io_u, state_total;
+  size_t o_red, o_twx, o_twy, o_twz, o_posx, o_Kx, o_Ky, o_Kz, table_total;
+  size_t total;  // single handle: align(state_total) + table_total
   char* ws = nullptr;
-  size_t ws_bytes = 0;
-  bool kernels_configured = false;
+  char* wt = nullptr;
   CUtensorMap zmap;  // z-pass tensor map of the workspace spectrum
   // graph cache
   cudaGraphExec_t gexec = nullptr;
-  const void* gkey[3] = {nullptr, nullptr, nullptr};
+  std::vector<const void*> gkey;
   cudaStream_t cap = nullptr;
+  // batched handle: the pairs, their lane (concurrent graph branch) and
+  // the byte offsets of each lane's state and each pair's tables
+  bool batched = false;
+  std::vector<nadmm_context*> pairs;
+  int lanes = 0;
+  std::vector<int> lane_of;
+  std::vector<size_t> lane_off, tab_off;
+  std::vector<cudaStream_t> lane_cap;
+  std::vector<cudaEvent_t> lane_ev;  // [0] fork, [1 + l] join of lane l
 
   template <class T>
   T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+  template <class T>
+  T* tab(size_t off) const { return reinterpret_cast<T*>(wt + off); }
 };
 
 namespace {
@@ -71,7 +89,7 @@ bool good_factors(int n) {
 void invalidate_graph(nadmm_context* h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   h->gexec = nullptr;
-  h->gkey[0] = h->gkey[1] = h->gkey[2] = nullptr;
+  h->gkey.clear();
 }
 
 nadmm_status validate(const nadmm_config* c) {
@@ -132,14 +150,14 @@ PlaneArgs plane_args(const nadmm_context* h) {
   a.bp = h->at<float>(h->o_bp);
   a.J = h->at<float>(h->o_J);
   a.c = h->at<float>(h->o_c);
-  a.twx = h->at<float2>(h->o_twx);
-  a.posx = h->at<int>(h->o_posx);
+  a.twx = h->tab<float2>(h->o_twx);
+  a.posx = h->tab<int>(h->o_posx);
   a.px = h->px;
   a.nx = h->cfg.nx;
   a.ny = h->cfg.ny;
   a.nz = h->cfg.nz;
   a.nkx = (int)h->nkx;
-  a.status = h->at<unsigned>(h->o_red) + 2;
+  a.status = h->tab<unsigned>(h->o_red) + 2;
   a.theta = h->cfg.theta;
   a.eps = h->cfg.eps;
   a.data_term = h->cfg.data_term;
@@ -151,17 +169,17 @@ PencilArgs pencil_args(const nadmm_context* h) {
   PencilArgs a;
   std::memset(&a, 0, sizeof(a));
   a.spec = h->at<float2>(h->o_spec);
-  a.twy = h->at<float2>(h->o_twy);
-  a.twz = h->at<float2>(h->o_twz);
-  a.Kx = h->at<float>(h->o_Kx);
-  a.Ky = h->at<float>(h->o_Ky);
-  a.Kz = h->at<float>(h->o_Kz);
+  a.twy = h->tab<float2>(h->o_twy);
+  a.twz = h->tab<float2>(h->o_twz);
+  a.Kx = h->tab<float>(h->o_Kx);
+  a.Ky = h->tab<float>(h->o_Ky);
+  a.Kz = h->tab<float>(h->o_Kz);
   a.py = h->py;
   a.pz = h->pz;
   a.ny = h->cfg.ny;
   a.nz = h->cfg.nz;
   a.nkx = (int)h->nkx;
-  a.status = h->at<unsigned>(h->o_red) + 2;
+  a.status = h->tab<unsigned>(h->o_red) + 2;
   a.order_n = h->cfg.order_n;
   a.gamma = h->cfg.lambda / h->cfg.theta;
   a.scale = (float)(1.0 / ((double)h->cfg.nx * h->cfg.ny * h->cfg.nz));
@@ -252,7 +270,7 @@ cudaError_t enqueue_register(nadmm_context* h, const float* I0, const float* I1,
   float* J = h->at<float>(h->o_J);
   float* c = h->at<float>(h->o_c);
   float* vbuf = h->at<float>(h->o_wp);  // velocity w^K reuses the w state slot
-  unsigned* red = h->at<unsigned>(h->o_red);
+  unsigned* red = h->tab<unsigned>(h->o_red);
   // u ping-pongs between u_out and ut so that the last compose lands in u_out
   auto dst_of = [&](int o) { return ((O - 1 - o) % 2 == 0) ? u_out : ut; };
   float* u_cur = (dst_of(0) == u_out) ? ut : u_out;
@@ -278,9 +296,12 @@ cudaError_t enqueue_register(nadmm_context* h, const float* I0, const float* I1,
   return cudaSuccess;
 }
 
-nadmm_status need_ws(const nadmm_context* h) {
+nadmm_status need_ws(const nadmm_context* h, bool batched = false) {
   if (!h) return fail(NADMM_ERR_INVALID_ARG, "handle is NULL");
-  if (!h->ws) return fail(NADMM_ERR_NO_WORKSPACE, "no workspace attached (nadmm_set_workspace)");
+  if (h->batched != batched)
+    return fail(NADMM_ERR_INVALID_ARG, batched ? "handle is not a batched handle (nadmm_create_batched)"
+                                               : "a batched handle only takes the *_batched calls");
+  if (!h->wt) return fail(NADMM_ERR_NO_WORKSPACE, "no workspace attached (nadmm_set_workspace)");
   return NADMM_OK;
 }
 
@@ -292,13 +313,201 @@ nadmm_status check_dev_ptrs(std::initializer_list<const void*> ptrs) {
   return NADMM_OK;
 }
 
-nadmm_status run_register(nadmm_context* h, const float* I0, const float* I1, float* u_out,
-                          cudaStream_t stream) {
-  if (h->cfg.flags & NADMM_FLAG_NO_GRAPH) {
-    cudaError_t e = enqueue_register(h, I0, I1, u_out, stream);
-    return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_register");
+constexpr int kDefaultLanes = 4;
+
+// Plans, tables and the workspace layout of one grid (host memory only).
+nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
+  nadmm_status st = validate(cfg);
+  if (st != NADMM_OK) return st;
+  nadmm_context* h = new nadmm_context();
+  h->cfg = *cfg;
+  if (!factor_axis(cfg->nx, h->px, true) || !factor_axis(cfg->ny, h->py, true) ||
+      !factor_axis(cfg->nz, h->pz, true)) {
+    delete h;
+    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "no radix plan for these dimensions");
   }
-  if (!h->gexec || h->gkey[0] != I0 || h->gkey[1] != I1 || h->gkey[2] != u_out) {
+  h->V = (size_t)cfg->nx * cfg->ny * cfg->nz;
+  h->nkx = (size_t)cfg->nx / 2 + 1;
+  {
+    PlaneArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.nx = cfg->nx;
+    pa.ny = cfg->ny;
+    pa.nz = cfg->nz;
+    pa.px = h->px;
+    finish_plane_args(pa);
+    PencilArgs qa;
+    std::memset(&qa, 0, sizeof(qa));
+    qa.ny = cfg->ny;
+    qa.nz = cfg->nz;
+    qa.nkx = (int)h->nkx;
+    qa.py = h->py;
+    qa.pz = h->pz;
+    finish_pencil_args(qa);
+    h->R = pa.R;
+    h->plane_smem = plane_smem_max(pa);
+    h->pencil_smem = pencil_smem_bytes(qa);
+  }
+  if (h->pencil_smem > kMaxSmem || h->plane_smem > kMaxSmem) {
+    delete h;
+    return fail(NADMM_ERR_UNSUPPORTED_SIZE,
+                "a pass's shared-memory tile exceeds the 227 KB per CTA (nx too large)");
+  }
+  if (cfg->nz > 256) {
+    delete h;
+    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "nz must be <= 256 (one TMA box spans the z axis)");
+  }
+  h->twx = axis_twiddles(h->px);
+  h->twy = axis_twiddles(h->py);
+  h->twz = axis_twiddles(h->pz);
+  h->posx = pos_table(h->px);
+  h->Kx = symbol_natural(cfg->nx, (int)h->nkx);
+  h->Ky = symbol_by_position(h->py);
+  h->Kz = symbol_by_position(h->pz);
+  compute_beta(h);
+  const size_t V = h->V;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o = align_up(o + bytes);
+    return r;
+  };
+  h->o_spec = take(3 * h->nkx * cfg->ny * cfg->nz * sizeof(float2));
+  h->o_y = take(3 * V * sizeof(float));
+  h->o_wp = take(3 * V * sizeof(float));
+  h->o_bp = take(3 * V * sizeof(float));
+  h->o_J = take(3 * V * sizeof(float));
+  h->o_c = take(V * sizeof(float));
+  h->o_I1w = take(V * sizeof(float));
+  h->o_ut = take(3 * V * sizeof(float));
+  h->o_io_f = take(V * sizeof(float));
+  h->o_io_m = take(V * sizeof(float));
+  h->o_io_u = take(3 * V * sizeof(float));
+  h->state_total = o;
+  o = 0;
+  h->o_red = take(4 * sizeof(unsigned));
+  h->o_twx = take(h->twx.size() * sizeof(float2));
+  h->o_twy = take(h->twy.size() * sizeof(float2));
+  h->o_twz = take(h->twz.size() * sizeof(float2));
+  h->o_posx = take(h->posx.size() * sizeof(int));
+  h->o_Kx = take(h->Kx.size() * sizeof(float));
+  h->o_Ky = take(h->Ky.size() * sizeof(float));
+  h->o_Kz = take(h->Kz.size() * sizeof(float));
+  h->table_total = o;
+  *out = h;
+  return NADMM_OK;
+}
+
+void destroy_context(nadmm_context* h) {
+  if (!h) return;
+  invalidate_graph(h);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  for (cudaStream_t s : h->lane_cap) cudaStreamDestroy(s);
+  for (cudaEvent_t e : h->lane_ev) cudaEventDestroy(e);
+  for (nadmm_context* p : h->pairs) destroy_context(p);
+  delete h;
+}
+
+// Longest-first greedy split of the pairs over `lanes` graph branches
+// (balanced by voxel count), then the batched workspace layout: one state
+// region per lane, sized for its largest pair, followed by every pair's
+// tables.
+void assign_lanes(nadmm_context* b, int lanes) {
+  const int n = (int)b->pairs.size();
+  b->lanes = lanes;
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b->pairs[x]->V > b->pairs[y]->V; });
+  std::vector<size_t> load(lanes, 0), state(lanes, 0);
+  b->lane_of.assign(n, 0);
+  for (int i : order) {
+    int best = 0;
+    for (int l = 1; l < lanes; ++l)
+      if (load[l] < load[best]) best = l;
+    b->lane_of[i] = best;
+    load[best] += b->pairs[i]->V;
+    state[best] = std::max(state[best], b->pairs[i]->state_total);
+  }
+  size_t o = 0;
+  b->lane_off.assign(lanes, 0);
+  for (int l = 0; l < lanes; ++l) {
+    b->lane_off[l] = o;
+    o = align_up(o + state[l]);
+  }
+  b->tab_off.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    b->tab_off[i] = o;
+    o = align_up(o + b->pairs[i]->table_total);
+  }
+  b->total = o;
+}
+
+// Every pass kernel may take up to the opt-in shared-memory limit; the
+// attribute is per function and process-wide, so it is set once to the
+// maximum and each launch asks for what its grid needs.
+cudaError_t configure_kernels_once() {
+  static std::once_flag once;
+  static cudaError_t result = cudaSuccess;
+  std::call_once(once, [] { result = configure_admm_kernels(kMaxSmem, kMaxSmem); });
+  return result;
+}
+
+// Attach the state region ws and the table region wt to a single-grid
+// context: upload the tables, clear the status words, encode the z-pass
+// tensor map.
+nadmm_status attach(nadmm_context* h, char* ws, char* wt) {
+  invalidate_graph(h);
+  h->ws = ws;
+  h->wt = wt;
+  struct Up { size_t off; const void* src; size_t n; } ups[] = {
+      {h->o_twx, h->twx.data(), h->twx.size() * sizeof(float2)},
+      {h->o_twy, h->twy.data(), h->twy.size() * sizeof(float2)},
+      {h->o_twz, h->twz.data(), h->twz.size() * sizeof(float2)},
+      {h->o_posx, h->posx.data(), h->posx.size() * sizeof(int)},
+      {h->o_Kx, h->Kx.data(), h->Kx.size() * sizeof(float)},
+      {h->o_Ky, h->Ky.data(), h->Ky.size() * sizeof(float)},
+      {h->o_Kz, h->Kz.data(), h->Kz.size() * sizeof(float)},
+  };
+  cudaError_t e = cudaSuccess;
+  for (const Up& u : ups) {
+    e = cudaMemcpy(wt + u.off, u.src, u.n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) break;
+  }
+  if (e == cudaSuccess) e = cudaMemset(wt + h->o_red, 0, 4 * sizeof(unsigned));
+  if (e != cudaSuccess) {
+    h->ws = h->wt = nullptr;
+    return cuda_fail(e, "upload of FFT tables");
+  }
+  PencilArgs pa = pencil_args(h);
+  e = encode_pencil_map(pa);
+  if (e != cudaSuccess) {
+    h->ws = h->wt = nullptr;
+    return cuda_fail(e, "cuTensorMapEncodeTiled");
+  }
+  h->zmap = pa.zmap;
+  return NADMM_OK;
+}
+
+// Read and clear one context's device status word (stream already synced).
+nadmm_status read_status(nadmm_context* h) {
+  unsigned word = 0;
+  unsigned* dev = h->tab<unsigned>(h->o_red) + 2;
+  cudaError_t e = cudaMemcpy(&word, dev, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(dev, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (word & kStatusTimeout)
+    return fail(NADMM_ERR_TIMEOUT, "a kernel's bounded wait for its bulk copies expired");
+  if (word & kStatusNonfinite)
+    return fail(NADMM_ERR_NONFINITE, "non-finite velocity met in the bound step");
+  return NADMM_OK;
+}
+
+// Capture fn(stream) into h's graph (re-captured when key changes), then replay.
+template <class F>
+nadmm_status replay(nadmm_context* h, const std::vector<const void*>& key, cudaStream_t stream,
+                    const char* what, F&& fn) {
+  if (!h->gexec || h->gkey != key) {
     invalidate_graph(h);
     cudaError_t e;
     if (!h->cap) {
@@ -307,12 +516,12 @@ nadmm_status run_register(nadmm_context* h, const float* I0, const float* I1, fl
     }
     e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    cudaError_t le = enqueue_register(h, I0, I1, u_out, h->cap);
+    cudaError_t le = fn(h->cap);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(h->cap, &g);
     if (le != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
-      return cuda_fail(le, "capture of nadmm_register");
+      return cuda_fail(le, what);
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(&h->gexec, g, 0);
@@ -321,12 +530,57 @@ nadmm_status run_register(nadmm_context* h, const float* I0, const float* I1, fl
       h->gexec = nullptr;
       return cuda_fail(e, "cudaGraphInstantiate");
     }
-    h->gkey[0] = I0;
-    h->gkey[1] = I1;
-    h->gkey[2] = u_out;
+    h->gkey = key;
   }
   cudaError_t e = cudaGraphLaunch(h->gexec, stream);
   return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+// Streams and events of the lanes (created outside any stream capture).
+cudaError_t ensure_lanes(nadmm_context* b) {
+  if ((int)b->lane_cap.size() == b->lanes) return cudaSuccess;
+  for (cudaStream_t q : b->lane_cap) cudaStreamDestroy(q);
+  for (cudaEvent_t ev : b->lane_ev) cudaEventDestroy(ev);
+  b->lane_cap.clear();
+  b->lane_ev.clear();
+  for (int l = 0; l < b->lanes; ++l) {
+    cudaStream_t q;
+    TRY(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+    b->lane_cap.push_back(q);
+  }
+  for (int l = 0; l <= b->lanes; ++l) {
+    cudaEvent_t ev;
+    TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    b->lane_ev.push_back(ev);
+  }
+  return cudaSuccess;
+}
+
+// All pairs of a batched handle: lane l's pairs in order on its own stream,
+// the lanes forked from and joined back into `s`.
+cudaError_t enqueue_batched(nadmm_context* b, const float* const* I0, const float* const* I1,
+                            float* const* u_out, cudaStream_t s) {
+  const int n = (int)b->pairs.size();
+  TRY(cudaEventRecord(b->lane_ev[0], s));
+  for (int l = 0; l < b->lanes; ++l) {
+    cudaStream_t q = b->lane_cap[l];
+    TRY(cudaStreamWaitEvent(q, b->lane_ev[0], 0));
+    for (int i = 0; i < n; ++i)
+      if (b->lane_of[i] == l) TRY(enqueue_register(b->pairs[i], I0[i], I1[i], u_out[i], q));
+    TRY(cudaEventRecord(b->lane_ev[1 + l], q));
+    TRY(cudaStreamWaitEvent(s, b->lane_ev[1 + l], 0));
+  }
+  return cudaSuccess;
+}
+
+nadmm_status run_register(nadmm_context* h, const float* I0, const float* I1, float* u_out,
+                          cudaStream_t stream) {
+  if (h->cfg.flags & NADMM_FLAG_NO_GRAPH) {
+    cudaError_t e = enqueue_register(h, I0, I1, u_out, stream);
+    return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_register");
+  }
+  return replay(h, {I0, I1, u_out}, stream, "capture of nadmm_register",
+                [&](cudaStream_t cs) { return enqueue_register(h, I0, I1, u_out, cs); });
 }
 
 }  // namespace
@@ -371,91 +625,51 @@ const char* nadmm_status_string(nadmm_status s) {
 nadmm_status nadmm_create(const nadmm_config* cfg, nadmm_handle* out) {
   if (!out) return fail(NADMM_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  nadmm_status st = validate(cfg);
+  nadmm_context* h = nullptr;
+  nadmm_status st = create_single(cfg, &h);
   if (st != NADMM_OK) return st;
-  nadmm_context* h = new nadmm_context();
-  h->cfg = *cfg;
-  if (!factor_axis(cfg->nx, h->px, true) || !factor_axis(cfg->ny, h->py, true) || !factor_axis(cfg->nz, h->pz, true)) {
-    delete h;
-    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "no radix plan for these dimensions");
-  }
-  h->V = (size_t)cfg->nx * cfg->ny * cfg->nz;
-  h->nkx = (size_t)cfg->nx / 2 + 1;
-  {
-    PlaneArgs pa;
-    std::memset(&pa, 0, sizeof(pa));
-    pa.nx = cfg->nx;
-    pa.ny = cfg->ny;
-    pa.nz = cfg->nz;
-    pa.px = h->px;
-    finish_plane_args(pa);
-    PencilArgs qa;
-    std::memset(&qa, 0, sizeof(qa));
-    qa.ny = cfg->ny;
-    qa.nz = cfg->nz;
-    qa.nkx = (int)h->nkx;
-    qa.py = h->py;
-    qa.pz = h->pz;
-    finish_pencil_args(qa);
-    h->R = pa.R;
-    h->plane_smem = plane_smem_max(pa);
-    h->pencil_smem = pencil_smem_bytes(qa);
-  }
-  if (h->pencil_smem > 227 * 1024 || h->plane_smem > 227 * 1024) {
-    delete h;
-    return fail(NADMM_ERR_UNSUPPORTED_SIZE,
-                "a pass's shared-memory tile exceeds the 227 KB per CTA (nx too large)");
-  }
-  if (cfg->nz > 256) {
-    delete h;
-    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "nz must be <= 256 (one TMA box spans the z axis)");
-  }
-  h->twx = axis_twiddles(h->px);
-  h->twy = axis_twiddles(h->py);
-  h->twz = axis_twiddles(h->pz);
-  h->posx = pos_table(h->px);
-  h->Kx = symbol_natural(cfg->nx, (int)h->nkx);
-  h->Ky = symbol_by_position(h->py);
-  h->Kz = symbol_by_position(h->pz);
-  compute_beta(h);
-  // workspace layout
-  const size_t V = h->V;
-  size_t o = 0;
-  auto take = [&](size_t bytes) {
-    size_t r = o;
-    o = align_up(o + bytes);
-    return r;
-  };
-  h->o_spec = take(3 * h->nkx * cfg->ny * cfg->nz * sizeof(float2));
-  h->o_y = take(3 * V * sizeof(float));
-  h->o_wp = take(3 * V * sizeof(float));
-  h->o_bp = take(3 * V * sizeof(float));
-  h->o_J = take(3 * V * sizeof(float));
-  h->o_c = take(V * sizeof(float));
-  h->o_I1w = take(V * sizeof(float));
-  h->o_ut = take(3 * V * sizeof(float));
-  h->o_io_f = take(V * sizeof(float));
-  h->o_io_m = take(V * sizeof(float));
-  h->o_io_u = take(3 * V * sizeof(float));
-  h->o_red = take(4 * sizeof(unsigned));
-  h->o_twx = take(h->twx.size() * sizeof(float2));
-  h->o_twy = take(h->twy.size() * sizeof(float2));
-  h->o_twz = take(h->twz.size() * sizeof(float2));
-  h->o_posx = take(h->posx.size() * sizeof(int));
-  h->o_Kx = take(h->Kx.size() * sizeof(float));
-  h->o_Ky = take(h->Ky.size() * sizeof(float));
-  h->o_Kz = take(h->Kz.size() * sizeof(float));
-  h->total = o;
+  h->total = align_up(h->state_total) + h->table_total;
   *out = h;
   return NADMM_OK;
 }
 
-void nadmm_destroy(nadmm_handle h) {
-  if (!h) return;
-  invalidate_graph(h);
-  if (h->cap) cudaStreamDestroy(h->cap);
-  delete h;
+nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, const int32_t* dims,
+                                  nadmm_handle* out) {
+  if (!out) return fail(NADMM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!base || !dims) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
+  if (npairs < 1) return fail(NADMM_ERR_INVALID_ARG, "npairs must be >= 1");
+  nadmm_context* b = new nadmm_context();
+  b->cfg = *base;
+  b->batched = true;
+  for (int i = 0; i < npairs; ++i) {
+    nadmm_config c = *base;
+    c.nx = dims[3 * i];
+    c.ny = dims[3 * i + 1];
+    c.nz = dims[3 * i + 2];
+    nadmm_context* p = nullptr;
+    nadmm_status st = create_single(&c, &p);
+    if (st != NADMM_OK) {
+      g_err = "pair " + std::to_string(i) + ": " + g_err;
+      destroy_context(b);
+      return st;
+    }
+    b->pairs.push_back(p);
+  }
+  assign_lanes(b, std::min(npairs, kDefaultLanes));
+  *out = b;
+  return NADMM_OK;
 }
+
+nadmm_status nadmm_batch_set_lanes(nadmm_handle h, int32_t lanes) {
+  if (!h || !h->batched) return fail(NADMM_ERR_INVALID_ARG, "not a batched handle");
+  if (lanes < 1) return fail(NADMM_ERR_INVALID_ARG, "lanes must be >= 1");
+  if (h->wt) return fail(NADMM_ERR_INVALID_ARG, "set the lane count before nadmm_set_workspace");
+  assign_lanes(h, std::min<int>(lanes, (int)h->pairs.size()));
+  return NADMM_OK;
+}
+
+void nadmm_destroy(nadmm_handle h) { destroy_context(h); }
 
 nadmm_status nadmm_workspace_size(nadmm_handle h, size_t* bytes) {
   if (!h || !bytes) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
@@ -469,45 +683,30 @@ nadmm_status nadmm_set_workspace(nadmm_handle h, void* dev_ptr, size_t bytes) {
     return fail(NADMM_ERR_ALIGNMENT, "workspace must be 256-byte aligned");
   if (bytes < h->total) return fail(NADMM_ERR_NO_WORKSPACE, "workspace smaller than nadmm_workspace_size");
   invalidate_graph(h);
-  h->ws = static_cast<char*>(dev_ptr);
-  h->ws_bytes = bytes;
-  cudaError_t e;
-  if (!h->kernels_configured) {
-    e = configure_admm_kernels(h->plane_smem, h->pencil_smem);
-    if (e != cudaSuccess) {
-      h->ws = nullptr;
-      return cuda_fail(e, "cudaFuncSetAttribute");
+  h->ws = h->wt = nullptr;
+  char* base = static_cast<char*>(dev_ptr);
+  cudaError_t e = configure_kernels_once();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  if (!h->batched) {
+    nadmm_status st = attach(h, base, base + align_up(h->state_total));
+    if (st != NADMM_OK) return st;
+  } else {
+    for (size_t i = 0; i < h->pairs.size(); ++i) {
+      nadmm_context* p = h->pairs[i];
+      nadmm_status st = attach(p, base + h->lane_off[h->lane_of[i]], base + h->tab_off[i]);
+      if (st != NADMM_OK) {
+        for (nadmm_context* q : h->pairs) q->ws = q->wt = nullptr;
+        return st;
+      }
     }
-    h->kernels_configured = true;
-  }
-  struct Up { size_t off; const void* src; size_t n; } ups[] = {
-      {h->o_twx, h->twx.data(), h->twx.size() * sizeof(float2)},
-      {h->o_twy, h->twy.data(), h->twy.size() * sizeof(float2)},
-      {h->o_twz, h->twz.data(), h->twz.size() * sizeof(float2)},
-      {h->o_posx, h->posx.data(), h->posx.size() * sizeof(int)},
-      {h->o_Kx, h->Kx.data(), h->Kx.size() * sizeof(float)},
-      {h->o_Ky, h->Ky.data(), h->Ky.size() * sizeof(float)},
-      {h->o_Kz, h->Kz.data(), h->Kz.size() * sizeof(float)},
-  };
-  for (const Up& u : ups) {
-    e = cudaMemcpy(h->ws + u.off, u.src, u.n, cudaMemcpyHostToDevice);
+    e = ensure_lanes(h);
     if (e != cudaSuccess) {
-      h->ws = nullptr;
-      return cuda_fail(e, "upload of FFT tables");
+      for (nadmm_context* q : h->pairs) q->ws = q->wt = nullptr;
+      return cuda_fail(e, "lane streams");
     }
+    h->ws = base;
+    h->wt = base;
   }
-  e = cudaMemset(h->ws + h->o_red, 0, 4 * sizeof(unsigned));
-  if (e != cudaSuccess) {
-    h->ws = nullptr;
-    return cuda_fail(e, "cudaMemset");
-  }
-  PencilArgs pa = pencil_args(h);
-  e = encode_pencil_map(pa);
-  if (e != cudaSuccess) {
-    h->ws = nullptr;
-    return cuda_fail(e, "cuTensorMapEncodeTiled");
-  }
-  h->zmap = pa.zmap;
   return NADMM_OK;
 }
 
@@ -581,20 +780,51 @@ nadmm_status nadmm_register_profiled(nadmm_handle h, const float* fixed, const f
 }
 
 nadmm_status nadmm_get_status(nadmm_handle h, void* stream) {
-  nadmm_status st = need_ws(h);
-  if (st != NADMM_OK) return st;
+  if (!h) return fail(NADMM_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->wt) return fail(NADMM_ERR_NO_WORKSPACE, "no workspace attached (nadmm_set_workspace)");
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  unsigned word = 0;
-  unsigned* dev = h->at<unsigned>(h->o_red) + 2;
-  e = cudaMemcpy(&word, dev, sizeof(unsigned), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemset(dev, 0, sizeof(unsigned));
-  if (e != cudaSuccess) return cuda_fail(e, "status read");
-  if (word & kStatusTimeout)
-    return fail(NADMM_ERR_TIMEOUT, "a kernel's bounded wait for its bulk copies expired");
-  if (word & kStatusNonfinite)
-    return fail(NADMM_ERR_NONFINITE, "non-finite velocity met in the bound step");
-  return NADMM_OK;
+  if (!h->batched) return read_status(h);
+  nadmm_status worst = NADMM_OK;
+  std::string msg;
+  for (size_t i = 0; i < h->pairs.size(); ++i) {
+    nadmm_status st = read_status(h->pairs[i]);
+    if (st != NADMM_OK && worst == NADMM_OK) {
+      worst = st;
+      msg = "pair " + std::to_string(i) + ": " + g_err;
+    }
+  }
+  if (worst != NADMM_OK) g_err = msg;
+  return worst;
+}
+
+nadmm_status nadmm_register_batched(nadmm_handle h, const float* const* fixed,
+                                    const float* const* moving, float* const* u_out, void* stream) {
+  nadmm_status st = need_ws(h, true);
+  if (st != NADMM_OK) return st;
+  if (!fixed || !moving || !u_out) return fail(NADMM_ERR_INVALID_ARG, "NULL pointer array");
+  const int n = (int)h->pairs.size();
+  std::vector<const void*> key;
+  key.reserve(3 * n);
+  for (int i = 0; i < n; ++i) {
+    if ((st = check_dev_ptrs({fixed[i], moving[i], u_out[i]})) != NADMM_OK) {
+      g_err = "pair " + std::to_string(i) + ": " + g_err;
+      return st;
+    }
+    key.push_back(fixed[i]);
+    key.push_back(moving[i]);
+    key.push_back(u_out[i]);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->cfg.flags & NADMM_FLAG_NO_GRAPH) {
+    for (int i = 0; i < n; ++i) {
+      cudaError_t e = enqueue_register(h->pairs[i], fixed[i], moving[i], u_out[i], s);
+      if (e != cudaSuccess) return cuda_fail(e, "nadmm_register_batched");
+    }
+    return NADMM_OK;
+  }
+  return replay(h, key, s, "capture of nadmm_register_batched",
+                [&](cudaStream_t cs) { return enqueue_batched(h, fixed, moving, u_out, cs); });
 }
 
 nadmm_status nadmm_spectral_solve(nadmm_handle h, const float* y, float* w, void* stream) {
@@ -663,7 +893,7 @@ nadmm_status nadmm_bound_compose(nadmm_handle h, const float* w, const float* u_
   if (st != NADMM_OK) return st;
   if ((st = check_dev_ptrs({w, u_in, u_out})) != NADMM_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  unsigned* red = h->at<unsigned>(h->o_red);
+  unsigned* red = h->tab<unsigned>(h->o_red);
   cudaError_t e = cudaMemsetAsync(red, 0, 2 * sizeof(unsigned), s);
   if (e == cudaSuccess) e = launch_bound_reduce(dims_of(h), w, red, s);
   if (e == cudaSuccess)
@@ -675,6 +905,7 @@ nadmm_status nadmm_bound_compose(nadmm_handle h, const float* w, const float* u_
 nadmm_status nadmm_jacobian_det(nadmm_handle h, const float* u, float* det, uint32_t* nonpositive,
                                 void* stream) {
   if (!h) return fail(NADMM_ERR_INVALID_ARG, "handle is NULL");
+  if (h->batched) return fail(NADMM_ERR_INVALID_ARG, "a batched handle only takes the *_batched calls");
   if (nadmm_status st = check_dev_ptrs({u}); st != NADMM_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;

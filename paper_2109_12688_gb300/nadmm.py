@@ -69,6 +69,11 @@ _SIGS = {
                                                      ctypes.c_float, ctypes.c_float, _P, _P, _P]),
     "nadmm_register_profiled": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_float),
                                                ctypes.POINTER(ctypes.c_int32)]),
+    "nadmm_create_batched": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(_P)]),
+    "nadmm_batch_set_lanes": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "nadmm_register_batched": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                              ctypes.POINTER(_P), _P]),
 }
 
 
@@ -129,6 +134,26 @@ def nadmm_create(cfg):
     h = _P()
     _check(load().nadmm_create(ctypes.byref(cfg), ctypes.byref(h)))
     return h
+
+
+def nadmm_create_batched(base, dims_list):
+    n = len(dims_list)
+    arr = (ctypes.c_int32 * (3 * n))(*[int(v) for d in dims_list for v in d])
+    h = _P()
+    _check(load().nadmm_create_batched(ctypes.byref(base), n, arr, ctypes.byref(h)))
+    return h
+
+
+def nadmm_batch_set_lanes(h, lanes):
+    _check(load().nadmm_batch_set_lanes(h, lanes))
+
+
+def nadmm_register_batched(h, fixed, moving, u_out, stream=None):
+    n = len(fixed)
+    if len(moving) != n or len(u_out) != n:
+        raise ValueError("fixed, moving and u_out need one entry per pair")
+    arr = lambda xs: (_P * n)(*[_ptr(x) for x in xs])
+    _check(load().nadmm_register_batched(h, arr(fixed), arr(moving), arr(u_out), _stream(stream)))
 
 
 def nadmm_destroy(h):
@@ -260,3 +285,30 @@ class Registration:
             self.close()
         except Exception:
             pass
+
+
+class BatchedRegistration(Registration):
+    """A batched handle (pairs of different grid sizes) plus its workspace."""
+
+    def __init__(self, dims_list, device="cuda", lanes=None, **kw):
+        import torch
+        self.dims_list = [tuple(d) for d in dims_list]
+        self.cfg = make_config(self.dims_list[0], **kw)
+        self.handle = nadmm_create_batched(self.cfg, self.dims_list)
+        if lanes is not None:
+            nadmm_batch_set_lanes(self.handle, lanes)
+        nbytes = nadmm_workspace_size(self.handle)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        nadmm_set_workspace(self.handle, self._ws_ptr, nbytes)
+
+    def register(self, fixed, moving, u_out=None, stream=None):
+        import torch
+        if u_out is None:
+            u_out = [torch.empty((3, nz, ny, nx), dtype=torch.float32, device=f.device)
+                     for (nx, ny, nz), f in zip(self.dims_list, fixed)]
+        if stream is None:
+            stream = torch.cuda.current_stream(fixed[0].device)
+        nadmm_register_batched(self.handle, fixed, moving, u_out, stream)
+        return u_out

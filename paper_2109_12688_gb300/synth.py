@@ -203,3 +203,29 @@ def random_field(shape, seed, scale=1.0):
     """Seeded float32 normal field of the given shape."""
     rng = np.random.default_rng(seed)
     return (scale * rng.normal(size=shape)).astype(np.float32)
+
+
+BATCH_XY = (96, 112, 128, 144, 160)
+BATCH_Z = (64, 80, 96, 112)
+
+
+def draw_batch_dims(npairs, seed):
+    """Grid sizes of a batch of uneven pairs: nx, ny uniform from
+    {96, 112, 128, 144, 160}, nz uniform from {64, 80, 96, 112} (multiples of
+    16, so every prime factor is 2, 3, 5 or 7).  Returns a list of (nx, ny, nz)."""
+    rng = np.random.default_rng(seed)
+    return [(int(rng.choice(BATCH_XY)), int(rng.choice(BATCH_XY)), int(rng.choice(BATCH_Z)))
+            for _ in range(npairs)]
+
+
+def phase_pair(dims, seed, noise=0.02):
+    """A cheap pair for large batches: two independent phantoms (different
+    centre offsets, radii and myocardial thickness, as between two cardiac
+    phases) with noise on the fixed one.  Returns float32 (fixed, moving)."""
+    dims = tuple(int(d) for d in dims)
+    rng = np.random.default_rng(seed)
+    fixed, _ = phantom(dims, rng)
+    fixed = fixed + rng.normal(0.0, noise, fixed.shape)
+    moving, _ = phantom(dims, np.random.default_rng(seed + 1_000_003))
+    return (np.ascontiguousarray(fixed, dtype=np.float32),
+            np.ascontiguousarray(moving, dtype=np.float32))

@@ -114,3 +114,52 @@ def test_status_strings(lib):
     assert lib.nadmm_status_string(0) == "NADMM_OK"
     assert lib.nadmm_status_string(lib.NADMM_ERR_NONFINITE) == "NADMM_ERR_NONFINITE"
     assert "unknown" in lib.nadmm_status_string(99)
+
+
+def _ws_parts(dims):
+    nx, ny, nz = dims
+    V = nx * ny * nz
+    return 3 * (nx // 2 + 1) * ny * nz * 8 + (6 * 3 + 4) * V * 4
+
+
+def test_batched_create_layout(lib):
+    dims = [(32, 32, 24), (96, 96, 64), (20, 12, 14), (160, 160, 112), (12, 6, 7)]
+    h = lib.nadmm_create_batched(lib.make_config(dims[0]), dims)
+    ws = lib.nadmm_workspace_size(h)
+    # default: 4 lanes, largest pairs first -> lanes hold {160^2x112}, {96^2x64},
+    # {32^2x24, 12x6x7}, {20x12x14}: one state region per lane plus tables
+    states = [_ws_parts((160, 160, 112)), _ws_parts((96, 96, 64)), _ws_parts((32, 32, 24)),
+              _ws_parts((20, 12, 14))]
+    assert sum(states) <= ws <= sum(states) + 5 * 64 * 1024
+    lib.nadmm_batch_set_lanes(h, 1)  # one lane: the largest pair's state only
+    ws1 = lib.nadmm_workspace_size(h)
+    assert _ws_parts((160, 160, 112)) <= ws1 <= _ws_parts((160, 160, 112)) + 5 * 64 * 1024
+    lib.nadmm_batch_set_lanes(h, 99)  # clamped to npairs
+    assert lib.nadmm_workspace_size(h) >= sum(_ws_parts(d) for d in dims)
+    lib.nadmm_destroy(h)
+
+
+def test_batched_create_rejects_bad_pair(lib):
+    dims = [(32, 32, 24), (44, 8, 8)]
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_create_batched(lib.make_config(dims[0]), dims)
+    assert e.value.status == lib.NADMM_ERR_UNSUPPORTED_SIZE
+    assert "pair 1" in str(e.value)
+    with pytest.raises(lib.NadmmError):
+        lib.nadmm_create_batched(lib.make_config(dims[0]), [])
+
+
+def test_batched_handle_only_takes_batched_calls(lib):
+    h = lib.nadmm_create_batched(lib.make_config((32, 32, 24)), [(32, 32, 24), (16, 16, 8)])
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_register(h, 16, 16, 16)
+    assert e.value.status == lib.NADMM_ERR_INVALID_ARG
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_register_batched(h, [16, 16], [16, 16], [16, 16])
+    assert e.value.status == lib.NADMM_ERR_NO_WORKSPACE
+    lib.nadmm_destroy(h)
+    single = lib.nadmm_create(lib.make_config((32, 32, 24)))
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_batch_set_lanes(single, 2)
+    assert e.value.status == lib.NADMM_ERR_INVALID_ARG
+    lib.nadmm_destroy(single)

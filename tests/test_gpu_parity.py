@@ -319,3 +319,55 @@ def test_nonfinite_input_sets_status(lib):
     # the status word is cleared by the read, and a clean call reports OK
     reg.register(dev(pair["fixed"]), dev(pair["moving"]))
     assert lib.nadmm_get_status(reg.handle, torch.cuda.current_stream()) == lib.NADMM_OK
+
+
+# ------------------------------------------------------------------ 256 x 256 x 192
+LARGE = (256, 256, 192)
+
+
+@pytest.fixture(scope="module")
+def large_pair():
+    return synth.phase_pair(LARGE, seed=0)
+
+
+def test_large_spectral_solve_n3(lib):
+    nx, ny, nz = LARGE
+    reg = lib.Registration(LARGE, device=DEV, order_n=3)
+    y = synth.random_field((3, nz, ny, nx), seed=5)
+    w = empty((3, nz, ny, nx))
+    lib.nadmm_spectral_solve(reg.handle, dev(y), w, torch.cuda.current_stream())
+    ref = O.spectral_solve(y, 10.0, 0.1, 3)
+    got = host(w)
+    assert rel_l2(got, ref) <= 1e-6
+    assert np.abs(got - ref).max() <= 2e-6 * np.abs(y).max()
+
+
+def test_large_register_short_schedule_n3(lib, large_pair):
+    fixed, moving = large_pair
+    u_ref = O.register(fixed, moving, lam=10.0, theta=0.1, n=3, outer=1, inner=3)
+    reg = lib.Registration(LARGE, device=DEV, order_n=3, outer=1, inner=3)
+    u = host(reg.register(dev(fixed), dev(moving)))
+    assert np.abs(u - u_ref).max() <= 1e-3
+
+
+def test_large_register_full_schedule_n3(lib, large_pair):
+    """256 x 256 x 192, n = 3, 10 x 10: no folds, lower SSD, and the device
+    memory it needs (workspace + inputs + output) stays below 2 GB."""
+    fixed, moving = large_pair
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    base = torch.cuda.memory_allocated()
+    reg = lib.Registration(LARGE, device=DEV, order_n=3, outer=10, inner=10)
+    f, m = dev(fixed), dev(moving)
+    u = reg.register(f, m)
+    assert lib.nadmm_get_status(reg.handle, torch.cuda.current_stream()) == lib.NADMM_OK
+    torch.cuda.synchronize()
+    peak = torch.cuda.max_memory_allocated() - base
+    assert peak < 2 * 1024 ** 3
+    assert torch.isfinite(u).all()
+    cnt = torch.zeros(1, dtype=torch.int32, device=DEV)
+    lib.nadmm_jacobian_det(reg.handle, u, None, cnt, torch.cuda.current_stream())
+    assert int(cnt.item()) == 0
+    warped = O.warp(moving, host(u))
+    ssd0 = ((moving.astype(float) - fixed) ** 2).sum()
+    assert ((warped - fixed) ** 2).sum() < ssd0
