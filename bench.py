@@ -157,6 +157,11 @@ def parse_args():
     ap.add_argument("--orders", default="1,2,3",
                     help="regulariser orders registered per step (profiling runs use one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--workload", choices=("registration", "batch64", "large"),
+                    default="registration",
+                    help="registration: the 128x128x96 benchmark (default); batch64: 64 uneven "
+                         "pairs in one batched graph vs 64 sequential calls; large: one "
+                         "256x256x192 n=3 registration with its device-memory peak")
     return ap.parse_args()
 
 
@@ -207,6 +212,99 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_extra(args, rank, world):
+    """The batched (64 uneven pairs) and large (256x256x192) workloads, one
+    JSON line each; single GPU, device-resident inputs, events on the stream."""
+    import torch
+    if world > 1 and rank != 0:
+        return
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2109_12688_gb300 import nadmm, synth
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    kw = dict(lam=LAM, theta=THETA, outer=OUTER, inner=INNER)
+
+    def timed(fn):
+        for i in range(args.warmup):
+            flush.fill_(i & 0xFF)
+            fn()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        time.sleep(0.3)
+        total = 0.0
+        for i in range(args.steps):
+            flush.fill_((i + 7) & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        return total / args.steps, clocks.stop()
+
+    if args.workload == "batch64":
+        dims = synth.draw_batch_dims(64, seed=1234)
+        data = [synth.phase_pair(d, seed=i) for i, d in enumerate(dims)]
+        I0 = [torch.from_numpy(f).to(dev) for f, _ in data]
+        I1 = [torch.from_numpy(m).to(dev) for _, m in data]
+        breg = nadmm.BatchedRegistration(dims, device=dev, order_n=2, **kw)
+        U = [torch.empty((3, d[2], d[1], d[0]), device=dev) for d in dims]
+        ms, clk = timed(lambda: nadmm.nadmm_register_batched(breg.handle, I0, I1, U, stream))
+        del breg
+        regs = [nadmm.Registration(d, device=dev, order_n=2, **kw) for d in dims]
+
+        def sequential():
+            for r, a, b, u in zip(regs, I0, I1, U):
+                nadmm.nadmm_register(r.handle, a, b, u, stream)
+        seq_ms, _ = timed(sequential)
+        vox = sum(d[0] * d[1] * d[2] for d in dims)
+        line = {
+            "metric": "ms per batch of 64 uneven pairs", "value": ms, "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "64 pairs, nx, ny from {96,112,128,144,160}, nz from "
+                                   "{64,80,96,112} (seed 1234), two-phase phantoms, n=2, 10 x 10 "
+                                   "iterations, one batched graph with 4 lanes",
+                       "voxels": vox,
+                       "l2": "flushed between timed steps (256 MB write outside the step events)"},
+            "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms,
+            "voxel_admm_iters_per_s": vox * OUTER * INNER / (ms / 1e3),
+            "clocks": clk,
+        }
+    else:
+        dims = (256, 256, 192)
+        f, m = synth.phase_pair(dims, seed=0)
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats(dev)
+        base = torch.cuda.memory_allocated(dev)
+        I0 = torch.from_numpy(f).to(dev)
+        I1 = torch.from_numpy(m).to(dev)
+        reg = nadmm.Registration(dims, device=dev, order_n=3, **kw)
+        U = torch.empty((3, 192, 256, 256), device=dev)
+        ms, clk = timed(lambda: nadmm.nadmm_register(reg.handle, I0, I1, U, stream))
+        peak = torch.cuda.max_memory_allocated(dev) - base
+        V = 256 * 256 * 192
+        line = {
+            "metric": "ms per 256x256x192 registration", "value": ms, "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "256x256x192 two-phase phantom pair, n=3, 10 x 10 iterations",
+                       "l2": "inputs larger than L2; 256 MB flush between steps"},
+            "voxel_admm_iters_per_s": V * OUTER * INNER / (ms / 1e3),
+            "device_bytes_peak": peak,
+            "workspace_bytes": nadmm.nadmm_workspace_size(reg.handle),
+            "clocks": clk,
+        }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -214,6 +312,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload != "registration":
+        run_extra(args, rank, world)
         return
 
     import numpy as np
