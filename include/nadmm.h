@@ -60,13 +60,19 @@ typedef enum nadmm_status {
   NADMM_ERR_NO_WORKSPACE = 4,     /* workspace missing or too small            */
   NADMM_ERR_CUDA = 5,             /* a CUDA runtime call failed                */
   NADMM_ERR_NONFINITE = 6,        /* device status: NaN/Inf met in a bound step */
-  NADMM_ERR_TIMEOUT = 7           /* device status: a kernel's bounded wait for its
+  NADMM_ERR_TIMEOUT = 7,          /* device status: a kernel's bounded wait for its
                                      own bulk copies expired; the kernel returned */
+  NADMM_ERR_NO_SAVED_FORWARD = 8  /* nadmm_backward without a saved forward pass   */
 } nadmm_status;
 
 /* flags */
 #define NADMM_FLAG_NO_GRAPH 1u    /* launch kernels directly instead of replaying
                                      a captured CUDA graph                      */
+#define NADMM_FLAG_SAVE_FOR_BACKWARD 2u /* keep what nadmm_backward needs: u at the
+                                     start of every outer step (outer_iters x 3V
+                                     floats) plus the reverse-sweep scratch
+                                     (2 inner_iters + 16 vector fields); single
+                                     handles only                               */
 
 typedef struct nadmm_config {
   int32_t nx, ny, nz;         /* grid (M, N, H); see NADMM_ERR_UNSUPPORTED_SIZE */
@@ -249,6 +255,51 @@ nadmm_status nadmm_jacobian_det(nadmm_handle h, const float* u, float* det,
 nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, int32_t order_n,
                                           float lambda, float theta, const float* y, float* w,
                                           void* stream);
+
+/* ---------------------------------------------------------------------
+ * Reverse mode (gradients through the registration).  The paper has no
+ * counterpart; it differentiates Sec. 2's outer loop around Eq. 5/6 with the
+ * s = 2 data step, so that the registration can sit inside a learned
+ * pipeline.  Conventions at the non-smooth points: a clamped sample
+ * coordinate passes no gradient unless strictly inside [0, dim - 1];
+ * sign(0) = 0; the maxima of the velocity bound share their gradient equally
+ * among the entries attaining them; s = min(1, kappa/max||Dw||,
+ * delta/max|w|) follows the first candidate, in that order, attaining it.
+ * --------------------------------------------------------------------- */
+
+/* Vector-Jacobian product of the last nadmm_register (or nadmm_register_host)
+ * on this handle, which must have NADMM_FLAG_SAVE_FOR_BACKWARD, data_term 2
+ * and lambda > 0:
+ *   fixed, moving: device [nz][ny][nx], the SAME data the forward pass used;
+ *   grad_u: device [3][nz][ny][nx], dL/du for the forward output u;
+ *   grad_fixed, grad_moving: device [nz][ny][nx], overwritten with dL/dI0,
+ *   dL/dI1 through the registration;
+ *   grad_lambda, grad_theta: device float (16-byte aligned) receiving
+ *   dL/dlambda, dL/dtheta, or NULL.
+ * Recomputes each outer step's ADMM iterates from the saved displacements
+ * (one forward sweep plus one reverse sweep of K spectral solves per outer
+ * step).  Captured into a CUDA graph (re-captured when a pointer changes)
+ * unless NADMM_FLAG_NO_GRAPH.  Scatter-adds use float atomics, so results
+ * may differ in the last bits between runs.
+ * Errors: INVALID_ARG, ALIGNMENT, NO_WORKSPACE, NO_SAVED_FORWARD, CUDA. */
+nadmm_status nadmm_backward(nadmm_handle h, const float* fixed, const float* moving,
+                            const float* grad_u, float* grad_fixed, float* grad_moving,
+                            float* grad_lambda, float* grad_theta, void* stream);
+
+/* Loss L = 1/2 sum_x (I1(x + u(x)) - I0(x))^2 (trilinear, clamped), the
+ * quantity whose gradients the reverse mode is tested on:
+ * fixed, moving device [nz][ny][nx]; u device [3][nz][ny][nx];
+ * loss: device float (16-byte aligned), summed in double, stored as float. */
+nadmm_status nadmm_ssd_after_warp(nadmm_handle h, const float* fixed, const float* moving,
+                                  const float* u, float* loss, void* stream);
+
+/* Gradient of the loss above scaled by the device scalar grad_loss:
+ * grad_fixed (or NULL), grad_moving, grad_u (or NULL) overwritten, device,
+ * shaped like fixed, moving and u. */
+nadmm_status nadmm_ssd_after_warp_backward(nadmm_handle h, const float* fixed,
+                                           const float* moving, const float* u,
+                                           const float* grad_loss, float* grad_fixed,
+                                           float* grad_moving, float* grad_u, void* stream);
 
 /* ---------------------------------------------------------------------
  * Measurement

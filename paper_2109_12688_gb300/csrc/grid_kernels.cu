@@ -7,43 +7,10 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "grid_common.cuh"
 #include "nadmm_internal.h"
 
 namespace nadmm {
-
-// (1 - t) a + t b, exact at t = 0 and t = 1 (a sample on a grid point, or
-// clamped to the last one, returns the grid value itself)
-__device__ __forceinline__ float lerp(float a, float b, float t) {
-  return fmaf(t, b, fmaf(-t, a, a));
-}
-
-__device__ __forceinline__ float trilerp(const float* __restrict__ f, Dims d, float px, float py,
-                                         float pz) {
-  px = fminf(fmaxf(px, 0.0f), (float)(d.nx - 1));
-  py = fminf(fmaxf(py, 0.0f), (float)(d.ny - 1));
-  pz = fminf(fmaxf(pz, 0.0f), (float)(d.nz - 1));
-  int ix = min((int)floorf(px), d.nx - 2);
-  int iy = min((int)floorf(py), d.ny - 2);
-  int iz = min((int)floorf(pz), d.nz - 2);
-  float fx = px - (float)ix, fy = py - (float)iy, fz = pz - (float)iz;
-  const size_t sx = 1, sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
-  const float* p = f + (size_t)iz * sz + (size_t)iy * sy + ix;
-  float c000 = __ldg(p), c001 = __ldg(p + sx);
-  float c010 = __ldg(p + sy), c011 = __ldg(p + sy + sx);
-  float c100 = __ldg(p + sz), c101 = __ldg(p + sz + sx);
-  float c110 = __ldg(p + sz + sy), c111 = __ldg(p + sz + sy + sx);
-  float c00 = lerp(c000, c001, fx);
-  float c01 = lerp(c010, c011, fx);
-  float c10 = lerp(c100, c101, fx);
-  float c11 = lerp(c110, c111, fx);
-  float c0 = lerp(c00, c01, fy);
-  float c1 = lerp(c10, c11, fy);
-  return lerp(c0, c1, fz);
-}
-
-// Block (32, 8) covers 32 x-consecutive voxels of 8 rows; grid (nx/32, ny/8,
-// z-slices).  Coordinates come from the block indices (no division).
-constexpr int kBX = 32, kBY = 8;
 
 // I1w(x) = I1(x + u(x)).  Also clears the bound reduction words of the next
 // outer step (the compose that read them has completed).
@@ -95,22 +62,17 @@ __global__ void __launch_bounds__(kBX * kBY) k_bound_reduce(Dims d, const float*
   pdl_wait();
   pdl_trigger();
   const size_t V = (size_t)d.nx * d.ny * d.nz;
-  const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
   float mabs = 0.0f, mjac = 0.0f;
   if (x < d.nx && y < d.ny) {
     for (int z = blockIdx.z; z < d.nz; z += gridDim.z) {
       const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
-      const size_t xp = i + (x + 1 < d.nx ? 1 : 0), xm = i - (x > 0 ? 1 : 0);
-      const size_t yp = i + (y + 1 < d.ny ? sy : 0), ym = i - (y > 0 ? sy : 0);
-      const size_t zp = i + (z + 1 < d.nz ? sz : 0), zm = i - (z > 0 ? sz : 0);
+      const Nbr nb = neighbours(d, x, y, z, i);
 #pragma unroll
       for (int comp = 0; comp < 3; ++comp) {
         const float* f = w + comp * V;
         const float a = fabsf(__ldg(f + i));
-        const float row = fabsf(0.5f * (__ldg(f + xp) - __ldg(f + xm))) +
-                          fabsf(0.5f * (__ldg(f + yp) - __ldg(f + ym))) +
-                          fabsf(0.5f * (__ldg(f + zp) - __ldg(f + zm)));
+        const float row = jacobian_row(f, nb);
         // fmaxf drops NaN; keep it visible through the bit-pattern max instead
         mabs = (a != a || a > mabs) ? a : mabs;
         mjac = (row != row || row > mjac) ? row : mjac;
@@ -136,20 +98,6 @@ __global__ void __launch_bounds__(kBX * kBY) k_bound_reduce(Dims d, const float*
     atomicMax(red, ua);
     atomicMax(red + 1, uj);
   }
-}
-
-__device__ __forceinline__ float bound_factor(const unsigned* red, float kappa, float delta,
-                                              unsigned* status) {
-  float mabs = __uint_as_float(red[0]);
-  float mjac = __uint_as_float(red[1]);
-  if (!isfinite(mabs) || !isfinite(mjac)) {
-    if (status) atomicOr(status, 1u);
-    return 0.0f;
-  }
-  float s = 1.0f;
-  if (isfinite(kappa) && mjac > 0.0f) s = fminf(s, kappa / mjac);
-  if (isfinite(delta) && mabs > 0.0f) s = fminf(s, delta / mabs);
-  return s;
 }
 
 // u_out(x) = v(x) + u_in(x + v(x)), v = s w

@@ -53,14 +53,20 @@ struct nadmm_context {
   // after the state; the pairs of a batched handle that run one after
   // another on the same lane share one state region and own their tables.
   size_t o_spec, o_y, o_wp, o_bp, o_J, o_c, o_I1w, o_ut, o_io_f, o_io_m, o_io_u, state_total;
-  size_t o_red, o_twx, o_twy, o_twz, o_posx, o_Kx, o_Ky, o_Kz, table_total;
+  // reverse mode (NADMM_FLAG_SAVE_FOR_BACKWARD): u at the start of every
+  // outer step, the ADMM history w^k, b^k of one outer step, the rotating
+  // adjoint slots wbar/bbar (3 each) and the adjoint work fields
+  size_t o_tape = 0, o_hist = 0, o_adj = 0, o_g = 0, o_Sg = 0, o_gJ = 0, o_gc = 0, o_ub0 = 0,
+         o_ub1 = 0;
+  bool saved_forward = false;
+  size_t o_red, o_acc, o_twx, o_twy, o_twz, o_posx, o_Kx, o_Ky, o_Kz, table_total;
   size_t total;  // single handle: align(state_total) + table_total
   char* ws = nullptr;
   char* wt = nullptr;
   CUtensorMap zmap;  // z-pass tensor map of the workspace spectrum
-  // graph cache
-  cudaGraphExec_t gexec = nullptr;
-  std::vector<const void*> gkey;
+  // graph cache: slot 0 the forward registration, slot 1 the backward
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  std::vector<const void*> gkey[2];
   cudaStream_t cap = nullptr;
   // batched handle: the pairs, their lane (concurrent graph branch) and
   // the byte offsets of each lane's state and each pair's tables
@@ -87,9 +93,11 @@ bool good_factors(int n) {
 }
 
 void invalidate_graph(nadmm_context* h) {
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  h->gexec = nullptr;
-  h->gkey.clear();
+  for (int k = 0; k < 2; ++k) {
+    if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
+    h->gexec[k] = nullptr;
+    h->gkey[k].clear();
+  }
 }
 
 nadmm_status validate(const nadmm_config* c) {
@@ -112,7 +120,8 @@ nadmm_status validate(const nadmm_config* c) {
   if (!(c->eps > 0.0f) || !std::isfinite(c->eps)) return fail(NADMM_ERR_INVALID_ARG, "eps must be > 0");
   if (!(c->bound_kappa > 0.0f) || !(c->bound_delta > 0.0f))
     return fail(NADMM_ERR_INVALID_ARG, "bound_kappa and bound_delta must be > 0 (INFINITY disables)");
-  if (c->flags & ~NADMM_FLAG_NO_GRAPH) return fail(NADMM_ERR_INVALID_ARG, "unknown flag bits");
+  if (c->flags & ~(NADMM_FLAG_NO_GRAPH | NADMM_FLAG_SAVE_FOR_BACKWARD))
+    return fail(NADMM_ERR_INVALID_ARG, "unknown flag bits");
   return NADMM_OK;
 }
 
@@ -234,9 +243,12 @@ thread_local Profiler* g_prof = nullptr;
 
 // ADMM iterations k0 .. k0+steps-1 starting from `first` (plane pass that
 // starts iteration k0), then the final inverse transform into w_out/b_out.
+// With hist_w/hist_b (k0 = 0 only), w^k and b^k of every iteration are kept
+// in hist_w + k 3V and hist_b + k 3V (the last one is w_out/b_out).
 cudaError_t enqueue_inner(nadmm_context* h, PlaneArgs first, int in_first, bool prev_first, int k0,
                           int steps, const float* J, const float* c, float* w_out, float* b_out,
-                          cudaStream_t s) {
+                          cudaStream_t s, float* hist_w = nullptr, float* hist_b = nullptr) {
+  const size_t F3 = 3 * h->V * sizeof(float);
   first.J = J;
   first.c = c;
   first.beta = beta_for(h, k0);
@@ -250,6 +262,10 @@ cudaError_t enqueue_inner(nadmm_context* h, PlaneArgs first, int in_first, bool 
     KLAUNCH(NADMM_KC_PENCIL, s, launch_pencil(pa, s));
     a.beta = beta_for(h, k);
     KLAUNCH(k >= 2 ? NADMM_KC_PLANE : NADMM_KC_PLANE_K1, s, launch_plane(IN_SPEC, k >= 2, true, a, s));
+    if (hist_w) {  // the pass wrote w^{k-1}, b^{k-1} into the state slots
+      TRY(cudaMemcpyAsync(hist_w + (size_t)(k - 1) * 3 * h->V, a.wp, F3, cudaMemcpyDeviceToDevice, s));
+      TRY(cudaMemcpyAsync(hist_b + (size_t)(k - 1) * 3 * h->V, a.bp, F3, cudaMemcpyDeviceToDevice, s));
+    }
   }
   KLAUNCH(NADMM_KC_PENCIL, s, launch_pencil(pa, s));
   PlaneArgs fin = plane_args(h);
@@ -279,6 +295,9 @@ cudaError_t enqueue_register(nadmm_context* h, const float* I0, const float* I1,
   KLAUNCH(NADMM_KC_WARP, s, launch_warp(d, I1, u_cur, I1w, nullptr, s));
   KLAUNCH(NADMM_KC_GRAD, s, launch_grad_residual(d, I1w, I0, J, c, s));
   for (int o = 0; o < O; ++o) {
+    if (h->o_tape)  // u at the start of outer step o, for the reverse sweep
+      TRY(cudaMemcpyAsync(h->at<float>(h->o_tape) + (size_t)o * 3 * V, u_cur, 3 * V * sizeof(float),
+                          cudaMemcpyDeviceToDevice, s));
     PlaneArgs first = plane_args(h);
     TRY(enqueue_inner(h, first, IN_NONE, false, 0, K, J, c, vbuf, nullptr, s));
     // red[0..1] are zero here: cleared at the start, then by each re-warp
@@ -383,9 +402,22 @@ nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
   h->o_io_f = take(V * sizeof(float));
   h->o_io_m = take(V * sizeof(float));
   h->o_io_u = take(3 * V * sizeof(float));
+  if (cfg->flags & NADMM_FLAG_SAVE_FOR_BACKWARD) {
+    const size_t F3 = 3 * V * sizeof(float);
+    h->o_tape = take((size_t)cfg->outer_iters * F3);
+    h->o_hist = take(2 * (size_t)cfg->inner_iters * F3);
+    h->o_adj = take(6 * F3);
+    h->o_g = take(F3);
+    h->o_Sg = take(F3);
+    h->o_gJ = take(F3);
+    h->o_gc = take(V * sizeof(float));
+    h->o_ub0 = take(F3);
+    h->o_ub1 = take(F3);
+  }
   h->state_total = o;
   o = 0;
   h->o_red = take(4 * sizeof(unsigned));
+  h->o_acc = take(4 * sizeof(double));
   h->o_twx = take(h->twx.size() * sizeof(float2));
   h->o_twy = take(h->twy.size() * sizeof(float2));
   h->o_twz = take(h->twz.size() * sizeof(float2));
@@ -458,6 +490,7 @@ cudaError_t configure_kernels_once() {
 // tensor map.
 nadmm_status attach(nadmm_context* h, char* ws, char* wt) {
   invalidate_graph(h);
+  h->saved_forward = false;
   h->ws = ws;
   h->wt = wt;
   struct Up { size_t off; const void* src; size_t n; } ups[] = {
@@ -505,10 +538,13 @@ nadmm_status read_status(nadmm_context* h) {
 
 // Capture fn(stream) into h's graph (re-captured when key changes), then replay.
 template <class F>
-nadmm_status replay(nadmm_context* h, const std::vector<const void*>& key, cudaStream_t stream,
-                    const char* what, F&& fn) {
-  if (!h->gexec || h->gkey != key) {
-    invalidate_graph(h);
+nadmm_status replay(nadmm_context* h, int slot, const std::vector<const void*>& key,
+                    cudaStream_t stream, const char* what, F&& fn) {
+  cudaGraphExec_t& gexec = h->gexec[slot];
+  if (!gexec || h->gkey[slot] != key) {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    h->gkey[slot].clear();
     cudaError_t e;
     if (!h->cap) {
       e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
@@ -524,15 +560,15 @@ nadmm_status replay(nadmm_context* h, const std::vector<const void*>& key, cudaS
       return cuda_fail(le, what);
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    e = cudaGraphInstantiate(&gexec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-      h->gexec = nullptr;
+      gexec = nullptr;
       return cuda_fail(e, "cudaGraphInstantiate");
     }
-    h->gkey = key;
+    h->gkey[slot] = key;
   }
-  cudaError_t e = cudaGraphLaunch(h->gexec, stream);
+  cudaError_t e = cudaGraphLaunch(gexec, stream);
   return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "cudaGraphLaunch");
 }
 
@@ -579,8 +615,115 @@ nadmm_status run_register(nadmm_context* h, const float* I0, const float* I1, fl
     cudaError_t e = enqueue_register(h, I0, I1, u_out, stream);
     return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_register");
   }
-  return replay(h, {I0, I1, u_out}, stream, "capture of nadmm_register",
+  return replay(h, 0, {I0, I1, u_out}, stream, "capture of nadmm_register",
                 [&](cudaStream_t cs) { return enqueue_register(h, I0, I1, u_out, cs); });
+}
+
+
+// Reverse sweep of nadmm_register (s = 2): for the gradient gu of the final
+// displacement, grad_fixed, grad_moving (overwritten) and, if not null,
+// grad_lambda, grad_theta (device floats).  Outer steps are taken backwards;
+// each recomputes its linearisation and its ADMM iterates from the saved u
+// at its start, then runs the adjoints of compose, bound, the K ADMM steps
+// and the linearisation.
+cudaError_t enqueue_backward(nadmm_context* h, const float* I0, const float* I1, const float* gu,
+                             float* gI0, float* gI1, float* glam, float* gtheta, cudaStream_t s) {
+  const Dims d = dims_of(h);
+  const size_t V = h->V, F3 = 3 * V * sizeof(float);
+  const int O = h->cfg.outer_iters, K = h->cfg.inner_iters;
+  const float kappa = h->cfg.bound_kappa, delta = h->cfg.bound_delta;
+  float* I1w = h->at<float>(h->o_I1w);
+  float* J = h->at<float>(h->o_J);
+  float* c = h->at<float>(h->o_c);
+  float* tape = h->at<float>(h->o_tape);
+  float* hw = h->at<float>(h->o_hist);
+  float* hb = hw + (size_t)K * 3 * V;
+  float* adj = h->at<float>(h->o_adj);
+  auto Wbar = [&](int k) { return adj + (size_t)(((k % 3) + 3) % 3) * 3 * V; };
+  auto Bbar = [&](int k) { return adj + (size_t)(3 + ((k % 3) + 3) % 3) * 3 * V; };
+  auto hist = [&](float* base, int k) { return base + (size_t)k * 3 * V; };
+  float* g = h->at<float>(h->o_g);
+  float* Sg = h->at<float>(h->o_Sg);
+  float* gJ = h->at<float>(h->o_gJ);
+  float* gc = h->at<float>(h->o_gc);
+  float* ub0 = h->at<float>(h->o_ub0);
+  float* ub1 = h->at<float>(h->o_ub1);
+  unsigned* red = h->tab<unsigned>(h->o_red);
+  double* acc = h->tab<double>(h->o_acc);
+  PencilArgs pa = pencil_args(h);
+
+  TRY(cudaMemsetAsync(gI0, 0, V * sizeof(float), s));
+  TRY(cudaMemsetAsync(gI1, 0, V * sizeof(float), s));
+  TRY(cudaMemsetAsync(acc, 0, 3 * sizeof(double), s));
+  TRY(cudaMemcpyAsync(ub0, gu, F3, cudaMemcpyDeviceToDevice, s));
+  for (int o = O - 1; o >= 0; --o) {
+    const float* u_o = tape + (size_t)o * 3 * V;
+    // forward recomputation of outer step o
+    TRY(launch_warp(d, I1, u_o, I1w, red, s));  // also clears red[0..1]
+    TRY(launch_grad_residual(d, I1w, I0, J, c, s));
+    TRY(enqueue_inner(h, plane_args(h), IN_NONE, false, 0, K, J, c, hist(hw, K - 1),
+                      hist(hb, K - 1), s, hw, hb));
+    const float* w = hist(hw, K - 1);
+    TRY(launch_bound_reduce(d, w, red, s));
+    // compose and bound
+    TRY(cudaMemsetAsync(ub1, 0, F3, s));
+    TRY(cudaMemsetAsync(acc, 0, sizeof(double), s));
+    TRY(cudaMemsetAsync(red + 3, 0, sizeof(unsigned), s));
+    TRY(cudaMemsetAsync(adj, 0, 6 * F3, s));
+    TRY(launch_compose_vjp(d, u_o, w, red, kappa, delta, ub0, ub1, Wbar(K - 1), acc, s));
+    TRY(launch_bound_vjp(d, w, red, kappa, delta, acc, red + 3, Wbar(K - 1), s));
+    // ADMM iterations K-1 .. 0
+    TRY(cudaMemsetAsync(gJ, 0, F3, s));
+    TRY(cudaMemsetAsync(gc, 0, V * sizeof(float), s));
+    const float* g_in = Wbar(K - 1);  // bbar^{K-1} = 0
+    for (int k = K - 1; k >= 0; --k) {
+      PlaneArgs fa = plane_args(h);
+      fa.y = nullptr;
+      fa.w_in = g_in;
+      TRY(launch_plane(IN_FIELD, false, true, fa, s));
+      TRY(launch_pencil(pa, s));
+      PlaneArgs fb = plane_args(h);
+      fb.y = nullptr;
+      fb.w_out = Sg;
+      fb.b_out = nullptr;
+      TRY(launch_plane(IN_SPEC, false, false, fb, s));
+      AdjArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.d = d;
+      a.wk = hist(hw, k);
+      a.bk = hist(hb, k);
+      if (k >= 1) {
+        a.w1 = hist(hw, k - 1);
+        a.b1 = hist(hb, k - 1);
+        a.W1bar = Wbar(k - 1);
+        a.B1bar = Bbar(k - 1);
+      }
+      if (k >= 2) {
+        a.w2 = hist(hw, k - 2);
+        a.b2 = hist(hb, k - 2);
+        a.W2bar = Wbar(k - 2);
+        a.B2bar = Bbar(k - 2);
+      }
+      a.J = J;
+      a.c = c;
+      a.Sg = Sg;
+      a.g_in = g_in;
+      a.Bk = Bbar(k);
+      a.Wk_zero = Wbar(k);
+      a.Bk_zero = Bbar(k);
+      a.g_out = g;
+      a.gJ = gJ;
+      a.gc = gc;
+      a.acc = acc;
+      a.beta = beta_for(h, k);
+      a.theta = h->cfg.theta;
+      a.inv_gamma = h->cfg.theta / h->cfg.lambda;
+      TRY(launch_adj_step(a, s));
+      g_in = g;
+    }
+    TRY(launch_linearise_vjp(d, I1, u_o, gJ, gc, gI0, gI1, ub1, ub0, s));
+  }
+  return launch_param_grads(acc, h->cfg.lambda, h->cfg.theta, glam, gtheta, s);
 }
 
 }  // namespace
@@ -618,6 +761,7 @@ const char* nadmm_status_string(nadmm_status s) {
     case NADMM_ERR_CUDA: return "NADMM_ERR_CUDA";
     case NADMM_ERR_NONFINITE: return "NADMM_ERR_NONFINITE";
     case NADMM_ERR_TIMEOUT: return "NADMM_ERR_TIMEOUT";
+    case NADMM_ERR_NO_SAVED_FORWARD: return "NADMM_ERR_NO_SAVED_FORWARD";
   }
   return "unknown nadmm_status";
 }
@@ -639,6 +783,8 @@ nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, cons
   *out = nullptr;
   if (!base || !dims) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
   if (npairs < 1) return fail(NADMM_ERR_INVALID_ARG, "npairs must be >= 1");
+  if (base->flags & NADMM_FLAG_SAVE_FOR_BACKWARD)
+    return fail(NADMM_ERR_INVALID_ARG, "batched handles have no reverse mode");
   nadmm_context* b = new nadmm_context();
   b->cfg = *base;
   b->batched = true;
@@ -727,7 +873,9 @@ nadmm_status nadmm_register(nadmm_handle h, const float* fixed, const float* mov
   nadmm_status st = need_ws(h);
   if (st != NADMM_OK) return st;
   if ((st = check_dev_ptrs({fixed, moving, u_out})) != NADMM_OK) return st;
-  return run_register(h, fixed, moving, u_out, (cudaStream_t)stream);
+  st = run_register(h, fixed, moving, u_out, (cudaStream_t)stream);
+  if (st == NADMM_OK && h->o_tape) h->saved_forward = true;
+  return st;
 }
 
 nadmm_status nadmm_register_host(nadmm_handle h, const float* fixed_host, const float* moving_host,
@@ -744,6 +892,7 @@ nadmm_status nadmm_register_host(nadmm_handle h, const float* fixed_host, const 
   if (e == cudaSuccess) e = cudaMemcpyAsync(m, moving_host, V * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
   if ((st = run_register(h, f, m, u, s)) != NADMM_OK) return st;
+  if (h->o_tape) h->saved_forward = true;
   e = cudaMemcpyAsync(u_out_host, u, 3 * V * sizeof(float), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "device-to-host copy");
@@ -823,7 +972,7 @@ nadmm_status nadmm_register_batched(nadmm_handle h, const float* const* fixed,
     }
     return NADMM_OK;
   }
-  return replay(h, key, s, "capture of nadmm_register_batched",
+  return replay(h, 0, key, s, "capture of nadmm_register_batched",
                 [&](cudaStream_t cs) { return enqueue_batched(h, fixed, moving, u_out, cs); });
 }
 
@@ -912,6 +1061,62 @@ nadmm_status nadmm_jacobian_det(nadmm_handle h, const float* u, float* det, uint
   if (nonpositive) e = cudaMemsetAsync(nonpositive, 0, sizeof(uint32_t), s);
   if (e == cudaSuccess) e = launch_jacobian(dims_of(h), u, det, nonpositive, s);
   return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_jacobian_det");
+}
+
+nadmm_status nadmm_backward(nadmm_handle h, const float* fixed, const float* moving,
+                            const float* grad_u, float* grad_fixed, float* grad_moving,
+                            float* grad_lambda, float* grad_theta, void* stream) {
+  nadmm_status st = need_ws(h);
+  if (st != NADMM_OK) return st;
+  if (!(h->cfg.flags & NADMM_FLAG_SAVE_FOR_BACKWARD))
+    return fail(NADMM_ERR_NO_SAVED_FORWARD, "handle created without NADMM_FLAG_SAVE_FOR_BACKWARD");
+  if (!h->saved_forward)
+    return fail(NADMM_ERR_NO_SAVED_FORWARD, "no nadmm_register call since the workspace was attached");
+  if (h->cfg.data_term != 2)
+    return fail(NADMM_ERR_INVALID_ARG, "the reverse mode supports the s = 2 data term only");
+  if (!(h->cfg.lambda > 0.0f)) return fail(NADMM_ERR_INVALID_ARG, "the reverse mode needs lambda > 0");
+  if ((st = check_dev_ptrs({fixed, moving, grad_u, grad_fixed, grad_moving})) != NADMM_OK) return st;
+  if (grad_lambda && !aligned16(grad_lambda)) return fail(NADMM_ERR_ALIGNMENT, "grad_lambda not aligned");
+  if (grad_theta && !aligned16(grad_theta)) return fail(NADMM_ERR_ALIGNMENT, "grad_theta not aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  auto fn = [&](cudaStream_t cs) {
+    return enqueue_backward(h, fixed, moving, grad_u, grad_fixed, grad_moving, grad_lambda,
+                            grad_theta, cs);
+  };
+  if (h->cfg.flags & NADMM_FLAG_NO_GRAPH) {
+    cudaError_t e = fn(s);
+    return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_backward");
+  }
+  return replay(h, 1, {fixed, moving, grad_u, grad_fixed, grad_moving, grad_lambda, grad_theta}, s,
+                "capture of nadmm_backward", fn);
+}
+
+nadmm_status nadmm_ssd_after_warp(nadmm_handle h, const float* fixed, const float* moving,
+                                  const float* u, float* loss, void* stream) {
+  nadmm_status st = need_ws(h);
+  if (st != NADMM_OK) return st;
+  if ((st = check_dev_ptrs({fixed, moving, u, loss})) != NADMM_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* acc = h->tab<double>(h->o_acc) + 3;
+  cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double), s);
+  if (e == cudaSuccess) e = launch_ssd(dims_of(h), fixed, moving, u, acc, loss, s);
+  return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_ssd_after_warp");
+}
+
+nadmm_status nadmm_ssd_after_warp_backward(nadmm_handle h, const float* fixed, const float* moving,
+                                           const float* u, const float* grad_loss,
+                                           float* grad_fixed, float* grad_moving, float* grad_u,
+                                           void* stream) {
+  nadmm_status st = need_ws(h);
+  if (st != NADMM_OK) return st;
+  if ((st = check_dev_ptrs({fixed, moving, u, grad_loss, grad_moving})) != NADMM_OK) return st;
+  if (grad_fixed && !aligned16(grad_fixed)) return fail(NADMM_ERR_ALIGNMENT, "grad_fixed not aligned");
+  if (grad_u && !aligned16(grad_u)) return fail(NADMM_ERR_ALIGNMENT, "grad_u not aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(grad_moving, 0, h->V * sizeof(float), s);
+  if (e == cudaSuccess)
+    e = launch_ssd_vjp(dims_of(h), fixed, moving, u, grad_loss, grad_fixed, grad_moving, grad_u, s);
+  return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_ssd_after_warp_backward");
 }
 
 }  // extern "C"

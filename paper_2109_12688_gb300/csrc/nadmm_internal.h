@@ -154,4 +154,44 @@ cudaError_t launch_compose(Dims d, const float* w, const float* u_in, float* u_o
                            float* scale_out, cudaStream_t s);
 cudaError_t launch_jacobian(Dims d, const float* u, float* det, unsigned* count, cudaStream_t s);
 
+// ---------------------------------------------------------------- reverse mode
+// One reverse ADMM step k (grad_kernels.cu).  State of the forward sweep:
+// wk, bk = w^k, b^k; w1, b1 = w^{k-1}, b^{k-1} (null for k = 0); w2, b2 =
+// w^{k-2}, b^{k-2} (null for k < 2).  g_in = wbar^k - bbar^k, Sg = S g_in,
+// Bk = bbar^k.  Adds into W1bar/B1bar (k-1, null for k = 0) and W2bar/B2bar
+// (k-2), writes g_out = wbar^{k-1} - bbar^{k-1}, zeroes Wk_zero/Bk_zero,
+// accumulates gJ, gc and acc[1] (theta, data step), acc[2] (gamma).
+struct AdjArgs {
+  Dims d;
+  const float *wk, *bk, *w1, *b1, *w2, *b2;
+  const float *J, *c, *Sg, *g_in, *Bk;
+  float *W1bar, *B1bar, *W2bar, *B2bar, *Wk_zero, *Bk_zero, *g_out;
+  float *gJ, *gc;
+  double* acc;
+  float beta;       // beta'_k (0 for k = 0)
+  float theta;
+  float inv_gamma;  // theta / lambda
+};
+
+// acc[0] += <vbar, w> (gradient of the bound scale)
+cudaError_t launch_compose_vjp(Dims d, const float* u_o, const float* w, const unsigned* red,
+                               float kappa, float delta, const float* ubar, float* ubar_prev,
+                               float* wbar, double* acc, cudaStream_t s);
+// count must start at 0
+cudaError_t launch_bound_vjp(Dims d, const float* w, const unsigned* red, float kappa,
+                             float delta, const double* acc, unsigned* count, float* wbar,
+                             cudaStream_t s);
+cudaError_t launch_adj_step(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_linearise_vjp(Dims d, const float* I1, const float* u_o, const float* gJ,
+                                 const float* gc, float* grad_fixed, float* grad_moving,
+                                 const float* ubar_prev, float* ubar_out, cudaStream_t s);
+cudaError_t launch_param_grads(const double* acc, float lambda, float theta, float* glam,
+                               float* gtheta, cudaStream_t s);
+// *loss = acc[0] after acc[0] += 1/2 sum r^2 (acc[0] must start at 0)
+cudaError_t launch_ssd(Dims d, const float* I0, const float* I1, const float* u, double* acc,
+                       float* loss, cudaStream_t s);
+cudaError_t launch_ssd_vjp(Dims d, const float* I0, const float* I1, const float* u,
+                           const float* gL, float* grad_fixed, float* grad_moving, float* grad_u,
+                           cudaStream_t s);
+
 }  // namespace nadmm

@@ -22,7 +22,9 @@ NADMM_ERR_NO_WORKSPACE = 4
 NADMM_ERR_CUDA = 5
 NADMM_ERR_NONFINITE = 6
 NADMM_ERR_TIMEOUT = 7
+NADMM_ERR_NO_SAVED_FORWARD = 8
 NADMM_FLAG_NO_GRAPH = 1
+NADMM_FLAG_SAVE_FOR_BACKWARD = 2
 
 KERNEL_CLASSES = ("plane_first", "plane_k1", "plane", "plane_final", "pencil", "warp", "grad",
                   "bound", "compose")
@@ -74,6 +76,9 @@ _SIGS = {
     "nadmm_batch_set_lanes": (ctypes.c_int, [_P, ctypes.c_int32]),
     "nadmm_register_batched": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                               ctypes.POINTER(_P), _P]),
+    "nadmm_backward": (ctypes.c_int, [_P] * 9),
+    "nadmm_ssd_after_warp": (ctypes.c_int, [_P] * 6),
+    "nadmm_ssd_after_warp_backward": (ctypes.c_int, [_P] * 9),
 }
 
 
@@ -154,6 +159,25 @@ def nadmm_register_batched(h, fixed, moving, u_out, stream=None):
         raise ValueError("fixed, moving and u_out need one entry per pair")
     arr = lambda xs: (_P * n)(*[_ptr(x) for x in xs])
     _check(load().nadmm_register_batched(h, arr(fixed), arr(moving), arr(u_out), _stream(stream)))
+
+
+def nadmm_backward(h, fixed, moving, grad_u, grad_fixed, grad_moving, grad_lambda=None,
+                   grad_theta=None, stream=None):
+    _check(load().nadmm_backward(h, _ptr(fixed), _ptr(moving), _ptr(grad_u), _ptr(grad_fixed),
+                                 _ptr(grad_moving), _ptr(grad_lambda), _ptr(grad_theta),
+                                 _stream(stream)))
+
+
+def nadmm_ssd_after_warp(h, fixed, moving, u, loss, stream=None):
+    _check(load().nadmm_ssd_after_warp(h, _ptr(fixed), _ptr(moving), _ptr(u), _ptr(loss),
+                                       _stream(stream)))
+
+
+def nadmm_ssd_after_warp_backward(h, fixed, moving, u, grad_loss, grad_fixed, grad_moving,
+                                  grad_u, stream=None):
+    _check(load().nadmm_ssd_after_warp_backward(h, _ptr(fixed), _ptr(moving), _ptr(u),
+                                                _ptr(grad_loss), _ptr(grad_fixed),
+                                                _ptr(grad_moving), _ptr(grad_u), _stream(stream)))
 
 
 def nadmm_destroy(h):
@@ -254,10 +278,13 @@ class Registration:
     """A handle plus a torch-allocated device workspace (PyTorch is used for
     device memory only)."""
 
-    def __init__(self, dims, device="cuda", **kw):
+    def __init__(self, dims, device="cuda", requires_grad=False, **kw):
         import torch
         self.dims = tuple(dims)
+        if requires_grad:
+            kw["flags"] = kw.get("flags", 0) | NADMM_FLAG_SAVE_FOR_BACKWARD
         self.cfg = make_config(self.dims, **kw)
+        self.serial = 0  # forward passes run on this handle
         self.handle = nadmm_create(self.cfg)
         nbytes = nadmm_workspace_size(self.handle)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
@@ -273,7 +300,27 @@ class Registration:
         if stream is None:
             stream = torch.cuda.current_stream(fixed.device)
         nadmm_register(self.handle, fixed, moving, u_out, stream)
+        self.serial += 1
         return u_out
+
+    def set_params(self, lam, theta):
+        if (lam, theta) != (self.cfg.lambda_, self.cfg.theta):
+            nadmm_set_params(self.handle, lam, theta)
+            self.cfg.lambda_ = lam
+            self.cfg.theta = theta
+
+    def backward(self, fixed, moving, grad_u, stream=None):
+        """Gradients (I0, I1, lambda, theta) of <grad_u, u> through the last
+        forward pass; lambda/theta as 0-dim device tensors."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(fixed.device)
+        g0 = torch.empty_like(fixed)
+        g1 = torch.empty_like(moving)
+        par = torch.zeros(8, dtype=torch.float32, device=fixed.device)  # [0]: lambda, [4]: theta
+        nadmm_backward(self.handle, fixed, moving, grad_u.contiguous(), g0, g1, par.data_ptr(),
+                       par.data_ptr() + 16, stream)
+        return g0, g1, par[0], par[4]
 
     def close(self):
         if self.handle:
@@ -312,3 +359,78 @@ class BatchedRegistration(Registration):
             stream = torch.cuda.current_stream(fixed[0].device)
         nadmm_register_batched(self.handle, fixed, moving, u_out, stream)
         return u_out
+
+
+# ---------------------------------------------------------------- autograd
+def _autograd():
+    import torch
+
+    class RegisterFn(torch.autograd.Function):
+        """u = register(I0, I1; lambda, theta) with its reverse mode
+        (nadmm_backward).  The handle must be created with requires_grad."""
+
+        @staticmethod
+        def forward(ctx, fixed, moving, lam, theta, reg):
+            params = (float(lam), float(theta))
+            reg.set_params(*params)
+            fixed, moving = fixed.contiguous(), moving.contiguous()
+            u = reg.register(fixed, moving)
+            ctx.reg, ctx.params, ctx.serial = reg, params, reg.serial
+            ctx.save_for_backward(fixed, moving)
+            return u
+
+        @staticmethod
+        def backward(ctx, gu):
+            fixed, moving = ctx.saved_tensors
+            reg = ctx.reg
+            if reg.serial != ctx.serial or (reg.cfg.lambda_, reg.cfg.theta) != ctx.params:
+                reg.set_params(*ctx.params)  # the handle ran another forward since: redo ours
+                reg.register(fixed, moving)
+                ctx.serial = reg.serial
+            g0, g1, gl, gt = reg.backward(fixed, moving, gu)
+            return g0, g1, gl, gt, None
+
+    class SSDFn(torch.autograd.Function):
+        """L = 1/2 sum (I1 o (Id + u) - I0)^2 on the handle's grid."""
+
+        @staticmethod
+        def forward(ctx, fixed, moving, u, reg):
+            fixed, moving, u = fixed.contiguous(), moving.contiguous(), u.contiguous()
+            loss = torch.empty(4, dtype=torch.float32, device=fixed.device)
+            nadmm_ssd_after_warp(reg.handle, fixed, moving, u, loss,
+                                 torch.cuda.current_stream(fixed.device))
+            ctx.reg = reg
+            ctx.save_for_backward(fixed, moving, u)
+            return loss[0]
+
+        @staticmethod
+        def backward(ctx, gL):
+            fixed, moving, u = ctx.saved_tensors
+            g0, g1, gu = torch.empty_like(fixed), torch.empty_like(moving), torch.empty_like(u)
+            gl = torch.zeros(4, dtype=torch.float32, device=fixed.device)
+            gl[0] = gL
+            nadmm_ssd_after_warp_backward(ctx.reg.handle, fixed, moving, u, gl, g0, g1, gu,
+                                          torch.cuda.current_stream(fixed.device))
+            return g0, g1, gu, None
+
+    return RegisterFn, SSDFn
+
+
+_fns = None
+
+
+def register(fixed, moving, lam, theta, reg):
+    """Differentiable registration: u with gradients to fixed, moving and the
+    0-dim tensors lam, theta (reg: Registration(..., requires_grad=True))."""
+    global _fns
+    if _fns is None:
+        _fns = _autograd()
+    return _fns[0].apply(fixed, moving, lam, theta, reg)
+
+
+def ssd_after_warp(fixed, moving, u, reg):
+    """Differentiable 1/2 sum (I1 o (Id + u) - I0)^2."""
+    global _fns
+    if _fns is None:
+        _fns = _autograd()
+    return _fns[1].apply(fixed, moving, u, reg)

@@ -1,0 +1,201 @@
+"""Reverse mode on the GPU (nadmm_backward, nadmm_ssd_after_warp*) against
+the FP64 oracle's hand-written adjoints and against finite differences.
+
+Tolerances: the GPU sweeps run in FP32 with float atomics for the scatters;
+the adjoint recursion has the forward's conditioning, so gradients are
+compared by relative L2 error <= 2e-3 (elementwise where noted) against the
+FP64 oracle; the 128x128x96 gradients against central differences of the
+GPU forward (step 1e-3), whose FP32 rounding noise in the loss bounds the
+agreement to a few 1e-3 absolute."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2109_12688_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2109_12688_gb300 import nadmm
+    return nadmm
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-30))
+
+
+def stream():
+    return torch.cuda.current_stream()
+
+
+# ---------------------------------------------------------------- SSD loss
+def test_ssd_after_warp_and_vjp(lib):
+    dims = (32, 32, 24)
+    p = synth.make_pair(dims, seed=3)
+    u = synth.random_velocity(dims, np.random.default_rng(5), max_amp=2.5)
+    reg = lib.Registration(dims, device=DEV)
+    loss = torch.zeros(4, device=DEV)
+    f, m, ud = dev(p["fixed"]), dev(p["moving"]), dev(u)
+    lib.nadmm_ssd_after_warp(reg.handle, f, m, ud, loss, stream())
+    ref = O.ssd_after_warp(p["fixed"], p["moving"], u.astype(np.float32))
+    assert abs(float(loss[0]) - ref) <= 1e-5 * ref
+    gl = torch.tensor([0.7, 0, 0, 0], device=DEV)
+    g0, g1, gu = torch.empty_like(f), torch.empty_like(m), torch.empty_like(ud)
+    lib.nadmm_ssd_after_warp_backward(reg.handle, f, m, ud, gl, g0, g1, gu, stream())
+    r0, r1, ru = O.ssd_after_warp_vjp(p["fixed"], p["moving"], u.astype(np.float32), 0.7)
+    assert rel_l2(host(g0), r0) <= 1e-5
+    assert rel_l2(host(g1), r1) <= 1e-5
+    assert rel_l2(host(gu), ru) <= 1e-4
+
+
+# ---------------------------------------------------------------- registration
+CASES = [dict(n=2, outer=3, inner=5, kappa=0.5, delta=1.0),
+         dict(n=1, outer=2, inner=6, kappa=math.inf, delta=math.inf),
+         dict(n=3, outer=3, inner=4, kappa=0.05, delta=math.inf)]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_backward_matches_oracle_vjp(lib, case):
+    c = CASES[case]
+    dims = (32, 32, 24)
+    p = synth.make_pair(dims, seed=case)
+    gu = synth.random_field((3,) + dims[::-1], seed=40 + case)
+    kw = dict(lam=10.0, theta=0.1, n=c["n"], outer=c["outer"], inner=c["inner"],
+              kappa=c["kappa"], delta=c["delta"])
+    reg = lib.Registration(dims, device=DEV, requires_grad=True, order_n=c["n"], lam=10.0,
+                           theta=0.1, outer=c["outer"], inner=c["inner"], kappa=c["kappa"],
+                           delta=c["delta"])
+    f, m = dev(p["fixed"]), dev(p["moving"])
+    u = reg.register(f, m)
+    u_ref, tape = O.register_tape(p["fixed"], p["moving"], **kw)
+    assert np.abs(host(u) - u_ref).max() <= 1e-3
+    if c["kappa"] < 0.1:
+        assert all(t[4] < 1.0 for t in tape)  # bound active
+    g0, g1, gl, gt = reg.backward(f, m, dev(gu))
+    r0, r1, rl, rt = O.register_vjp(p["fixed"], p["moving"], gu, **kw)
+    assert rel_l2(host(g0), r0) <= 2e-3
+    assert rel_l2(host(g1), r1) <= 2e-3
+    assert abs(float(gl) - rl) <= 2e-3 * abs(rl) + 1e-6
+    assert abs(float(gt) - rt) <= 2e-3 * abs(rt) + 1e-6
+
+
+def test_backward_graph_and_direct_agree(lib):
+    dims = (32, 32, 24)
+    p = synth.make_pair(dims, seed=9)
+    gu = dev(synth.random_field((3,) + dims[::-1], seed=1))
+    f, m = dev(p["fixed"]), dev(p["moving"])
+    out = []
+    for flags in (0, lib.NADMM_FLAG_NO_GRAPH):
+        reg = lib.Registration(dims, device=DEV, requires_grad=True, outer=3, inner=4,
+                               flags=flags)
+        reg.register(f, m)
+        res = [host(t) for t in reg.backward(f, m, gu)]
+        res2 = [host(t) for t in reg.backward(f, m, gu)]  # replay
+        for a, b in zip(res, res2):
+            np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-6)
+        out.append(res)
+    for a, b in zip(*out):
+        np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-6)
+
+
+def test_backward_errors(lib):
+    dims = (16, 16, 8)
+    f = torch.zeros(dims[::-1], device=DEV)
+    gu = torch.zeros((3,) + dims[::-1], device=DEV)
+    plain = lib.Registration(dims, device=DEV)
+    with pytest.raises(lib.NadmmError) as e:
+        plain.backward(f, f, gu)
+    assert e.value.status == lib.NADMM_ERR_NO_SAVED_FORWARD
+    reg = lib.Registration(dims, device=DEV, requires_grad=True)
+    with pytest.raises(lib.NadmmError) as e:
+        reg.backward(f, f, gu)  # no forward yet
+    assert e.value.status == lib.NADMM_ERR_NO_SAVED_FORWARD
+    l1 = lib.Registration(dims, device=DEV, requires_grad=True, data_term=1)
+    l1.register(f, f)
+    with pytest.raises(lib.NadmmError) as e:
+        l1.backward(f, f, gu)
+    assert e.value.status == lib.NADMM_ERR_INVALID_ARG
+
+
+def test_autograd_chain_matches_oracle(lib):
+    """L = SSD(I1 o (Id + register(I0, I1)), I0) through torch.autograd."""
+    dims = (32, 32, 24)
+    p = synth.make_pair(dims, seed=4)
+    kw = dict(lam=10.0, theta=0.1, n=2, outer=3, inner=5)
+    reg = lib.Registration(dims, device=DEV, requires_grad=True, order_n=2, outer=3, inner=5)
+    f = dev(p["fixed"]).requires_grad_()
+    m = dev(p["moving"]).requires_grad_()
+    lam = torch.tensor(10.0, device=DEV, requires_grad=True)
+    theta = torch.tensor(0.1, device=DEV, requires_grad=True)
+    u = lib.register(f, m, lam, theta, reg)
+    L = lib.ssd_after_warp(f, m, u, reg)
+    L.backward()
+    Lr, r0, r1, rl, rt = O.loss_and_gradients(p["fixed"], p["moving"], **kw)
+    assert abs(float(L) - Lr) <= 1e-4 * Lr
+    assert rel_l2(host(f.grad), r0) <= 2e-3
+    assert rel_l2(host(m.grad), r1) <= 2e-3
+    assert abs(float(lam.grad) - rl) <= 2e-3 * abs(rl) + 1e-6
+    assert abs(float(theta.grad) - rt) <= 2e-3 * abs(rt) + 1e-6
+
+
+def test_gradients_128x128x96_against_finite_differences(lib):
+    """The gradient workload: 128x128x96 seed 0, n = 2, 8 compositions x 20
+    ADMM iterations; dL/dI0, dL/dI1 at 16 voxels drawn with seed 7 and
+    dL/dlambda, dL/dtheta against central differences (step 1e-3) of the GPU
+    forward, the loss evaluated in FP64 from the GPU displacement."""
+    dims = (128, 128, 96)
+    nx, ny, nz = dims
+    p = synth.make_pair(dims, seed=0)
+    I0, I1 = p["fixed"], p["moving"]
+    reg = lib.Registration(dims, device=DEV, requires_grad=True, order_n=2, outer=8, inner=20)
+    f, m = dev(I0), dev(I1)
+    lam = torch.tensor(10.0, device=DEV, requires_grad=True)
+    theta = torch.tensor(0.1, device=DEV, requires_grad=True)
+    fg, mg = f.clone().requires_grad_(), m.clone().requires_grad_()
+    L = lib.ssd_after_warp(fg, mg, lib.register(fg, mg, lam, theta, reg), reg)
+    L.backward()
+    g0, g1 = host(fg.grad), host(mg.grad)
+    gl, gt = float(lam.grad), float(theta.grad)
+
+    fwd = lib.Registration(dims, device=DEV, order_n=2, outer=8, inner=20)
+
+    def loss(a=I0, b=I1, lam_=10.0, th_=0.1):
+        fwd.set_params(lam_, th_)
+        u = host(fwd.register(dev(a), dev(b)))
+        return O.ssd_after_warp(a, b, u)
+
+    h = 1e-3
+    rng = np.random.default_rng(7)
+    idx = [(int(rng.integers(nz)), int(rng.integers(ny)), int(rng.integers(nx))) for _ in range(16)]
+    for (z, y, x) in idx:
+        for arr, g, name in ((I0, g0, "I0"), (I1, g1, "I1")):
+            ap, am = arr.copy(), arr.copy()
+            ap[z, y, x] += h
+            am[z, y, x] -= h
+            num = ((loss(a=ap) - loss(a=am)) if name == "I0" else (loss(b=ap) - loss(b=am))) / (2 * h)
+            assert abs(num - g[z, y, x]) <= 0.02 * abs(num) + 5e-3, (name, (z, y, x), num, g[z, y, x])
+    num_l = (loss(lam_=10.0 + h) - loss(lam_=10.0 - h)) / (2 * h)
+    num_t = (loss(th_=0.1 + h) - loss(th_=0.1 - h)) / (2 * h)
+    assert abs(num_l - gl) <= 0.02 * abs(num_l) + 5e-3, (num_l, gl)
+    assert abs(num_t - gt) <= 0.02 * abs(num_t) + 5e-3, (num_t, gt)
