@@ -157,12 +157,38 @@ def parse_args():
     ap.add_argument("--orders", default="1,2,3",
                     help="regulariser orders registered per step (profiling runs use one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
-    ap.add_argument("--workload", choices=("registration", "batch64", "large"),
+    ap.add_argument("--workload", choices=("registration", "batch64", "large", "grad"),
                     default="registration",
                     help="registration: the 128x128x96 benchmark (default); batch64: 64 uneven "
                          "pairs in one batched graph vs 64 sequential calls; large: one "
-                         "256x256x192 n=3 registration with its device-memory peak")
+                         "256x256x192 n=3 registration with its device-memory peak; grad: "
+                         "128x128x96 n=2 8x20 forward + SSD + reverse mode")
     return ap.parse_args()
+
+
+def rank_seeds(rank, orders):
+    """Seeds of the pairs rank `rank` registers (one per order): distinct
+    across ranks, so replicas never register the same pair."""
+    return [100 * rank + n for n in orders]
+
+
+def max_over_ranks(value, world, device="cpu"):
+    """The largest of every rank's `value` (all ranks call it)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(total_ms, steps, regs_per_rank_step, world, voxels, outer, inner):
+    """Whole-job figures from the slowest rank's time: every rank registers
+    regs_per_rank_step pairs per step, so the job registers that times world
+    per step.  Returns (ms per registration, ms per step, voxel-ADMM-iters/s)."""
+    regs_total = steps * regs_per_rank_step * world
+    return (total_ms / regs_total, total_ms / steps,
+            voxels * outer * inner * regs_total / (total_ms / 1e3))
 
 
 def oracle_sample_ms(pair, n):
@@ -252,10 +278,15 @@ def run_extra(args, rank, world):
         data = [synth.phase_pair(d, seed=i) for i, d in enumerate(dims)]
         I0 = [torch.from_numpy(f).to(dev) for f, _ in data]
         I1 = [torch.from_numpy(m).to(dev) for _, m in data]
-        breg = nadmm.BatchedRegistration(dims, device=dev, order_n=2, **kw)
         U = [torch.empty((3, d[2], d[1], d[0]), device=dev) for d in dims]
-        ms, clk = timed(lambda: nadmm.nadmm_register_batched(breg.handle, I0, I1, U, stream))
-        del breg
+        lanes_ms = {}
+        for lanes in (1, 2, 4):
+            breg = nadmm.BatchedRegistration(dims, device=dev, lanes=lanes, order_n=2, **kw)
+            lanes_ms[lanes], c = timed(
+                lambda: nadmm.nadmm_register_batched(breg.handle, I0, I1, U, stream))
+            if lanes == 1:
+                ms, clk = lanes_ms[1], c
+            del breg
         regs = [nadmm.Registration(d, device=dev, order_n=2, **kw) for d in dims]
 
         def sequential():
@@ -270,11 +301,49 @@ def run_extra(args, rank, world):
             "data": "synthetic",
             "config": {"workload": "64 pairs, nx, ny from {96,112,128,144,160}, nz from "
                                    "{64,80,96,112} (seed 1234), two-phase phantoms, n=2, 10 x 10 "
-                                   "iterations, one batched graph with 4 lanes",
+                                   "iterations, one batched graph (1 lane; 2 and 4 in ms_by_lanes)",
                        "voxels": vox,
                        "l2": "flushed between timed steps (256 MB write outside the step events)"},
             "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms,
+            "ms_by_lanes": lanes_ms,
             "voxel_admm_iters_per_s": vox * OUTER * INNER / (ms / 1e3),
+            "clocks": clk,
+        }
+    elif args.workload == "grad":
+        dims = (128, 128, 96)
+        p = synth.make_pair(dims, seed=0)
+        I0 = torch.from_numpy(p["fixed"]).to(dev)
+        I1 = torch.from_numpy(p["moving"]).to(dev)
+        reg = nadmm.Registration(dims, device=dev, requires_grad=True, order_n=2, lam=LAM,
+                                 theta=THETA, outer=8, inner=20)
+        fwd = nadmm.Registration(dims, device=dev, order_n=2, lam=LAM, theta=THETA, outer=8,
+                                 inner=20)
+        U = torch.empty((3, 96, 128, 128), device=dev)
+        loss = torch.zeros(4, device=dev)
+        gl = torch.ones(4, device=dev)
+        g0, g1, gu = torch.empty_like(I0), torch.empty_like(I1), torch.empty_like(U)
+        h0, h1 = torch.empty_like(I0), torch.empty_like(I1)
+        par = torch.zeros(8, device=dev)
+
+        def fwd_bwd():
+            nadmm.nadmm_register(reg.handle, I0, I1, U, stream)
+            nadmm.nadmm_ssd_after_warp(reg.handle, I0, I1, U, loss, stream)
+            nadmm.nadmm_ssd_after_warp_backward(reg.handle, I0, I1, U, gl, g0, g1, gu, stream)
+            nadmm.nadmm_backward(reg.handle, I0, I1, gu, h0, h1, par.data_ptr(),
+                                 par.data_ptr() + 16, stream)
+        ms, clk = timed(fwd_bwd)
+        fwd_ms, _ = timed(lambda: nadmm.nadmm_register(fwd.handle, I0, I1, U, stream))
+        line = {
+            "metric": "ms per 128x128x96 forward + backward (gradients of the SSD after warp "
+                      "w.r.t. I0, I1, lambda, theta)", "value": ms, "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "128x128x96 phantom pair seed 0, n=2, 8 compositions x 20 "
+                                   "ADMM iterations, forward (saving the tape) + SSD + reverse",
+                       "l2": "flushed between timed steps (256 MB write outside the step events)"},
+            "forward_only_ms": fwd_ms, "backward_over_forward": (ms - fwd_ms) / fwd_ms,
+            "workspace_bytes": nadmm.nadmm_workspace_size(reg.handle),
             "clocks": clk,
         }
     else:
@@ -336,7 +405,7 @@ def main():
     nx, ny, nz = DIMS
     V = nx * ny * nz
     ORDERS = tuple(int(o) for o in args.orders.split(","))
-    pairs = [synth.make_pair(DIMS, seed=100 * rank + n) for n in ORDERS]
+    pairs = [synth.make_pair(DIMS, seed=sd) for sd in rank_seeds(rank, ORDERS)]
     I0 = [torch.from_numpy(p["fixed"]).to(dev) for p in pairs]
     I1 = [torch.from_numpy(p["moving"]).to(dev) for p in pairs]
     U = [torch.empty((3, nz, ny, nx), dtype=torch.float32, device=dev) for _ in ORDERS]
@@ -377,14 +446,10 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world, dev)
     regs_total = args.steps * len(ORDERS) * world
-    ms_per_reg = total_ms / regs_total
-    ms_per_step = total_ms / args.steps
+    ms_per_reg, ms_per_step, vox_rate = aggregate(total_ms, args.steps, len(ORDERS), world, V,
+                                                  OUTER, INNER)
 
     # end to end through the C ABI with pinned host buffers (copies timed)
     e2e_per_reg = None
@@ -400,11 +465,8 @@ def main():
         for _ in range(args.steps):
             for r, a, b, u in zip(regs, hf, hm, hu):
                 nadmm.nadmm_register_host(r.handle, a, b, u, stream)
-        e2e_ms = (time.perf_counter() - t0) * 1e3
-        te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_per_reg = float(te.item()) / regs_total
+        e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world, dev)
+        e2e_per_reg = e2e_ms / regs_total
 
     # per-kernel device time: events on the launch stream around every kernel
     prof = {}
@@ -443,7 +505,7 @@ def main():
                    "outer": OUTER, "inner": INNER, "registrations_per_step": len(ORDERS),
                    "l2": "flushed between timed steps (256 MB write outside the step events)",
                    "parallelism": f"replicas x{world}"},
-        "voxel_admm_iters_per_s": V * OUTER * INNER * regs_total / (total_ms / 1e3),
+        "voxel_admm_iters_per_s": vox_rate,
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                      "traffic": ncu_traffic(dominant),

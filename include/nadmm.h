@@ -154,11 +154,14 @@ const char* nadmm_status_string(nadmm_status s);
  * dims[3i+2] (nx, ny, nz) and every other setting from `base` (its nx, ny,
  * nz are ignored).  Each grid is validated as by nadmm_create; the first
  * failure is returned with "pair i: ..." in nadmm_last_error.  The pairs
- * are spread over min(npairs, 4) lanes -- concurrent branches of one CUDA
- * graph -- longest first, balancing voxel counts; pairs of one lane run one
- * after another and share that lane's scratch, so the workspace is one
- * state region per lane (its largest pair's) plus every pair's small
- * tables.  Host only. */
+ * run in one CUDA graph on `lanes` concurrent branches (default 1, see
+ * nadmm_batch_set_lanes), spread longest first to balance voxel counts;
+ * pairs of one lane run one after another and share that lane's scratch,
+ * so the workspace is one state region per lane (its largest pair's) plus
+ * every pair's small tables.  One lane is the default because a pair's
+ * ADMM working set (about 64 bytes per voxel) already fills most of the
+ * 126 MB L2 at 128 x 128 x 96: concurrent pairs evict each other.
+ * Host only. */
 nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, const int32_t* dims,
                                   nadmm_handle* out);
 
@@ -300,6 +303,15 @@ nadmm_status nadmm_ssd_after_warp_backward(nadmm_handle h, const float* fixed,
                                            const float* moving, const float* u,
                                            const float* grad_loss, float* grad_fixed,
                                            float* grad_moving, float* grad_u, void* stream);
+
+/* Failure-detection self-test (the paper has no counterpart): one block
+ * waits, with the same bounded mbarrier wait the passes use for their bulk
+ * copies but `attempts` (1 .. 2^20) tries, on a barrier that nothing
+ * arrives at and no copy targets.  The wait expires, the kernel records
+ * NADMM_ERR_TIMEOUT in the handle's status word and returns normally, so
+ * the next nadmm_get_status reports NADMM_ERR_TIMEOUT and the context stays
+ * usable.  Errors: INVALID_ARG, NO_WORKSPACE, CUDA. */
+nadmm_status nadmm_selftest_wait_timeout(nadmm_handle h, int32_t attempts, void* stream);
 
 /* ---------------------------------------------------------------------
  * Measurement

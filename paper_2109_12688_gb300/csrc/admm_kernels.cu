@@ -122,12 +122,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // count bounds the whole wait well under a second of a stuck copy.
 constexpr int kWaitAttempts = 1 << 20;
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < kWaitAttempts; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  int attempts = kWaitAttempts) {
+  for (int i = 0; i < attempts; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
 #endif
+
+// Self-test of the timeout path: one barrier that nothing ever arrives at
+// (no copy is issued), waited on with the bounded wait of the passes; the
+// expired wait sets the status bit and the kernel returns normally.
+__global__ void k_wait_selftest(unsigned* status, int attempts) {
+#if defined(__CUDA_ARCH__)
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, attempts));
+  if (!ok && threadIdx.x == 0 && status != nullptr) atomicOr(status, kStatusTimeout);
+#endif
+}
+
+cudaError_t launch_wait_selftest(unsigned* status, int attempts, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(status, attempts);
+  return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------- plane pass
 // Shared-memory staging of the real-space tiles: slot s holds R rows x nx.

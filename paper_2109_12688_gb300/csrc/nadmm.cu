@@ -332,7 +332,7 @@ nadmm_status check_dev_ptrs(std::initializer_list<const void*> ptrs) {
   return NADMM_OK;
 }
 
-constexpr int kDefaultLanes = 4;
+constexpr int kDefaultLanes = 1;
 
 // Plans, tables and the workspace layout of one grid (host memory only).
 nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
@@ -1117,6 +1117,16 @@ nadmm_status nadmm_ssd_after_warp_backward(nadmm_handle h, const float* fixed, c
   if (e == cudaSuccess)
     e = launch_ssd_vjp(dims_of(h), fixed, moving, u, grad_loss, grad_fixed, grad_moving, grad_u, s);
   return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_ssd_after_warp_backward");
+}
+
+nadmm_status nadmm_selftest_wait_timeout(nadmm_handle h, int32_t attempts, void* stream) {
+  nadmm_status st = need_ws(h);
+  if (st != NADMM_OK) return st;
+  if (attempts < 1 || attempts > (1 << 20))
+    return fail(NADMM_ERR_INVALID_ARG, "attempts must be in 1 .. 2^20");
+  cudaError_t e = launch_wait_selftest(h->tab<unsigned>(h->o_red) + 2, attempts,
+                                       (cudaStream_t)stream);
+  return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_selftest_wait_timeout");
 }
 
 }  // extern "C"

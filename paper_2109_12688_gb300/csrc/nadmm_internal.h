@@ -82,6 +82,9 @@ struct PencilArgs {
 constexpr unsigned kStatusNonfinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;
 
+// One block waits (bounded, `attempts` tries) on a barrier nothing arrives at.
+cudaError_t launch_wait_selftest(unsigned* status, int attempts, cudaStream_t s);
+
 // Fill the FastDiv fields and pitches of the pass arguments from the sizes.
 void finish_plane_args(PlaneArgs& a);
 void finish_pencil_args(PencilArgs& a);

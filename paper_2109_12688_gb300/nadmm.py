@@ -77,6 +77,7 @@ _SIGS = {
     "nadmm_register_batched": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                               ctypes.POINTER(_P), _P]),
     "nadmm_backward": (ctypes.c_int, [_P] * 9),
+    "nadmm_selftest_wait_timeout": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "nadmm_ssd_after_warp": (ctypes.c_int, [_P] * 6),
     "nadmm_ssd_after_warp_backward": (ctypes.c_int, [_P] * 9),
 }
@@ -178,6 +179,10 @@ def nadmm_ssd_after_warp_backward(h, fixed, moving, u, grad_loss, grad_fixed, gr
     _check(load().nadmm_ssd_after_warp_backward(h, _ptr(fixed), _ptr(moving), _ptr(u),
                                                 _ptr(grad_loss), _ptr(grad_fixed),
                                                 _ptr(grad_moving), _ptr(grad_u), _stream(stream)))
+
+
+def nadmm_selftest_wait_timeout(h, attempts, stream=None):
+    _check(load().nadmm_selftest_wait_timeout(h, attempts, _stream(stream)))
 
 
 def nadmm_destroy(h):

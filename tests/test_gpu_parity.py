@@ -321,6 +321,23 @@ def test_nonfinite_input_sets_status(lib):
     assert lib.nadmm_get_status(reg.handle, torch.cuda.current_stream()) == lib.NADMM_OK
 
 
+@pytest.mark.parametrize("attempts", [1, 4096])
+def test_expired_wait_sets_timeout_and_context_survives(lib, attempts):
+    """A bounded mbarrier wait that nothing completes reports
+    NADMM_ERR_TIMEOUT through the status word; the next registration on the
+    same context runs and matches the oracle."""
+    dims = (32, 32, 24)
+    reg = lib.Registration(dims, device=DEV, outer=2, inner=3)
+    lib.nadmm_selftest_wait_timeout(reg.handle, attempts, torch.cuda.current_stream())
+    assert lib.nadmm_get_status(reg.handle, torch.cuda.current_stream()) == lib.NADMM_ERR_TIMEOUT
+    assert lib.nadmm_get_status(reg.handle, torch.cuda.current_stream()) == lib.NADMM_OK
+    pair = synth.make_pair(dims, seed=6)
+    u = host(reg.register(dev(pair["fixed"]), dev(pair["moving"])))
+    assert lib.nadmm_get_status(reg.handle, torch.cuda.current_stream()) == lib.NADMM_OK
+    ref = O.register(pair["fixed"], pair["moving"], lam=10.0, theta=0.1, n=2, outer=2, inner=3)
+    assert np.abs(u - ref).max() <= 1e-3
+
+
 # ------------------------------------------------------------------ 256 x 256 x 192
 LARGE = (256, 256, 192)
 
@@ -371,3 +388,23 @@ def test_large_register_full_schedule_n3(lib, large_pair):
     warped = O.warp(moving, host(u))
     ssd0 = ((moving.astype(float) - fixed) ** 2).sum()
     assert ((warped - fixed) ** 2).sum() < ssd0
+
+
+@pytest.mark.parametrize("seed,n", [(0, 1), (1, 2), (2, 3)])
+def test_register_128x128x96_label_metrics(lib, seed, n):
+    """The paper's measures on the synthetic labels (Sec. 4): after the
+    10 x 10 registration the warped source labels overlap the target labels
+    better (mean Dice over LV, LVM, RV), lie closer (mean per-slice
+    Hausdorff) and no voxel folds."""
+    dims = (128, 128, 96)
+    pair = synth.make_pair(dims, seed=seed)
+    u, reg = _register_gpu(lib, pair, dims, order_n=n, lam=10.0, theta=0.1, outer=10, inner=10)
+    fixed_lab, moving_lab = pair["labels_fixed"], pair["labels_moving"]
+    warped = O.warp_labels(moving_lab, u)
+    d0 = np.mean([O.dice(moving_lab, fixed_lab, k) for k in (1, 2, 3)])
+    d1 = np.mean([O.dice(warped, fixed_lab, k) for k in (1, 2, 3)])
+    h0 = np.mean([O.hausdorff_per_slice(moving_lab, fixed_lab, k) for k in (1, 2, 3)])
+    h1 = np.mean([O.hausdorff_per_slice(warped, fixed_lab, k) for k in (1, 2, 3)])
+    assert d1 > d0
+    assert h1 < h0
+    assert O.nonpositive_jacobian_percent(u) == 0.0
