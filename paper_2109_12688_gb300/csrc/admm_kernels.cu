@@ -240,7 +240,7 @@ NADMM_HD void plane_scatter(const PlaneArgs& a, const float2* lines, const int* 
 
 // Point-wise part of the iteration on staged tiles (fld) and lines.
 template <int IN, bool PREV, bool STEP>
-NADMM_HD void plane_pointwise(const PlaneArgs& a, const float* fld, float2* lines, int z, int y0,
+NADMM_HD void plane_pointwise(const PlaneArgs& a, float* fld, float2* lines, int z, int y0,
                               int tid, int nthr) {
   constexpr FieldMap F = field_map<IN, PREV, STEP>();
   const int h = a.R / 2;
@@ -288,8 +288,15 @@ NADMM_HD void plane_pointwise(const PlaneArgs& a, const float* fld, float2* line
           a.w_out[i] = wk1[comp];
           if (a.b_out != nullptr) a.b_out[i] = bk1[comp];
         } else if (IN == IN_SPEC || IN == IN_STATE) {
-          a.wp[i] = wk1[comp];
-          a.bp[i] = bk1[comp];
+          if (F.wp >= 0) {
+            // w^{k-2}, b^{k-2} of this element were read above: their staged
+            // tiles take w^{k-1}, b^{k-1} and leave by bulk stores
+            fld[(F.wp + comp) * tile + so] = wk1[comp];
+            fld[(F.bp + comp) * tile + so] = bk1[comp];
+          } else {
+            a.wp[i] = wk1[comp];
+            a.bp[i] = bk1[comp];
+          }
         }
       }
       if (STEP) {
@@ -307,7 +314,10 @@ NADMM_HD void plane_pointwise(const PlaneArgs& a, const float* fld, float2* line
 #pragma unroll
           for (int comp = 0; comp < 3; ++comp) {
             ynew[half][comp] = v[comp] + bh[comp];
-            if (a.y != nullptr) a.y[comp * V + vox] = ynew[half][comp];
+            if (F.y >= 0)  // y^{k-1} of this element was read above
+              fld[(F.y + comp) * tile + so] = ynew[half][comp];
+            else if (a.y != nullptr)
+              a.y[comp * V + vox] = ynew[half][comp];
           }
         }
       }
@@ -436,8 +446,23 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
     }
   }
   plane_pointwise<IN, PREV, STEP>(a, fld, lines, z, y0, tid, nthr);
+  // tiles rewritten in shared memory by the point-wise step (w, b, y state)
+  constexpr bool kTileStores = STEP && (F.wp >= 0 || F.y >= 0);
+  if (kTileStores) fence_proxy_async();  // make them visible to the bulk copies
   if (STEP) {
     __syncthreads();
+    if (kTileStores && tid == 0) {
+      const size_t V = (size_t)a.nx * a.ny * a.nz;
+      for (int comp = 0; comp < 3; ++comp) {
+        const size_t g = comp * V + tile_off;
+        if (F.wp >= 0) {
+          bulk_store(a.wp + g, fld + (size_t)(F.wp + comp) * a.R * a.nx, tile_bytes);
+          bulk_store(a.bp + g, fld + (size_t)(F.bp + comp) * a.R * a.nx, tile_bytes);
+        }
+        if (F.y >= 0) bulk_store(a.y + g, fld + (size_t)(F.y + comp) * a.R * a.nx, tile_bytes);
+      }
+      bulk_commit();
+    }
     if (a.xr2 != 0) {
       plane_lane_fft<false>(a, lines, tw, nlines, tid);
       __syncthreads();
@@ -448,6 +473,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
       }
     }
     plane_scatter(a, lines, pos, z, y0, tid, nthr);
+    // the staged tiles must stay until the bulk stores have read them
+    if (kTileStores && tid == 0) bulk_wait_read();
   }
 #endif
 }

@@ -340,7 +340,7 @@ nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
   if (st != NADMM_OK) return st;
   nadmm_context* h = new nadmm_context();
   h->cfg = *cfg;
-  if (!factor_axis(cfg->nx, h->px, true) || !factor_axis(cfg->ny, h->py, true) ||
+  if (!factor_axis(cfg->nx, h->px, true) || !factor_axis(cfg->ny, h->py, true, 16) ||
       !factor_axis(cfg->nz, h->pz, true)) {
     delete h;
     return fail(NADMM_ERR_UNSUPPORTED_SIZE, "no radix plan for these dimensions");

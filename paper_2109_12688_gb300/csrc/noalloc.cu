@@ -180,7 +180,7 @@ extern "C" nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int
   if (((uintptr_t)y & 15u) || ((uintptr_t)w & 15u))
     return fail(NADMM_ERR_ALIGNMENT, "device pointer not 16-byte aligned");
   AxisPlan px, py, pz;
-  if (!factor_axis(nx, px, true) || !factor_axis(ny, py, true) || !factor_axis(nz, pz, true))
+  if (!factor_axis(nx, px, true) || !factor_axis(ny, py, true, 16) || !factor_axis(nz, pz, true))
     return fail(NADMM_ERR_UNSUPPORTED_SIZE, "no radix plan for these dimensions");
   PlaneArgs a = {};
   a.px = px;

@@ -26,8 +26,9 @@ inline bool lane_pair_supported(int r1, int r2) {
   return false;
 }
 
-inline int lane_split(int n) {
-  for (int r2 : {8, 16}) {
+// R2 of the lane plan of n (0 if none); `first` (8 or 16) is tried first.
+inline int lane_split(int n, int first = 8) {
+  for (int r2 : {first, 24 - first}) {
     if (n % r2) continue;
     for (int r1 : kLaneR1)
       if (r1 == n / r2) return r2;
@@ -53,10 +54,10 @@ inline bool best_factors(int n, int depth, int* out, int& best_len, int* cur, in
   return found;
 }
 
-inline bool factor_axis(int n, AxisPlan& p, bool lane_plan = false) {
+inline bool factor_axis(int n, AxisPlan& p, bool lane_plan = false, int lane_first = 8) {
   if (n < 2) return false;
   int out[kMaxStages], cur[kMaxStages], best = kMaxStages + 1;
-  const int r2 = lane_plan ? lane_split(n) : 0;
+  const int r2 = lane_plan ? lane_split(n, lane_first) : 0;
   if (r2) {
     out[0] = n / r2;
     out[1] = r2;
