@@ -95,6 +95,24 @@ __device__ __forceinline__ void tensor_load_2d(void* dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
       : "memory");
 }
+// 3D tiled TMA load of box {x, y, z} of `map` into shared memory
+__device__ __forceinline__ void tensor_load_3d(void* dst, const CUtensorMap* map, int x, int y,
+                                               int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+// 3D tiled TMA store of a shared-memory box to {x, y, z} of `map`
+__device__ __forceinline__ void tensor_store_3d(const CUtensorMap* map, int x, int y, int z,
+                                                const void* src) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(z), "r"(smem_addr(src))
+      : "memory");
+}
 // 2D tiled TMA store of a shared-memory box to {x, y} of `map`
 __device__ __forceinline__ void tensor_store_2d(const CUtensorMap* map, int x, int y,
                                                 const void* src) {
@@ -337,10 +355,10 @@ struct PlaneSmem {
 
 NADMM_HD PlaneSmem plane_layout(const PlaneArgs& a, int nfields) {
   PlaneSmem L;
-  size_t o = 16;  // mbarrier
+  size_t o = 16;  // two mbarriers: field tiles, spectrum block
   L.fld = o;
   o += (size_t)nfields * a.R * a.nx * sizeof(float);
-  o = (o + 15) & ~(size_t)15;
+  o = (o + 127) & ~(size_t)127;  // tensor copies land here
   L.lines = o;
   o += (size_t)3 * (a.R / 2) * a.pitch * sizeof(float2);
   L.total = (o + 15) & ~(size_t)15;
@@ -348,6 +366,83 @@ NADMM_HD PlaneSmem plane_layout(const PlaneArgs& a, int nfields) {
 }
 
 #if defined(__CUDA_ARCH__)
+// Spectrum block moved by tensor copies: box {R, 1, 3 nkx} lands densely at
+// the start of the line buffer as T[ckx][r] (ckx = comp nkx + kx, r < R).
+// Unpack it in place into the complex lines of the two-for-one transform:
+// every thread first reads all its items, then (after a barrier) writes.
+__device__ __forceinline__ void plane_unpack(const PlaneArgs& a, float2* lines,
+                                             const int* __restrict__ pos, int tid, int nthr) {
+  const int h = a.R / 2;
+  const int total = 3 * a.nkx * h;
+  const float2* T = lines;
+  float2 A[kGatherItems], B[kGatherItems];
+#pragma unroll
+  for (int it = 0; it < kGatherItems; ++it) {
+    const int g = tid + it * nthr;
+    if (g < total) {
+      const int rest = (int)fdiv((uint32_t)g, a.half_div);  // ckx
+      const int r = g - rest * h;
+      A[it] = T[rest * a.R + r];
+      B[it] = T[rest * a.R + r + h];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kGatherItems; ++it) {
+    const int g = tid + it * nthr;
+    if (g < total) {
+      const int rest = (int)fdiv((uint32_t)g, a.half_div);
+      const int r = g - rest * h;
+      const int comp = (int)fdiv((uint32_t)rest, a.nkx_div);
+      const int kx = rest - comp * a.nkx;
+      float2* line = lines + (comp * h + r) * a.pitch;
+      const float2 Av = A[it], Bv = B[it];
+      if (kx == 0 || 2 * kx == a.nx) {
+        line[swz_rt(pos[kx], a.xlog2r2)] = make_float2(Av.x, Bv.x);
+      } else {
+        line[swz_rt(pos[kx], a.xlog2r2)] = make_float2(Av.x - Bv.y, Av.y + Bv.x);
+        line[swz_rt(pos[a.nx - kx], a.xlog2r2)] = make_float2(Av.x + Bv.y, Bv.x - Av.y);
+      }
+    }
+  }
+}
+
+// Inverse of plane_unpack for the forward transform's output: half spectra
+// of the two rows of each line, packed in place as T[ckx][r].
+__device__ __forceinline__ void plane_pack(const PlaneArgs& a, float2* lines,
+                                           const int* __restrict__ pos, int tid, int nthr) {
+  const int h = a.R / 2;
+  const int total = 3 * a.nkx * h;
+  float2 A[kGatherItems], B[kGatherItems];
+#pragma unroll
+  for (int it = 0; it < kGatherItems; ++it) {
+    const int g = tid + it * nthr;
+    if (g < total) {
+      const int rest = (int)fdiv((uint32_t)g, a.half_div);
+      const int r = g - rest * h;
+      const int comp = (int)fdiv((uint32_t)rest, a.nkx_div);
+      const int kx = rest - comp * a.nkx;
+      const float2* line = lines + (comp * h + r) * a.pitch;
+      const float2 Zk = line[swz_rt(pos[kx], a.xlog2r2)];
+      const float2 Zm = line[swz_rt(pos[kx == 0 ? 0 : a.nx - kx], a.xlog2r2)];
+      A[it] = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
+      B[it] = make_float2(0.5f * (Zk.y + Zm.y), 0.5f * (Zm.x - Zk.x));
+    }
+  }
+  __syncthreads();
+  float2* T = lines;
+#pragma unroll
+  for (int it = 0; it < kGatherItems; ++it) {
+    const int g = tid + it * nthr;
+    if (g < total) {
+      const int rest = (int)fdiv((uint32_t)g, a.half_div);
+      const int r = g - rest * h;
+      T[rest * a.R + r] = A[it];
+      T[rest * a.R + r + h] = B[it];
+    }
+  }
+}
+
 // x-DFT of the CTA's lines by groups of xr2 lanes (lane FFT, swizzled lines).
 template <bool INV>
 __device__ __forceinline__ void plane_lane_fft(const PlaneArgs& a, float2* lines,
@@ -376,7 +471,7 @@ __device__ __forceinline__ const float* field_src(const PlaneArgs& a, int slot) 
 #endif
 
 template <int IN, bool PREV, bool STEP>
-__global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
+__global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constant__ PlaneArgs a) {
 #if defined(__CUDA_ARCH__)
   constexpr FieldMap F = field_map<IN, PREV, STEP>();
   extern __shared__ __align__(128) unsigned char smem[];
@@ -401,12 +496,17 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
   constexpr bool kEarlyLoads = (IN == IN_SPEC);
   const uint32_t tile_bytes = (uint32_t)(a.R * a.nx * sizeof(float));
   const size_t tile_off = ((size_t)z * a.ny + y0) * a.nx;
-  if (F.n > 0) {
+  const bool spec_tma = a.spec_tma != 0;
+  const int nckx = 3 * a.nkx;
+  if (F.n > 0 || spec_tma) {
     if (tid == 0) {
       mbar_init(bar, 1);
+      mbar_init(bar + 1, 1);
       fence_barrier_init();
     }
     __syncthreads();
+  }
+  if (F.n > 0) {
     if (kEarlyLoads && tid < 32) {
       if (tid == 0) mbar_expect_tx(bar, tile_bytes * F.n);
       __syncwarp();
@@ -417,6 +517,11 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
   }
   pdl_wait();
   pdl_trigger();
+  if (IN == IN_SPEC && spec_tma && tid == 0) {
+    // the CTA's spectrum block {R rows, this z, all (comp, kx)}: one box
+    mbar_expect_tx(bar + 1, (uint32_t)(nckx * a.R * sizeof(float2)));
+    tensor_load_3d(lines, &a.smap, y0, z, 0, bar + 1);
+  }
   if (F.n > 0 && !kEarlyLoads && tid < 32) {
     if (tid == 0) mbar_expect_tx(bar, tile_bytes * F.n);
     __syncwarp();
@@ -425,7 +530,18 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
                 tile_bytes, bar);
   }
   if (IN == IN_SPEC) {
-    plane_gather(a, lines, pos, z, y0, tid, nthr);
+    if (spec_tma) {
+      const bool ok = __syncthreads_and(mbar_wait_bounded(bar + 1, 0));
+      if (!ok) {
+        if (tid == 0 && a.status != nullptr) atomicOr(a.status, kStatusTimeout);
+        mbar_wait_bounded(bar + 1, 0);  // let copies still in flight land before exit
+        if (F.n > 0) mbar_wait_bounded(bar, 0);
+        return;
+      }
+      plane_unpack(a, lines, pos, tid, nthr);
+    } else {
+      plane_gather(a, lines, pos, z, y0, tid, nthr);
+    }
     __syncthreads();
     if (a.xr2 != 0) {
       plane_lane_fft<true>(a, lines, tw, nlines, tid);
@@ -472,9 +588,19 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(PlaneArgs a) {
         __syncthreads();
       }
     }
-    plane_scatter(a, lines, pos, z, y0, tid, nthr);
-    // the staged tiles must stay until the bulk stores have read them
-    if (kTileStores && tid == 0) bulk_wait_read();
+    if (spec_tma) {
+      plane_pack(a, lines, pos, tid, nthr);
+      fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        tensor_store_3d(&a.smap, y0, z, 0, lines);
+        bulk_commit();
+      }
+    } else {
+      plane_scatter(a, lines, pos, z, y0, tid, nthr);
+    }
+    // shared memory must stay until the bulk stores have read it
+    if ((kTileStores || spec_tma) && tid == 0) bulk_wait_read();
   }
 #endif
 }
@@ -676,8 +802,13 @@ void finish_plane_args(PlaneArgs& a) {
   } else {
     a.xr1 = a.xr2 = 0;
     a.xlog2r2 = -1;
-    a.pitch = a.nx + 1;  // odd: lanes on different lines hit different banks
+    a.pitch = a.nx + 3;  // odd: lanes on different lines hit different banks
   }
+  // The spectrum block (3 nkx R values) fits the line buffer (3 R/2 lines of
+  // pitch >= nx + 2 = 2 nkx) and moves by one tensor copy when the box spans
+  // all (comp, kx) (3 nkx <= 256, i.e. nx <= 168) and each thread holds at
+  // most kGatherItems (comp, kx, row) items in the in-place (un)pack.
+  a.spec_tma = (3 * a.nkx <= 256 && 3 * a.nkx * (a.R / 2) <= kGatherItems * kPlaneThreads) ? 1 : 0;
   a.nx_div = make_fastdiv((uint32_t)a.nx);
   a.lines_div = make_fastdiv((uint32_t)(3 * (a.R / 2)));
   a.half_div = make_fastdiv((uint32_t)(a.R / 2));
@@ -716,6 +847,35 @@ cudaError_t encode_pencil_map(PencilArgs& a) {
   const cuuint32_t box[2] = {(cuuint32_t)a.zcols, (cuuint32_t)a.nz};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(&a.zmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, a.spec, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t encode_plane_map(PlaneArgs& a) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (encode == nullptr) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorSymbolNotFound;
+    encode = reinterpret_cast<EncodeFn>(fn);
+  }
+  // complex64 values as 8-byte elements: dims {ny, nz, 3 nkx}; box {R, 1, <= 256}
+  const int nckx = 3 * a.nkx;
+  const cuuint64_t dims[3] = {(cuuint64_t)a.ny, (cuuint64_t)a.nz, (cuuint64_t)nckx};
+  const cuuint64_t strides[2] = {(cuuint64_t)a.ny * sizeof(float2),
+                                 (cuuint64_t)a.ny * a.nz * sizeof(float2)};
+  if (nckx > 256) return cudaErrorInvalidValue;  // one box must span every (comp, kx)
+  const cuuint32_t box[3] = {(cuuint32_t)a.R, 1u, (cuuint32_t)nckx};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(&a.smap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, a.spec, dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;

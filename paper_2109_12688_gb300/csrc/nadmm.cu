@@ -64,6 +64,8 @@ struct nadmm_context {
   char* ws = nullptr;
   char* wt = nullptr;
   CUtensorMap zmap;  // z-pass tensor map of the workspace spectrum
+  CUtensorMap smap;  // plane-pass tensor map of the workspace spectrum
+  bool smap_ok = false;
   // graph cache: slot 0 the forward registration, slot 1 the backward
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   std::vector<const void*> gkey[2];
@@ -171,6 +173,8 @@ PlaneArgs plane_args(const nadmm_context* h) {
   a.eps = h->cfg.eps;
   a.data_term = h->cfg.data_term;
   finish_plane_args(a);
+  a.smap = h->smap;
+  if (!h->smap_ok) a.spec_tma = 0;
   return a;
 }
 
@@ -519,6 +523,17 @@ nadmm_status attach(nadmm_context* h, char* ws, char* wt) {
     return cuda_fail(e, "cuTensorMapEncodeTiled");
   }
   h->zmap = pa.zmap;
+  h->smap_ok = false;
+  PlaneArgs sa = plane_args(h);
+  if (sa.spec_tma) {
+    e = encode_plane_map(sa);
+    if (e != cudaSuccess) {
+      h->ws = h->wt = nullptr;
+      return cuda_fail(e, "cuTensorMapEncodeTiled (plane)");
+    }
+    h->smap = sa.smap;
+    h->smap_ok = true;
+  }
   return NADMM_OK;
 }
 

@@ -25,6 +25,7 @@ enum InMode : int {
 // starts iteration k (Nesterov extrapolation, closed-form v-step, forward
 // x-DFT), so the 3D transform needs only this pass and the pencil pass.
 struct PlaneArgs {
+  CUtensorMap smap;        // 3D view {ny, nz, 3 nkx} of the spectrum, box {R, 1, <= 256}
   float2* spec;            // [3][nkx][nz][ny] half spectrum (in/out)
   float* y;                // [3][V] y = v + b_hat of the current iteration (in/out) or null
   float* wp;               // [3][V] w state slot (in: w^{k-2}, out: w^{k-1})
@@ -51,6 +52,8 @@ struct PlaneArgs {
   int pitch;               // shared-memory line pitch (>= nx)
   int xr1, xr2;            // lane-FFT plan of the x axis (xr2 = 0: shared-memory stages)
   int xlog2r2;             // log2(xr2), or -1 (line positions not swizzled)
+  int spec_tma;            // 1: the CTA's spectrum block moves by tensor copies through
+                           // the line buffer (needs smap); 0: per-thread loads/stores
   float beta;              // beta_{k-1}
   float theta, eps;
   int data_term;           // 1 or 2
@@ -90,6 +93,8 @@ void finish_plane_args(PlaneArgs& a);
 void finish_pencil_args(PencilArgs& a);
 // Encode a.zmap for a.spec (host only; needs finish_pencil_args first).
 cudaError_t encode_pencil_map(PencilArgs& a);
+// Encode a.smap for a.spec (host only; needs finish_plane_args first).
+cudaError_t encode_plane_map(PlaneArgs& a);
 
 // Lane-FFT y/z passes (lane_passes.cu) for two-stage plans [R1, R2 in {8, 16}].
 bool lane_y_supported(const PencilArgs& a);

@@ -242,6 +242,10 @@ extern "C" nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int
   a.spec = reinterpret_cast<float2*>(base + L.spec);
   a.twx = twx;
   a.posx = posx;
+  if (a.spec_tma) {
+    e = encode_plane_map(a);
+    if (e != cudaSuccess) return cuda_fail(e, "cuTensorMapEncodeTiled (plane)");
+  }
   PlaneArgs fwd = a;
   fwd.y = nullptr;
   fwd.w_in = y;
