@@ -157,12 +157,13 @@ def parse_args():
     ap.add_argument("--orders", default="1,2,3",
                     help="regulariser orders registered per step (profiling runs use one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
-    ap.add_argument("--workload", choices=("registration", "batch64", "large", "grad"),
+    ap.add_argument("--workload", choices=("registration", "batch64", "large", "grad", "pyramid"),
                     default="registration",
                     help="registration: the 128x128x96 benchmark (default); batch64: 64 uneven "
                          "pairs in one batched graph vs 64 sequential calls; large: one "
                          "256x256x192 n=3 registration with its device-memory peak; grad: "
-                         "128x128x96 n=2 8x20 forward + SSD + reverse mode")
+                         "128x128x96 n=2 8x20 forward + SSD + reverse mode; pyramid: the paper's "
+                         "three-level first schedule on 128x128x96, n = 1, 2, 3")
     return ap.parse_args()
 
 
@@ -307,6 +308,38 @@ def run_extra(args, rank, world):
             "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms,
             "ms_by_lanes": lanes_ms,
             "voxel_admm_iters_per_s": vox * OUTER * INNER / (ms / 1e3),
+            "clocks": clk,
+        }
+    elif args.workload == "pyramid":
+        dims = (128, 128, 96)
+        # Table 1, first hyper-parameter version, L2 data term: seconds on a 16 GB V100
+        paper_s = {1: 2.17, 2: 1.38, 3: 1.37}
+        per = {}
+        clk = None
+        for n in (1, 2, 3):
+            p = synth.make_pair(dims, seed=n)
+            I0 = torch.from_numpy(p["fixed"]).to(dev)
+            I1 = torch.from_numpy(p["moving"]).to(dev)
+            reg = nadmm.PyramidRegistration(dims, device=dev, order_n=n, lam=LAM, theta=THETA)
+            U = torch.empty((3, 96, 128, 128), device=dev)
+            per[n], c = timed(lambda: nadmm.nadmm_register_pyramid(reg.handle, I0, I1, U, stream))
+            clk = clk or c
+        ms = sum(per.values()) / 3
+        paper_ms = 1000.0 * sum(paper_s.values()) / 3
+        line = {
+            "metric": "ms per 128x128x96 registration, three-level pyramid (paper's first "
+                      "schedule)", "value": ms, "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 3 * ms,
+            "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": ms / paper_ms, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "128x128x96 phantom pairs, n = 1, 2, 3, s = 2, lambda=10, "
+                                   "theta=0.1; levels 32x32x24, 64x64x48, 128x128x96 with ADMM "
+                                   "10/5/5 and warpings 10/10/5",
+                       "l2": "flushed between timed steps (256 MB write outside the step events)"},
+            "ms_by_order": per,
+            "paper_s_by_order": paper_s,
+            "paper_context": "Table 1, L2 + n-th order, first version, 16 GB Tesla V100, "
+                             "PyTorch, mean over 100 private test pairs",
             "clocks": clk,
         }
     elif args.workload == "grad":

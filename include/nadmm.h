@@ -185,6 +185,38 @@ nadmm_status nadmm_register_batched(nadmm_handle h, const float* const* fixed,
                                     void* stream);
 
 /* ---------------------------------------------------------------------
+ * Pyramid (Sec. 4, "Hyperparameter tuning"): the registration run on
+ * `levels` grids, each half the size of the next, coarsest first.
+ * --------------------------------------------------------------------- */
+
+/* Create a pyramid handle.  `finest` gives the full-resolution grid and every
+ * other setting; level l (0 = finest) has grid (nx, ny, nz) / 2^l, which must
+ * pass nadmm_create's checks, so every dimension must be divisible by
+ * 2^(levels - 1).  outer[i] and inner[i] are the warpings and ADMM iterations
+ * of the i-th level run, COARSEST FIRST (the paper's first version: outer
+ * {10, 10, 5}, inner {10, 5, 5} on three levels).  Readings where the paper
+ * gives no detail: a coarser image is the 2 x 2 x 2 block average of the
+ * finer one; a level starts from the coarser level's displacement resampled
+ * at cell centres and doubled, u_fine(x) = 2 u_coarse((x - 1/2) / 2)
+ * (trilinear, clamped); lambda, theta, n, s and the velocity bound (in voxels
+ * of each level) are shared.  1 <= levels <= 5; NADMM_FLAG_SAVE_FOR_BACKWARD
+ * is rejected.  The workspace holds one shared state region, every level's
+ * tables and the coarse images and displacements.  Host only.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE ("level l: ..."). */
+nadmm_status nadmm_create_pyramid(const nadmm_config* finest, int32_t levels,
+                                  const int32_t* outer, const int32_t* inner,
+                                  nadmm_handle* out);
+
+/* Register with a pyramid handle: fixed, moving device [nz][ny][nx] and u_out
+ * device [3][nz][ny][nx] on the finest grid, as one CUDA-graph replay (or
+ * direct launches with NADMM_FLAG_NO_GRAPH).  Only nadmm_register_pyramid,
+ * nadmm_get_status, nadmm_workspace_size, nadmm_set_workspace and
+ * nadmm_destroy accept a pyramid handle.
+ * Errors: INVALID_ARG, ALIGNMENT, NO_WORKSPACE, CUDA. */
+nadmm_status nadmm_register_pyramid(nadmm_handle h, const float* fixed, const float* moving,
+                                    float* u_out, void* stream);
+
+/* ---------------------------------------------------------------------
  * Step-level entry points: one part of the path each, on device buffers of
  * the handle's grid, using the handle's workspace as scratch.  They run the
  * same kernels as nadmm_register.

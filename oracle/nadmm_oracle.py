@@ -308,15 +308,15 @@ def jacobian_determinant(u):
 # ---------------------------------------------------------------- outer loop
 def register(I0, I1, lam=10.0, theta=0.1, n=2, outer=5, inner=10, s=2,
              eps=1e-6, kappa=0.5, delta=1.0, accelerate=True,
-             return_scales=False):
+             return_scales=False, u0=None):
     """Greedy diffeomorphic registration (Sec. 2, text after Eq. 2; Eq. 1
-    with N = 1): u <- 0; repeat ``outer`` times: linearise at the current
-    warp of the original I1, run ``inner`` iterations of Eq. 5, bound the
-    velocity (R8), compose phi <- phi o (Id + v).  Returns u with
+    with N = 1): u <- u0 (default 0); repeat ``outer`` times: linearise at
+    the current warp of the original I1, run ``inner`` iterations of Eq. 5,
+    bound the velocity (R8), compose phi <- phi o (Id + v).  Returns u with
     I1 o (Id + u) ~ I0."""
     I0 = np.asarray(I0, np.float64)
     I1 = np.asarray(I1, np.float64)
-    u = np.zeros((3,) + I0.shape)
+    u = np.zeros((3,) + I0.shape) if u0 is None else np.array(u0, np.float64)
     scales = []
     for _ in range(outer):
         J, c, _ = linearise(I0, I1, u)

@@ -161,6 +161,36 @@ __global__ void __launch_bounds__(kBX * kBY) k_jacobian(Dims d, const float* __r
   }
 }
 
+// Pyramid (Sec. 4): coarse(x) = mean of the 2 x 2 x 2 fine block at 2x.
+__global__ void __launch_bounds__(kBX * kBY) k_downsample2(Dims c, const float* __restrict__ fine,
+                                                           float* __restrict__ coarse) {
+  pdl_wait();
+  pdl_trigger();
+  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= c.nx || y >= c.ny) return;
+  const size_t fx = 2 * (size_t)c.nx, fxy = fx * 2 * (size_t)c.ny;
+  const float* p = fine + (2 * (size_t)z) * fxy + (2 * (size_t)y) * fx + 2 * (size_t)x;
+  const float s = (__ldg(p) + __ldg(p + 1)) + (__ldg(p + fx) + __ldg(p + fx + 1)) +
+                  ((__ldg(p + fxy) + __ldg(p + fxy + 1)) + (__ldg(p + fxy + fx) + __ldg(p + fxy + fx + 1)));
+  coarse[((size_t)z * c.ny + y) * c.nx + x] = 0.125f * s;
+}
+
+// u_fine(x) = 2 u_coarse((x - 1/2) / 2), trilinear with clamped coordinates.
+__global__ void __launch_bounds__(kBX * kBY) k_upsample_u(Dims c, Dims f, const float* __restrict__ uc,
+                                                          float* __restrict__ uf) {
+  pdl_wait();
+  pdl_trigger();
+  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= f.nx || y >= f.ny) return;
+  const size_t Vc = (size_t)c.nx * c.ny * c.nz, Vf = (size_t)f.nx * f.ny * f.nz;
+  const size_t i = ((size_t)z * f.ny + y) * f.nx + x;
+  const float px = 0.5f * ((float)x - 0.5f), py = 0.5f * ((float)y - 0.5f), pz = 0.5f * ((float)z - 0.5f);
+#pragma unroll
+  for (int comp = 0; comp < 3; ++comp) uf[comp * Vf + i] = 2.0f * trilerp(uc + comp * Vc, c, px, py, pz);
+}
+
 static dim3 grid3(Dims d, int zslices) {
   return dim3((unsigned)((d.nx + kBX - 1) / kBX), (unsigned)((d.ny + kBY - 1) / kBY),
               (unsigned)zslices);
@@ -187,6 +217,14 @@ cudaError_t launch_compose(Dims d, const float* w, const float* u_in, float* u_o
                            float* scale_out, cudaStream_t s) {
   return launch_pdl(k_compose, grid3(d, d.nz), kBlock, 0, s, d, w, u_in, u_out,
                     (const unsigned*)red, kappa, delta, status, scale_out);
+}
+
+cudaError_t launch_downsample2(Dims coarse, const float* fine, float* out, cudaStream_t s) {
+  return launch_pdl(k_downsample2, grid3(coarse, coarse.nz), kBlock, 0, s, coarse, fine, out);
+}
+
+cudaError_t launch_upsample_u(Dims coarse, Dims fine, const float* uc, float* uf, cudaStream_t s) {
+  return launch_pdl(k_upsample_u, grid3(fine, fine.nz), kBlock, 0, s, coarse, fine, uc, uf);
 }
 
 cudaError_t launch_jacobian(Dims d, const float* u, float* det, unsigned* count, cudaStream_t s) {

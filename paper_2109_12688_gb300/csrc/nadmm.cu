@@ -73,6 +73,10 @@ struct nadmm_context {
   // batched handle: the pairs, their lane (concurrent graph branch) and
   // the byte offsets of each lane's state and each pair's tables
   bool batched = false;
+  // pyramid handle (Sec. 4): pairs[l] is level l (0 = finest), all levels
+  // share one state region; lvl_off[l] holds I0_l, I1_l, u_l, u_up_l
+  bool pyramid = false;
+  std::vector<size_t> lvl_off;
   std::vector<nadmm_context*> pairs;
   int lanes = 0;
   std::vector<int> lane_of;
@@ -281,7 +285,7 @@ cudaError_t enqueue_inner(nadmm_context* h, PlaneArgs first, int in_first, bool 
 }
 
 cudaError_t enqueue_register(nadmm_context* h, const float* I0, const float* I1, float* u_out,
-                             cudaStream_t s) {
+                             cudaStream_t s, const float* u_init = nullptr) {
   const Dims d = dims_of(h);
   const size_t V = h->V;
   const int O = h->cfg.outer_iters, K = h->cfg.inner_iters;
@@ -295,7 +299,10 @@ cudaError_t enqueue_register(nadmm_context* h, const float* I0, const float* I1,
   auto dst_of = [&](int o) { return ((O - 1 - o) % 2 == 0) ? u_out : ut; };
   float* u_cur = (dst_of(0) == u_out) ? ut : u_out;
   TRY(cudaMemsetAsync(red, 0, 4 * sizeof(unsigned), s));  // red[0..1], status red[2]
-  TRY(cudaMemsetAsync(u_cur, 0, 3 * V * sizeof(float), s));
+  if (u_init)  // start from a given displacement (a coarser pyramid level's)
+    TRY(cudaMemcpyAsync(u_cur, u_init, 3 * V * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  else
+    TRY(cudaMemsetAsync(u_cur, 0, 3 * V * sizeof(float), s));
   KLAUNCH(NADMM_KC_WARP, s, launch_warp(d, I1, u_cur, I1w, nullptr, s));
   KLAUNCH(NADMM_KC_GRAD, s, launch_grad_residual(d, I1w, I0, J, c, s));
   for (int o = 0; o < O; ++o) {
@@ -319,11 +326,19 @@ cudaError_t enqueue_register(nadmm_context* h, const float* I0, const float* I1,
   return cudaSuccess;
 }
 
-nadmm_status need_ws(const nadmm_context* h, bool batched = false) {
+enum HandleKind { kSingle = 0, kBatched = 1, kPyramid = 2 };
+
+int kind_of(const nadmm_context* h) { return h->batched ? kBatched : h->pyramid ? kPyramid : kSingle; }
+
+nadmm_status need_ws(const nadmm_context* h, int want = kSingle) {
   if (!h) return fail(NADMM_ERR_INVALID_ARG, "handle is NULL");
-  if (h->batched != batched)
-    return fail(NADMM_ERR_INVALID_ARG, batched ? "handle is not a batched handle (nadmm_create_batched)"
-                                               : "a batched handle only takes the *_batched calls");
+  if (kind_of(h) != want) {
+    static const char* const names[3] = {"a single-pair handle (nadmm_create)",
+                                         "a batched handle (nadmm_create_batched)",
+                                         "a pyramid handle (nadmm_create_pyramid)"};
+    return fail(NADMM_ERR_INVALID_ARG, std::string("this call needs ") + names[want] + ", got " +
+                                           names[kind_of(h)]);
+  }
   if (!h->wt) return fail(NADMM_ERR_NO_WORKSPACE, "no workspace attached (nadmm_set_workspace)");
   return NADMM_OK;
 }
@@ -624,6 +639,33 @@ cudaError_t enqueue_batched(nadmm_context* b, const float* const* I0, const floa
   return cudaSuccess;
 }
 
+// The levels of a pyramid handle, coarsest first: block-average the images
+// down, register each level from the upsampled result of the coarser one.
+cudaError_t enqueue_pyramid(nadmm_context* p, const float* I0, const float* I1, float* u_out,
+                            cudaStream_t s) {
+  const int L = (int)p->pairs.size();
+  auto lvl = [&](int l, int part) -> float* {  // part: 0 I0, 1 I1, 2 u, 3 u_up
+    const nadmm_context* c = p->pairs[l];
+    const size_t V = c->V;
+    const size_t off[4] = {0, align_up(V * 4), 2 * align_up(V * 4),
+                           2 * align_up(V * 4) + align_up(3 * V * 4)};
+    return reinterpret_cast<float*>(p->ws + p->lvl_off[l] + off[part]);
+  };
+  for (int l = 1; l < L; ++l) {
+    const Dims dc = dims_of(p->pairs[l]);
+    TRY(launch_downsample2(dc, l == 1 ? I0 : lvl(l - 1, 0), lvl(l, 0), s));
+    TRY(launch_downsample2(dc, l == 1 ? I1 : lvl(l - 1, 1), lvl(l, 1), s));
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    const float* f = l == 0 ? I0 : lvl(l, 0);
+    const float* m = l == 0 ? I1 : lvl(l, 1);
+    float* dst = l == 0 ? u_out : lvl(l, 2);
+    TRY(enqueue_register(p->pairs[l], f, m, dst, s, l == L - 1 ? nullptr : lvl(l, 3)));
+    if (l > 0) TRY(launch_upsample_u(dims_of(p->pairs[l]), dims_of(p->pairs[l - 1]), dst, lvl(l - 1, 3), s));
+  }
+  return cudaSuccess;
+}
+
 nadmm_status run_register(nadmm_context* h, const float* I0, const float* I1, float* u_out,
                           cudaStream_t stream) {
   if (h->cfg.flags & NADMM_FLAG_NO_GRAPH) {
@@ -822,6 +864,69 @@ nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, cons
   return NADMM_OK;
 }
 
+nadmm_status nadmm_create_pyramid(const nadmm_config* finest, int32_t levels, const int32_t* outer,
+                                  const int32_t* inner, nadmm_handle* out) {
+  if (!out) return fail(NADMM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!finest || !outer || !inner) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
+  if (levels < 1 || levels > 5) return fail(NADMM_ERR_INVALID_ARG, "levels must be in 1..5");
+  if (finest->flags & NADMM_FLAG_SAVE_FOR_BACKWARD)
+    return fail(NADMM_ERR_INVALID_ARG, "pyramid handles have no reverse mode");
+  const int f = 1 << (levels - 1);
+  if (finest->nx % f || finest->ny % f || finest->nz % f)
+    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "every dimension must be divisible by 2^(levels-1)");
+  nadmm_context* p = new nadmm_context();
+  p->cfg = *finest;
+  p->pyramid = true;
+  for (int l = 0; l < levels; ++l) {
+    nadmm_config c = *finest;
+    c.nx >>= l;
+    c.ny >>= l;
+    c.nz >>= l;
+    c.outer_iters = outer[levels - 1 - l];  // arrays run coarsest first
+    c.inner_iters = inner[levels - 1 - l];
+    nadmm_context* q = nullptr;
+    nadmm_status st = create_single(&c, &q);
+    if (st != NADMM_OK) {
+      g_err = "level " + std::to_string(l) + ": " + g_err;
+      destroy_context(p);
+      return st;
+    }
+    p->pairs.push_back(q);
+  }
+  size_t state = 0;
+  for (nadmm_context* q : p->pairs) state = std::max(state, q->state_total);
+  size_t o = align_up(state);
+  p->tab_off.assign(levels, 0);
+  p->lvl_off.assign(levels, 0);
+  for (int l = 0; l < levels; ++l) {
+    p->tab_off[l] = o;
+    o = align_up(o + p->pairs[l]->table_total);
+  }
+  for (int l = 0; l < levels; ++l) {  // I0_l, I1_l, u_l, u_up_l (level 0 uses u_up only)
+    const size_t V = p->pairs[l]->V;
+    p->lvl_off[l] = o;
+    o += 2 * align_up(V * 4) + 2 * align_up(3 * V * 4);
+  }
+  p->total = o;
+  *out = p;
+  return NADMM_OK;
+}
+
+nadmm_status nadmm_register_pyramid(nadmm_handle h, const float* fixed, const float* moving,
+                                    float* u_out, void* stream) {
+  nadmm_status st = need_ws(h, kPyramid);
+  if (st != NADMM_OK) return st;
+  if ((st = check_dev_ptrs({fixed, moving, u_out})) != NADMM_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->cfg.flags & NADMM_FLAG_NO_GRAPH) {
+    cudaError_t e = enqueue_pyramid(h, fixed, moving, u_out, s);
+    return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_register_pyramid");
+  }
+  return replay(h, 0, {fixed, moving, u_out}, s, "capture of nadmm_register_pyramid",
+                [&](cudaStream_t cs) { return enqueue_pyramid(h, fixed, moving, u_out, cs); });
+}
+
 nadmm_status nadmm_batch_set_lanes(nadmm_handle h, int32_t lanes) {
   if (!h || !h->batched) return fail(NADMM_ERR_INVALID_ARG, "not a batched handle");
   if (lanes < 1) return fail(NADMM_ERR_INVALID_ARG, "lanes must be >= 1");
@@ -848,7 +953,17 @@ nadmm_status nadmm_set_workspace(nadmm_handle h, void* dev_ptr, size_t bytes) {
   char* base = static_cast<char*>(dev_ptr);
   cudaError_t e = configure_kernels_once();
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-  if (!h->batched) {
+  if (h->pyramid) {
+    for (size_t l = 0; l < h->pairs.size(); ++l) {
+      nadmm_status st = attach(h->pairs[l], base, base + h->tab_off[l]);
+      if (st != NADMM_OK) {
+        for (nadmm_context* q : h->pairs) q->ws = q->wt = nullptr;
+        return st;
+      }
+    }
+    h->ws = base;
+    h->wt = base;
+  } else if (!h->batched) {
     nadmm_status st = attach(h, base, base + align_up(h->state_total));
     if (st != NADMM_OK) return st;
   } else {
@@ -948,7 +1063,7 @@ nadmm_status nadmm_get_status(nadmm_handle h, void* stream) {
   if (!h->wt) return fail(NADMM_ERR_NO_WORKSPACE, "no workspace attached (nadmm_set_workspace)");
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  if (!h->batched) return read_status(h);
+  if (!h->batched && !h->pyramid) return read_status(h);
   nadmm_status worst = NADMM_OK;
   std::string msg;
   for (size_t i = 0; i < h->pairs.size(); ++i) {
@@ -964,7 +1079,7 @@ nadmm_status nadmm_get_status(nadmm_handle h, void* stream) {
 
 nadmm_status nadmm_register_batched(nadmm_handle h, const float* const* fixed,
                                     const float* const* moving, float* const* u_out, void* stream) {
-  nadmm_status st = need_ws(h, true);
+  nadmm_status st = need_ws(h, kBatched);
   if (st != NADMM_OK) return st;
   if (!fixed || !moving || !u_out) return fail(NADMM_ERR_INVALID_ARG, "NULL pointer array");
   const int n = (int)h->pairs.size();
@@ -1069,7 +1184,8 @@ nadmm_status nadmm_bound_compose(nadmm_handle h, const float* w, const float* u_
 nadmm_status nadmm_jacobian_det(nadmm_handle h, const float* u, float* det, uint32_t* nonpositive,
                                 void* stream) {
   if (!h) return fail(NADMM_ERR_INVALID_ARG, "handle is NULL");
-  if (h->batched) return fail(NADMM_ERR_INVALID_ARG, "a batched handle only takes the *_batched calls");
+  if (h->batched || h->pyramid)
+    return fail(NADMM_ERR_INVALID_ARG, "this call needs a single-pair handle (nadmm_create)");
   if (nadmm_status st = check_dev_ptrs({u}); st != NADMM_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;

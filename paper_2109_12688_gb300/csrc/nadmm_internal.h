@@ -161,6 +161,9 @@ cudaError_t launch_compose(Dims d, const float* w, const float* u_in, float* u_o
                            const unsigned* red, float kappa, float delta, unsigned* status,
                            float* scale_out, cudaStream_t s);
 cudaError_t launch_jacobian(Dims d, const float* u, float* det, unsigned* count, cudaStream_t s);
+// pyramid: 2 x 2 x 2 block average onto `coarse`; cell-centred doubling upsample of u
+cudaError_t launch_downsample2(Dims coarse, const float* fine, float* out, cudaStream_t s);
+cudaError_t launch_upsample_u(Dims coarse, Dims fine, const float* uc, float* uf, cudaStream_t s);
 
 // ---------------------------------------------------------------- reverse mode
 // One reverse ADMM step k (grad_kernels.cu).  State of the forward sweep:

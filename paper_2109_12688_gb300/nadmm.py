@@ -78,6 +78,9 @@ _SIGS = {
                                               ctypes.POINTER(_P), _P]),
     "nadmm_backward": (ctypes.c_int, [_P] * 9),
     "nadmm_selftest_wait_timeout": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "nadmm_create_pyramid": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_P)]),
+    "nadmm_register_pyramid": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "nadmm_ssd_after_warp": (ctypes.c_int, [_P] * 6),
     "nadmm_ssd_after_warp_backward": (ctypes.c_int, [_P] * 9),
 }
@@ -183,6 +186,23 @@ def nadmm_ssd_after_warp_backward(h, fixed, moving, u, grad_loss, grad_fixed, gr
 
 def nadmm_selftest_wait_timeout(h, attempts, stream=None):
     _check(load().nadmm_selftest_wait_timeout(h, attempts, _stream(stream)))
+
+
+def nadmm_create_pyramid(finest, outer, inner):
+    """outer, inner: per-level counts, coarsest first."""
+    n = len(outer)
+    if len(inner) != n:
+        raise ValueError("outer and inner need one entry per level")
+    o = (ctypes.c_int32 * n)(*outer)
+    i = (ctypes.c_int32 * n)(*inner)
+    h = _P()
+    _check(load().nadmm_create_pyramid(ctypes.byref(finest), n, o, i, ctypes.byref(h)))
+    return h
+
+
+def nadmm_register_pyramid(h, fixed, moving, u_out, stream=None):
+    _check(load().nadmm_register_pyramid(h, _ptr(fixed), _ptr(moving), _ptr(u_out),
+                                         _stream(stream)))
 
 
 def nadmm_destroy(h):
@@ -337,6 +357,36 @@ class Registration:
             self.close()
         except Exception:
             pass
+
+
+PAPER_V1_OUTER = (10, 10, 5)   # warpings per level, coarsest first (Sec. 4, first version)
+PAPER_V1_INNER = (10, 5, 5)    # ADMM iterations per level
+
+
+class PyramidRegistration(Registration):
+    """A pyramid handle (coarsest level first in outer/inner) plus its workspace."""
+
+    def __init__(self, dims, outer=PAPER_V1_OUTER, inner=PAPER_V1_INNER, device="cuda", **kw):
+        import torch
+        self.dims = tuple(dims)
+        self.cfg = make_config(self.dims, **kw)
+        self.handle = nadmm_create_pyramid(self.cfg, outer, inner)
+        self.serial = 0
+        nbytes = nadmm_workspace_size(self.handle)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        nadmm_set_workspace(self.handle, self._ws_ptr, nbytes)
+
+    def register(self, fixed, moving, u_out=None, stream=None):
+        import torch
+        nx, ny, nz = self.dims
+        if u_out is None:
+            u_out = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=fixed.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(fixed.device)
+        nadmm_register_pyramid(self.handle, fixed, moving, u_out, stream)
+        return u_out
 
 
 class BatchedRegistration(Registration):

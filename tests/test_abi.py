@@ -166,3 +166,24 @@ def test_batched_handle_only_takes_batched_calls(lib):
         lib.nadmm_batch_set_lanes(single, 2)
     assert e.value.status == lib.NADMM_ERR_INVALID_ARG
     lib.nadmm_destroy(single)
+
+
+def test_pyramid_create_checks(lib):
+    cfg = lib.make_config((128, 128, 96))
+    h = lib.nadmm_create_pyramid(cfg, (10, 10, 5), (10, 5, 5))
+    ws = lib.nadmm_workspace_size(h)
+    assert ws >= _ws_parts((128, 128, 96))  # the shared state region is the finest level's
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_register(h, 16, 16, 16)
+    assert e.value.status == lib.NADMM_ERR_INVALID_ARG
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_register_pyramid(h, 16, 16, 16)
+    assert e.value.status == lib.NADMM_ERR_NO_WORKSPACE
+    lib.nadmm_destroy(h)
+    with pytest.raises(lib.NadmmError) as e:  # 96 / 4 = 24 but 20 / 4 = 5 is odd -> ny check
+        lib.nadmm_create_pyramid(lib.make_config((128, 20, 96)), (1, 1, 1), (1, 1, 1))
+    assert e.value.status == lib.NADMM_ERR_UNSUPPORTED_SIZE
+    with pytest.raises(lib.NadmmError) as e:  # coarsest 32/8 = 4 -> nx % 4 ok, 24 / 8 = 3 < 4
+        lib.nadmm_create_pyramid(lib.make_config((32, 32, 24)), (1,) * 4, (1,) * 4)
+    assert e.value.status == lib.NADMM_ERR_UNSUPPORTED_SIZE
+    assert "level 3" in str(e.value)
