@@ -157,7 +157,8 @@ def parse_args():
     ap.add_argument("--orders", default="1,2,3",
                     help="regulariser orders registered per step (profiling runs use one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
-    ap.add_argument("--workload", choices=("registration", "batch64", "large", "grad", "pyramid"),
+    ap.add_argument("--workload", choices=("registration", "batch64", "large", "grad", "pyramid",
+                                           "batch16grad"),
                     default="registration",
                     help="registration: the 128x128x96 benchmark (default); batch64: 64 uneven "
                          "pairs in one batched graph vs 64 sequential calls; large: one "
@@ -340,6 +341,44 @@ def run_extra(args, rank, world):
             "paper_s_by_order": paper_s,
             "paper_context": "Table 1, L2 + n-th order, first version, 16 GB Tesla V100, "
                              "PyTorch, mean over 100 private test pairs",
+            "clocks": clk,
+        }
+    elif args.workload == "batch16grad":
+        dims = synth.draw_batch_dims(16, seed=4321)
+        data = [synth.phase_pair(d, seed=100 + i) for i, d in enumerate(dims)]
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats(dev)
+        base = torch.cuda.memory_allocated(dev)
+        I0 = [torch.from_numpy(f).to(dev) for f, _ in data]
+        I1 = [torch.from_numpy(m).to(dev) for _, m in data]
+        breg = nadmm.BatchedRegistration(dims, device=dev, requires_grad=True, order_n=2, **kw)
+        U = [torch.empty((3, d[2], d[1], d[0]), device=dev) for d in dims]
+        GU = [torch.full((3, d[2], d[1], d[0]), 1e-3, device=dev) for d in dims]
+        G0 = [torch.empty_like(a) for a in I0]
+        G1 = [torch.empty_like(a) for a in I1]
+        par = torch.zeros((16, 8), device=dev)
+        pl = [par.data_ptr() + 32 * i for i in range(16)]
+        pt = [par.data_ptr() + 32 * i + 16 for i in range(16)]
+
+        def fwd_bwd():
+            nadmm.nadmm_register_batched(breg.handle, I0, I1, U, stream)
+            nadmm.nadmm_backward_batched(breg.handle, I0, I1, GU, G0, G1, pl, pt, stream)
+        ms, clk = timed(fwd_bwd)
+        fwd_ms, _ = timed(lambda: nadmm.nadmm_register_batched(breg.handle, I0, I1, U, stream))
+        peak = torch.cuda.max_memory_allocated(dev) - base
+        vox = sum(d[0] * d[1] * d[2] for d in dims)
+        line = {
+            "metric": "ms per batch of 16 uneven pairs, forward + backward", "value": ms,
+            "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "16 pairs, nx, ny from {96..160}, nz from {64..112} (seed "
+                                   "4321), two-phase phantoms, n=2, 10 x 10, forward and reverse "
+                                   "mode as two graph replays",
+                       "voxels": vox,
+                       "l2": "flushed between timed steps (256 MB write outside the step events)"},
+            "forward_only_ms": fwd_ms, "device_bytes_peak": peak,
+            "workspace_bytes": nadmm.nadmm_workspace_size(breg.handle),
             "clocks": clk,
         }
     elif args.workload == "grad":

@@ -72,7 +72,7 @@ typedef enum nadmm_status {
                                      start of every outer step (outer_iters x 3V
                                      floats) plus the reverse-sweep scratch
                                      (2 inner_iters + 16 vector fields); single
-                                     handles only                               */
+                                     and batched handles                        */
 
 typedef struct nadmm_config {
   int32_t nx, ny, nz;         /* grid (M, N, H); see NADMM_ERR_UNSUPPORTED_SIZE */
@@ -177,8 +177,9 @@ nadmm_status nadmm_batch_set_lanes(nadmm_handle h, int32_t lanes);
  * pointer changes) or, with NADMM_FLAG_NO_GRAPH, direct launches of the
  * pairs in order.  nadmm_get_status on the handle reports the first pair
  * whose status word is set.  Only nadmm_register_batched,
- * nadmm_get_status, nadmm_workspace_size, nadmm_set_workspace,
- * nadmm_batch_set_lanes and nadmm_destroy accept a batched handle.
+ * nadmm_backward_batched, nadmm_get_status, nadmm_workspace_size,
+ * nadmm_set_workspace, nadmm_batch_set_lanes and nadmm_destroy accept a
+ * batched handle.
  * Errors: INVALID_ARG, ALIGNMENT, NO_WORKSPACE, CUDA. */
 nadmm_status nadmm_register_batched(nadmm_handle h, const float* const* fixed,
                                     const float* const* moving, float* const* u_out,
@@ -320,6 +321,20 @@ nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, in
 nadmm_status nadmm_backward(nadmm_handle h, const float* fixed, const float* moving,
                             const float* grad_u, float* grad_fixed, float* grad_moving,
                             float* grad_lambda, float* grad_theta, void* stream);
+
+/* nadmm_backward for every pair of a batched handle created with
+ * NADMM_FLAG_SAVE_FOR_BACKWARD, after a nadmm_register_batched on it: host
+ * arrays of npairs device pointers, each entry as in nadmm_backward for that
+ * pair's grid; grad_lambda and grad_theta may be NULL arrays or hold NULL
+ * entries.  Each pair keeps its own tape (outer_iters x 3V floats); the
+ * reverse-sweep scratch is shared by the pairs of a lane.  One CUDA-graph
+ * replay (re-captured when a pointer changes) on `stream`.
+ * Errors: INVALID_ARG, ALIGNMENT, NO_WORKSPACE, NO_SAVED_FORWARD, CUDA. */
+nadmm_status nadmm_backward_batched(nadmm_handle h, const float* const* fixed,
+                                    const float* const* moving, const float* const* grad_u,
+                                    float* const* grad_fixed, float* const* grad_moving,
+                                    float* const* grad_lambda, float* const* grad_theta,
+                                    void* stream);
 
 /* Loss L = 1/2 sum_x (I1(x + u(x)) - I0(x))^2 (trilinear, clamped), the
  * quantity whose gradients the reverse mode is tested on:

@@ -59,6 +59,7 @@ struct nadmm_context {
   size_t o_tape = 0, o_hist = 0, o_adj = 0, o_g = 0, o_Sg = 0, o_gJ = 0, o_gc = 0, o_ub0 = 0,
          o_ub1 = 0;
   bool saved_forward = false;
+  bool has_tape = false;  // o_tape (table region) is allocated
   size_t o_red, o_acc, o_twx, o_twy, o_twz, o_posx, o_Kx, o_Ky, o_Kz, table_total;
   size_t total;  // single handle: align(state_total) + table_total
   char* ws = nullptr;
@@ -306,8 +307,8 @@ cudaError_t enqueue_register(nadmm_context* h, const float* I0, const float* I1,
   KLAUNCH(NADMM_KC_WARP, s, launch_warp(d, I1, u_cur, I1w, nullptr, s));
   KLAUNCH(NADMM_KC_GRAD, s, launch_grad_residual(d, I1w, I0, J, c, s));
   for (int o = 0; o < O; ++o) {
-    if (h->o_tape)  // u at the start of outer step o, for the reverse sweep
-      TRY(cudaMemcpyAsync(h->at<float>(h->o_tape) + (size_t)o * 3 * V, u_cur, 3 * V * sizeof(float),
+    if (h->has_tape)  // u at the start of outer step o, for the reverse sweep
+      TRY(cudaMemcpyAsync(h->tab<float>(h->o_tape) + (size_t)o * 3 * V, u_cur, 3 * V * sizeof(float),
                           cudaMemcpyDeviceToDevice, s));
     PlaneArgs first = plane_args(h);
     TRY(enqueue_inner(h, first, IN_NONE, false, 0, K, J, c, vbuf, nullptr, s));
@@ -423,7 +424,6 @@ nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
   h->o_io_u = take(3 * V * sizeof(float));
   if (cfg->flags & NADMM_FLAG_SAVE_FOR_BACKWARD) {
     const size_t F3 = 3 * V * sizeof(float);
-    h->o_tape = take((size_t)cfg->outer_iters * F3);
     h->o_hist = take(2 * (size_t)cfg->inner_iters * F3);
     h->o_adj = take(6 * F3);
     h->o_g = take(F3);
@@ -444,6 +444,12 @@ nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
   h->o_Kx = take(h->Kx.size() * sizeof(float));
   h->o_Ky = take(h->Ky.size() * sizeof(float));
   h->o_Kz = take(h->Kz.size() * sizeof(float));
+  // the tape belongs to the pair (it must outlive other pairs' use of a
+  // shared state region), so it sits with the tables
+  if (cfg->flags & NADMM_FLAG_SAVE_FOR_BACKWARD) {
+    h->has_tape = true;
+    h->o_tape = take((size_t)cfg->outer_iters * 3 * V * sizeof(float));
+  }
   h->table_total = o;
   *out = h;
   return NADMM_OK;
@@ -639,6 +645,29 @@ cudaError_t enqueue_batched(nadmm_context* b, const float* const* I0, const floa
   return cudaSuccess;
 }
 
+cudaError_t enqueue_backward(nadmm_context* h, const float* I0, const float* I1, const float* gu,
+                             float* gI0, float* gI1, float* glam, float* gtheta, cudaStream_t s);
+
+// Reverse sweeps of all pairs of a batched handle, lanes as in enqueue_batched.
+cudaError_t enqueue_batched_backward(nadmm_context* b, const float* const* I0,
+                                     const float* const* I1, const float* const* gu,
+                                     float* const* gI0, float* const* gI1, float* const* glam,
+                                     float* const* gtheta, cudaStream_t s) {
+  const int n = (int)b->pairs.size();
+  TRY(cudaEventRecord(b->lane_ev[0], s));
+  for (int l = 0; l < b->lanes; ++l) {
+    cudaStream_t q = b->lane_cap[l];
+    TRY(cudaStreamWaitEvent(q, b->lane_ev[0], 0));
+    for (int i = 0; i < n; ++i)
+      if (b->lane_of[i] == l)
+        TRY(enqueue_backward(b->pairs[i], I0[i], I1[i], gu[i], gI0[i], gI1[i],
+                             glam ? glam[i] : nullptr, gtheta ? gtheta[i] : nullptr, q));
+    TRY(cudaEventRecord(b->lane_ev[1 + l], q));
+    TRY(cudaStreamWaitEvent(s, b->lane_ev[1 + l], 0));
+  }
+  return cudaSuccess;
+}
+
 // The levels of a pyramid handle, coarsest first: block-average the images
 // down, register each level from the upsampled result of the coarser one.
 cudaError_t enqueue_pyramid(nadmm_context* p, const float* I0, const float* I1, float* u_out,
@@ -692,7 +721,7 @@ cudaError_t enqueue_backward(nadmm_context* h, const float* I0, const float* I1,
   float* I1w = h->at<float>(h->o_I1w);
   float* J = h->at<float>(h->o_J);
   float* c = h->at<float>(h->o_c);
-  float* tape = h->at<float>(h->o_tape);
+  float* tape = h->tab<float>(h->o_tape);
   float* hw = h->at<float>(h->o_hist);
   float* hb = hw + (size_t)K * 3 * V;
   float* adj = h->at<float>(h->o_adj);
@@ -840,8 +869,6 @@ nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, cons
   *out = nullptr;
   if (!base || !dims) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
   if (npairs < 1) return fail(NADMM_ERR_INVALID_ARG, "npairs must be >= 1");
-  if (base->flags & NADMM_FLAG_SAVE_FOR_BACKWARD)
-    return fail(NADMM_ERR_INVALID_ARG, "batched handles have no reverse mode");
   nadmm_context* b = new nadmm_context();
   b->cfg = *base;
   b->batched = true;
@@ -1004,7 +1031,7 @@ nadmm_status nadmm_register(nadmm_handle h, const float* fixed, const float* mov
   if (st != NADMM_OK) return st;
   if ((st = check_dev_ptrs({fixed, moving, u_out})) != NADMM_OK) return st;
   st = run_register(h, fixed, moving, u_out, (cudaStream_t)stream);
-  if (st == NADMM_OK && h->o_tape) h->saved_forward = true;
+  if (st == NADMM_OK && h->has_tape) h->saved_forward = true;
   return st;
 }
 
@@ -1022,7 +1049,7 @@ nadmm_status nadmm_register_host(nadmm_handle h, const float* fixed_host, const 
   if (e == cudaSuccess) e = cudaMemcpyAsync(m, moving_host, V * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
   if ((st = run_register(h, f, m, u, s)) != NADMM_OK) return st;
-  if (h->o_tape) h->saved_forward = true;
+  if (h->has_tape) h->saved_forward = true;
   e = cudaMemcpyAsync(u_out_host, u, 3 * V * sizeof(float), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "device-to-host copy");
@@ -1100,10 +1127,61 @@ nadmm_status nadmm_register_batched(nadmm_handle h, const float* const* fixed,
       cudaError_t e = enqueue_register(h->pairs[i], fixed[i], moving[i], u_out[i], s);
       if (e != cudaSuccess) return cuda_fail(e, "nadmm_register_batched");
     }
-    return NADMM_OK;
-  }
-  return replay(h, 0, key, s, "capture of nadmm_register_batched",
+  } else {
+    st = replay(h, 0, key, s, "capture of nadmm_register_batched",
                 [&](cudaStream_t cs) { return enqueue_batched(h, fixed, moving, u_out, cs); });
+  }
+  if (st == NADMM_OK)
+    for (nadmm_context* p : h->pairs)
+      if (p->has_tape) p->saved_forward = true;
+  return st;
+}
+
+nadmm_status nadmm_backward_batched(nadmm_handle h, const float* const* fixed,
+                                    const float* const* moving, const float* const* grad_u,
+                                    float* const* grad_fixed, float* const* grad_moving,
+                                    float* const* grad_lambda, float* const* grad_theta,
+                                    void* stream) {
+  nadmm_status st = need_ws(h, kBatched);
+  if (st != NADMM_OK) return st;
+  if (!(h->cfg.flags & NADMM_FLAG_SAVE_FOR_BACKWARD))
+    return fail(NADMM_ERR_NO_SAVED_FORWARD, "handle created without NADMM_FLAG_SAVE_FOR_BACKWARD");
+  if (h->cfg.data_term != 2)
+    return fail(NADMM_ERR_INVALID_ARG, "the reverse mode supports the s = 2 data term only");
+  if (!(h->cfg.lambda > 0.0f)) return fail(NADMM_ERR_INVALID_ARG, "the reverse mode needs lambda > 0");
+  if (!fixed || !moving || !grad_u || !grad_fixed || !grad_moving)
+    return fail(NADMM_ERR_INVALID_ARG, "NULL pointer array");
+  const int n = (int)h->pairs.size();
+  std::vector<const void*> key;
+  for (int i = 0; i < n; ++i) {
+    if (!h->pairs[i]->saved_forward)
+      return fail(NADMM_ERR_NO_SAVED_FORWARD, "no nadmm_register_batched call since the workspace was attached");
+    if ((st = check_dev_ptrs({fixed[i], moving[i], grad_u[i], grad_fixed[i], grad_moving[i]})) != NADMM_OK) {
+      g_err = "pair " + std::to_string(i) + ": " + g_err;
+      return st;
+    }
+    const void* gl = grad_lambda ? grad_lambda[i] : nullptr;
+    const void* gt = grad_theta ? grad_theta[i] : nullptr;
+    if ((gl && !aligned16(gl)) || (gt && !aligned16(gt)))
+      return fail(NADMM_ERR_ALIGNMENT, "pair " + std::to_string(i) + ": grad_lambda/theta not aligned");
+    for (const void* p : {(const void*)fixed[i], (const void*)moving[i], (const void*)grad_u[i],
+                          (const void*)grad_fixed[i], (const void*)grad_moving[i], gl, gt})
+      key.push_back(p);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  auto fn = [&](cudaStream_t cs) {
+    return enqueue_batched_backward(h, fixed, moving, grad_u, grad_fixed, grad_moving, grad_lambda,
+                                    grad_theta, cs);
+  };
+  if (h->cfg.flags & NADMM_FLAG_NO_GRAPH) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+      e = enqueue_backward(h->pairs[i], fixed[i], moving[i], grad_u[i], grad_fixed[i],
+                           grad_moving[i], grad_lambda ? grad_lambda[i] : nullptr,
+                           grad_theta ? grad_theta[i] : nullptr, s);
+    return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_backward_batched");
+  }
+  return replay(h, 1, key, s, "capture of nadmm_backward_batched", fn);
 }
 
 nadmm_status nadmm_spectral_solve(nadmm_handle h, const float* y, float* w, void* stream) {

@@ -81,6 +81,7 @@ _SIGS = {
     "nadmm_create_pyramid": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_P)]),
     "nadmm_register_pyramid": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "nadmm_backward_batched": (ctypes.c_int, [_P] + [ctypes.POINTER(_P)] * 7 + [_P]),
     "nadmm_ssd_after_warp": (ctypes.c_int, [_P] * 6),
     "nadmm_ssd_after_warp_backward": (ctypes.c_int, [_P] * 9),
 }
@@ -202,6 +203,15 @@ def nadmm_create_pyramid(finest, outer, inner):
 
 def nadmm_register_pyramid(h, fixed, moving, u_out, stream=None):
     _check(load().nadmm_register_pyramid(h, _ptr(fixed), _ptr(moving), _ptr(u_out),
+                                         _stream(stream)))
+
+
+def nadmm_backward_batched(h, fixed, moving, grad_u, grad_fixed, grad_moving, grad_lambda=None,
+                           grad_theta=None, stream=None):
+    n = len(fixed)
+    arr = lambda xs: None if xs is None else (_P * n)(*[_ptr(x) for x in xs])
+    _check(load().nadmm_backward_batched(h, arr(fixed), arr(moving), arr(grad_u), arr(grad_fixed),
+                                         arr(grad_moving), arr(grad_lambda), arr(grad_theta),
                                          _stream(stream)))
 
 
@@ -392,9 +402,11 @@ class PyramidRegistration(Registration):
 class BatchedRegistration(Registration):
     """A batched handle (pairs of different grid sizes) plus its workspace."""
 
-    def __init__(self, dims_list, device="cuda", lanes=None, **kw):
+    def __init__(self, dims_list, device="cuda", lanes=None, requires_grad=False, **kw):
         import torch
         self.dims_list = [tuple(d) for d in dims_list]
+        if requires_grad:
+            kw["flags"] = kw.get("flags", 0) | NADMM_FLAG_SAVE_FOR_BACKWARD
         self.cfg = make_config(self.dims_list[0], **kw)
         self.handle = nadmm_create_batched(self.cfg, self.dims_list)
         if lanes is not None:
@@ -414,6 +426,22 @@ class BatchedRegistration(Registration):
             stream = torch.cuda.current_stream(fixed[0].device)
         nadmm_register_batched(self.handle, fixed, moving, u_out, stream)
         return u_out
+
+    def backward(self, fixed, moving, grad_u, stream=None):
+        """Per-pair gradients (I0, I1, lambda, theta) of <grad_u[i], u[i]>
+        through the last nadmm_register_batched (handle made with
+        requires_grad=True)."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(fixed[0].device)
+        g0 = [torch.empty_like(f) for f in fixed]
+        g1 = [torch.empty_like(m) for m in moving]
+        par = torch.zeros((len(fixed), 8), dtype=torch.float32, device=fixed[0].device)
+        base = par.data_ptr()
+        nadmm_backward_batched(self.handle, fixed, moving, [g.contiguous() for g in grad_u], g0, g1,
+                               [base + 32 * i for i in range(len(fixed))],
+                               [base + 32 * i + 16 for i in range(len(fixed))], stream)
+        return g0, g1, par[:, 0], par[:, 4]
 
 
 # ---------------------------------------------------------------- autograd
