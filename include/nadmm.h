@@ -73,6 +73,13 @@ typedef enum nadmm_status {
                                      floats) plus the reverse-sweep scratch
                                      (2 inner_iters + 16 vector fields); single
                                      and batched handles                        */
+/* FFT plan choice per axis (bits 2-3 x, 4-5 y, 6-7 z): an axis of n = R1 R2
+ * with both R2 = 8 and R2 = 16 available is split with the R2 chosen here;
+ * 0 keeps the library default (x 8, y 16, z 8).  nadmm_autotune picks them. */
+#define NADMM_FLAG_LANE_SHIFT(axis) (2u + 2u * (axis))   /* axis 0 x, 1 y, 2 z */
+#define NADMM_FLAG_LANE8(axis)  (1u << NADMM_FLAG_LANE_SHIFT(axis))
+#define NADMM_FLAG_LANE16(axis) (2u << NADMM_FLAG_LANE_SHIFT(axis))
+#define NADMM_FLAG_LANE_MASK 0xFCu
 
 typedef struct nadmm_config {
   int32_t nx, ny, nz;         /* grid (M, N, H); see NADMM_ERR_UNSUPPORTED_SIZE */
@@ -169,6 +176,12 @@ nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, cons
  * before its workspace is attached.  lanes > npairs is clamped to npairs.
  * Errors: INVALID_ARG (not batched, lanes < 1, workspace already attached). */
 nadmm_status nadmm_batch_set_lanes(nadmm_handle h, int32_t lanes);
+
+/* Replace the NADMM_FLAG_LANE* plan bits of pair `pair` (0-based) of a
+ * batched handle before its workspace is attached (e.g. with the result of
+ * nadmm_autotune for that pair's grid); the workspace size may change.
+ * Errors: INVALID_ARG. */
+nadmm_status nadmm_batch_set_pair_plan(nadmm_handle h, int32_t pair, uint32_t plan_flags);
 
 /* Register every pair of a batched handle: fixed[i], moving[i] device
  * [nz_i][ny_i][nx_i], u_out[i] device [3][nz_i][ny_i][nx_i] (host arrays of
@@ -291,6 +304,25 @@ nadmm_status nadmm_jacobian_det(nadmm_handle h, const float* u, float* det,
 nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, int32_t order_n,
                                           float lambda, float theta, const float* y, float* w,
                                           void* stream);
+
+/* ---------------------------------------------------------------------
+ * Autotuning of the FFT plans (the paper has no counterpart).
+ * --------------------------------------------------------------------- */
+
+/* Device bytes nadmm_autotune needs for `cfg`'s grid (host only). */
+nadmm_status nadmm_autotune_workspace_size(const nadmm_config* cfg, size_t* bytes);
+
+/* Time every plan choice of `cfg`'s grid -- each axis with both an 8- and a
+ * 16-lane split tried both ways -- on one ADMM iteration (the k >= 2 plane
+ * pass and the y/z passes; 3 warm-up and 10 timed repetitions, CUDA events
+ * on `stream`, minimum kept) in the caller's device workspace (at least
+ * nadmm_autotune_workspace_size bytes, 256-byte aligned; its contents are
+ * overwritten) and write the fastest choice as NADMM_FLAG_LANE* bits to
+ * *best_flags (cfg->flags with its plan bits replaced) and its time in ms to
+ * *best_ms (host pointers; best_ms may be NULL).  Synchronises `stream`.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, ALIGNMENT, NO_WORKSPACE, CUDA. */
+nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t bytes,
+                            void* stream, uint32_t* best_flags, float* best_ms);
 
 /* ---------------------------------------------------------------------
  * Reverse mode (gradients through the registration).  The paper has no

@@ -127,8 +127,11 @@ nadmm_status validate(const nadmm_config* c) {
   if (!(c->eps > 0.0f) || !std::isfinite(c->eps)) return fail(NADMM_ERR_INVALID_ARG, "eps must be > 0");
   if (!(c->bound_kappa > 0.0f) || !(c->bound_delta > 0.0f))
     return fail(NADMM_ERR_INVALID_ARG, "bound_kappa and bound_delta must be > 0 (INFINITY disables)");
-  if (c->flags & ~(NADMM_FLAG_NO_GRAPH | NADMM_FLAG_SAVE_FOR_BACKWARD))
+  if (c->flags & ~(NADMM_FLAG_NO_GRAPH | NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK))
     return fail(NADMM_ERR_INVALID_ARG, "unknown flag bits");
+  for (int ax = 0; ax < 3; ++ax)
+    if (((c->flags >> NADMM_FLAG_LANE_SHIFT(ax)) & 3u) == 3u)
+      return fail(NADMM_ERR_INVALID_ARG, "plan bits of an axis ask for both 8 and 16 lanes");
   return NADMM_OK;
 }
 
@@ -354,14 +357,24 @@ nadmm_status check_dev_ptrs(std::initializer_list<const void*> ptrs) {
 
 constexpr int kDefaultLanes = 1;
 
+// R2 tried first for an axis's lane plan: the flag bits, else the defaults
+// measured on 128x128x96 (x 8, y 16, z 8).
+int lane_first(uint32_t flags, int axis) {
+  const uint32_t b = (flags >> NADMM_FLAG_LANE_SHIFT(axis)) & 3u;
+  if (b == 1u) return 8;
+  if (b == 2u) return 16;
+  return axis == 1 ? 16 : 8;
+}
+
 // Plans, tables and the workspace layout of one grid (host memory only).
 nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
   nadmm_status st = validate(cfg);
   if (st != NADMM_OK) return st;
   nadmm_context* h = new nadmm_context();
   h->cfg = *cfg;
-  if (!factor_axis(cfg->nx, h->px, true) || !factor_axis(cfg->ny, h->py, true, 16) ||
-      !factor_axis(cfg->nz, h->pz, true)) {
+  if (!factor_axis(cfg->nx, h->px, true, lane_first(cfg->flags, 0)) ||
+      !factor_axis(cfg->ny, h->py, true, lane_first(cfg->flags, 1)) ||
+      !factor_axis(cfg->nz, h->pz, true, lane_first(cfg->flags, 2))) {
     delete h;
     return fail(NADMM_ERR_UNSUPPORTED_SIZE, "no radix plan for these dimensions");
   }
@@ -954,6 +967,22 @@ nadmm_status nadmm_register_pyramid(nadmm_handle h, const float* fixed, const fl
                 [&](cudaStream_t cs) { return enqueue_pyramid(h, fixed, moving, u_out, cs); });
 }
 
+nadmm_status nadmm_batch_set_pair_plan(nadmm_handle h, int32_t pair, uint32_t plan_flags) {
+  if (!h || !h->batched) return fail(NADMM_ERR_INVALID_ARG, "not a batched handle");
+  if (h->wt) return fail(NADMM_ERR_INVALID_ARG, "set plans before nadmm_set_workspace");
+  if (pair < 0 || pair >= (int32_t)h->pairs.size()) return fail(NADMM_ERR_INVALID_ARG, "pair out of range");
+  if (plan_flags & ~NADMM_FLAG_LANE_MASK) return fail(NADMM_ERR_INVALID_ARG, "only NADMM_FLAG_LANE* bits");
+  nadmm_config c = h->pairs[pair]->cfg;
+  c.flags = (c.flags & ~NADMM_FLAG_LANE_MASK) | plan_flags;
+  nadmm_context* q = nullptr;
+  nadmm_status st = create_single(&c, &q);
+  if (st != NADMM_OK) return st;
+  destroy_context(h->pairs[pair]);
+  h->pairs[pair] = q;
+  assign_lanes(h, h->lanes);
+  return NADMM_OK;
+}
+
 nadmm_status nadmm_batch_set_lanes(nadmm_handle h, int32_t lanes) {
   if (!h || !h->batched) return fail(NADMM_ERR_INVALID_ARG, "not a batched handle");
   if (lanes < 1) return fail(NADMM_ERR_INVALID_ARG, "lanes must be >= 1");
@@ -1336,6 +1365,99 @@ nadmm_status nadmm_selftest_wait_timeout(nadmm_handle h, int32_t attempts, void*
   cudaError_t e = launch_wait_selftest(h->tab<unsigned>(h->o_red) + 2, attempts,
                                        (cudaStream_t)stream);
   return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_selftest_wait_timeout");
+}
+
+nadmm_status nadmm_autotune_workspace_size(const nadmm_config* cfg, size_t* bytes) {
+  if (!bytes) return fail(NADMM_ERR_INVALID_ARG, "bytes is NULL");
+  nadmm_config c = *cfg;
+  c.flags &= ~(NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK);
+  size_t most = 0;
+  for (uint32_t combo = 0; combo < 8; ++combo) {
+    nadmm_config t = c;
+    for (int ax = 0; ax < 3; ++ax)
+      t.flags |= (((combo >> ax) & 1u) ? 2u : 1u) << NADMM_FLAG_LANE_SHIFT(ax);
+    nadmm_context* h = nullptr;
+    nadmm_status st = create_single(&t, &h);
+    if (st != NADMM_OK) return st;
+    most = std::max(most, align_up(h->state_total) + h->table_total);
+    destroy_context(h);
+  }
+  *bytes = most;
+  return NADMM_OK;
+}
+
+nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t bytes, void* stream,
+                            uint32_t* best_flags, float* best_ms) {
+  if (!cfg || !workspace || !best_flags) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
+  if (((uintptr_t)workspace % kAlign) != 0)
+    return fail(NADMM_ERR_ALIGNMENT, "workspace must be 256-byte aligned");
+  size_t need = 0;
+  nadmm_status st = nadmm_autotune_workspace_size(cfg, &need);
+  if (st != NADMM_OK) return st;
+  if (bytes < need) return fail(NADMM_ERR_NO_WORKSPACE, "workspace smaller than nadmm_autotune_workspace_size");
+  cudaError_t e = configure_kernels_once();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = static_cast<char*>(workspace);
+  e = cudaMemsetAsync(base, 0, need, s);  // defined (zero) inputs for every trial
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  nadmm_config c = *cfg;
+  c.flags &= ~(NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK);
+  std::vector<std::vector<int>> seen;
+  float best = -1.0f;
+  uint32_t best_f = c.flags;
+  for (uint32_t combo = 0; combo < 8 && st == NADMM_OK; ++combo) {
+    nadmm_config t = c;
+    for (int ax = 0; ax < 3; ++ax)
+      t.flags |= (((combo >> ax) & 1u) ? 2u : 1u) << NADMM_FLAG_LANE_SHIFT(ax);
+    nadmm_context* h = nullptr;
+    if ((st = create_single(&t, &h)) != NADMM_OK) break;
+    // skip combinations whose plans coincide with one already timed
+    std::vector<int> key = {h->px.radix[0], h->px.radix[1], h->py.radix[0], h->py.radix[1],
+                            h->pz.radix[0], h->pz.radix[1]};
+    bool dup = false;
+    for (const auto& k : seen) dup = dup || k == key;
+    if (!dup) {
+      seen.push_back(key);
+      st = attach(h, base, base + align_up(h->state_total));
+      if (st == NADMM_OK) {
+        PlaneArgs a = plane_args(h);
+        a.J = h->at<float>(h->o_J);
+        a.c = h->at<float>(h->o_c);
+        a.beta = 0.5f;
+        const PencilArgs pa = pencil_args(h);
+        float ms = 0.0f, t_min = -1.0f;
+        for (int rep = 0; rep < 13 && e == cudaSuccess; ++rep) {
+          if (rep >= 3) e = cudaEventRecord(e0, s);
+          if (e == cudaSuccess) e = launch_plane(IN_SPEC, true, true, a, s);
+          if (e == cudaSuccess) e = launch_pencil(pa, s);
+          if (rep >= 3) {
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && (t_min < 0.0f || ms < t_min)) t_min = ms;
+          }
+        }
+        if (e != cudaSuccess) st = cuda_fail(e, "autotune trial");
+        else if (best < 0.0f || t_min < best) {
+          best = t_min;
+          best_f = t.flags;
+        }
+      }
+    }
+    destroy_context(h);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != NADMM_OK) return st;
+  *best_flags = (cfg->flags & ~NADMM_FLAG_LANE_MASK) | (best_f & NADMM_FLAG_LANE_MASK);
+  if (best_ms) *best_ms = best;
+  return NADMM_OK;
 }
 
 }  // extern "C"

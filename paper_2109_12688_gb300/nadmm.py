@@ -25,6 +25,15 @@ NADMM_ERR_TIMEOUT = 7
 NADMM_ERR_NO_SAVED_FORWARD = 8
 NADMM_FLAG_NO_GRAPH = 1
 NADMM_FLAG_SAVE_FOR_BACKWARD = 2
+NADMM_FLAG_LANE_MASK = 0xFC
+
+
+def NADMM_FLAG_LANE8(axis):
+    return 1 << (2 + 2 * axis)
+
+
+def NADMM_FLAG_LANE16(axis):
+    return 2 << (2 + 2 * axis)
 
 KERNEL_CLASSES = ("plane_first", "plane_k1", "plane", "plane_final", "pencil", "warp", "grad",
                   "bound", "compose")
@@ -82,6 +91,10 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_P)]),
     "nadmm_register_pyramid": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "nadmm_backward_batched": (ctypes.c_int, [_P] + [ctypes.POINTER(_P)] * 7 + [_P]),
+    "nadmm_autotune_workspace_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "nadmm_autotune": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, ctypes.POINTER(ctypes.c_uint32),
+                                      ctypes.POINTER(ctypes.c_float)]),
+    "nadmm_batch_set_pair_plan": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32]),
     "nadmm_ssd_after_warp": (ctypes.c_int, [_P] * 6),
     "nadmm_ssd_after_warp_backward": (ctypes.c_int, [_P] * 9),
 }
@@ -215,6 +228,25 @@ def nadmm_backward_batched(h, fixed, moving, grad_u, grad_fixed, grad_moving, gr
                                          _stream(stream)))
 
 
+def nadmm_autotune_workspace_size(cfg):
+    n = ctypes.c_size_t()
+    _check(load().nadmm_autotune_workspace_size(ctypes.byref(cfg), ctypes.byref(n)))
+    return n.value
+
+
+def nadmm_autotune(cfg, workspace, nbytes, stream=None):
+    """Returns (flags with the fastest plan bits, its ms per ADMM iteration)."""
+    f = ctypes.c_uint32()
+    ms = ctypes.c_float()
+    _check(load().nadmm_autotune(ctypes.byref(cfg), _ptr(workspace), nbytes, _stream(stream),
+                                 ctypes.byref(f), ctypes.byref(ms)))
+    return f.value, ms.value
+
+
+def nadmm_batch_set_pair_plan(h, pair, plan_flags):
+    _check(load().nadmm_batch_set_pair_plan(h, pair, plan_flags))
+
+
 def nadmm_destroy(h):
     load().nadmm_destroy(h)
 
@@ -313,11 +345,15 @@ class Registration:
     """A handle plus a torch-allocated device workspace (PyTorch is used for
     device memory only)."""
 
-    def __init__(self, dims, device="cuda", requires_grad=False, **kw):
+    def __init__(self, dims, device="cuda", requires_grad=False, autotune_cache=None,
+                 tune=False, **kw):
         import torch
         self.dims = tuple(dims)
         if requires_grad:
             kw["flags"] = kw.get("flags", 0) | NADMM_FLAG_SAVE_FOR_BACKWARD
+        if tune or autotune_cache:
+            kw["flags"] = (kw.get("flags", 0) & ~NADMM_FLAG_LANE_MASK) | autotune(
+                self.dims, device, autotune_cache)
         self.cfg = make_config(self.dims, **kw)
         self.serial = 0  # forward passes run on this handle
         self.handle = nadmm_create(self.cfg)
@@ -369,6 +405,35 @@ class Registration:
             pass
 
 
+def autotune(dims, device="cuda", cache=None, **kw):
+    """Plan bits (NADMM_FLAG_LANE*) for a grid: nadmm_autotune's choice,
+    remembered in the JSON file `cache` (if given) under the key
+    "nx,ny,nz|<SM count>|<device name>" so that a grid is timed once per GPU
+    type.  Extra keywords shape the config as in make_config."""
+    import json
+    import torch
+    dev = torch.device(device)
+    props = torch.cuda.get_device_properties(dev)
+    key = "%d,%d,%d|%d|%s" % (tuple(dims) + (props.multi_processor_count, props.name))
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as fh:
+            table = json.load(fh)
+    if key in table:
+        return int(table[key]["plan_flags"])
+    cfg = make_config(tuple(dims), **kw)
+    nbytes = nadmm_autotune_workspace_size(cfg)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    ptr = (ws.data_ptr() + 255) // 256 * 256
+    flags, ms = nadmm_autotune(cfg, ptr, nbytes, torch.cuda.current_stream(dev))
+    plan = flags & NADMM_FLAG_LANE_MASK
+    if cache:
+        table[key] = {"plan_flags": plan, "ms_per_iteration": ms}
+        with open(cache, "w") as fh:
+            json.dump(table, fh, indent=1, sort_keys=True)
+    return plan
+
+
 PAPER_V1_OUTER = (10, 10, 5)   # warpings per level, coarsest first (Sec. 4, first version)
 PAPER_V1_INNER = (10, 5, 5)    # ADMM iterations per level
 
@@ -402,7 +467,8 @@ class PyramidRegistration(Registration):
 class BatchedRegistration(Registration):
     """A batched handle (pairs of different grid sizes) plus its workspace."""
 
-    def __init__(self, dims_list, device="cuda", lanes=None, requires_grad=False, **kw):
+    def __init__(self, dims_list, device="cuda", lanes=None, requires_grad=False,
+                 autotune_cache=None, tune=False, **kw):
         import torch
         self.dims_list = [tuple(d) for d in dims_list]
         if requires_grad:
@@ -411,6 +477,12 @@ class BatchedRegistration(Registration):
         self.handle = nadmm_create_batched(self.cfg, self.dims_list)
         if lanes is not None:
             nadmm_batch_set_lanes(self.handle, lanes)
+        if tune or autotune_cache:
+            plans = {}
+            for i, d in enumerate(self.dims_list):
+                if d not in plans:
+                    plans[d] = autotune(d, device, autotune_cache)
+                nadmm_batch_set_pair_plan(self.handle, i, plans[d])
         nbytes = nadmm_workspace_size(self.handle)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
         base = self.workspace.data_ptr()

@@ -73,7 +73,7 @@ def test_unsupported_sizes_are_rejected(lib, dims, why):
                                          ("lambda_", float("nan")), ("outer_iters", 0),
                                          ("inner_iters", 0), ("data_term", 3), ("eps", 0.0),
                                          ("bound_kappa", 0.0), ("bound_delta", -1.0),
-                                         ("flags", 8)])
+                                         ("flags", 0x100), ("flags", 12)])
 def test_bad_parameters_are_rejected(lib, field, value):
     cfg = lib.make_config((32, 32, 24))
     setattr(cfg, field, value)
@@ -187,3 +187,25 @@ def test_pyramid_create_checks(lib):
         lib.nadmm_create_pyramid(lib.make_config((32, 32, 24)), (1,) * 4, (1,) * 4)
     assert e.value.status == lib.NADMM_ERR_UNSUPPORTED_SIZE
     assert "level 3" in str(e.value)
+
+
+def test_plan_flags_and_autotune_sizes(lib):
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_create(lib.make_config((32, 32, 24),
+                                         flags=lib.NADMM_FLAG_LANE8(1) | lib.NADMM_FLAG_LANE16(1)))
+    assert e.value.status == lib.NADMM_ERR_INVALID_ARG
+    for ax in range(3):  # either choice creates a handle for 96 x 96 x 64 (12.8 / 6.16 splits)
+        for f in (lib.NADMM_FLAG_LANE8(ax), lib.NADMM_FLAG_LANE16(ax)):
+            lib.nadmm_destroy(lib.nadmm_create(lib.make_config((96, 96, 64), flags=f)))
+    cfg = lib.make_config((128, 128, 96))
+    need = lib.nadmm_autotune_workspace_size(cfg)
+    h = lib.nadmm_create(cfg)
+    assert need >= lib.nadmm_workspace_size(h)
+    lib.nadmm_destroy(h)
+    b = lib.nadmm_create_batched(cfg, [(128, 128, 96), (96, 96, 64)])
+    lib.nadmm_batch_set_pair_plan(b, 1, lib.NADMM_FLAG_LANE16(2))
+    with pytest.raises(lib.NadmmError):
+        lib.nadmm_batch_set_pair_plan(b, 2, 0)
+    with pytest.raises(lib.NadmmError):
+        lib.nadmm_batch_set_pair_plan(b, 0, lib.NADMM_FLAG_NO_GRAPH)
+    lib.nadmm_destroy(b)
