@@ -93,6 +93,14 @@ typedef struct nadmm_config {
   float bound_kappa;          /* max ||D v||_inf per step, > 0 or INFINITY    */
   float bound_delta;          /* max |v|_inf per step (voxels), > 0 or INFINITY */
   uint32_t flags;             /* NADMM_FLAG_*                                 */
+  float admm_tol;             /* 0 or the ADMM stop: after iteration k >= 1,
+                                 stop when ||w^k - w^(k-1)||_2 <= admm_tol
+                                 ||w^k||_2; inner_iters is then a cap
+                                 (Sec. 4, second version; default 0)       */
+  float warp_tol;             /* 0 or the outer stop: after a re-warp, stop
+                                 when ||I1w_o - I1w_(o-1)||_2 <= warp_tol
+                                 ||I1w_(o-1)||_2; outer_iters is then a cap
+                                 (the paper's "2 %" is 0.02; default 0)    */
 } nadmm_config;
 
 typedef struct nadmm_context* nadmm_handle;
@@ -145,6 +153,16 @@ nadmm_status nadmm_register_host(nadmm_handle h, const float* fixed_host,
  * Returns NADMM_OK, NADMM_ERR_TIMEOUT or NADMM_ERR_NONFINITE (or CUDA on a
  * runtime error). */
 nadmm_status nadmm_get_status(nadmm_handle h, void* stream);
+
+/* Iterations the last registration on a single handle ran (synchronises
+ * `stream`): outer steps composed and ADMM iterations whose result was used,
+ * summed over the outer steps.  Without thresholds these are outer_iters and
+ * outer_iters x inner_iters.  With admm_tol / warp_tol (Sec. 4, second
+ * version) the kernels of a stopped loop still launch from the graph but
+ * return at once; these counters say how much work ran.
+ * Errors: INVALID_ARG, NO_WORKSPACE, CUDA. */
+nadmm_status nadmm_get_iterations(nadmm_handle h, void* stream, int32_t* outer_run,
+                                  int32_t* admm_run);
 
 /* Thread-local description of the last failure of this thread. */
 const char* nadmm_last_error(void);

@@ -59,7 +59,7 @@ __all__ = [
     "nesterov_sequence", "data_step_l2", "data_step_l1", "laplacian_symbol",
     "spectral_solve", "apply_periodic_laplacian", "admm_step", "admm",
     "trilinear", "warp", "central_gradient", "linearise", "compose",
-    "bound_scale", "jacobian_determinant", "register", "energy",
+    "bound_scale", "jacobian_determinant", "register", "admm_until", "energy",
     "augmented_lagrangian", "dense_minimiser_l2",
 ]
 
@@ -306,25 +306,69 @@ def jacobian_determinant(u):
 
 
 # ---------------------------------------------------------------- outer loop
+def admm_until(J, c, lam, theta, n, max_iters, tol, s=2, eps=1e-6):
+    """Eq. 5 stopped by a threshold (Sec. 4, second hyper-parameter version;
+    reading R18): after iteration k >= 1 stop when
+    ||w^k - w^{k-1}||_2 <= tol ||w^k||_2, at most max_iters iterations.
+    Returns (w, iterations run)."""
+    J = np.asarray(J, np.float64)
+    c = np.asarray(c, np.float64)
+    _, beta = nesterov_sequence(max(max_iters, 1))
+    zero = np.zeros_like(J)
+    w_km1, w_km2, b_km1, b_km2 = zero, zero, zero, zero
+    for k in range(max_iters):
+        bk = 0.0 if k == 0 else beta[k - 1]
+        w, b, _ = admm_step(w_km1, w_km2, b_km1, b_km2, bk, J, c, lam, theta, n, s, eps)
+        w_km2, b_km2 = w_km1, b_km1
+        w_km1, b_km1 = w, b
+        if k >= 1 and np.sqrt(((w_km1 - w_km2) ** 2).sum()) <= tol * np.sqrt((w_km1 ** 2).sum()):
+            return w_km1, k + 1
+    return w_km1, max_iters
+
+
 def register(I0, I1, lam=10.0, theta=0.1, n=2, outer=5, inner=10, s=2,
              eps=1e-6, kappa=0.5, delta=1.0, accelerate=True,
-             return_scales=False, u0=None):
+             return_scales=False, u0=None, admm_tol=0.0, warp_tol=0.0,
+             return_counts=False):
     """Greedy diffeomorphic registration (Sec. 2, text after Eq. 2; Eq. 1
     with N = 1): u <- u0 (default 0); repeat ``outer`` times: linearise at
     the current warp of the original I1, run ``inner`` iterations of Eq. 5,
     bound the velocity (R8), compose phi <- phi o (Id + v).  Returns u with
-    I1 o (Id + u) ~ I0."""
+    I1 o (Id + u) ~ I0.
+
+    Thresholds (Sec. 4, second version; reading R18), 0 = off: ADMM stops
+    early as in admm_until (then outer/inner are caps); the outer loop stops
+    after the re-warp of step o when ||I1w_o - I1w_{o-1}||_2 <= warp_tol
+    ||I1w_{o-1}||_2.  return_counts adds the list of ADMM iterations run per
+    outer step."""
     I0 = np.asarray(I0, np.float64)
     I1 = np.asarray(I1, np.float64)
     u = np.zeros((3,) + I0.shape) if u0 is None else np.array(u0, np.float64)
     scales = []
-    for _ in range(outer):
-        J, c, _ = linearise(I0, I1, u)
-        w = admm(J, c, lam, theta, n, inner, s, eps, accelerate)
+    counts = []
+    J, c, I1w = linearise(I0, I1, u)
+    for o in range(outer):
+        if admm_tol > 0.0:
+            w, k = admm_until(J, c, lam, theta, n, inner, admm_tol, s, eps)
+        else:
+            w, k = admm(J, c, lam, theta, n, inner, s, eps, accelerate), inner
+        counts.append(k)
         sc, _, _ = bound_scale(w, kappa, delta)
         scales.append(sc)
         u = compose(u, sc * w)
-    return (u, scales) if return_scales else u
+        if o + 1 < outer:
+            J, c, I1w_new = linearise(I0, I1, u)
+            stop = warp_tol > 0.0 and (np.sqrt(((I1w_new - I1w) ** 2).sum())
+                                       <= warp_tol * np.sqrt((I1w ** 2).sum()))
+            I1w = I1w_new
+            if stop:
+                break
+    out = [u]
+    if return_scales:
+        out.append(scales)
+    if return_counts:
+        out.append(counts)
+    return out[0] if len(out) == 1 else tuple(out)
 
 
 # ---------------------------------------------------------------- energies

@@ -259,7 +259,7 @@ NADMM_HD void plane_scatter(const PlaneArgs& a, const float2* lines, const int* 
 // Point-wise part of the iteration on staged tiles (fld) and lines.
 template <int IN, bool PREV, bool STEP>
 NADMM_HD void plane_pointwise(const PlaneArgs& a, float* fld, float2* lines, int z, int y0,
-                              int tid, int nthr) {
+                              int tid, int nthr, float* racc = nullptr) {
   constexpr FieldMap F = field_map<IN, PREV, STEP>();
   const int h = a.R / 2;
   const int tile = a.R * a.nx;
@@ -296,6 +296,11 @@ NADMM_HD void plane_pointwise(const PlaneArgs& a, float* fld, float2* lines, int
           bk1[comp] = 0.0f;
         }
         if (STEP && PREV) {
+          if (racc != nullptr) {  // ADMM residual: change of w and its size
+            const float dw = wk1[comp] - fld[(F.wp + comp) * tile + so];
+            racc[0] += dw * dw;
+            racc[1] += wk1[comp] * wk1[comp];
+          }
           wh[comp] = wk1[comp] + a.beta * (wk1[comp] - fld[(F.wp + comp) * tile + so]);
           bh[comp] = bk1[comp] + a.beta * (bk1[comp] - fld[(F.bp + comp) * tile + so]);
         } else {
@@ -443,6 +448,43 @@ __device__ __forceinline__ void plane_pack(const PlaneArgs& a, float2* lines,
   }
 }
 
+// ADMM residual of the pass (w^{k-1} against w^{k-2}): CTA sums into
+// conv_acc[0..1]; the last CTA to report decides the ADMM stop.
+__device__ __forceinline__ void plane_residual(const PlaneArgs& a, const float (&racc)[2]) {
+  float d = racc[0], w = racc[1];
+  for (int off = 16; off > 0; off >>= 1) {
+    d += __shfl_xor_sync(0xffffffffu, d, off);
+    w += __shfl_xor_sync(0xffffffffu, w, off);
+  }
+  __shared__ float pd[kPlaneThreads / 32], pw[kPlaneThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    pd[warp] = d;
+    pw[warp] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sd = 0.0, sw = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      sd += pd[k];
+      sw += pw[k];
+    }
+    atomicAdd(a.conv_acc, sd);
+    atomicAdd(a.conv_acc + 1, sw);
+    __threadfence();
+    if (atomicAdd(a.conv + kConvPlaneDone, 1u) == gridDim.x - 1) {  // last CTA
+      __threadfence();
+      const double d2 = atomicAdd(a.conv_acc, 0.0), w2 = atomicAdd(a.conv_acc + 1, 0.0);
+      a.conv[kConvInner] = (sqrt(d2) <= (double)a.admm_tol * sqrt(w2)) ? 1u : 0u;
+      // the velocity is w^{k-1}: iteration k, started by this pass, does not count
+      if (a.conv[kConvInner]) atomicSub(a.conv + kConvAdmmRun, 1u);
+      a.conv_acc[0] = 0.0;
+      a.conv_acc[1] = 0.0;
+      a.conv[kConvPlaneDone] = 0u;
+    }
+  }
+}
+
 // x-DFT of the CTA's lines by groups of xr2 lanes (lane FFT, swizzled lines).
 template <bool INV>
 __device__ __forceinline__ void plane_lane_fft(const PlaneArgs& a, float2* lines,
@@ -493,7 +535,9 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constan
   // only the spectrum: their bulk loads are issued before waiting on it.
   // Every other variant reads data of the immediately preceding kernel (the
   // gradient kernel, or the caller's own work), so it loads after the wait.
-  constexpr bool kEarlyLoads = (IN == IN_SPEC);
+  constexpr bool kSpecIn = (IN == IN_SPEC);
+  // with thresholds the pass may have to stop before loading anything
+  const bool kEarlyLoads = kSpecIn && a.conv == nullptr;
   const uint32_t tile_bytes = (uint32_t)(a.R * a.nx * sizeof(float));
   const size_t tile_off = ((size_t)z * a.ny + y0) * a.nx;
   const bool spec_tma = a.spec_tma != 0;
@@ -517,6 +561,16 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constan
   }
   pdl_wait();
   pdl_trigger();
+  if (a.conv != nullptr) {
+    // threshold stop: a new inner loop (k = 0) clears the ADMM stop; later
+    // passes of a stopped loop, and every pass after the outer stop, return
+    if (a.conv[kConvOuter]) return;
+    if (IN == IN_SPEC && a.conv[kConvInner]) return;
+    if (tid == 0 && (IN == IN_SPEC || IN == IN_NONE) && STEP) {
+      if (IN == IN_NONE && blockIdx.x == 0) a.conv[kConvInner] = 0u;
+      if (blockIdx.x == 0) atomicAdd(a.conv + kConvAdmmRun, 1u);
+    }
+  }
   if (IN == IN_SPEC && spec_tma && tid == 0) {
     // the CTA's spectrum block {R rows, this z, all (comp, kx)}: one box
     mbar_expect_tx(bar + 1, (uint32_t)(nckx * a.R * sizeof(float2)));
@@ -561,7 +615,10 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constan
       return;
     }
   }
-  plane_pointwise<IN, PREV, STEP>(a, fld, lines, z, y0, tid, nthr);
+  float racc[2] = {0.0f, 0.0f};
+  const bool measure = PREV && STEP && IN == IN_SPEC && a.conv != nullptr && a.admm_tol > 0.0f;
+  plane_pointwise<IN, PREV, STEP>(a, fld, lines, z, y0, tid, nthr, measure ? racc : nullptr);
+  if (measure) plane_residual(a, racc);
   // tiles rewritten in shared memory by the point-wise step (w, b, y state)
   constexpr bool kTileStores = STEP && (F.wp >= 0 || F.y >= 0);
   if (kTileStores) fence_proxy_async();  // make them visible to the bulk copies
@@ -709,6 +766,7 @@ __global__ void __launch_bounds__(kYThreads) k_ypass(PencilArgs a) {
   }
   __syncthreads();
   pdl_wait();  // the spectrum comes from the previous kernel
+  if (a.conv != nullptr && (a.conv[kConvInner] | a.conv[kConvOuter])) return;  // threshold stop
   if (tid < 32) {
     if (tid == 0) mbar_expect_tx(bar, row_bytes * a.yrows);
     __syncwarp();
@@ -760,6 +818,7 @@ __global__ void __launch_bounds__(kZThreads) k_zpass(const __grid_constant__ Pen
   }
   __syncthreads();
   pdl_wait();
+  if (a.conv != nullptr && (a.conv[kConvInner] | a.conv[kConvOuter])) return;  // threshold stop
   if (tid == 0) {
     mbar_expect_tx(bar, (uint32_t)(a.nz * a.zcols * sizeof(float2)));
     tensor_load_2d(tile, &a.zmap, y0, row0, bar);
@@ -905,10 +964,25 @@ size_t pencil_smem_bytes(const PencilArgs& a) {
   return y > z ? y : z;
 }
 
+// Dynamic shared-memory limit of a kernel: the request, capped so that the
+// kernel's static shared memory still fits the opt-in maximum per block.
+template <typename K>
+static cudaError_t set_smem_limit(K kernel, size_t smem) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  int dev = 0, optin = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+    return e;
+  const size_t cap = (size_t)optin - fa.sharedSizeBytes;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(smem < cap ? smem : cap));
+}
+
 template <int IN, bool PREV, bool STEP>
 static cudaError_t set_plane_attr(size_t smem) {
-  return cudaFuncSetAttribute(k_plane<IN, PREV, STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  return set_smem_limit(k_plane<IN, PREV, STEP>, smem);
 }
 
 cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem) {
@@ -920,14 +994,9 @@ cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem) {
   if ((e = set_plane_attr<IN_STATE, false, true>(plane_smem)) != cudaSuccess) return e;
   if ((e = set_plane_attr<IN_STATE, true, true>(plane_smem)) != cudaSuccess) return e;
   if ((e = set_plane_attr<IN_FIELD, false, true>(plane_smem)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_ypass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pencil_smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_ypass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pencil_smem)) != cudaSuccess)
-    return e;
-  return cudaFuncSetAttribute(k_zpass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)pencil_smem);
+  if ((e = set_smem_limit(k_ypass<false>, pencil_smem)) != cudaSuccess) return e;
+  if ((e = set_smem_limit(k_ypass<true>, pencil_smem)) != cudaSuccess) return e;
+  return set_smem_limit(k_zpass, pencil_smem);
 }
 
 cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, cudaStream_t s) {

@@ -12,22 +12,70 @@
 
 namespace nadmm {
 
+// Sums (a, b) over the block, added to acc[0..1] (double) by one thread.
+__device__ __forceinline__ void block_add2(float a, float b, double* acc) {
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, off);
+    b += __shfl_xor_sync(0xffffffffu, b, off);
+  }
+  __shared__ float pa[kBY], pb[kBY];
+  if (threadIdx.x == 0) {
+    pa[threadIdx.y] = a;
+    pb[threadIdx.y] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < kBY; ++k) {
+      sa += pa[k];
+      sb += pb[k];
+    }
+    atomicAdd(acc, sa);
+    atomicAdd(acc + 1, sb);
+  }
+}
+
 // I1w(x) = I1(x + u(x)).  Also clears the bound reduction words of the next
-// outer step (the compose that read them has completed).
-__global__ void __launch_bounds__(kBX * kBY) k_warp(Dims d, const float* __restrict__ I1,
-                                                    const float* __restrict__ u,
-                                                    float* __restrict__ I1w, unsigned* red) {
+// outer step (the compose that read them has completed).  With `measure`,
+// the change against the previous I1w is summed, and the last block to
+// finish decides the outer stop (sqrt(sum d^2) <= warp_tol sqrt(sum old^2)).
+__global__ void __launch_bounds__(kBX * kBY)
+    k_warp(Dims d, const float* __restrict__ I1, const float* __restrict__ u, float* I1w,
+           unsigned* red, unsigned* conv, double* conv_acc, float warp_tol, int measure) {
   const size_t V = (size_t)d.nx * d.ny * d.nz;
   pdl_wait();
   pdl_trigger();
+  if (conv != nullptr && conv[kConvOuter]) return;
   const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
   const int z = blockIdx.z;
   if (red != nullptr && (blockIdx.x | blockIdx.y | blockIdx.z) == 0 && threadIdx.y == 0 &&
       threadIdx.x < 2)
     red[threadIdx.x] = 0u;
-  if (x >= d.nx || y >= d.ny) return;
-  const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
-  I1w[i] = trilerp(I1, d, (float)x + u[i], (float)y + u[V + i], (float)z + u[2 * V + i]);
+  float dd = 0.0f, oo = 0.0f;
+  if (x < d.nx && y < d.ny) {
+    const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
+    const float v = trilerp(I1, d, (float)x + u[i], (float)y + u[V + i], (float)z + u[2 * V + i]);
+    if (measure) {
+      const float old = I1w[i];
+      dd = (v - old) * (v - old);
+      oo = old * old;
+    }
+    I1w[i] = v;
+  }
+  if (!measure) return;
+  block_add2(dd, oo, conv_acc + 2);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __threadfence();
+    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+    if (atomicAdd(conv + kConvWarpDone, 1u) == nblk - 1) {  // last block: all sums are in
+      __threadfence();
+      const double d2 = atomicAdd(conv_acc + 2, 0.0), o2 = atomicAdd(conv_acc + 3, 0.0);
+      conv[kConvOuter] = (sqrt(d2) <= (double)warp_tol * sqrt(o2)) ? 1u : 0u;
+      conv_acc[2] = 0.0;
+      conv_acc[3] = 0.0;
+      conv[kConvWarpDone] = 0u;
+    }
+  }
 }
 
 // J = grad I1w (clamped central differences), c = I1w - I0
@@ -35,9 +83,11 @@ __global__ void __launch_bounds__(kBX * kBY) k_grad_residual(Dims d,
                                                              const float* __restrict__ I1w,
                                                              const float* __restrict__ I0,
                                                              float* __restrict__ J,
-                                                             float* __restrict__ c) {
+                                                             float* __restrict__ c,
+                                                             const unsigned* conv) {
   pdl_wait();
   pdl_trigger();
+  if (conv != nullptr && conv[kConvOuter]) return;
   const size_t V = (size_t)d.nx * d.ny * d.nz;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
@@ -58,9 +108,10 @@ __global__ void __launch_bounds__(kBX * kBY) k_grad_residual(Dims d,
 // floats order like their bits; NaN bits sort above +inf).  Each block
 // loops over the z-slices blockIdx.z, blockIdx.z + gridDim.z, ...
 __global__ void __launch_bounds__(kBX * kBY) k_bound_reduce(Dims d, const float* __restrict__ w,
-                                                            unsigned* red) {
+                                                            unsigned* red, const unsigned* conv) {
   pdl_wait();
   pdl_trigger();
+  if (conv != nullptr && conv[kConvOuter]) return;
   const size_t V = (size_t)d.nx * d.ny * d.nz;
   const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
   float mabs = 0.0f, mjac = 0.0f;
@@ -106,10 +157,21 @@ __global__ void __launch_bounds__(kBX * kBY) k_compose(Dims d, const float* __re
                                                        float* __restrict__ u_out,
                                                        const unsigned* red, float kappa,
                                                        float delta, unsigned* status,
-                                                       float* scale_out) {
+                                                       float* scale_out, unsigned* conv) {
   pdl_wait();
   pdl_trigger();
   const size_t V = (size_t)d.nx * d.ny * d.nz;
+  if (conv != nullptr && conv[kConvOuter]) {  // stopped: carry u over to u_out
+    const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
+    if (x >= d.nx || y >= d.ny || u_in == u_out) return;
+    const size_t i = ((size_t)blockIdx.z * d.ny + y) * d.nx + x;
+    u_out[i] = u_in[i];
+    u_out[V + i] = u_in[V + i];
+    u_out[2 * V + i] = u_in[2 * V + i];
+    return;
+  }
+  if (conv != nullptr && (blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0)
+    atomicAdd(conv + kConvOuterRun, 1u);  // one more outer step composed
   const bool first = (blockIdx.x | blockIdx.y | blockIdx.z) == 0 && threadIdx.x == 0 &&
                      threadIdx.y == 0;
   const float s = bound_factor(red, kappa, delta, first ? status : nullptr);
@@ -199,24 +261,39 @@ static const dim3 kBlock(kBX, kBY);
 
 cudaError_t launch_warp(Dims d, const float* I1, const float* u, float* I1w, unsigned* red_reset,
                         cudaStream_t s) {
-  return launch_pdl(k_warp, grid3(d, d.nz), kBlock, 0, s, d, I1, u, I1w, red_reset);
+  return launch_pdl(k_warp, grid3(d, d.nz), kBlock, 0, s, d, I1, u, I1w, red_reset,
+                    (unsigned*)nullptr, (double*)nullptr, 0.0f, 0);
+}
+
+cudaError_t launch_warp_measured(Dims d, const float* I1, const float* u, float* I1w,
+                                 unsigned* red_reset, unsigned* conv, double* conv_acc,
+                                 float warp_tol, bool measure, cudaStream_t s) {
+  return launch_pdl(k_warp, grid3(d, d.nz), kBlock, 0, s, d, I1, u, I1w, red_reset, conv, conv_acc,
+                    warp_tol, measure ? 1 : 0);
 }
 
 cudaError_t launch_grad_residual(Dims d, const float* I1w, const float* I0, float* J, float* c,
                                  cudaStream_t s) {
-  return launch_pdl(k_grad_residual, grid3(d, d.nz), kBlock, 0, s, d, I1w, I0, J, c);
+  return launch_pdl(k_grad_residual, grid3(d, d.nz), kBlock, 0, s, d, I1w, I0, J, c,
+                    (const unsigned*)nullptr);
 }
 
-cudaError_t launch_bound_reduce(Dims d, const float* w, unsigned* red, cudaStream_t s) {
+cudaError_t launch_grad_residual_conv(Dims d, const float* I1w, const float* I0, float* J, float* c,
+                                      const unsigned* conv, cudaStream_t s) {
+  return launch_pdl(k_grad_residual, grid3(d, d.nz), kBlock, 0, s, d, I1w, I0, J, c, conv);
+}
+
+cudaError_t launch_bound_reduce(Dims d, const float* w, unsigned* red, cudaStream_t s,
+                                const unsigned* conv) {
   // a few z-slices per block keep the number of atomics small
-  return launch_pdl(k_bound_reduce, grid3(d, d.nz < 8 ? d.nz : 8), kBlock, 0, s, d, w, red);
+  return launch_pdl(k_bound_reduce, grid3(d, d.nz < 8 ? d.nz : 8), kBlock, 0, s, d, w, red, conv);
 }
 
 cudaError_t launch_compose(Dims d, const float* w, const float* u_in, float* u_out,
                            const unsigned* red, float kappa, float delta, unsigned* status,
-                           float* scale_out, cudaStream_t s) {
+                           float* scale_out, cudaStream_t s, unsigned* conv) {
   return launch_pdl(k_compose, grid3(d, d.nz), kBlock, 0, s, d, w, u_in, u_out,
-                    (const unsigned*)red, kappa, delta, status, scale_out);
+                    (const unsigned*)red, kappa, delta, status, scale_out, conv);
 }
 
 cudaError_t launch_downsample2(Dims coarse, const float* fine, float* out, cudaStream_t s) {

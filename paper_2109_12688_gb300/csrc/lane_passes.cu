@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_ylane(const __grid_constant__ 
   const int row = (blockIdx.x * (kLaneThreads / 32) + warp) * LPW + g;
   const bool active = row < total;
   pdl_wait();  // the spectrum comes from the previous kernel
+  if (a.conv != nullptr && (a.conv[kConvInner] | a.conv[kConvOuter])) return;  // threshold stop
   pdl_trigger();
   float2* line = a.spec + (size_t)(active ? row : 0) * N;
   float2 v[R1];
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(kLaneThreads, zlane_min_blocks<R1, R2>())
   const int y = (active ? task - plane * groups : 0) * CPW + col;
   const int kx = plane % a.nkx;
   pdl_wait();
+  if (a.conv != nullptr && (a.conv[kConvInner] | a.conv[kConvOuter])) return;  // threshold stop
   pdl_trigger();
   float2* base = a.spec + (size_t)plane * a.ny * a.nz + y;
   const size_t zs = (size_t)a.ny;

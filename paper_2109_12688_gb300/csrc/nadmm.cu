@@ -60,7 +60,7 @@ struct nadmm_context {
          o_ub1 = 0;
   bool saved_forward = false;
   bool has_tape = false;  // o_tape (table region) is allocated
-  size_t o_red, o_acc, o_twx, o_twy, o_twz, o_posx, o_Kx, o_Ky, o_Kz, table_total;
+  size_t o_red, o_acc, o_conv, o_convacc, o_twx, o_twy, o_twz, o_posx, o_Kx, o_Ky, o_Kz, table_total;
   size_t total;  // single handle: align(state_total) + table_total
   char* ws = nullptr;
   char* wt = nullptr;
@@ -125,6 +125,11 @@ nadmm_status validate(const nadmm_config* c) {
   if (c->data_term != 1 && c->data_term != 2)
     return fail(NADMM_ERR_INVALID_ARG, "data_term must be 1 or 2");
   if (!(c->eps > 0.0f) || !std::isfinite(c->eps)) return fail(NADMM_ERR_INVALID_ARG, "eps must be > 0");
+  if (!(c->admm_tol >= 0.0f) || !std::isfinite(c->admm_tol) || !(c->warp_tol >= 0.0f) ||
+      !std::isfinite(c->warp_tol))
+    return fail(NADMM_ERR_INVALID_ARG, "admm_tol and warp_tol must be finite and >= 0");
+  if ((c->admm_tol > 0.0f || c->warp_tol > 0.0f) && (c->flags & NADMM_FLAG_SAVE_FOR_BACKWARD))
+    return fail(NADMM_ERR_INVALID_ARG, "the reverse mode needs fixed iteration counts (no thresholds)");
   if (!(c->bound_kappa > 0.0f) || !(c->bound_delta > 0.0f))
     return fail(NADMM_ERR_INVALID_ARG, "bound_kappa and bound_delta must be > 0 (INFINITY disables)");
   if (c->flags & ~(NADMM_FLAG_NO_GRAPH | NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK))
@@ -160,6 +165,8 @@ float beta_for(const nadmm_context* h, int k) {  // factor used to form w_hat^k
   return (float)b;
 }
 
+bool thresholds(const nadmm_context* h) { return h->cfg.admm_tol > 0.0f || h->cfg.warp_tol > 0.0f; }
+
 PlaneArgs plane_args(const nadmm_context* h) {
   PlaneArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -183,6 +190,11 @@ PlaneArgs plane_args(const nadmm_context* h) {
   finish_plane_args(a);
   a.smap = h->smap;
   if (!h->smap_ok) a.spec_tma = 0;
+  if (thresholds(h)) {
+    a.conv = h->tab<unsigned>(h->o_conv);
+    a.conv_acc = h->tab<double>(h->o_convacc);
+    a.admm_tol = h->cfg.admm_tol;
+  }
   return a;
 }
 
@@ -206,6 +218,7 @@ PencilArgs pencil_args(const nadmm_context* h) {
   a.scale = (float)(1.0 / ((double)h->cfg.nx * h->cfg.ny * h->cfg.nz));
   finish_pencil_args(a);
   a.zmap = h->zmap;
+  if (thresholds(h)) a.conv = h->tab<unsigned>(h->o_conv);
   return a;
 }
 
@@ -303,6 +316,12 @@ cudaError_t enqueue_register(nadmm_context* h, const float* I0, const float* I1,
   auto dst_of = [&](int o) { return ((O - 1 - o) % 2 == 0) ? u_out : ut; };
   float* u_cur = (dst_of(0) == u_out) ? ut : u_out;
   TRY(cudaMemsetAsync(red, 0, 4 * sizeof(unsigned), s));  // red[0..1], status red[2]
+  unsigned* conv = thresholds(h) ? h->tab<unsigned>(h->o_conv) : nullptr;
+  double* conv_acc = h->tab<double>(h->o_convacc);
+  if (conv) {
+    TRY(cudaMemsetAsync(conv, 0, kConvWords * sizeof(unsigned), s));
+    TRY(cudaMemsetAsync(conv_acc, 0, 4 * sizeof(double), s));
+  }
   if (u_init)  // start from a given displacement (a coarser pyramid level's)
     TRY(cudaMemcpyAsync(u_cur, u_init, 3 * V * sizeof(float), cudaMemcpyDeviceToDevice, s));
   else
@@ -316,15 +335,17 @@ cudaError_t enqueue_register(nadmm_context* h, const float* I0, const float* I1,
     PlaneArgs first = plane_args(h);
     TRY(enqueue_inner(h, first, IN_NONE, false, 0, K, J, c, vbuf, nullptr, s));
     // red[0..1] are zero here: cleared at the start, then by each re-warp
-    KLAUNCH(NADMM_KC_BOUND, s, launch_bound_reduce(d, vbuf, red, s));
+    KLAUNCH(NADMM_KC_BOUND, s, launch_bound_reduce(d, vbuf, red, s, conv));
     float* u_new = dst_of(o);
     KLAUNCH(NADMM_KC_COMPOSE, s,
             launch_compose(d, vbuf, u_cur, u_new, red, h->cfg.bound_kappa, h->cfg.bound_delta,
-                           red + 2, nullptr, s));
+                           red + 2, nullptr, s, conv));
     u_cur = u_new;
     if (o + 1 < O) {
-      KLAUNCH(NADMM_KC_WARP, s, launch_warp(d, I1, u_cur, I1w, red, s));
-      KLAUNCH(NADMM_KC_GRAD, s, launch_grad_residual(d, I1w, I0, J, c, s));
+      KLAUNCH(NADMM_KC_WARP, s,
+              launch_warp_measured(d, I1, u_cur, I1w, red, conv, conv_acc, h->cfg.warp_tol,
+                                   conv != nullptr && h->cfg.warp_tol > 0.0f, s));
+      KLAUNCH(NADMM_KC_GRAD, s, launch_grad_residual_conv(d, I1w, I0, J, c, conv, s));
     }
   }
   return cudaSuccess;
@@ -450,6 +471,8 @@ nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
   o = 0;
   h->o_red = take(4 * sizeof(unsigned));
   h->o_acc = take(4 * sizeof(double));
+  h->o_conv = take(kConvWords * sizeof(unsigned));
+  h->o_convacc = take(4 * sizeof(double));
   h->o_twx = take(h->twx.size() * sizeof(float2));
   h->o_twy = take(h->twy.size() * sizeof(float2));
   h->o_twz = take(h->twz.size() * sizeof(float2));
@@ -846,6 +869,8 @@ void nadmm_config_init(nadmm_config* c, int32_t nx, int32_t ny, int32_t nz) {
   c->bound_kappa = 0.5f;
   c->bound_delta = 1.0f;
   c->flags = 0;
+  c->admm_tol = 0.0f;
+  c->warp_tol = 0.0f;
 }
 
 const char* nadmm_last_error(void) { return g_err.c_str(); }
@@ -1457,6 +1482,27 @@ nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t byt
   if (st != NADMM_OK) return st;
   *best_flags = (cfg->flags & ~NADMM_FLAG_LANE_MASK) | (best_f & NADMM_FLAG_LANE_MASK);
   if (best_ms) *best_ms = best;
+  return NADMM_OK;
+}
+
+nadmm_status nadmm_get_iterations(nadmm_handle h, void* stream, int32_t* outer_run,
+                                  int32_t* admm_run) {
+  if (!h || !outer_run || !admm_run) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
+  if (h->batched || h->pyramid)
+    return fail(NADMM_ERR_INVALID_ARG, "this call needs a single-pair handle (nadmm_create)");
+  if (!h->wt) return fail(NADMM_ERR_NO_WORKSPACE, "no workspace attached (nadmm_set_workspace)");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  if (!thresholds(h)) {
+    *outer_run = h->cfg.outer_iters;
+    *admm_run = h->cfg.outer_iters * h->cfg.inner_iters;
+    return NADMM_OK;
+  }
+  unsigned w[kConvWords];
+  e = cudaMemcpy(w, h->tab<unsigned>(h->o_conv), sizeof(w), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "counter read");
+  *outer_run = (int32_t)w[kConvOuterRun];
+  *admm_run = (int32_t)w[kConvAdmmRun];
   return NADMM_OK;
 }
 

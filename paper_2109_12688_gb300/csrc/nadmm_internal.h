@@ -41,6 +41,9 @@ struct PlaneArgs {
   const float2* twx;       // x-axis stage twiddles
   const int* posx;         // position of frequency kx after the forward x-DFT
   unsigned* status;        // device status word (bit 1: a bounded wait expired) or null
+  unsigned* conv;          // threshold words (kConv*) or null when no threshold is set
+  double* conv_acc;        // [0] sum (w^{k-1} - w^{k-2})^2, [1] sum (w^{k-1})^2
+  float admm_tol;
   AxisPlan px;
   FastDiv nx_div;          // division by nx
   FastDiv lines_div;       // division by the line count 3 R / 2
@@ -71,6 +74,7 @@ struct PencilArgs {
   const float* Ky;         // [ny] 4 sin^2(pi ky / ny) by position
   const float* Kz;         // [nz] 4 sin^2(pi kz / nz) by position
   unsigned* status;        // device status word (bit 1: a bounded wait expired) or null
+  const unsigned* conv;    // threshold words (kConv*) or null
   AxisPlan py, pz;
   FastDiv yrows_div, zcols_div, ztiles_div, nkx_div;
   int ny, nz, nkx;
@@ -84,6 +88,19 @@ struct PencilArgs {
 
 constexpr unsigned kStatusNonfinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;
+
+// Threshold stopping (Sec. 4, second version): words of a handle's `conv`
+// array.  A kernel of the inner loop returns at once when kConvInner or
+// kConvOuter is set; a kernel of the outer step when kConvOuter is set.
+enum ConvWord : int {
+  kConvInner = 0,      // the ADMM residual met admm_tol in this outer step
+  kConvOuter = 1,      // the warped-image change met warp_tol
+  kConvPlaneDone = 2,  // CTAs of the measuring plane pass that have reported
+  kConvWarpDone = 3,   // blocks of the measuring re-warp that have reported
+  kConvAdmmRun = 4,    // ADMM iterations run (all outer steps)
+  kConvOuterRun = 5,   // outer steps run
+  kConvWords = 8
+};
 
 // One block waits (bounded, `attempts` tries) on a barrier nothing arrives at.
 cudaError_t launch_wait_selftest(unsigned* status, int attempts, cudaStream_t s);
@@ -155,11 +172,21 @@ cudaError_t launch_warp(Dims d, const float* I1, const float* u, float* I1w, uns
 cudaError_t launch_grad_residual(Dims d, const float* I1w, const float* I0, float* J, float* c,
                                  cudaStream_t s);
 // red[0] = bits of max |w|_inf, red[1] = bits of max ||Dw||_inf (must start at 0)
-cudaError_t launch_bound_reduce(Dims d, const float* w, unsigned* red, cudaStream_t s);
-// s from red; u_out = s w + u_in(x + s w); status |= 1 on non-finite maxima
+cudaError_t launch_bound_reduce(Dims d, const float* w, unsigned* red, cudaStream_t s,
+                                const unsigned* conv = nullptr);
+// s from red; u_out = s w + u_in(x + s w); status |= 1 on non-finite maxima;
+// with conv[kConvOuter] set: u_out = u_in
 cudaError_t launch_compose(Dims d, const float* w, const float* u_in, float* u_out,
                            const unsigned* red, float kappa, float delta, unsigned* status,
-                           float* scale_out, cudaStream_t s);
+                           float* scale_out, cudaStream_t s, unsigned* conv = nullptr);
+// Re-warp that also measures the change of I1w against its previous content
+// (conv_acc[2..3]) and sets conv[kConvOuter] when it is <= warp_tol; skipped
+// when conv[kConvOuter] is already set.
+cudaError_t launch_warp_measured(Dims d, const float* I1, const float* u, float* I1w,
+                                 unsigned* red_reset, unsigned* conv, double* conv_acc,
+                                 float warp_tol, bool measure, cudaStream_t s);
+cudaError_t launch_grad_residual_conv(Dims d, const float* I1w, const float* I0, float* J, float* c,
+                                      const unsigned* conv, cudaStream_t s);
 cudaError_t launch_jacobian(Dims d, const float* u, float* det, unsigned* count, cudaStream_t s);
 // pyramid: 2 x 2 x 2 block average onto `coarse`; cell-centred doubling upsample of u
 cudaError_t launch_downsample2(Dims coarse, const float* fine, float* out, cudaStream_t s);

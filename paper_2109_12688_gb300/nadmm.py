@@ -51,7 +51,8 @@ class nadmm_config(ctypes.Structure):
                 ("theta", ctypes.c_float), ("outer_iters", ctypes.c_int32),
                 ("inner_iters", ctypes.c_int32), ("data_term", ctypes.c_int32),
                 ("eps", ctypes.c_float), ("bound_kappa", ctypes.c_float),
-                ("bound_delta", ctypes.c_float), ("flags", ctypes.c_uint32)]
+                ("bound_delta", ctypes.c_float), ("flags", ctypes.c_uint32),
+                ("admm_tol", ctypes.c_float), ("warp_tol", ctypes.c_float)]
 
 
 _lib = None
@@ -95,6 +96,8 @@ _SIGS = {
     "nadmm_autotune": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, ctypes.POINTER(ctypes.c_uint32),
                                       ctypes.POINTER(ctypes.c_float)]),
     "nadmm_batch_set_pair_plan": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32]),
+    "nadmm_get_iterations": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32)]),
     "nadmm_ssd_after_warp": (ctypes.c_int, [_P] * 6),
     "nadmm_ssd_after_warp_backward": (ctypes.c_int, [_P] * 9),
 }
@@ -247,6 +250,13 @@ def nadmm_batch_set_pair_plan(h, pair, plan_flags):
     _check(load().nadmm_batch_set_pair_plan(h, pair, plan_flags))
 
 
+def nadmm_get_iterations(h, stream=None):
+    o = ctypes.c_int32()
+    a = ctypes.c_int32()
+    _check(load().nadmm_get_iterations(h, _stream(stream), ctypes.byref(o), ctypes.byref(a)))
+    return o.value, a.value
+
+
 def nadmm_destroy(h):
     load().nadmm_destroy(h)
 
@@ -324,7 +334,7 @@ def nadmm_jacobian_det(h, u, det=None, nonpositive=None, stream=None):
 
 # ---------------------------------------------------------------- convenience
 def make_config(dims, order_n=2, lam=10.0, theta=0.1, outer=10, inner=10, data_term=2,
-                eps=1e-6, kappa=0.5, delta=1.0, flags=0):
+                eps=1e-6, kappa=0.5, delta=1.0, flags=0, admm_tol=0.0, warp_tol=0.0):
     """nadmm_config for dims = (nx, ny, nz); kappa/delta may be math.inf."""
     nx, ny, nz = dims
     cfg = nadmm_config_init(nx, ny, nz)
@@ -338,6 +348,8 @@ def make_config(dims, order_n=2, lam=10.0, theta=0.1, outer=10, inner=10, data_t
     cfg.bound_kappa = kappa if math.isfinite(kappa) else float("inf")
     cfg.bound_delta = delta if math.isfinite(delta) else float("inf")
     cfg.flags = flags
+    cfg.admm_tol = admm_tol
+    cfg.warp_tol = warp_tol
     return cfg
 
 

@@ -491,3 +491,35 @@ def test_outer_loop_composes_in_the_paper_order(monkeypatch):
         np.testing.assert_allclose(u[inner], ref[inner], atol=1e-12)
         if delta == 0.1:
             assert max(scales) < 1.0
+
+
+# ---------------------------------------------------------------- thresholds (Sec. 4, version 2)
+def test_admm_until_stops_at_the_first_small_change():
+    p = synth.make_pair((16, 16, 12), seed=2)
+    J, c, _ = O.linearise(p["fixed"], p["moving"], np.zeros((3, 12, 16, 16)))
+    hist = O.admm(J, c, 10.0, 0.1, 2, 30, history=True)
+    rel = [np.linalg.norm(hist[k][0] - hist[k - 1][0]) / np.linalg.norm(hist[k][0])
+           for k in range(1, 30)]
+    tol = 0.5 * (rel[4] + rel[5]) if rel[5] < rel[4] else rel[5] * 1.0001
+    k_expect = 1 + next(i for i, r in enumerate(rel) if r <= tol) + 1
+    w, k = O.admm_until(J, c, 10.0, 0.1, 2, 30, tol)
+    assert k == k_expect
+    np.testing.assert_array_equal(w, hist[k - 1][0])
+    w0, k0 = O.admm_until(J, c, 10.0, 0.1, 2, 7, 1e-30)  # never met: the cap
+    assert k0 == 7 and np.array_equal(w0, hist[6][0])
+
+
+def test_register_thresholds_reduce_to_caps_and_stop_early():
+    p = synth.make_pair((16, 16, 12), seed=4)
+    kw = dict(lam=10.0, theta=0.1, n=2, outer=4, inner=6)
+    base = O.register(p["fixed"], p["moving"], **kw)
+    tiny = O.register(p["fixed"], p["moving"], admm_tol=1e-30, warp_tol=1e-30, **kw)
+    np.testing.assert_array_equal(base, tiny)          # thresholds never met = caps
+    u, counts = O.register(p["fixed"], p["moving"], admm_tol=0.3, warp_tol=0.5,
+                           return_counts=True, **kw)
+    assert all(k < 6 for k in counts) and len(counts) < 4  # both stop early
+    # the outer loop stopped right after the first composition whose re-warp
+    # changed the warped image by at most 50 %
+    u1 = O.register(p["fixed"], p["moving"], admm_tol=0.3, outer=len(counts), inner=6,
+                    lam=10.0, theta=0.1, n=2)
+    np.testing.assert_array_equal(u, u1)
