@@ -179,14 +179,14 @@ const char* nadmm_status_string(nadmm_status s);
  * dims[3i+2] (nx, ny, nz) and every other setting from `base` (its nx, ny,
  * nz are ignored).  Each grid is validated as by nadmm_create; the first
  * failure is returned with "pair i: ..." in nadmm_last_error.  The pairs
- * run in one CUDA graph on `lanes` concurrent branches (default 1, see
- * nadmm_batch_set_lanes), spread longest first to balance voxel counts;
- * pairs of one lane run one after another and share that lane's scratch,
- * so the workspace is one state region per lane (its largest pair's) plus
- * every pair's small tables.  One lane is the default because a pair's
- * ADMM working set (about 64 bytes per voxel) already fills most of the
- * 126 MB L2 at 128 x 128 x 96: concurrent pairs evict each other.
- * Host only. */
+ * run in one CUDA graph on `lanes` concurrent branches (default
+ * min(npairs, 2), see nadmm_batch_set_lanes), spread longest first to
+ * balance voxel counts; pairs of one lane run one after another and share
+ * that lane's scratch, so the workspace is one state region per lane (its
+ * largest pair's) plus every pair's own region (tables, tape).  Two lanes
+ * let one pair's DRAM-heavy plane passes overlap another's L2-resident FFT
+ * passes; more lanes can lose again to L2 evictions (64 uneven pairs:
+ * 488 / 466 / 514 ms with 1 / 2 / 4 lanes).  Host only. */
 nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, const int32_t* dims,
                                   nadmm_handle* out);
 

@@ -376,7 +376,7 @@ nadmm_status check_dev_ptrs(std::initializer_list<const void*> ptrs) {
   return NADMM_OK;
 }
 
-constexpr int kDefaultLanes = 1;
+constexpr int kDefaultLanes = 2;
 
 // R2 tried first for an axis's lane plan: the flag bits, else the defaults
 // measured on 128x128x96 (x 8, y 16, z 8).
