@@ -80,6 +80,11 @@ typedef enum nadmm_status {
 #define NADMM_FLAG_LANE8(axis)  (1u << NADMM_FLAG_LANE_SHIFT(axis))
 #define NADMM_FLAG_LANE16(axis) (2u << NADMM_FLAG_LANE_SHIFT(axis))
 #define NADMM_FLAG_LANE_MASK 0xFCu
+#define NADMM_FLAG_FUSED_PENCIL 0x100u /* run the y/z FFT pass as one kernel (a
+                                     2-CTA cluster per (component, kx) plane that
+                                     swaps column halves through distributed
+                                     shared memory) where it applies, instead of
+                                     three kernels; nadmm_autotune tries both  */
 
 typedef struct nadmm_config {
   int32_t nx, ny, nz;         /* grid (M, N, H); see NADMM_ERR_UNSUPPORTED_SIZE */
@@ -195,7 +200,8 @@ nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, cons
  * Errors: INVALID_ARG (not batched, lanes < 1, workspace already attached). */
 nadmm_status nadmm_batch_set_lanes(nadmm_handle h, int32_t lanes);
 
-/* Replace the NADMM_FLAG_LANE* plan bits of pair `pair` (0-based) of a
+/* Replace the NADMM_FLAG_LANE* and NADMM_FLAG_FUSED_PENCIL bits of pair
+ * `pair` (0-based) of a
  * batched handle before its workspace is attached (e.g. with the result of
  * nadmm_autotune for that pair's grid); the workspace size may change.
  * Errors: INVALID_ARG. */
@@ -331,12 +337,14 @@ nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, in
 nadmm_status nadmm_autotune_workspace_size(const nadmm_config* cfg, size_t* bytes);
 
 /* Time every plan choice of `cfg`'s grid -- each axis with both an 8- and a
- * 16-lane split tried both ways -- on one ADMM iteration (the k >= 2 plane
- * pass and the y/z passes; 3 warm-up and 10 timed repetitions, CUDA events
+ * 16-lane split tried both ways, and the fused y/z pass where it applies --
+ * on one ADMM iteration (the k >= 2 plane pass and the y/z passes; 3
+ * warm-up and 10 timed repetitions, CUDA events
  * on `stream`, minimum kept) in the caller's device workspace (at least
  * nadmm_autotune_workspace_size bytes, 256-byte aligned; its contents are
- * overwritten) and write the fastest choice as NADMM_FLAG_LANE* bits to
- * *best_flags (cfg->flags with its plan bits replaced) and its time in ms to
+ * overwritten) and write the fastest choice as NADMM_FLAG_LANE* and
+ * NADMM_FLAG_FUSED_PENCIL bits to *best_flags (cfg->flags with those bits
+ * replaced) and its time in ms to
  * *best_ms (host pointers; best_ms may be NULL).  Synchronises `stream`.
  * Errors: INVALID_ARG, UNSUPPORTED_SIZE, ALIGNMENT, NO_WORKSPACE, CUDA. */
 nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t bytes,

@@ -25,6 +25,7 @@
 
 #include "fft_device.cuh"
 #include "lane_fft.cuh"
+#include "tma.cuh"
 #include "nadmm_internal.h"
 #include "plan.h"
 
@@ -51,102 +52,7 @@ NADMM_HD void v_step(int data_term, float theta, float eps, const float (&J)[3],
   v[2] = u[2] - f * J[2];
 }
 
-// ---------------------------------------------------------------- TMA / mbarrier
-#if defined(__CUDA_ARCH__)
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-// global -> shared bulk copy completing on `bar` (16-byte aligned, size % 16 == 0)
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
-                                          uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-// shared -> global bulk copy in the thread's bulk group
-__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
-               "r"(smem_addr(src)), "r"(bytes)
-               : "memory");
-}
-// 2D tiled TMA load of box {x, y} of `map` into shared memory (128-byte aligned)
-__device__ __forceinline__ void tensor_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                               uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
-      : "memory");
-}
-// 3D tiled TMA load of box {x, y, z} of `map` into shared memory
-__device__ __forceinline__ void tensor_load_3d(void* dst, const CUtensorMap* map, int x, int y,
-                                               int z, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
-      : "memory");
-}
-// 3D tiled TMA store of a shared-memory box to {x, y, z} of `map`
-__device__ __forceinline__ void tensor_store_3d(const CUtensorMap* map, int x, int y, int z,
-                                                const void* src) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-          reinterpret_cast<uint64_t>(map)),
-      "r"(x), "r"(y), "r"(z), "r"(smem_addr(src))
-      : "memory");
-}
-// 2D tiled TMA store of a shared-memory box to {x, y} of `map`
-__device__ __forceinline__ void tensor_store_2d(const CUtensorMap* map, int x, int y,
-                                                const void* src) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                   reinterpret_cast<uint64_t>(map)),
-               "r"(x), "r"(y), "r"(smem_addr(src))
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read() {
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// try_wait suspends for a hardware-bounded time per attempt; the attempt
-// count bounds the whole wait well under a second of a stuck copy.
-constexpr int kWaitAttempts = 1 << 20;
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
-                                                  int attempts = kWaitAttempts) {
-  for (int i = 0; i < attempts; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-#endif
+// TMA / mbarrier helpers: tma.cuh
 
 // Self-test of the timeout path: one barrier that nothing ever arrives at
 // (no copy is issued), waited on with the bounded wait of the passes; the
@@ -883,6 +789,7 @@ void finish_pencil_args(PencilArgs& a) {
   a.zcols_div = make_fastdiv((uint32_t)a.zcols);
   a.ztiles_div = make_fastdiv((uint32_t)(a.ny / a.zcols));
   a.nkx_div = make_fastdiv((uint32_t)a.nkx);
+  a.fused = 0;  // the caller opts in (NADMM_FLAG_FUSED_PENCIL) where fused_pencil_supported
 }
 
 cudaError_t encode_pencil_map(PencilArgs& a) {
@@ -996,6 +903,7 @@ cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem) {
   if ((e = set_plane_attr<IN_FIELD, false, true>(plane_smem)) != cudaSuccess) return e;
   if ((e = set_smem_limit(k_ypass<false>, pencil_smem)) != cudaSuccess) return e;
   if ((e = set_smem_limit(k_ypass<true>, pencil_smem)) != cudaSuccess) return e;
+  if ((e = configure_fused_pencil()) != cudaSuccess) return e;
   return set_smem_limit(k_zpass, pencil_smem);
 }
 
@@ -1016,6 +924,7 @@ cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, 
 }
 
 cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s) {
+  if (a.fused) return launch_fused_pencil(a, s);
   const unsigned yblocks = (unsigned)(3 * a.nkx * a.nz / a.yrows);
   const unsigned zblocks = (unsigned)(3 * a.nkx * (a.ny / a.zcols));
   const bool ly = lane_y_supported(a), lz = lane_z_supported(a);

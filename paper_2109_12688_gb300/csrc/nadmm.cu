@@ -132,7 +132,8 @@ nadmm_status validate(const nadmm_config* c) {
     return fail(NADMM_ERR_INVALID_ARG, "the reverse mode needs fixed iteration counts (no thresholds)");
   if (!(c->bound_kappa > 0.0f) || !(c->bound_delta > 0.0f))
     return fail(NADMM_ERR_INVALID_ARG, "bound_kappa and bound_delta must be > 0 (INFINITY disables)");
-  if (c->flags & ~(NADMM_FLAG_NO_GRAPH | NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK))
+  if (c->flags & ~(NADMM_FLAG_NO_GRAPH | NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK |
+                   NADMM_FLAG_FUSED_PENCIL))
     return fail(NADMM_ERR_INVALID_ARG, "unknown flag bits");
   for (int ax = 0; ax < 3; ++ax)
     if (((c->flags >> NADMM_FLAG_LANE_SHIFT(ax)) & 3u) == 3u)
@@ -217,6 +218,7 @@ PencilArgs pencil_args(const nadmm_context* h) {
   a.gamma = h->cfg.lambda / h->cfg.theta;
   a.scale = (float)(1.0 / ((double)h->cfg.nx * h->cfg.ny * h->cfg.nz));
   finish_pencil_args(a);
+  if (h->cfg.flags & NADMM_FLAG_FUSED_PENCIL) a.fused = fused_pencil_supported(a) ? 1 : 0;
   a.zmap = h->zmap;
   if (thresholds(h)) a.conv = h->tab<unsigned>(h->o_conv);
   return a;
@@ -996,9 +998,11 @@ nadmm_status nadmm_batch_set_pair_plan(nadmm_handle h, int32_t pair, uint32_t pl
   if (!h || !h->batched) return fail(NADMM_ERR_INVALID_ARG, "not a batched handle");
   if (h->wt) return fail(NADMM_ERR_INVALID_ARG, "set plans before nadmm_set_workspace");
   if (pair < 0 || pair >= (int32_t)h->pairs.size()) return fail(NADMM_ERR_INVALID_ARG, "pair out of range");
-  if (plan_flags & ~NADMM_FLAG_LANE_MASK) return fail(NADMM_ERR_INVALID_ARG, "only NADMM_FLAG_LANE* bits");
+  const uint32_t tuned = NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL;
+  if (plan_flags & ~tuned)
+    return fail(NADMM_ERR_INVALID_ARG, "only NADMM_FLAG_LANE* and NADMM_FLAG_FUSED_PENCIL bits");
   nadmm_config c = h->pairs[pair]->cfg;
-  c.flags = (c.flags & ~NADMM_FLAG_LANE_MASK) | plan_flags;
+  c.flags = (c.flags & ~tuned) | plan_flags;
   nadmm_context* q = nullptr;
   nadmm_status st = create_single(&c, &q);
   if (st != NADMM_OK) return st;
@@ -1432,19 +1436,21 @@ nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t byt
     return cuda_fail(e, "cudaEventCreate");
   }
   nadmm_config c = *cfg;
-  c.flags &= ~(NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK);
+  c.flags &= ~(NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL);
   std::vector<std::vector<int>> seen;
   float best = -1.0f;
   uint32_t best_f = c.flags;
-  for (uint32_t combo = 0; combo < 8 && st == NADMM_OK; ++combo) {
+  for (uint32_t combo = 0; combo < 16 && st == NADMM_OK; ++combo) {
     nadmm_config t = c;
     for (int ax = 0; ax < 3; ++ax)
       t.flags |= (((combo >> ax) & 1u) ? 2u : 1u) << NADMM_FLAG_LANE_SHIFT(ax);
+    if (combo & 8u) t.flags |= NADMM_FLAG_FUSED_PENCIL;
     nadmm_context* h = nullptr;
     if ((st = create_single(&t, &h)) != NADMM_OK) break;
-    // skip combinations whose plans coincide with one already timed
+    // skip combinations whose kernels coincide with ones already timed
+    const int fused = (combo & 8u) ? (int)fused_pencil_supported(pencil_args(h)) : 0;
     std::vector<int> key = {h->px.radix[0], h->px.radix[1], h->py.radix[0], h->py.radix[1],
-                            h->pz.radix[0], h->pz.radix[1]};
+                            h->pz.radix[0], h->pz.radix[1], fused};
     bool dup = false;
     for (const auto& k : seen) dup = dup || k == key;
     if (!dup) {
@@ -1480,7 +1486,8 @@ nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t byt
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != NADMM_OK) return st;
-  *best_flags = (cfg->flags & ~NADMM_FLAG_LANE_MASK) | (best_f & NADMM_FLAG_LANE_MASK);
+  const uint32_t tuned = NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL;
+  *best_flags = (cfg->flags & ~tuned) | (best_f & tuned);
   if (best_ms) *best_ms = best;
   return NADMM_OK;
 }

@@ -84,6 +84,7 @@ struct PencilArgs {
   int order_n;
   float gamma;             // lambda / theta
   float scale;             // 1 / (nx ny nz)
+  int fused;               // 1: one fused y/z/y kernel (pencil_fused.cu) runs the pass
 };
 
 constexpr unsigned kStatusNonfinite = 1u;
@@ -112,6 +113,12 @@ void finish_pencil_args(PencilArgs& a);
 cudaError_t encode_pencil_map(PencilArgs& a);
 // Encode a.smap for a.spec (host only; needs finish_plane_args first).
 cudaError_t encode_plane_map(PlaneArgs& a);
+
+// Fused y/z/y pass (pencil_fused.cu): one cluster of two CTAs per (comp, kx).
+bool fused_pencil_supported(const PencilArgs& a);
+size_t fused_pencil_smem(const PencilArgs& a);
+cudaError_t configure_fused_pencil();
+cudaError_t launch_fused_pencil(const PencilArgs& a, cudaStream_t s);
 
 // Lane-FFT y/z passes (lane_passes.cu) for two-stage plans [R1, R2 in {8, 16}].
 bool lane_y_supported(const PencilArgs& a);

@@ -26,6 +26,7 @@ NADMM_ERR_NO_SAVED_FORWARD = 8
 NADMM_FLAG_NO_GRAPH = 1
 NADMM_FLAG_SAVE_FOR_BACKWARD = 2
 NADMM_FLAG_LANE_MASK = 0xFC
+NADMM_FLAG_FUSED_PENCIL = 0x100
 
 
 def NADMM_FLAG_LANE8(axis):
@@ -364,7 +365,7 @@ class Registration:
         if requires_grad:
             kw["flags"] = kw.get("flags", 0) | NADMM_FLAG_SAVE_FOR_BACKWARD
         if tune or autotune_cache:
-            kw["flags"] = (kw.get("flags", 0) & ~NADMM_FLAG_LANE_MASK) | autotune(
+            kw["flags"] = (kw.get("flags", 0) & ~(NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL)) | autotune(
                 self.dims, device, autotune_cache)
         self.cfg = make_config(self.dims, **kw)
         self.serial = 0  # forward passes run on this handle
@@ -438,7 +439,7 @@ def autotune(dims, device="cuda", cache=None, **kw):
     ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
     ptr = (ws.data_ptr() + 255) // 256 * 256
     flags, ms = nadmm_autotune(cfg, ptr, nbytes, torch.cuda.current_stream(dev))
-    plan = flags & NADMM_FLAG_LANE_MASK
+    plan = flags & (NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL)
     if cache:
         table[key] = {"plan_flags": plan, "ms_per_iteration": ms}
         with open(cache, "w") as fh:

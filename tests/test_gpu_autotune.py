@@ -51,7 +51,7 @@ def test_every_plan_solves_like_the_oracle(lib, combo):
 def test_autotune_and_cache(lib, tmp_path):
     cache = str(tmp_path / "plans.json")
     plan = lib.autotune(DIMS, DEV, cache)
-    assert plan & ~lib.NADMM_FLAG_LANE_MASK == 0
+    assert plan & ~(lib.NADMM_FLAG_LANE_MASK | lib.NADMM_FLAG_FUSED_PENCIL) == 0
     table = json.load(open(cache))
     (key, rec), = table.items()
     assert key.startswith("96,96,64|") and rec["plan_flags"] == plan and rec["ms_per_iteration"] > 0
@@ -77,3 +77,18 @@ def test_batched_with_tuned_plans(lib, tmp_path):
         ref = O.register(pairs[i]["fixed"], pairs[i]["moving"], lam=10.0, theta=0.1, n=2,
                          outer=2, inner=3)
         assert np.abs(us[i].cpu().numpy() - ref).max() <= 1e-3
+
+
+@pytest.mark.parametrize("dims", [(128, 128, 96), (96, 96, 64), (160, 160, 112), (32, 32, 24)])
+def test_fused_pencil_is_the_split_pass(lib, dims):
+    """The fused y/z/y cluster kernel computes exactly what the three split
+    kernels compute (same transforms, same order of operations), so the
+    registrations are bit-identical; grids it does not cover fall back."""
+    pair = synth.make_pair(dims, seed=11)
+    kw = dict(outer=2, inner=4)
+    a = lib.Registration(dims, device=DEV, **kw)
+    b = lib.Registration(dims, device=DEV, flags=lib.NADMM_FLAG_FUSED_PENCIL, **kw)
+    ua = a.register(dev(pair["fixed"]), dev(pair["moving"]))
+    ub = b.register(dev(pair["fixed"]), dev(pair["moving"]))
+    assert lib.nadmm_get_status(b.handle, torch.cuda.current_stream()) == lib.NADMM_OK
+    assert torch.equal(ua, ub)
