@@ -163,7 +163,7 @@ NADMM_HD void plane_scatter(const PlaneArgs& a, const float2* lines, const int* 
 }
 
 // Point-wise part of the iteration on staged tiles (fld) and lines.
-template <int IN, bool PREV, bool STEP>
+template <int IN, bool PREV, bool STEP, bool MEASURE = false>
 NADMM_HD void plane_pointwise(const PlaneArgs& a, float* fld, float2* lines, int z, int y0,
                               int tid, int nthr, float* racc = nullptr) {
   constexpr FieldMap F = field_map<IN, PREV, STEP>();
@@ -202,7 +202,7 @@ NADMM_HD void plane_pointwise(const PlaneArgs& a, float* fld, float2* lines, int
           bk1[comp] = 0.0f;
         }
         if (STEP && PREV) {
-          if (racc != nullptr) {  // ADMM residual: change of w and its size
+          if (MEASURE) {  // ADMM residual: change of w and its size
             const float dw = wk1[comp] - fld[(F.wp + comp) * tile + so];
             racc[0] += dw * dw;
             racc[1] += wk1[comp] * wk1[comp];
@@ -418,7 +418,7 @@ __device__ __forceinline__ const float* field_src(const PlaneArgs& a, int slot) 
 }
 #endif
 
-template <int IN, bool PREV, bool STEP>
+template <int IN, bool PREV, bool STEP, bool CONV>
 __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constant__ PlaneArgs a) {
 #if defined(__CUDA_ARCH__)
   constexpr FieldMap F = field_map<IN, PREV, STEP>();
@@ -441,9 +441,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constan
   // only the spectrum: their bulk loads are issued before waiting on it.
   // Every other variant reads data of the immediately preceding kernel (the
   // gradient kernel, or the caller's own work), so it loads after the wait.
-  constexpr bool kSpecIn = (IN == IN_SPEC);
-  // with thresholds the pass may have to stop before loading anything
-  const bool kEarlyLoads = kSpecIn && a.conv == nullptr;
+  // with thresholds (CONV) the pass may have to stop before loading anything
+  constexpr bool kEarlyLoads = (IN == IN_SPEC) && !CONV;
   const uint32_t tile_bytes = (uint32_t)(a.R * a.nx * sizeof(float));
   const size_t tile_off = ((size_t)z * a.ny + y0) * a.nx;
   const bool spec_tma = a.spec_tma != 0;
@@ -467,7 +466,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constan
   }
   pdl_wait();
   pdl_trigger();
-  if (a.conv != nullptr) {
+  if (CONV) {
     // threshold stop: a new inner loop (k = 0) clears the ADMM stop; later
     // passes of a stopped loop, and every pass after the outer stop, return
     if (a.conv[kConvOuter]) return;
@@ -521,10 +520,14 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constan
       return;
     }
   }
-  float racc[2] = {0.0f, 0.0f};
-  const bool measure = PREV && STEP && IN == IN_SPEC && a.conv != nullptr && a.admm_tol > 0.0f;
-  plane_pointwise<IN, PREV, STEP>(a, fld, lines, z, y0, tid, nthr, measure ? racc : nullptr);
-  if (measure) plane_residual(a, racc);
+  constexpr bool kMeasure = CONV && PREV && STEP && IN == IN_SPEC;  // ADMM residual of this pass
+  if (kMeasure && a.admm_tol > 0.0f) {
+    float racc[2] = {0.0f, 0.0f};
+    plane_pointwise<IN, PREV, STEP, kMeasure>(a, fld, lines, z, y0, tid, nthr, racc);
+    plane_residual(a, racc);
+  } else {
+    plane_pointwise<IN, PREV, STEP>(a, fld, lines, z, y0, tid, nthr);
+  }
   // tiles rewritten in shared memory by the point-wise step (w, b, y state)
   constexpr bool kTileStores = STEP && (F.wp >= 0 || F.y >= 0);
   if (kTileStores) fence_proxy_async();  // make them visible to the bulk copies
@@ -889,7 +892,8 @@ static cudaError_t set_smem_limit(K kernel, size_t smem) {
 
 template <int IN, bool PREV, bool STEP>
 static cudaError_t set_plane_attr(size_t smem) {
-  return set_smem_limit(k_plane<IN, PREV, STEP>, smem);
+  cudaError_t e = set_smem_limit(k_plane<IN, PREV, STEP, false>, smem);
+  return e != cudaSuccess ? e : set_smem_limit(k_plane<IN, PREV, STEP, true>, smem);
 }
 
 cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem) {
@@ -907,20 +911,28 @@ cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem) {
   return set_smem_limit(k_zpass, pencil_smem);
 }
 
-cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, cudaStream_t s) {
+template <bool CONV>
+static cudaError_t launch_plane_t(int in_mode, bool prev, bool step, const PlaneArgs& a,
+                                  cudaStream_t s) {
   dim3 grid((unsigned)((a.ny / a.R) * a.nz));
   dim3 block(kPlaneThreads);
   const size_t smem = plane_smem_bytes(a, in_mode, prev, step);
   switch (in_mode * 4 + (prev ? 2 : 0) + (step ? 1 : 0)) {
-    case IN_NONE * 4 + 1: return launch_pdl(k_plane<IN_NONE, false, true>, grid, block, smem, s, a);
-    case IN_SPEC * 4 + 1: return launch_pdl(k_plane<IN_SPEC, false, true>, grid, block, smem, s, a);
-    case IN_SPEC * 4 + 3: return launch_pdl(k_plane<IN_SPEC, true, true>, grid, block, smem, s, a);
-    case IN_SPEC * 4 + 0: return launch_pdl(k_plane<IN_SPEC, false, false>, grid, block, smem, s, a);
-    case IN_STATE * 4 + 1: return launch_pdl(k_plane<IN_STATE, false, true>, grid, block, smem, s, a);
-    case IN_STATE * 4 + 3: return launch_pdl(k_plane<IN_STATE, true, true>, grid, block, smem, s, a);
-    case IN_FIELD * 4 + 1: return launch_pdl(k_plane<IN_FIELD, false, true>, grid, block, smem, s, a);
+    case IN_NONE * 4 + 1: return launch_pdl(k_plane<IN_NONE, false, true, CONV>, grid, block, smem, s, a);
+    case IN_SPEC * 4 + 1: return launch_pdl(k_plane<IN_SPEC, false, true, CONV>, grid, block, smem, s, a);
+    case IN_SPEC * 4 + 3: return launch_pdl(k_plane<IN_SPEC, true, true, CONV>, grid, block, smem, s, a);
+    case IN_SPEC * 4 + 0: return launch_pdl(k_plane<IN_SPEC, false, false, CONV>, grid, block, smem, s, a);
+    case IN_STATE * 4 + 1: return launch_pdl(k_plane<IN_STATE, false, true, CONV>, grid, block, smem, s, a);
+    case IN_STATE * 4 + 3: return launch_pdl(k_plane<IN_STATE, true, true, CONV>, grid, block, smem, s, a);
+    case IN_FIELD * 4 + 1: return launch_pdl(k_plane<IN_FIELD, false, true, CONV>, grid, block, smem, s, a);
   }
   return cudaErrorInvalidValue;
+}
+
+// Fixed schedules use the kernels without the threshold code (CONV = false).
+cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, cudaStream_t s) {
+  return a.conv != nullptr ? launch_plane_t<true>(in_mode, prev, step, a, s)
+                           : launch_plane_t<false>(in_mode, prev, step, a, s);
 }
 
 cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s) {

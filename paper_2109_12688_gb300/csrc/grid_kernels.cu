@@ -116,6 +116,8 @@ __global__ void __launch_bounds__(kBX * kBY) k_bound_reduce(Dims d, const float*
   const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
   float mabs = 0.0f, mjac = 0.0f;
   if (x < d.nx && y < d.ny) {
+    // unrolled so that the loads of several z-slices are in flight together
+#pragma unroll 4
     for (int z = blockIdx.z; z < d.nz; z += gridDim.z) {
       const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
       const Nbr nb = neighbours(d, x, y, z, i);
