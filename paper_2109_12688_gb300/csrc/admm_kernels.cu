@@ -95,6 +95,7 @@ NADMM_HD constexpr FieldMap field_map() {
 }
 
 constexpr int kGatherItems = 4;   // spectrum values per thread held in flight per round
+enum PlaneExtra : int { kPlanePlain = 0, kPlaneConv = 1, kPlaneHist = 2 };
 constexpr int kPlaneThreads = 256;
 
 // Lines: line l = comp * (R/2) + r holds rows (y0 + r) [real part] and
@@ -163,7 +164,7 @@ NADMM_HD void plane_scatter(const PlaneArgs& a, const float2* lines, const int* 
 }
 
 // Point-wise part of the iteration on staged tiles (fld) and lines.
-template <int IN, bool PREV, bool STEP, bool MEASURE = false>
+template <int IN, bool PREV, bool STEP, bool MEASURE = false, bool HIST = false>
 NADMM_HD void plane_pointwise(const PlaneArgs& a, float* fld, float2* lines, int z, int y0,
                               int tid, int nthr, float* racc = nullptr) {
   constexpr FieldMap F = field_map<IN, PREV, STEP>();
@@ -238,6 +239,7 @@ NADMM_HD void plane_pointwise(const PlaneArgs& a, float* fld, float2* lines, int
           for (int comp = 0; comp < 3; ++comp) {
             Jv[comp] = fld[(F.J + comp) * tile + so];
             u[comp] = wh[comp] - bh[comp];
+            if (HIST) a.u_hist[comp * V + vox] = u[comp];  // reverse-mode recompute
           }
           v_step(a.data_term, a.theta, a.eps, Jv, fld[F.c * tile + so], u, v);
 #pragma unroll
@@ -418,7 +420,9 @@ __device__ __forceinline__ const float* field_src(const PlaneArgs& a, int slot) 
 }
 #endif
 
-template <int IN, bool PREV, bool STEP, bool CONV>
+// XTRA: kPlanePlain, kPlaneConv (threshold stopping), kPlaneHist (reverse-mode
+// recompute: u^k history, w^{k-1} to w_tile_out)
+template <int IN, bool PREV, bool STEP, int XTRA>
 __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constant__ PlaneArgs a) {
 #if defined(__CUDA_ARCH__)
   constexpr FieldMap F = field_map<IN, PREV, STEP>();
@@ -441,6 +445,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constan
   // only the spectrum: their bulk loads are issued before waiting on it.
   // Every other variant reads data of the immediately preceding kernel (the
   // gradient kernel, or the caller's own work), so it loads after the wait.
+  constexpr bool CONV = (XTRA == kPlaneConv);
   // with thresholds (CONV) the pass may have to stop before loading anything
   constexpr bool kEarlyLoads = (IN == IN_SPEC) && !CONV;
   const uint32_t tile_bytes = (uint32_t)(a.R * a.nx * sizeof(float));
@@ -525,6 +530,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constan
     float racc[2] = {0.0f, 0.0f};
     plane_pointwise<IN, PREV, STEP, kMeasure>(a, fld, lines, z, y0, tid, nthr, racc);
     plane_residual(a, racc);
+  } else if (XTRA == kPlaneHist) {
+    plane_pointwise<IN, PREV, STEP, false, STEP && IN != IN_FIELD>(a, fld, lines, z, y0, tid, nthr);
   } else {
     plane_pointwise<IN, PREV, STEP>(a, fld, lines, z, y0, tid, nthr);
   }
@@ -538,7 +545,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constan
       for (int comp = 0; comp < 3; ++comp) {
         const size_t g = comp * V + tile_off;
         if (F.wp >= 0) {
-          bulk_store(a.wp + g, fld + (size_t)(F.wp + comp) * a.R * a.nx, tile_bytes);
+          float* wdst = (XTRA == kPlaneHist && a.w_tile_out != nullptr) ? a.w_tile_out : a.wp;
+          bulk_store(wdst + g, fld + (size_t)(F.wp + comp) * a.R * a.nx, tile_bytes);
           bulk_store(a.bp + g, fld + (size_t)(F.bp + comp) * a.R * a.nx, tile_bytes);
         }
         if (F.y >= 0) bulk_store(a.y + g, fld + (size_t)(F.y + comp) * a.R * a.nx, tile_bytes);
@@ -892,8 +900,9 @@ static cudaError_t set_smem_limit(K kernel, size_t smem) {
 
 template <int IN, bool PREV, bool STEP>
 static cudaError_t set_plane_attr(size_t smem) {
-  cudaError_t e = set_smem_limit(k_plane<IN, PREV, STEP, false>, smem);
-  return e != cudaSuccess ? e : set_smem_limit(k_plane<IN, PREV, STEP, true>, smem);
+  cudaError_t e = set_smem_limit(k_plane<IN, PREV, STEP, kPlanePlain>, smem);
+  if (e == cudaSuccess) e = set_smem_limit(k_plane<IN, PREV, STEP, kPlaneConv>, smem);
+  return e != cudaSuccess ? e : set_smem_limit(k_plane<IN, PREV, STEP, kPlaneHist>, smem);
 }
 
 cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem) {
@@ -911,7 +920,7 @@ cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem) {
   return set_smem_limit(k_zpass, pencil_smem);
 }
 
-template <bool CONV>
+template <int CONV>
 static cudaError_t launch_plane_t(int in_mode, bool prev, bool step, const PlaneArgs& a,
                                   cudaStream_t s) {
   dim3 grid((unsigned)((a.ny / a.R) * a.nz));
@@ -929,10 +938,11 @@ static cudaError_t launch_plane_t(int in_mode, bool prev, bool step, const Plane
   return cudaErrorInvalidValue;
 }
 
-// Fixed schedules use the kernels without the threshold code (CONV = false).
+// Fixed schedules use the kernels without the threshold or history code.
 cudaError_t launch_plane(int in_mode, bool prev, bool step, const PlaneArgs& a, cudaStream_t s) {
-  return a.conv != nullptr ? launch_plane_t<true>(in_mode, prev, step, a, s)
-                           : launch_plane_t<false>(in_mode, prev, step, a, s);
+  if (a.conv != nullptr) return launch_plane_t<kPlaneConv>(in_mode, prev, step, a, s);
+  if (a.u_hist != nullptr) return launch_plane_t<kPlaneHist>(in_mode, prev, step, a, s);
+  return launch_plane_t<kPlanePlain>(in_mode, prev, step, a, s);
 }
 
 cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s) {

@@ -207,7 +207,8 @@ __global__ void __launch_bounds__(kBX * kBY)
 // ---------------------------------------------------------------- ADMM
 // One reverse step k of Eq. 5 (s = 2): from wbar^k, bbar^k (g = wbar -
 // bbar and its filtered Sg = S g) to the contributions to J, c, theta,
-// gamma = lambda/theta and to wbar, bbar of iterations k-1 and k-2.
+// gamma = lambda/theta and to wbar, bbar of iterations k-1 (added) and k-2
+// (the first contribution, stored).
 __global__ void __launch_bounds__(kBX * kBY) k_adj_step(AdjArgs a) {
   pdl_wait();
   pdl_trigger();
@@ -219,23 +220,18 @@ __global__ void __launch_bounds__(kBX * kBY) k_adj_step(AdjArgs a) {
   if (x < d.nx && y < d.ny) {
     const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
     const float beta = a.beta;
-    float Jv[3], u[3], yb[3], gk[3], wk[3];
+    float Jv[3], u[3], yb[3];
     float rho = a.c[i], dd = a.theta;
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
       const size_t j = comp * V + i;
-      const float w1 = a.w1 ? a.w1[j] : 0.0f, b1 = a.b1 ? a.b1[j] : 0.0f;
-      const float w2 = a.w2 ? a.w2[j] : 0.0f, b2 = a.b2 ? a.b2[j] : 0.0f;
-      const float wh = w1 + beta * (w1 - w2);
-      const float bh = b1 + beta * (b1 - b2);
-      u[comp] = wh - bh;
+      u[comp] = a.uk[j];
       Jv[comp] = a.J[j];
       rho += Jv[comp] * u[comp];
       dd += Jv[comp] * Jv[comp];
       const float sg = a.Sg[j];
-      gk[comp] = a.g_in[j] - sg;
+      p_gamma += (double)(a.g_in[j] - sg) * a.wk[j];
       yb[comp] = sg + a.Bk[j];
-      wk[comp] = a.wk[j];
     }
     const float jy = Jv[0] * yb[0] + Jv[1] * yb[1] + Jv[2] * yb[2];
     const float inv_d = 1.0f / dd;
@@ -246,7 +242,6 @@ __global__ void __launch_bounds__(kBX * kBY) k_adj_step(AdjArgs a) {
     for (int comp = 0; comp < 3; ++comp) {
       const size_t j = comp * V + i;
       a.gJ[j] += -(rho * inv_d) * yb[comp] - q * u[comp] + 2.0f * rho * q * inv_d * Jv[comp];
-      p_gamma += (double)gk[comp] * wk[comp];
       const float ub = yb[comp] - Jv[comp] * q;  // u_bar = w_hat_bar
       const float bb = yb[comp] - ub;             // b_hat_bar
       if (a.W1bar) {
@@ -256,12 +251,10 @@ __global__ void __launch_bounds__(kBX * kBY) k_adj_step(AdjArgs a) {
         a.B1bar[j] = nb;
         a.g_out[j] = nw - nb;
       }
-      if (a.W2bar && beta != 0.0f) {
-        a.W2bar[j] -= beta * ub;
-        a.B2bar[j] -= beta * bb;
+      if (a.W2bar) {  // slot of iteration k+1, dead: plain stores
+        a.W2bar[j] = -beta * ub;
+        a.B2bar[j] = -beta * bb;
       }
-      a.Wk_zero[j] = 0.0f;
-      a.Bk_zero[j] = 0.0f;
     }
     p_gamma *= -(double)a.inv_gamma;
   }

@@ -270,15 +270,19 @@ thread_local Profiler* g_prof = nullptr;
 
 // ADMM iterations k0 .. k0+steps-1 starting from `first` (plane pass that
 // starts iteration k0), then the final inverse transform into w_out/b_out.
-// With hist_w/hist_b (k0 = 0 only), w^k and b^k of every iteration are kept
-// in hist_w + k 3V and hist_b + k 3V (the last one is w_out/b_out).
+// With hist_w/hist_u (k0 = 0 only, the reverse-mode recompute), w^k and
+// u^k = w_hat^k - b_hat^k of every iteration go to hist_w + k 3V and
+// hist_u + k 3V: the plane passes write them directly (w^{k-1} by the tile
+// stores, u^k by the point-wise step), w^{K-1} comes from the final pass.
 cudaError_t enqueue_inner(nadmm_context* h, PlaneArgs first, int in_first, bool prev_first, int k0,
                           int steps, const float* J, const float* c, float* w_out, float* b_out,
-                          cudaStream_t s, float* hist_w = nullptr, float* hist_b = nullptr) {
-  const size_t F3 = 3 * h->V * sizeof(float);
+                          cudaStream_t s, float* hist_w = nullptr, float* hist_u = nullptr) {
+  const size_t F3 = 3 * h->V;
+  auto hw = [&](int k) { return hist_w + (size_t)k * F3; };
   first.J = J;
   first.c = c;
   first.beta = beta_for(h, k0);
+  if (hist_w) first.u_hist = hist_u;
   KLAUNCH(in_first == IN_NONE ? NADMM_KC_PLANE_FIRST : (prev_first ? NADMM_KC_PLANE : NADMM_KC_PLANE_K1),
           s, launch_plane(in_first, prev_first, true, first, s));
   PencilArgs pa = pencil_args(h);
@@ -288,11 +292,16 @@ cudaError_t enqueue_inner(nadmm_context* h, PlaneArgs first, int in_first, bool 
   for (int k = k0 + 1; k < k0 + steps; ++k) {
     KLAUNCH(NADMM_KC_PENCIL, s, launch_pencil(pa, s));
     a.beta = beta_for(h, k);
-    KLAUNCH(k >= 2 ? NADMM_KC_PLANE : NADMM_KC_PLANE_K1, s, launch_plane(IN_SPEC, k >= 2, true, a, s));
-    if (hist_w) {  // the pass wrote w^{k-1}, b^{k-1} into the state slots
-      TRY(cudaMemcpyAsync(hist_w + (size_t)(k - 1) * 3 * h->V, a.wp, F3, cudaMemcpyDeviceToDevice, s));
-      TRY(cudaMemcpyAsync(hist_b + (size_t)(k - 1) * 3 * h->V, a.bp, F3, cudaMemcpyDeviceToDevice, s));
+    if (hist_w) {  // w^{k-2} from the history, w^{k-1} into it, u^k recorded
+      a.u_hist = hist_u + (size_t)k * F3;
+      if (k == 1) {
+        a.wp = hw(0);  // the k = 1 pass writes w^0 with per-thread stores
+      } else {
+        a.wp = hw(k - 2);
+        a.w_tile_out = hw(k - 1);
+      }
     }
+    KLAUNCH(k >= 2 ? NADMM_KC_PLANE : NADMM_KC_PLANE_K1, s, launch_plane(IN_SPEC, k >= 2, true, a, s));
   }
   KLAUNCH(NADMM_KC_PENCIL, s, launch_pencil(pa, s));
   PlaneArgs fin = plane_args(h);
@@ -761,7 +770,7 @@ cudaError_t enqueue_backward(nadmm_context* h, const float* I0, const float* I1,
   float* c = h->at<float>(h->o_c);
   float* tape = h->tab<float>(h->o_tape);
   float* hw = h->at<float>(h->o_hist);
-  float* hb = hw + (size_t)K * 3 * V;
+  float* hu = hw + (size_t)K * 3 * V;
   float* adj = h->at<float>(h->o_adj);
   auto Wbar = [&](int k) { return adj + (size_t)(((k % 3) + 3) % 3) * 3 * V; };
   auto Bbar = [&](int k) { return adj + (size_t)(3 + ((k % 3) + 3) % 3) * 3 * V; };
@@ -785,8 +794,8 @@ cudaError_t enqueue_backward(nadmm_context* h, const float* I0, const float* I1,
     // forward recomputation of outer step o
     TRY(launch_warp(d, I1, u_o, I1w, red, s));  // also clears red[0..1]
     TRY(launch_grad_residual(d, I1w, I0, J, c, s));
-    TRY(enqueue_inner(h, plane_args(h), IN_NONE, false, 0, K, J, c, hist(hw, K - 1),
-                      hist(hb, K - 1), s, hw, hb));
+    TRY(enqueue_inner(h, plane_args(h), IN_NONE, false, 0, K, J, c, hist(hw, K - 1), nullptr, s,
+                      hw, hu));
     const float* w = hist(hw, K - 1);
     TRY(launch_bound_reduce(d, w, red, s));
     // compose and bound
@@ -815,16 +824,12 @@ cudaError_t enqueue_backward(nadmm_context* h, const float* I0, const float* I1,
       std::memset(&a, 0, sizeof(a));
       a.d = d;
       a.wk = hist(hw, k);
-      a.bk = hist(hb, k);
+      a.uk = hist(hu, k);
       if (k >= 1) {
-        a.w1 = hist(hw, k - 1);
-        a.b1 = hist(hb, k - 1);
         a.W1bar = Wbar(k - 1);
         a.B1bar = Bbar(k - 1);
       }
       if (k >= 2) {
-        a.w2 = hist(hw, k - 2);
-        a.b2 = hist(hb, k - 2);
         a.W2bar = Wbar(k - 2);
         a.B2bar = Bbar(k - 2);
       }
@@ -833,8 +838,6 @@ cudaError_t enqueue_backward(nadmm_context* h, const float* I0, const float* I1,
       a.Sg = Sg;
       a.g_in = g_in;
       a.Bk = Bbar(k);
-      a.Wk_zero = Wbar(k);
-      a.Bk_zero = Bbar(k);
       a.g_out = g;
       a.gJ = gJ;
       a.gc = gc;

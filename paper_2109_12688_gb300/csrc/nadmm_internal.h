@@ -41,6 +41,8 @@ struct PlaneArgs {
   const float2* twx;       // x-axis stage twiddles
   const int* posx;         // position of frequency kx after the forward x-DFT
   unsigned* status;        // device status word (bit 1: a bounded wait expired) or null
+  float* u_hist;           // reverse-mode recompute: receives u^k = w_hat^k - b_hat^k, or null
+  float* w_tile_out;       // reverse-mode recompute: where w^{k-1} goes instead of wp, or null
   unsigned* conv;          // threshold words (kConv*) or null when no threshold is set
   double* conv_acc;        // [0] sum (w^{k-1} - w^{k-2})^2, [1] sum (w^{k-1})^2
   float admm_tol;
@@ -200,17 +202,17 @@ cudaError_t launch_downsample2(Dims coarse, const float* fine, float* out, cudaS
 cudaError_t launch_upsample_u(Dims coarse, Dims fine, const float* uc, float* uf, cudaStream_t s);
 
 // ---------------------------------------------------------------- reverse mode
-// One reverse ADMM step k (grad_kernels.cu).  State of the forward sweep:
-// wk, bk = w^k, b^k; w1, b1 = w^{k-1}, b^{k-1} (null for k = 0); w2, b2 =
-// w^{k-2}, b^{k-2} (null for k < 2).  g_in = wbar^k - bbar^k, Sg = S g_in,
-// Bk = bbar^k.  Adds into W1bar/B1bar (k-1, null for k = 0) and W2bar/B2bar
-// (k-2), writes g_out = wbar^{k-1} - bbar^{k-1}, zeroes Wk_zero/Bk_zero,
-// accumulates gJ, gc and acc[1] (theta, data step), acc[2] (gamma).
+// One reverse ADMM step k (grad_kernels.cu).  From the forward sweep: wk =
+// w^k, uk = w_hat^k - b_hat^k.  g_in = wbar^k - bbar^k, Sg = S g_in, Bk =
+// bbar^k.  Adds into W1bar/B1bar (k-1, null for k = 0), stores the first
+// contribution to W2bar/B2bar (k-2, null for k < 2), writes g_out =
+// wbar^{k-1} - bbar^{k-1}, accumulates gJ, gc and acc[1] (theta, data
+// step), acc[2] (gamma).
 struct AdjArgs {
   Dims d;
-  const float *wk, *bk, *w1, *b1, *w2, *b2;
+  const float *wk, *uk;
   const float *J, *c, *Sg, *g_in, *Bk;
-  float *W1bar, *B1bar, *W2bar, *B2bar, *Wk_zero, *Bk_zero, *g_out;
+  float *W1bar, *B1bar, *W2bar, *B2bar, *g_out;
   float *gJ, *gc;
   double* acc;
   float beta;       // beta'_k (0 for k = 0)
