@@ -157,6 +157,8 @@ def parse_args():
     ap.add_argument("--orders", default="1,2,3",
                     help="regulariser orders registered per step (profiling runs use one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--no-cufft-compare", action="store_true",
+                    help="skip the timed-only cuFFT comparison of one ADMM iteration")
     ap.add_argument("--workload", choices=("registration", "batch64", "large", "grad", "pyramid",
                                            "batch16grad"),
                     default="registration",
@@ -207,6 +209,62 @@ def oracle_sample_ms(pair, n):
     s, _, _ = O.bound_scale(w, 0.5, 1.0)
     O.compose(u, s * w)
     return (time.perf_counter() - t0) * 1e3
+
+
+def cufft_iteration_us(dev, n, iters=50):
+    """Comparison arm, timed only (nothing is checked against it): one k >= 2
+    Nesterov-ADMM iteration at 128x128x96 with the 3D transforms done by
+    cuFFT (torch.fft R2C / C2R) and the point-wise work (Nesterov pre-form,
+    s = 2 data step, dual update) as PyTorch element-wise kernels, the whole
+    iteration captured in one CUDA graph.  Returns microseconds per iteration."""
+    import torch
+    nx, ny, nz = DIMS
+    g = torch.Generator(device="cpu").manual_seed(5)
+    def field(c):
+        return torch.randn((c, nz, ny, nx), generator=g).to(dev)
+    w, wp, b, bp, J, c = field(3), field(3), field(3), field(3), field(3), field(1)[0]
+    gamma = LAM / THETA
+    kz = torch.arange(nz, device=dev, dtype=torch.float32).view(nz, 1, 1)
+    ky = torch.arange(ny, device=dev, dtype=torch.float32).view(1, ny, 1)
+    kx = torch.arange(nx // 2 + 1, device=dev, dtype=torch.float32).view(1, 1, nx // 2 + 1)
+    K = (4 * torch.sin(torch.pi * kz / nz) ** 2 + 4 * torch.sin(torch.pi * ky / ny) ** 2
+         + 4 * torch.sin(torch.pi * kx / nx) ** 2)
+    S = 1.0 / (1.0 + gamma * K ** n)
+    denom = THETA + (J * J).sum(0)
+    beta = 0.3
+
+    def iteration():
+        wh = w + beta * (w - wp)
+        bh = b + beta * (b - bp)
+        u = wh - bh
+        rho = c + (J * u).sum(0)
+        y = u - (rho / denom) * J + bh
+        wn = torch.fft.irfftn(torch.fft.rfftn(y, dim=(1, 2, 3)) * S, s=(nz, ny, nx), dim=(1, 2, 3))
+        wp.copy_(w)
+        bp.copy_(b)
+        w.copy_(wn)
+        b.copy_(y - wn)
+
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            iteration()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        iteration()
+    for _ in range(5):
+        graph.replay()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(iters):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / iters
 
 
 ORACLE_SAMPLE = ("1 of the 10 outer steps (re-linearise + 10 ADMM iterations + bound + compose) "
@@ -606,6 +664,14 @@ def main():
         ms = oracle_sample_ms(pairs[ORDERS.index(2)] if 2 in ORDERS else pairs[0], 2) * OUTER
         cpu = {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE}
 
+    cufft = None
+    if world == 1 and not args.no_cufft_compare:
+        ours_us = (prof["plane"][0] / prof["plane"][1] + prof["pencil"][0] / prof["pencil"][1]) * 1e3
+        cufft = {"what": "one k >= 2 ADMM iteration (n = 2) with cuFFT R2C/C2R and PyTorch "
+                         "element-wise kernels in one CUDA graph; timed only",
+                 "cufft_us_per_iteration": cufft_iteration_us(dev, 2),
+                 "ours_us_per_iteration": ours_us}
+
     total_kernel_ms = sum(m for m, _ in prof.values())
     line = {
         "metric": METRIC, "value": ms_per_reg, "unit": "ms", "n_gpus": world,
@@ -629,6 +695,7 @@ def main():
                         "gbs": round(bpv[k] * V * n / (m / 1e3) / 1e9, 1) if m > 0 else None}
                     for k, (m, n) in prof.items()},
         "cpu_baseline": cpu,
+        "cufft_compare": cufft,
         "e2e": None if e2e_per_reg is None else {
             "value": e2e_per_reg, "unit": "ms",
             "h2d_bytes_per_step": len(ORDERS) * 2 * V * 4,

@@ -80,6 +80,10 @@ typedef enum nadmm_status {
 #define NADMM_FLAG_LANE8(axis)  (1u << NADMM_FLAG_LANE_SHIFT(axis))
 #define NADMM_FLAG_LANE16(axis) (2u << NADMM_FLAG_LANE_SHIFT(axis))
 #define NADMM_FLAG_LANE_MASK 0xFCu
+#define NADMM_FLAG_PIPELINED_PLANE 0x200u /* run the k >= 2 plane pass of a
+                                     fixed schedule as a persistent kernel (two
+                                     CTAs per SM, double-buffered copies)
+                                     instead of one CTA per tile; same results */
 #define NADMM_FLAG_FUSED_PENCIL 0x100u /* run the y/z FFT pass as one kernel (a
                                      2-CTA cluster per (component, kx) plane that
                                      swaps column halves through distributed

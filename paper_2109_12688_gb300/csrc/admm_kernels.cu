@@ -579,6 +579,178 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constan
 #endif
 }
 
+// ---------------------------------------------------------------- pipelined plane pass
+// The k >= 2 pass of a fixed schedule as persistent CTAs (two per SM): CTA
+// c handles tiles c, c + G, c + 2G, ... (G CTAs).  A second line buffer lets
+// the next tile's spectrum block load while this tile is transformed, and
+// the next tile's field tiles load as soon as this tile's outputs have been
+// read out of the field buffer by their bulk stores.  The last thread of the
+// CTA (in a warp the lane FFTs leave idle) issues and retires the copies.
+// Same arithmetic as k_plane<IN_SPEC, true, true, kPlanePlain>.
+constexpr int kPipeCtasPerSm = 2;
+
+struct PipeSmem {
+  size_t fld, lines0, lines1, total;
+};
+
+NADMM_HD PipeSmem pipe_layout(const PlaneArgs& a, int nfields) {
+  PipeSmem L;
+  L.fld = 128;  // three mbarriers before it
+  size_t o = L.fld + (size_t)nfields * a.R * a.nx * sizeof(float);
+  const size_t lines = (((size_t)3 * (a.R / 2) * a.pitch * sizeof(float2)) + 127) & ~(size_t)127;
+  L.lines0 = (o + 127) & ~(size_t)127;
+  L.lines1 = L.lines0 + lines;
+  L.total = L.lines1 + lines;
+  return L;
+}
+
+__global__ void __launch_bounds__(kPlaneThreads, kPipeCtasPerSm)
+    k_plane_pipe(const __grid_constant__ PlaneArgs a) {
+#if defined(__CUDA_ARCH__)
+  constexpr int IN = IN_SPEC;
+  constexpr bool PREV = true, STEP = true;
+  constexpr FieldMap F = field_map<IN, PREV, STEP>();
+  extern __shared__ __align__(128) unsigned char smem[];
+  const PipeSmem L = pipe_layout(a, F.n);
+  uint64_t* fbar = reinterpret_cast<uint64_t*>(smem);  // field tiles
+  uint64_t* sbar = fbar + 1;                            // spectrum blocks, per line buffer
+  float* fld = reinterpret_cast<float*>(smem + L.fld);
+  float2* const lbuf[2] = {reinterpret_cast<float2*>(smem + L.lines0),
+                           reinterpret_cast<float2*>(smem + L.lines1)};
+  const float2* __restrict__ tw = a.twx;
+  const int* __restrict__ pos = a.posx;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int X = nthr - 1;  // copy thread
+  const int nlines = 3 * (a.R / 2);
+  const int tiles_y = a.ny / a.R;
+  const int ntiles = tiles_y * a.nz;
+  const int G = gridDim.x;
+  const int mine = (ntiles - (int)blockIdx.x + G - 1) / G;  // tiles of this CTA
+  const uint32_t tile_bytes = (uint32_t)(a.R * a.nx * sizeof(float));
+  const uint32_t spec_bytes = (uint32_t)(3 * a.nkx * a.R * sizeof(float2));
+  const size_t V = (size_t)a.nx * a.ny * a.nz;
+  auto tile_zy = [&](int i, int& z, int& y0) {
+    const int t = (int)blockIdx.x + i * G;
+    z = (int)fdiv((uint32_t)t, a.tiles_div);
+    y0 = (t - z * tiles_y) * a.R;
+  };
+  auto load_fields = [&](int i) {  // thread X
+    int z, y0;
+    tile_zy(i, z, y0);
+    const size_t off = ((size_t)z * a.ny + y0) * a.nx;
+    mbar_expect_tx(fbar, tile_bytes * F.n);
+    for (int sl = 0; sl < F.n; ++sl)
+      bulk_load(fld + (size_t)sl * a.R * a.nx, field_src<IN, PREV, STEP>(a, sl) + off, tile_bytes,
+                fbar);
+  };
+  auto load_spec = [&](int i) {  // thread X
+    int z, y0;
+    tile_zy(i, z, y0);
+    mbar_expect_tx(sbar + (i & 1), spec_bytes);
+    tensor_load_3d(lbuf[i & 1], &a.smap, y0, z, 0, sbar + (i & 1));
+  };
+  if (tid == 0) {
+    mbar_init(fbar, 1);
+    mbar_init(sbar, 1);
+    mbar_init(sbar + 1, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  int f_issued = 0, s_issued[2] = {0, 0};  // loads issued per barrier (thread X's view)
+  if (tid == X && mine > 0) {  // fields of the first tile: written four kernels back
+    load_fields(0);
+    f_issued = 1;
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (tid == X && mine > 0) {
+    load_spec(0);
+    s_issued[0] = 1;
+  }
+  bool failed = false;
+  int i = 0;
+  for (; i < mine; ++i) {
+    const int b = i & 1;
+    float2* lines = lbuf[b];
+    int z, y0;
+    tile_zy(i, z, y0);
+    const size_t tile_off = ((size_t)z * a.ny + y0) * a.nx;
+    if (!__syncthreads_and(mbar_wait_bounded(sbar + b, (uint32_t)((i >> 1) & 1)))) {
+      failed = true;
+      break;
+    }
+    plane_unpack(a, lines, pos, tid, nthr);
+    __syncthreads();
+    if (tid == X && i + 1 < mine) {
+      // the other line buffer is free once the previous tile's spectrum
+      // store has read it: prefetch the next tile's block there
+      bulk_wait_read();
+      load_spec(i + 1);
+      s_issued[(i + 1) & 1] += 1;
+    }
+    if (a.xr2 != 0) {
+      plane_lane_fft<true>(a, lines, tw, nlines, tid);
+    } else {
+      for (int s = a.px.nst - 1; s >= 0; --s) {
+        fft_stage<true>(a.px, s, lines, nlines, a.lines_div, 1, a.pitch, tw, tid, nthr);
+        __syncthreads();
+      }
+    }
+    if (!__syncthreads_and(mbar_wait_bounded(fbar, (uint32_t)(i & 1)))) {
+      failed = true;
+      break;
+    }
+    plane_pointwise<IN, PREV, STEP>(a, fld, lines, z, y0, tid, nthr);
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == X) {
+      for (int comp = 0; comp < 3; ++comp) {
+        const size_t g = comp * V + tile_off;
+        bulk_store(a.wp + g, fld + (size_t)(F.wp + comp) * a.R * a.nx, tile_bytes);
+        bulk_store(a.bp + g, fld + (size_t)(F.bp + comp) * a.R * a.nx, tile_bytes);
+        bulk_store(a.y + g, fld + (size_t)(F.y + comp) * a.R * a.nx, tile_bytes);
+      }
+      bulk_commit();
+      if (i + 1 < mine) {  // the field buffer is free once the stores have read it
+        bulk_wait_read();
+        load_fields(i + 1);
+        f_issued += 1;
+      }
+    }
+    if (a.xr2 != 0) {
+      plane_lane_fft<false>(a, lines, tw, nlines, tid);
+      __syncthreads();
+    } else {
+      for (int s = 0; s < a.px.nst; ++s) {
+        fft_stage<false>(a.px, s, lines, nlines, a.lines_div, 1, a.pitch, tw, tid, nthr);
+        __syncthreads();
+      }
+    }
+    plane_pack(a, lines, pos, tid, nthr);
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == X) {
+      tensor_store_3d(&a.smap, y0, z, 0, lines);
+      bulk_commit();
+    }
+  }
+  if (tid == X) {
+    if (failed) {
+      if (a.status != nullptr) atomicOr(a.status, kStatusTimeout);
+      // let every copy still in flight land before the CTA leaves: the
+      // barrier phases not yet waited for, from the issued counts
+      const int f_done = i;                       // tiles whose fields were consumed
+      if (f_issued > f_done) mbar_wait_bounded(fbar, (uint32_t)(f_done & 1));
+      for (int bb = 0; bb < 2; ++bb) {
+        const int s_done = (i + 1 - bb) / 2;      // uses of buffer bb consumed before tile i
+        if (s_issued[bb] > s_done) mbar_wait_bounded(sbar + bb, (uint32_t)(s_done & 1));
+      }
+    }
+    bulk_wait_read();  // shared memory must stay until the last stores have read it
+  }
+#endif
+}
+
 // ---------------------------------------------------------------- y / z passes
 // The pencil work of Eq. 6's 3D DFT on the half spectrum [3][nkx][nz][ny]:
 //   y-pass  (forward, then inverse after the z-pass): y-DFT of `yrows`
@@ -785,6 +957,7 @@ void finish_plane_args(PlaneArgs& a) {
   // all (comp, kx) (3 nkx <= 256, i.e. nx <= 168) and each thread holds at
   // most kGatherItems (comp, kx, row) items in the in-place (un)pack.
   a.spec_tma = (3 * a.nkx <= 256 && 3 * a.nkx * (a.R / 2) <= kGatherItems * kPlaneThreads) ? 1 : 0;
+  a.pipe = 0;  // opt-in: the persistent pass measured slower than one CTA per tile
   a.nx_div = make_fastdiv((uint32_t)a.nx);
   a.lines_div = make_fastdiv((uint32_t)(3 * (a.R / 2)));
   a.half_div = make_fastdiv((uint32_t)(a.R / 2));
@@ -875,7 +1048,10 @@ size_t plane_smem_bytes(const PlaneArgs& a, int in_mode, bool prev, bool step) {
   return plane_layout(a, field_count(in_mode, prev, step)).total;
 }
 
-size_t plane_smem_max(const PlaneArgs& a) { return plane_layout(a, 16).total; }
+size_t plane_smem_max(const PlaneArgs& a) {
+  const size_t p = a.spec_tma ? pipe_layout(a, 16).total : 0, q = plane_layout(a, 16).total;
+  return p > q ? p : q;
+}
 
 size_t pencil_smem_bytes(const PencilArgs& a) {
   const size_t y = ypass_smem(a), z = zpass_smem(a);
@@ -914,6 +1090,7 @@ cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem) {
   if ((e = set_plane_attr<IN_STATE, false, true>(plane_smem)) != cudaSuccess) return e;
   if ((e = set_plane_attr<IN_STATE, true, true>(plane_smem)) != cudaSuccess) return e;
   if ((e = set_plane_attr<IN_FIELD, false, true>(plane_smem)) != cudaSuccess) return e;
+  if ((e = set_smem_limit(k_plane_pipe, plane_smem)) != cudaSuccess) return e;
   if ((e = set_smem_limit(k_ypass<false>, pencil_smem)) != cudaSuccess) return e;
   if ((e = set_smem_limit(k_ypass<true>, pencil_smem)) != cudaSuccess) return e;
   if ((e = configure_fused_pencil()) != cudaSuccess) return e;
@@ -929,7 +1106,18 @@ static cudaError_t launch_plane_t(int in_mode, bool prev, bool step, const Plane
   switch (in_mode * 4 + (prev ? 2 : 0) + (step ? 1 : 0)) {
     case IN_NONE * 4 + 1: return launch_pdl(k_plane<IN_NONE, false, true, CONV>, grid, block, smem, s, a);
     case IN_SPEC * 4 + 1: return launch_pdl(k_plane<IN_SPEC, false, true, CONV>, grid, block, smem, s, a);
-    case IN_SPEC * 4 + 3: return launch_pdl(k_plane<IN_SPEC, true, true, CONV>, grid, block, smem, s, a);
+    case IN_SPEC * 4 + 3:
+      if (CONV == kPlanePlain && a.pipe && a.spec_tma) {  // persistent, pipelined
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const int ntiles = (a.ny / a.R) * a.nz;
+        const int G = ntiles < kPipeCtasPerSm * sms ? ntiles : kPipeCtasPerSm * sms;
+        return launch_pdl(k_plane_pipe, dim3((unsigned)G), block,
+                          pipe_layout(a, field_map<IN_SPEC, true, true>().n).total, s, a);
+      }
+      return launch_pdl(k_plane<IN_SPEC, true, true, CONV>, grid, block, smem, s, a);
     case IN_SPEC * 4 + 0: return launch_pdl(k_plane<IN_SPEC, false, false, CONV>, grid, block, smem, s, a);
     case IN_STATE * 4 + 1: return launch_pdl(k_plane<IN_STATE, false, true, CONV>, grid, block, smem, s, a);
     case IN_STATE * 4 + 3: return launch_pdl(k_plane<IN_STATE, true, true, CONV>, grid, block, smem, s, a);

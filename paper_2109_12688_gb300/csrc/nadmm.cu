@@ -133,7 +133,7 @@ nadmm_status validate(const nadmm_config* c) {
   if (!(c->bound_kappa > 0.0f) || !(c->bound_delta > 0.0f))
     return fail(NADMM_ERR_INVALID_ARG, "bound_kappa and bound_delta must be > 0 (INFINITY disables)");
   if (c->flags & ~(NADMM_FLAG_NO_GRAPH | NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK |
-                   NADMM_FLAG_FUSED_PENCIL))
+                   NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_PIPELINED_PLANE))
     return fail(NADMM_ERR_INVALID_ARG, "unknown flag bits");
   for (int ax = 0; ax < 3; ++ax)
     if (((c->flags >> NADMM_FLAG_LANE_SHIFT(ax)) & 3u) == 3u)
@@ -191,6 +191,7 @@ PlaneArgs plane_args(const nadmm_context* h) {
   finish_plane_args(a);
   a.smap = h->smap;
   if (!h->smap_ok) a.spec_tma = 0;
+  a.pipe = (h->cfg.flags & NADMM_FLAG_PIPELINED_PLANE) ? 1 : 0;
   if (thresholds(h)) {
     a.conv = h->tab<unsigned>(h->o_conv);
     a.conv_acc = h->tab<double>(h->o_convacc);

@@ -57,6 +57,8 @@ struct PlaneArgs {
   int pitch;               // shared-memory line pitch (>= nx)
   int xr1, xr2;            // lane-FFT plan of the x axis (xr2 = 0: shared-memory stages)
   int xlog2r2;             // log2(xr2), or -1 (line positions not swizzled)
+  int pipe;                // 1: the k >= 2 pass runs as the pipelined persistent kernel
+                           //    (needs spec_tma; opt-in)
   int spec_tma;            // 1: the CTA's spectrum block moves by tensor copies through
                            // the line buffer (needs smap); 0: per-thread loads/stores
   float beta;              // beta_{k-1}

@@ -27,6 +27,7 @@ NADMM_FLAG_NO_GRAPH = 1
 NADMM_FLAG_SAVE_FOR_BACKWARD = 2
 NADMM_FLAG_LANE_MASK = 0xFC
 NADMM_FLAG_FUSED_PENCIL = 0x100
+NADMM_FLAG_PIPELINED_PLANE = 0x200
 
 
 def NADMM_FLAG_LANE8(axis):
