@@ -54,8 +54,11 @@ extern "C" {
 typedef enum nadmm_status {
   NADMM_OK = 0,
   NADMM_ERR_INVALID_ARG = 1,      /* null pointer, bad parameter value         */
-  NADMM_ERR_UNSUPPORTED_SIZE = 2, /* dim < 4, nx % 4, ny % 2, prime factor not
-                                     in {2,3,5,7}, or plane beyond shared mem  */
+  NADMM_ERR_UNSUPPORTED_SIZE = 2, /* dim < 4, nx % 4, ny % 2, a prime factor
+                                     > 509 or more than 5 factors > 7, nz > 256,
+                                     or plane beyond shared memory.  Factors
+                                     2, 3, 5, 7 use codelet FFT stages, other
+                                     primes a direct-sum stage (O(p) per value) */
   NADMM_ERR_ALIGNMENT = 3,        /* device pointer not 16-byte aligned        */
   NADMM_ERR_NO_WORKSPACE = 4,     /* workspace missing or too small            */
   NADMM_ERR_CUDA = 5,             /* a CUDA runtime call failed                */

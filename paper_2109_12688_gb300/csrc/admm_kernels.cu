@@ -825,6 +825,24 @@ NADMM_HD void zpass_transform(const PencilArgs& a, float2* tile, const float2* t
 #else
 #define NADMM_PSYNC() (void)sync_between
 #endif
+  if (a.pz.root_off[a.pz.nst - 1] >= 0) {
+    // last stage generic (nz a product of primes > 7): transform, filter and
+    // transform back as separate steps
+    for (int s = 0; s < a.pz.nst; ++s) {
+      fft_stage<false>(a.pz, s, tile, a.zcols, a.zcols_div, a.zcols, 1, tw, tid, nthr);
+      NADMM_PSYNC();
+    }
+    for (int g = tid; g < a.nz * a.zcols; g += nthr) {
+      const int zpos = (int)fdiv((uint32_t)g, a.zcols_div), line = g - zpos * a.zcols;
+      tile[g] = cscale(tile[g], filt(line, zpos));
+    }
+    NADMM_PSYNC();
+    for (int s = a.pz.nst - 1; s >= 0; --s) {
+      fft_stage<true>(a.pz, s, tile, a.zcols, a.zcols_div, a.zcols, 1, tw, tid, nthr);
+      NADMM_PSYNC();
+    }
+    return;
+  }
   for (int s = 0; s + 1 < a.pz.nst; ++s) {
     fft_stage<false>(a.pz, s, tile, a.zcols, a.zcols_div, a.zcols, 1, tw, tid, nthr);
     NADMM_PSYNC();

@@ -16,6 +16,12 @@
 // multiplies output k by w_{L_i}^{n1 k} and stores it at n1 + m_i k.  The
 // frequency stored at position p = sum_i d_i m_i is k = sum_i d_i r_1..r_{i-1}.
 //
+// A prime factor r > 7 of N (sizes with no codelet radix) gets a generic
+// stage: the same stage with the r-point DFT evaluated directly as a sum of r
+// terms with the roots w_r^q (q < r) from the axis table.  It costs O(r) per
+// element instead of O(log r), needs no padding (unlike a chirp-z transform
+// of length >= 2r - 1), and the plan puts such stages first.
+//
 // Every function here is __host__ __device__ and takes (tid, nthr) so that a
 // block-level loop is plain C++; the kernels separate phases with barriers.
 #pragma once
@@ -31,6 +37,10 @@
 namespace nadmm {
 
 constexpr int kMaxStages = 5;
+// Largest prime factor an axis may have (a generic stage of radix r keeps at
+// most kPrimeItems outputs per thread per round; r <= 4 x 128 threads).
+constexpr int kMaxPrime = 509;
+constexpr int kPrimeItems = 4;
 
 // Division by a runtime-invariant divisor d >= 1 for 0 <= n < 2^31, by the
 // round-up multiplier method (Granlund & Montgomery, "Division by invariant
@@ -92,6 +102,8 @@ struct AxisPlan {
   int L[kMaxStages];         // block length at stage i
   int m[kMaxStages];         // L_i / r_i
   int tw_off[kMaxStages];    // offset of stage i's twiddles in the axis table
+  int root_off[kMaxStages];  // generic prime stage: offset of its roots w_r^q, q < r,
+                             // in the axis table; -1 for codelet stages
   int tw_count;              // entries in the axis table
   FastDiv mdiv[kMaxStages];  // division by m_i
 };
@@ -440,10 +452,87 @@ NADMM_HD void stage_loop(float2* buf, int nlines, const FastDiv& ldiv, int es, i
   }
 }
 
+// Output k of the r-point butterfly at `base` (elements base[j * step]):
+// forward  X_k = (sum_j x_j w_r^{jk}) w_L^{n1 k};
+// inverse  X_k = sum_j (x_j conj(w_L^{n1 j})) conj(w_r)^{jk}.
+template <bool INV>
+NADMM_HD float2 prime_output(const float2* base, int step, int r, int k, const float2* tw,
+                             const float2* root, int m, int n1) {
+  float2 acc = make_float2(0.0f, 0.0f);
+  int e = 0;  // j k mod r
+  for (int j = 0; j < r; ++j) {
+    float2 xj = base[j * step];
+    if (INV && j > 0 && m > 1) xj = cmulc(xj, tw[(j - 1) * m + n1]);
+    acc = cadd(acc, INV ? cmulc(xj, root[e]) : cmul(xj, root[e]));
+    e += k;
+    if (e >= r) e -= r;
+  }
+  if (!INV && k > 0 && m > 1) acc = cmul(acc, tw[(k - 1) * m + n1]);
+  return acc;
+}
+
+// Generic stage of prime radix r (every thread of the block calls it).  The
+// butterflies are taken in rounds of whole butterflies, at most kPrimeItems
+// outputs per thread: each round computes its outputs into registers, waits
+// for the block, then writes them over the round's own inputs (the rounds'
+// butterflies are disjoint, so no later round reads what a round writes).
+template <bool INV>
+NADMM_HD void prime_stage(const AxisPlan& p, int s, float2* buf, int nlines, int es, int ls,
+                          const float2* tw_axis, int tid, int nthr) {
+  const int r = p.radix[s], L = p.L[s], m = p.m[s], nblk = p.n / L;
+  const float2* tw = tw_axis + p.tw_off[s];
+  const float2* root = tw_axis + p.root_off[s];
+  const int step = m * es;
+  const int nbf = nlines * nblk * m;
+#if defined(__CUDA_ARCH__)
+  int per_round = (nthr * kPrimeItems) / r;
+  if (per_round < 1) per_round = 1;  // excluded by the plan (r <= kMaxPrime)
+  const int rounds = (nbf + per_round - 1) / per_round;
+  for (int rd = 0; rd < rounds; ++rd) {
+    float2 out[kPrimeItems];
+    int dst[kPrimeItems];
+#pragma unroll
+    for (int it = 0; it < kPrimeItems; ++it) {
+      dst[it] = -1;
+      const int g = tid + it * nthr;  // (butterfly in round, output k)
+      const int b = g / r, k = g - b * r;
+      const int bf = rd * per_round + b;
+      if (b < per_round && bf < nbf) {
+        const int q = bf / nlines, line = bf - q * nlines;
+        const int blk = q / m, n1 = q - blk * m;
+        const int off = line * ls + (blk * L + n1) * es;
+        out[it] = prime_output<INV>(buf + off, step, r, k, tw, root, m, n1);
+        dst[it] = off + k * step;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kPrimeItems; ++it)
+      if (dst[it] >= 0) buf[dst[it]] = out[it];
+    __syncthreads();
+  }
+#else
+  (void)tid;
+  (void)nthr;
+  float2 out[kMaxPrime];
+  for (int bf = 0; bf < nbf; ++bf) {
+    const int q = bf / nlines, line = bf - q * nlines;
+    const int blk = q / m, n1 = q - blk * m;
+    float2* base = buf + line * ls + (blk * L + n1) * es;
+    for (int k = 0; k < r; ++k) out[k] = prime_output<INV>(base, step, r, k, tw, root, m, n1);
+    for (int k = 0; k < r; ++k) base[k * step] = out[k];
+  }
+#endif
+}
+
 // Stage s of plan p (forward or inverse); tw_axis is the axis table.
 template <bool INV>
 NADMM_HD void fft_stage(const AxisPlan& p, int s, float2* buf, int nlines, const FastDiv& ldiv,
                         int es, int ls, const float2* tw_axis, int tid, int nthr) {
+  if (p.root_off[s] >= 0) {
+    prime_stage<INV>(p, s, buf, nlines, es, ls, tw_axis, tid, nthr);
+    return;
+  }
   const int L = p.L[s], m = p.m[s], nblk = p.n / L;
   const float2* tw = tw_axis + p.tw_off[s];
   const FastDiv& md = p.mdiv[s];

@@ -93,10 +93,12 @@ struct nadmm_context {
 
 namespace {
 
+// Prime factors above 7 get generic FFT stages: at most kMaxStages of them,
+// each at most kMaxPrime.
 bool good_factors(int n) {
-  for (int q : {2, 3, 5, 7})
-    while (n % q == 0) n /= q;
-  return n == 1;
+  int big[kMaxStages], smooth = 1;
+  const int cnt = generic_primes(n, big, kMaxStages, smooth);
+  return cnt == 0 || (cnt <= kMaxStages && big[cnt - 1] <= kMaxPrime);
 }
 
 void invalidate_graph(nadmm_context* h) {
@@ -114,7 +116,7 @@ nadmm_status validate(const nadmm_config* c) {
   if (c->nx % 4 != 0) return fail(NADMM_ERR_UNSUPPORTED_SIZE, "nx must be a multiple of 4");
   if (c->ny % 2 != 0) return fail(NADMM_ERR_UNSUPPORTED_SIZE, "ny must be even");
   if (!good_factors(c->nx) || !good_factors(c->ny) || !good_factors(c->nz))
-    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "dimensions must factor into 2, 3, 5, 7");
+    return fail(NADMM_ERR_UNSUPPORTED_SIZE, "every prime factor of a dimension must be <= 509");
   if (c->order_n < 1 || c->order_n > 8) return fail(NADMM_ERR_INVALID_ARG, "order_n must be in 1..8");
   if (!(c->lambda >= 0.0f) || !std::isfinite(c->lambda))
     return fail(NADMM_ERR_INVALID_ARG, "lambda must be finite and >= 0");

@@ -54,16 +54,50 @@ inline bool best_factors(int n, int depth, int* out, int& best_len, int* cur, in
   return found;
 }
 
+// Prime factors of n above 7 (the ones without a codelet), ascending, with
+// multiplicity; the rest of n (only factors 2, 3, 5, 7) is returned in smooth.
+inline int generic_primes(int n, int* out, int cap, int& smooth) {
+  int cnt = 0;
+  smooth = 1;
+  for (int q : {2, 3, 5, 7})
+    while (n % q == 0) {
+      n /= q;
+      smooth *= q;
+    }
+  for (int q = 11; n > 1 && q <= n; q += 2)
+    while (n % q == 0) {
+      n /= q;
+      if (cnt < cap) out[cnt] = q;
+      ++cnt;
+    }
+  return cnt;
+}
+
 inline bool factor_axis(int n, AxisPlan& p, bool lane_plan = false, int lane_first = 8) {
   if (n < 2) return false;
   int out[kMaxStages], cur[kMaxStages], best = kMaxStages + 1;
-  const int r2 = lane_plan ? lane_split(n, lane_first) : 0;
-  if (r2) {
-    out[0] = n / r2;
-    out[1] = r2;
-    best = 2;
-  } else if (!best_factors(n, kMaxStages, out, best, cur, 0)) {
-    return false;
+  int smooth = 1;
+  const int ng = generic_primes(n, out, kMaxStages, smooth);
+  if (ng > 0) {
+    // generic prime stages first, then the fewest codelet stages for the rest
+    if (ng > kMaxStages || out[ng - 1] > kMaxPrime) return false;
+    if (smooth == 1) {
+      best = ng;
+    } else {
+      int rest[kMaxStages], rbest = kMaxStages + 1;
+      if (!best_factors(smooth, kMaxStages - ng, rest, rbest, cur, 0)) return false;
+      for (int i = 0; i < rbest; ++i) out[ng + i] = rest[i];
+      best = ng + rbest;
+    }
+  } else {
+    const int r2 = lane_plan ? lane_split(n, lane_first) : 0;
+    if (r2) {
+      out[0] = n / r2;
+      out[1] = r2;
+      best = 2;
+    } else if (!best_factors(n, kMaxStages, out, best, cur, 0)) {
+      return false;
+    }
   }
   p.n = n;
   p.nst = best;
@@ -81,6 +115,11 @@ inline bool factor_axis(int n, AxisPlan& p, bool lane_plan = false, int lane_fir
     }
     p.mdiv[i] = make_fastdiv((uint32_t)p.m[i]);
   }
+  // the roots of the generic stages follow the stage twiddles
+  for (int i = 0; i < kMaxStages; ++i) {
+    p.root_off[i] = (i < ng) ? off : -1;
+    if (i < ng) off += out[i];
+  }
   p.tw_count = off > 0 ? off : 1;
   return true;
 }
@@ -97,6 +136,13 @@ inline std::vector<float2> axis_twiddles(const AxisPlan& p) {
         double a = -two_pi * (double)e / (double)p.L[i];
         tw.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
       }
+  }
+  for (int i = 0; i < p.nst; ++i) {
+    if (p.root_off[i] < 0) continue;
+    for (int q = 0; q < p.radix[i]; ++q) {
+      double a = -two_pi * (double)q / (double)p.radix[i];
+      tw.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+    }
   }
   if (tw.empty()) tw.push_back(make_float2(1.f, 0.f));
   return tw;

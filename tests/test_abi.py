@@ -58,14 +58,25 @@ def test_create_and_workspace_size(lib, dims):
 
 
 @pytest.mark.parametrize("dims,why", [((3, 8, 8), "dimension"), ((10, 8, 8), "multiple of 4"),
-                                      ((8, 7, 8), "even"), ((44, 8, 8), "factor"),
-                                      ((8, 8, 13), "factor"), ((512, 64, 64), "shared"),
+                                      ((8, 7, 8), "even"), ((8, 2 * 521, 8), "prime factor"),
+                                      ((4 * 521, 8, 8), "prime factor"), ((512, 64, 64), "shared"),
                                       ((64, 64, 320), "nz must be")])
 def test_unsupported_sizes_are_rejected(lib, dims, why):
     with pytest.raises(lib.NadmmError) as e:
         lib.nadmm_create(lib.make_config(dims))
     assert e.value.status == lib.NADMM_ERR_UNSUPPORTED_SIZE
     assert why in str(e.value)
+
+
+@pytest.mark.parametrize("dims", [(44, 8, 8), (8, 8, 13), (44, 26, 23), (88, 52, 34),
+                                  (100, 98, 97), (4, 4, 251), (20, 22, 11 * 13)])
+def test_sizes_with_prime_factors_above_7_are_planned(lib, dims):
+    """Prime factors above 7 get direct-sum FFT stages, so these grids plan
+    and size their workspace like smooth ones (host only)."""
+    h = lib.nadmm_create(lib.make_config(dims))
+    nx, ny, nz = dims
+    assert lib.nadmm_workspace_size(h) >= 3 * (nx // 2 + 1) * ny * nz * 8
+    lib.nadmm_destroy(h)
 
 
 @pytest.mark.parametrize("field,value", [("order_n", 0), ("order_n", 9), ("theta", 0.0),
@@ -144,7 +155,7 @@ def test_batched_create_layout(lib):
 
 
 def test_batched_create_rejects_bad_pair(lib):
-    dims = [(32, 32, 24), (44, 8, 8)]
+    dims = [(32, 32, 24), (10, 8, 8)]
     with pytest.raises(lib.NadmmError) as e:
         lib.nadmm_create_batched(lib.make_config(dims[0]), dims)
     assert e.value.status == lib.NADMM_ERR_UNSUPPORTED_SIZE
