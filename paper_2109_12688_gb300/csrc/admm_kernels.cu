@@ -97,6 +97,7 @@ NADMM_HD constexpr FieldMap field_map() {
 constexpr int kGatherItems = 4;   // spectrum values per thread held in flight per round
 enum PlaneExtra : int { kPlanePlain = 0, kPlaneConv = 1, kPlaneHist = 2 };
 constexpr int kPlaneThreads = 256;
+constexpr int kSpecIssuer = 32;  // lane 0 of warp 1 issues the spectrum-block copy
 
 // Lines: line l = comp * (R/2) + r holds rows (y0 + r) [real part] and
 // (y0 + r + R/2) [imaginary part] of component comp, at pitch a.pitch.
@@ -481,8 +482,10 @@ __global__ void __launch_bounds__(kPlaneThreads, 3) k_plane(const __grid_constan
       if (blockIdx.x == 0) atomicAdd(a.conv + kConvAdmmRun, 1u);
     }
   }
-  if (IN == IN_SPEC && spec_tma && tid == 0) {
-    // the CTA's spectrum block {R rows, this z, all (comp, kx)}: one box
+  if (IN == IN_SPEC && spec_tma && tid == kSpecIssuer) {
+    // the CTA's spectrum block {R rows, this z, all (comp, kx)}: one box,
+    // issued from warp 1 so that it does not wait behind warp 0's issue of
+    // the field loads
     mbar_expect_tx(bar + 1, (uint32_t)(nckx * a.R * sizeof(float2)));
     tensor_load_3d(lines, &a.smap, y0, z, 0, bar + 1);
   }
