@@ -177,6 +177,24 @@ def test_bound_compose(lib, kappa, delta):
     assert np.abs(host(u_out) - ref).max() <= tol
 
 
+@pytest.mark.parametrize("dims", [(40, 20, 13), (36, 18, 9), (128, 128, 96)])
+@pytest.mark.parametrize("kappa,delta,amp", [(0.5, 1.0, 1.7), (math.inf, math.inf, 0.9),
+                                             (math.inf, math.inf, 2.5)])
+def test_compose_ragged_grids(lib, dims, kappa, delta, amp):
+    """Bound and compose on grids with partial 32 x 8 tiles, for steps within
+    one voxel (first two cases) and beyond it (third)."""
+    nx, ny, nz = dims
+    w = smooth_field(dims, 11, amp=amp)
+    u = smooth_field(dims, 12, amp=2.0)
+    reg = lib.Registration(dims, device=DEV, kappa=kappa, delta=delta)
+    u_out, sc = empty((3, nz, ny, nx)), empty((1,))
+    lib.nadmm_bound_compose(reg.handle, dev(w), dev(u), u_out, sc, torch.cuda.current_stream())
+    s_ref, _, _ = O.bound_scale(w.astype(np.float64), kappa, delta)
+    ref = O.compose(u.astype(np.float64), s_ref * w.astype(np.float64))
+    tol = max(position_tol(dims, u[i]) for i in range(3)) + 1e-6 * np.abs(w).max()
+    assert np.abs(host(u_out) - ref).max() <= tol
+
+
 def test_jacobian_det(lib):
     dims = (32, 32, 24)
     nx, ny, nz = dims
