@@ -1,0 +1,146 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one single-term mistake (a dropped term, a flipped sign, a
+wrong index or operand order, a swapped component) into a temporary copy of
+`oracle/`, on the CPU, and runs the pin file that covers that function
+against the copy: the run must end with at least one failing test (pytest
+exit status 1, not a collection or import error).  A control run of the
+unmodified copy must pass.  Nothing here touches the repository's own files.
+"""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+FWD, GRAD = "nadmm_oracle.py", "nadmm_oracle_grad.py"
+EVAL, PYR = "nadmm_oracle_eval.py", "nadmm_oracle_pyramid.py"
+PINS = {FWD: "test_oracle_pins.py", GRAD: "test_oracle_grad_pins.py",
+        EVAL: "test_oracle_eval_pins.py", PYR: "test_oracle_pyramid_pins.py"}
+
+# (oracle file, text as it stands, planted mistake)
+MUTATIONS = [
+    # Eq. 6 regulariser step and symbol
+    (FWD, "theta * np.fft.fftn(y[i]) / denom", "np.fft.fftn(y[i]) / denom"),
+    (FWD, "(2.0 ** n) * base ** n", "(2.0 ** n) * base"),
+    (FWD, "- np.cos(2.0 * np.pi * q / ny)[None, :, None]",
+     "- np.cos(2.0 * np.pi * q / nx)[None, :, None]"),
+    # Eq. 5 dual update and Nesterov extrapolation
+    (FWD, "b = b_hat + v - w", "b = b_hat - v + w"),
+    (FWD, "else beta[k - 1]", "else beta[k]"),
+    (FWD, "w_hat = w_km1 + beta_km1 * (w_km1 - w_km2)", "w_hat = w_km1 - beta_km1 * (w_km1 - w_km2)"),
+    (FWD, "b_hat = b_km1 + beta_km1 * (b_km1 - b_km2)", "b_hat = b_km1"),
+    (FWD, "w_km2, b_km2 = w_km1, b_km1", "w_km2, b_km2 = w_km1 * 0, b_km1"),
+    (FWD, "a_next = (1.0 + math.sqrt(1.0 + 4.0 * alpha[k] * alpha[k])) / 2.0",
+     "a_next = (1.0 + math.sqrt(1.0 + 2.0 * alpha[k] * alpha[k])) / 2.0"),
+    # Eq. 6 data steps (s = 2, s = 1)
+    (FWD, "[None] * J\n\n\ndef data_step_l1", "[None] * J[::-1]\n\n\ndef data_step_l1"),
+    (FWD, "z = theta * rho / ((J * J).sum(axis=0) + eps)", "z = rho / ((J * J).sum(axis=0) + eps)"),
+    (FWD, "return u - (t / theta)[None] * J", "return u - t[None] * J"),
+    # gradient, interpolation, composition, bound, linearisation
+    (FWD, "for comp, ax in ((0, 2), (1, 1), (2, 0)):", "for comp, ax in ((0, 0), (1, 1), (2, 2)):"),
+    (FWD, "return c0 * (1 - fz) + c1 * fz", "return c0 * (1 - fy) + c1 * fy"),
+    (FWD, "ix = np.minimum(np.floor(px).astype(np.int64), nx - 2)",
+     "ix = np.minimum(np.rint(px).astype(np.int64), nx - 2)"),
+    (FWD, "return v + np.stack([trilinear(u[i], px, py, pz) for i in range(3)])", "return v + u"),
+    (FWD, "    return v + np.stack", "    return u + np.stack"),
+    (FWD, "px, py, pz = x + v[0], y + v[1], z + v[2]", "px, py, pz = x + v[1], y + v[0], z + v[2]"),
+    (FWD, "s = min(s, kappa / m_jac)", "s = min(s, m_jac / kappa)"),
+    (FWD, "jac = np.maximum(jac, np.abs(central_gradient(w[i])).sum(axis=0))",
+     "jac = np.maximum(jac, np.abs(central_gradient(w[i])).max(axis=0))"),
+    (FWD, "return central_gradient(I1w), I1w - np.asarray(I0, np.float64), I1w",
+     "return central_gradient(I1w), np.asarray(I0, np.float64) - I1w, I1w"),
+    (FWD, "u = compose(u, sc * w)", "u = compose(sc * w, u)"),
+    # reverse mode
+    (GRAD, "(2.0 * rho * Jv / (d * d))[None] * J", "(1.0 * rho * Jv / (d * d))[None] * J"),
+    (GRAD, "g_theta += float((rho * Jv / (d * d)).sum())", "g_theta += 0.0"),
+    (GRAD, "Wbar[k - 1] += (1.0 + bp) * what_bar", "Wbar[k - 1] += what_bar"),
+    (GRAD, "Bbar[k - 2] += -bp * bhat_bar", "Bbar[k - 2] += bp * bhat_bar"),
+    (GRAD, "bhat_bar = ybar - ubar", "bhat_bar = ybar"),
+    (GRAD, "ybar = spectral_solve(wbar - bbar, lam, theta, n) + bbar",
+     "ybar = spectral_solve(wbar - bbar, lam, theta, n)"),
+    (GRAD, "np.add.at(acc, np.maximum(idx - 1, 0), -0.5 * gc)",
+     "np.add.at(acc, np.maximum(idx - 1, 0), 0.5 * gc)"),
+    (GRAD, "gv[1] += gy", "gv[1] += gx"),
+    (GRAD, "ds = -kappa / (m_jac * m_jac) * gs", "ds = -kappa / m_jac * gs"),
+    (GRAD, "g_theta += -g_gamma * lam / (theta * theta)", "g_theta += g_gamma * lam / (theta * theta)"),
+    (GRAD, "return -np.asarray(gc, np.float64), gI1, gu", "return np.asarray(gc, np.float64), gI1, gu"),
+    (GRAD, "return -gL * r, gI1, gu", "return gL * r, gI1, gu"),
+    (GRAD, "ubar = gu_prev + gu_lin", "ubar = gu_prev"),
+    (GRAD, "wbar = wbar + bound_scale_vjp(w, kappa, delta, sbar)", "wbar = wbar"),
+    (GRAD, "mult = -Kn / (1.0 + gamma * Kn) ** 2", "mult = -Kn / (1.0 + gamma * Kn)"),
+    (GRAD, "inside_x = (px > 0.0) & (px < nx - 1.0)", "inside_x = np.ones_like(px, bool)"),
+    # Sec. 4 measures
+    (EVAL, "return 1.0 if s == 0 else 2.0 * int((A & B).sum()) / s",
+     "return 1.0 if s == 0 else int((A & B).sum()) / s"),
+    (EVAL, "vals.append(max(_directed(A, B), _directed(B, A)) * spacing)",
+     "vals.append(_directed(A, B) * spacing)"),
+    (EVAL, "return np.clip(np.floor(p + 0.5), 0, n - 1).astype(np.int64)",
+     "return np.clip(np.floor(p), 0, n - 1).astype(np.int64)"),
+    (EVAL, "return 100.0 * float((det <= 0).sum()) / det.size",
+     "return 100.0 * float((det < 0).sum()) / det.size"),
+    # pyramid
+    (PYR, "px, py, pz = (x - 0.5) / 2.0, (y - 0.5) / 2.0, (z - 0.5) / 2.0",
+     "px, py, pz = x / 2.0, y / 2.0, z / 2.0"),
+    (PYR, "return np.stack([2.0 * trilinear(uc[i], px, py, pz) for i in range(3)])",
+     "return np.stack([trilinear(uc[i], px, py, pz) for i in range(3)])"),
+    (PYR, "return f.reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2).mean(axis=(1, 3, 5))",
+     "return f[::2, ::2, ::2]"),
+]
+
+CONFTEST = '''import os, sys
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+'''
+
+
+def _stage(dst, oracle_file=None, old=None, new=None):
+    """Copy of oracle/, synth and one pin file under dst, with one edit."""
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(dst, "oracle"),
+                    ignore=shutil.ignore_patterns("__pycache__", "*.so", "*.o"))
+    pkg = os.path.join(dst, "paper_2109_12688_gb300")
+    os.makedirs(pkg)
+    open(os.path.join(pkg, "__init__.py"), "w").close()
+    shutil.copy(os.path.join(ROOT, "paper_2109_12688_gb300", "synth.py"), pkg)
+    with open(os.path.join(dst, "conftest.py"), "w") as fh:
+        fh.write(CONFTEST)
+    if oracle_file is not None:
+        path = os.path.join(dst, "oracle", oracle_file)
+        src = open(path).read()
+        assert old in src, f"{oracle_file} no longer contains {old!r}: update the case"
+        with open(path, "w") as fh:
+            fh.write(src.replace(old, new, 1))
+
+
+def _run_pins(dst, pin_file):
+    shutil.copy(os.path.join(ROOT, "tests", pin_file), dst)
+    # one thread per run: the runs themselves go in parallel
+    env = dict(os.environ, PYTHONPATH=dst, PYTHONDONTWRITEBYTECODE="1", OMP_NUM_THREADS="1",
+               OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "--rootdir", dst, os.path.join(dst, pin_file)],
+                       cwd=dst, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode, r.stdout[-400:]
+
+
+def test_unmodified_copy_passes_every_pin_file(tmp_path):
+    _stage(str(tmp_path))
+    for pin_file in sorted(set(PINS.values())):
+        rc, out = _run_pins(str(tmp_path), pin_file)
+        assert rc == 0, (pin_file, out)
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    def one(i):
+        oracle_file, old, new = MUTATIONS[i]
+        dst = str(tmp_path / f"m{i:02d}")
+        os.makedirs(dst)
+        _stage(dst, oracle_file, old, new)
+        return i, *_run_pins(dst, PINS[oracle_file])
+
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        results = list(ex.map(one, range(len(MUTATIONS))))
+    missed = [(MUTATIONS[i][0], MUTATIONS[i][2][:70], rc, out) for i, rc, out in results if rc != 1]
+    assert not missed, missed
