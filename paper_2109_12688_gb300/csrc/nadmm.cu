@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/nadmm.h"
 #include "nadmm_internal.h"
 #include "plan.h"
@@ -92,6 +94,15 @@ struct nadmm_context {
 };
 
 namespace {
+
+// NVTX range over one public call (host side: the enqueue or graph launch,
+// and the waits of the host-buffer path); free when no tool is attached.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Prime factors above 7 get generic FFT stages: at most kMaxStages of them,
 // each at most kMaxPrime.
@@ -988,6 +999,7 @@ nadmm_status nadmm_create_pyramid(const nadmm_config* finest, int32_t levels, co
 
 nadmm_status nadmm_register_pyramid(nadmm_handle h, const float* fixed, const float* moving,
                                     float* u_out, void* stream) {
+  const TraceRange trace("nadmm_register_pyramid");
   nadmm_status st = need_ws(h, kPyramid);
   if (st != NADMM_OK) return st;
   if ((st = check_dev_ptrs({fixed, moving, u_out})) != NADMM_OK) return st;
@@ -1091,6 +1103,7 @@ nadmm_status nadmm_set_params(nadmm_handle h, float lambda, float theta) {
 
 nadmm_status nadmm_register(nadmm_handle h, const float* fixed, const float* moving, float* u_out,
                             void* stream) {
+  const TraceRange trace("nadmm_register");
   nadmm_status st = need_ws(h);
   if (st != NADMM_OK) return st;
   if ((st = check_dev_ptrs({fixed, moving, u_out})) != NADMM_OK) return st;
@@ -1101,6 +1114,7 @@ nadmm_status nadmm_register(nadmm_handle h, const float* fixed, const float* mov
 
 nadmm_status nadmm_register_host(nadmm_handle h, const float* fixed_host, const float* moving_host,
                                  float* u_out_host, void* stream) {
+  const TraceRange trace("nadmm_register_host");
   nadmm_status st = need_ws(h);
   if (st != NADMM_OK) return st;
   if (!fixed_host || !moving_host || !u_out_host) return fail(NADMM_ERR_INVALID_ARG, "NULL host buffer");
@@ -1122,6 +1136,7 @@ nadmm_status nadmm_register_host(nadmm_handle h, const float* fixed_host, const 
 nadmm_status nadmm_register_profiled(nadmm_handle h, const float* fixed, const float* moving,
                                      float* u_out, void* stream, float* kernel_ms,
                                      int32_t* launches) {
+  const TraceRange trace("nadmm_register_profiled");
   nadmm_status st = need_ws(h);
   if (st != NADMM_OK) return st;
   if ((st = check_dev_ptrs({fixed, moving, u_out})) != NADMM_OK) return st;
@@ -1170,6 +1185,7 @@ nadmm_status nadmm_get_status(nadmm_handle h, void* stream) {
 
 nadmm_status nadmm_register_batched(nadmm_handle h, const float* const* fixed,
                                     const float* const* moving, float* const* u_out, void* stream) {
+  const TraceRange trace("nadmm_register_batched");
   nadmm_status st = need_ws(h, kBatched);
   if (st != NADMM_OK) return st;
   if (!fixed || !moving || !u_out) return fail(NADMM_ERR_INVALID_ARG, "NULL pointer array");
@@ -1206,6 +1222,7 @@ nadmm_status nadmm_backward_batched(nadmm_handle h, const float* const* fixed,
                                     float* const* grad_fixed, float* const* grad_moving,
                                     float* const* grad_lambda, float* const* grad_theta,
                                     void* stream) {
+  const TraceRange trace("nadmm_backward_batched");
   nadmm_status st = need_ws(h, kBatched);
   if (st != NADMM_OK) return st;
   if (!(h->cfg.flags & NADMM_FLAG_SAVE_FOR_BACKWARD))
@@ -1339,6 +1356,7 @@ nadmm_status nadmm_jacobian_det(nadmm_handle h, const float* u, float* det, uint
 nadmm_status nadmm_backward(nadmm_handle h, const float* fixed, const float* moving,
                             const float* grad_u, float* grad_fixed, float* grad_moving,
                             float* grad_lambda, float* grad_theta, void* stream) {
+  const TraceRange trace("nadmm_backward");
   nadmm_status st = need_ws(h);
   if (st != NADMM_OK) return st;
   if (!(h->cfg.flags & NADMM_FLAG_SAVE_FOR_BACKWARD))
@@ -1423,6 +1441,7 @@ nadmm_status nadmm_autotune_workspace_size(const nadmm_config* cfg, size_t* byte
 
 nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t bytes, void* stream,
                             uint32_t* best_flags, float* best_ms) {
+  const TraceRange trace("nadmm_autotune");
   if (!cfg || !workspace || !best_flags) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
   if (((uintptr_t)workspace % kAlign) != 0)
     return fail(NADMM_ERR_ALIGNMENT, "workspace must be 256-byte aligned");
