@@ -207,6 +207,10 @@ nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, cons
  * Errors: INVALID_ARG (not batched, lanes < 1, workspace already attached). */
 nadmm_status nadmm_batch_set_lanes(nadmm_handle h, int32_t lanes);
 
+/* The lane count of a batched handle (after clamping).  Host only.
+ * Errors: INVALID_ARG (not batched, lanes NULL). */
+nadmm_status nadmm_batch_get_lanes(nadmm_handle h, int32_t* lanes);
+
 /* Replace the NADMM_FLAG_LANE* and NADMM_FLAG_FUSED_PENCIL bits of pair
  * `pair` (0-based) of a
  * batched handle before its workspace is attached (e.g. with the result of

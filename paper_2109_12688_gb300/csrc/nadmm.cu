@@ -1038,6 +1038,12 @@ nadmm_status nadmm_batch_set_lanes(nadmm_handle h, int32_t lanes) {
   return NADMM_OK;
 }
 
+nadmm_status nadmm_batch_get_lanes(nadmm_handle h, int32_t* lanes) {
+  if (!h || !h->batched || !lanes) return fail(NADMM_ERR_INVALID_ARG, "not a batched handle");
+  *lanes = h->lanes;
+  return NADMM_OK;
+}
+
 void nadmm_destroy(nadmm_handle h) { destroy_context(h); }
 
 nadmm_status nadmm_workspace_size(nadmm_handle h, size_t* bytes) {

@@ -86,6 +86,7 @@ _SIGS = {
     "nadmm_create_batched": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(_P)]),
     "nadmm_batch_set_lanes": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "nadmm_batch_get_lanes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "nadmm_register_batched": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                               ctypes.POINTER(_P), _P]),
     "nadmm_backward": (ctypes.c_int, [_P] * 9),
@@ -174,6 +175,12 @@ def nadmm_create_batched(base, dims_list):
 
 def nadmm_batch_set_lanes(h, lanes):
     _check(load().nadmm_batch_set_lanes(h, lanes))
+
+
+def nadmm_batch_get_lanes(h):
+    n = ctypes.c_int32(0)
+    _check(load().nadmm_batch_get_lanes(h, ctypes.byref(n)))
+    return n.value
 
 
 def nadmm_register_batched(h, fixed, moving, u_out, stream=None):

@@ -137,6 +137,7 @@ def test_batched_create_layout(lib):
     dims = [(32, 32, 24), (96, 96, 64), (20, 12, 14), (160, 160, 112), (12, 6, 7)]
     h = lib.nadmm_create_batched(lib.make_config(dims[0]), dims)
     two = lib.nadmm_workspace_size(h)  # default: two lanes -> {160^2x112}, {the rest}
+    assert lib.nadmm_batch_get_lanes(h) == 2
     big, second = _ws_parts((160, 160, 112)), _ws_parts((96, 96, 64))
     assert big + second <= two <= big + second + 5 * 64 * 1024
     lib.nadmm_batch_set_lanes(h, 4)
@@ -150,6 +151,7 @@ def test_batched_create_layout(lib):
     ws1 = lib.nadmm_workspace_size(h)
     assert _ws_parts((160, 160, 112)) <= ws1 <= _ws_parts((160, 160, 112)) + 5 * 64 * 1024
     lib.nadmm_batch_set_lanes(h, 99)  # clamped to npairs
+    assert lib.nadmm_batch_get_lanes(h) == len(dims)
     assert lib.nadmm_workspace_size(h) >= sum(_ws_parts(d) for d in dims)
     lib.nadmm_destroy(h)
 
