@@ -198,7 +198,7 @@ const char* nadmm_status_string(nadmm_status s);
  * largest pair's) plus every pair's own region (tables, tape).  Two lanes
  * let one pair's DRAM-heavy plane passes overlap another's L2-resident FFT
  * passes; more lanes can lose again to L2 evictions (64 uneven pairs:
- * 488 / 466 / 514 ms with 1 / 2 / 4 lanes).  Host only. */
+ * 472 / 455 / 479 / 511 ms with 1 / 2 / 3 / 4 lanes).  Host only. */
 nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, const int32_t* dims,
                                   nadmm_handle* out);
 
