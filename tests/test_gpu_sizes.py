@@ -101,3 +101,38 @@ def test_batched_mixes_prime_and_smooth_sizes(lib):
     for p, d, u in zip(pairs, dims, us):
         ref = O.register(p["fixed"], p["moving"], lam=10.0, theta=0.1, n=2, outer=2, inner=3)
         assert np.abs(host(u) - ref).max() <= 1e-3, d
+
+
+def test_backward_prime_size(lib):
+    """Reverse mode on a grid with prime factors 11, 13, 23: the adjoint's
+    spectral solves run the same generic stages."""
+    dims = (44, 26, 23)
+    p = synth.make_pair(dims, seed=8)
+    gu = synth.random_field((3,) + dims[::-1], seed=48)
+    kw = dict(lam=10.0, theta=0.1, n=2, outer=2, inner=4, kappa=0.5, delta=1.0)
+    reg = lib.Registration(dims, device=DEV, requires_grad=True, order_n=2, lam=10.0, theta=0.1,
+                           outer=2, inner=4, kappa=0.5, delta=1.0)
+    f, m = dev(p["fixed"]), dev(p["moving"])
+    u = reg.register(f, m)
+    u_ref, _ = O.register_tape(p["fixed"], p["moving"], **kw)
+    assert np.abs(host(u) - u_ref).max() <= 1e-3
+    g0, g1, gl, gt = reg.backward(f, m, dev(gu))
+    r0, r1, rl, rt = O.register_vjp(p["fixed"], p["moving"], gu, **kw)
+    assert rel_l2(host(g0), r0) <= 1e-4
+    assert rel_l2(host(g1), r1) <= 1e-4
+    assert abs(float(gl) - rl) <= 1e-4 * abs(rl) + 1e-7
+    assert abs(float(gt) - rt) <= 1e-4 * abs(rt) + 1e-7
+
+
+def test_pyramid_prime_size(lib):
+    """Three levels 44 x 26 x 22 -> 88 x 52 x 44 -> 176 x 104 x 88 (factors
+    11 and 13 on every level), short schedule."""
+    dims = (176, 104, 88)
+    p = synth.make_pair(dims, seed=9)
+    outer, inner = (2, 2, 1), (3, 3, 2)
+    reg = lib.PyramidRegistration(dims, outer=outer, inner=inner, device=DEV, order_n=2)
+    u = reg.register(dev(p["fixed"]), dev(p["moving"]))
+    assert lib.nadmm_get_status(reg.handle, torch.cuda.current_stream()) == lib.NADMM_OK
+    ref = O.register_pyramid(p["fixed"], p["moving"], outer=outer, inner=inner, lam=10.0,
+                             theta=0.1, n=2)
+    assert np.abs(host(u) - ref).max() <= 1e-3
