@@ -4,6 +4,8 @@ documented.  No call here touches a CUDA device."""
 import math
 import os
 import re
+import subprocess
+import sys
 
 import pytest
 
@@ -223,3 +225,20 @@ def test_plan_flags_and_autotune_sizes(lib):
     with pytest.raises(lib.NadmmError):
         lib.nadmm_batch_set_pair_plan(b, 0, lib.NADMM_FLAG_NO_GRAPH)
     lib.nadmm_destroy(b)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library every entry point raises: there is no
+    fallback implementation (fresh interpreter, library path redirected)."""
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_2109_12688_gb300 import nadmm\n"
+        "nadmm.LIB_PATH = %r\n"
+        "try:\n"
+        "    nadmm.make_config((32, 32, 24)); nadmm.nadmm_create(nadmm.make_config((32, 32, 24)))\n"
+        "except ImportError as e:\n"
+        "    print('raised', 'no fallback' in str(e))\n"
+        "else:\n"
+        "    print('no error')\n" % (ROOT, str(tmp_path / "libnadmm.so")))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert out.stdout.strip() == "raised True", out.stdout + out.stderr
