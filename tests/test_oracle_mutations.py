@@ -52,6 +52,14 @@ MUTATIONS = [
     (FWD, "return central_gradient(I1w), I1w - np.asarray(I0, np.float64), I1w",
      "return central_gradient(I1w), np.asarray(I0, np.float64) - I1w, I1w"),
     (FWD, "u = compose(u, sc * w)", "u = compose(sc * w, u)"),
+    # threshold stopping (Sec. 4, second version)
+    (FWD, "<= tol * np.sqrt((w_km1 ** 2).sum())", "<= tol * np.sqrt((w_km2 ** 2).sum())"),
+    (FWD, "return w_km1, k + 1", "return w_km1, k"),
+    (FWD, "if k >= 1 and np.sqrt(((w_km1 - w_km2) ** 2).sum())",
+     "if k >= 2 and np.sqrt(((w_km1 - w_km2) ** 2).sum())"),
+    (FWD, "<= warp_tol * np.sqrt((I1w ** 2).sum()))", "<= warp_tol * np.sqrt((I1w_new ** 2).sum()))"),
+    (FWD, "            I1w = I1w_new\n", "\n"),
+    (FWD, "            if stop:\n                break", "            if stop and o > 0:\n                break"),
     # reverse mode
     (GRAD, "(2.0 * rho * Jv / (d * d))[None] * J", "(1.0 * rho * Jv / (d * d))[None] * J"),
     (GRAD, "g_theta += float((rho * Jv / (d * d)).sum())", "g_theta += 0.0"),

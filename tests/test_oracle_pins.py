@@ -509,6 +509,42 @@ def test_admm_until_stops_at_the_first_small_change():
     assert k0 == 7 and np.array_equal(w0, hist[6][0])
 
 
+def test_admm_threshold_can_stop_after_the_second_iteration():
+    """The ADMM test starts at k = 1 (reading R19): a threshold just above the
+    first change ||w^1 - w^0|| / ||w^1|| stops after two iterations, one just
+    below it does not."""
+    p = synth.make_pair((16, 16, 12), seed=2)
+    J, c, _ = O.linearise(p["fixed"], p["moving"], np.zeros((3, 12, 16, 16)))
+    hist = O.admm(J, c, 10.0, 0.1, 2, 12, history=True)
+    r1 = np.linalg.norm(hist[1][0] - hist[0][0]) / np.linalg.norm(hist[1][0])
+    _, k = O.admm_until(J, c, 10.0, 0.1, 2, 12, r1 * (1 + 1e-9))
+    assert k == 2
+    _, k = O.admm_until(J, c, 10.0, 0.1, 2, 12, r1 * (1 - 1e-9))
+    assert k > 2
+
+
+def test_warp_threshold_rule():
+    """Outer stop (reading R19): after the re-warp of composition j, stop when
+    ||I1w_j - I1w_{j-1}|| <= tol ||I1w_{j-1}||.  The warped images I1w_j are
+    taken from threshold-free runs of j compositions; thresholds just above
+    and just below each ratio give the first j whose ratio is within tol."""
+    p = synth.make_pair((16, 16, 12), seed=4)
+    kw = dict(lam=10.0, theta=0.1, n=2, inner=6)
+    zero = np.zeros((3, 12, 16, 16))
+    I1w = [O.linearise(p["fixed"], p["moving"], zero)[2]]
+    for j in range(1, 4):
+        u_j = O.register(p["fixed"], p["moving"], outer=j, **kw)
+        I1w.append(O.linearise(p["fixed"], p["moving"], u_j)[2])
+    r = [np.linalg.norm(I1w[j] - I1w[j - 1]) / np.linalg.norm(I1w[j - 1]) for j in range(1, 4)]
+    for j in range(3):
+        for f in (1 + 1e-9, 1 - 1e-9):
+            tol = r[j] * f
+            expect = next((i + 1 for i in range(3) if r[i] <= tol), 4)
+            _, counts = O.register(p["fixed"], p["moving"], outer=4, warp_tol=tol,
+                                   return_counts=True, **kw)
+            assert len(counts) == expect, (j, f, r)
+
+
 def test_register_thresholds_reduce_to_caps_and_stop_early():
     p = synth.make_pair((16, 16, 12), seed=4)
     kw = dict(lam=10.0, theta=0.1, n=2, outer=4, inner=6)
