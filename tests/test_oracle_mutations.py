@@ -29,7 +29,8 @@ MUTATIONS = [
     # Eq. 5 dual update and Nesterov extrapolation
     (FWD, "b = b_hat + v - w", "b = b_hat - v + w"),
     (FWD, "else beta[k - 1]", "else beta[k]"),
-    (FWD, "w_hat = w_km1 + beta_km1 * (w_km1 - w_km2)", "w_hat = w_km1 - beta_km1 * (w_km1 - w_km2)"),
+    (FWD, "w_hat = w_km1 + beta_km1 * (w_km1 - w_km2)",
+     "w_hat = w_km1 - beta_km1 * (w_km1 - w_km2)"),
     (FWD, "b_hat = b_km1 + beta_km1 * (b_km1 - b_km2)", "b_hat = b_km1"),
     (FWD, "w_km2, b_km2 = w_km1, b_km1", "w_km2, b_km2 = w_km1 * 0, b_km1"),
     (FWD, "a_next = (1.0 + math.sqrt(1.0 + 4.0 * alpha[k] * alpha[k])) / 2.0",
@@ -52,14 +53,56 @@ MUTATIONS = [
     (FWD, "return central_gradient(I1w), I1w - np.asarray(I0, np.float64), I1w",
      "return central_gradient(I1w), np.asarray(I0, np.float64) - I1w, I1w"),
     (FWD, "u = compose(u, sc * w)", "u = compose(sc * w, u)"),
+    # Nesterov scalars, data steps, symbol and stencil, interpolation and
+    # differences, bound and determinant, energies, dense minimiser, loop wiring
+    (FWD, "beta.append((alpha[k] - 1.0) / a_next)", "beta.append(alpha[k] / a_next)"),
+    (FWD, "t = z / np.maximum(np.abs(z), 1.0)", "t = z / np.maximum(np.abs(z), 2.0)"),
+    (FWD, "rho = (J * u).sum(axis=0) + c\n    return u - (rho",
+     "rho = (J * u).sum(axis=0) - c\n    return u - (rho"),
+    (FWD, "return u - (rho / (theta + (J * J).sum(axis=0)))[None] * J",
+     "return u - (rho / (1.0 + (J * J).sum(axis=0)))[None] * J"),
+    (FWD, "base = (3.0 - np.cos", "base = (6.0 - np.cos"),
+    (FWD, "acc = 6.0 * g", "acc = 4.0 * g"),
+    (FWD, "acc = acc - np.roll(g, 1, axis=ax) - np.roll(g, -1, axis=ax)",
+     "acc = acc - np.roll(g, 1, axis=ax) - np.roll(g, 1, axis=ax)"),
+    (FWD, "px = np.clip(np.asarray(px, np.float64), 0.0, nx - 1.0)",
+     "px = np.asarray(px, np.float64)"),
+    (FWD, "c01 = c010 * (1 - fx) + c011 * fx", "c01 = c010 * (1 - fx) + c001 * fx"),
+    (FWD, "return trilinear(I1, x + u[0], y + u[1], z + u[2])",
+     "return trilinear(I1, x + u[0], y + u[2], z + u[1])"),
+    (FWD, "out[comp] = 0.5 * (hi - lo)", "out[comp] = (hi - lo)"),
+    (FWD, "lo = np.take(f, np.maximum(idx - 1, 0), axis=ax)", "lo = np.take(f, idx, axis=ax)"),
+    (FWD, "s = min(s, delta / m_abs)", "s = min(s, m_abs / delta)"),
+    (FWD, "m_abs = float(np.abs(w).max()) if w.size else 0.0",
+     "m_abs = float(np.abs(w[0]).max()) if w.size else 0.0"),
+    (FWD, "A = D + np.eye(3)[:, :, None, None, None]", "A = D"),
+    (FWD, "- A[0, 1] * (A[1, 0] * A[2, 2] - A[1, 2] * A[2, 0])",
+     "+ A[0, 1] * (A[1, 0] * A[2, 2] - A[1, 2] * A[2, 0])"),
+    (FWD, "return data + 0.5 * lam * reg\n", "return data + lam * reg\n"),
+    (FWD, "data = (np.abs(rho) ** s).sum() / s\n    reg = sum(float((v[i]",
+     "data = (np.abs(rho) ** s).sum()\n    reg = sum(float((v[i]"),
+    (FWD, "0.5 * theta * float(((w - v - b) ** 2).sum())",
+     "0.5 * theta * float(((w - v + b) ** 2).sum())"),
+    (FWD, "rhs = -(Jf * c.reshape(1, V)).ravel()", "rhs = (Jf * c.reshape(1, V)).ravel()"),
+    (FWD, "A[i * V:(i + 1) * V, i * V:(i + 1) * V] += lam * lap",
+     "A[i * V:(i + 1) * V, i * V:(i + 1) * V] += lap"),
+    (FWD, "bk = 0.0 if (k == 0 or not accelerate) else beta[k - 1]",
+     "bk = 0.0 if (k == 0) else beta[k - 1]"),
+    (FWD, "w = spectral_solve(v + b_hat, lam, theta, n)", "w = spectral_solve(v, lam, theta, n)"),
+    (FWD, "v = _v_step(w_hat - b_hat, J, c, theta, s, eps)",
+     "v = _v_step(w_hat + b_hat, J, c, theta, s, eps)"),
+    (FWD, "J, c, I1w = linearise(I0, I1, u)\n    for o",
+     "J, c, I1w = linearise(I0, I1, np.zeros_like(u))\n    for o"),
     # threshold stopping (Sec. 4, second version)
     (FWD, "<= tol * np.sqrt((w_km1 ** 2).sum())", "<= tol * np.sqrt((w_km2 ** 2).sum())"),
     (FWD, "return w_km1, k + 1", "return w_km1, k"),
     (FWD, "if k >= 1 and np.sqrt(((w_km1 - w_km2) ** 2).sum())",
      "if k >= 2 and np.sqrt(((w_km1 - w_km2) ** 2).sum())"),
-    (FWD, "<= warp_tol * np.sqrt((I1w ** 2).sum()))", "<= warp_tol * np.sqrt((I1w_new ** 2).sum()))"),
+    (FWD, "<= warp_tol * np.sqrt((I1w ** 2).sum()))",
+     "<= warp_tol * np.sqrt((I1w_new ** 2).sum()))"),
     (FWD, "            I1w = I1w_new\n", "\n"),
-    (FWD, "            if stop:\n                break", "            if stop and o > 0:\n                break"),
+    (FWD, "            if stop:\n                break",
+     "            if stop and o > 0:\n                break"),
     # reverse mode
     (GRAD, "(2.0 * rho * Jv / (d * d))[None] * J", "(1.0 * rho * Jv / (d * d))[None] * J"),
     (GRAD, "g_theta += float((rho * Jv / (d * d)).sum())", "g_theta += 0.0"),

@@ -494,6 +494,39 @@ def test_outer_loop_composes_in_the_paper_order(monkeypatch):
 
 
 # ---------------------------------------------------------------- thresholds (Sec. 4, version 2)
+def test_admm_sub_steps_minimise_the_augmented_lagrangian():
+    """Eq. 5 lines 1-2 minimise Eq. 4 in v (w, b fixed) and in w (v, b fixed):
+    at the sub-step's output the central difference of Eq. 4 along random
+    directions vanishes (it is quadratic for s = 2) and moving away raises it."""
+    rng = np.random.default_rng(31)
+    dims, lam, theta, n = (6, 5, 4), 3.0, 0.4, 2
+    shape = (3,) + dims[::-1]
+    J, c = rng.normal(size=shape), rng.normal(size=dims[::-1])
+    w, b, v = rng.normal(size=shape), rng.normal(size=shape), rng.normal(size=shape)
+    v_star = O.data_step_l2(w - b, J, c, theta)
+    w_star = O.spectral_solve(v + b, lam, theta, n)
+    h = 1e-3
+    for _ in range(3):
+        d = rng.normal(size=shape)
+        Lv = [O.augmented_lagrangian(v_star + t * d, w, b, J, c, lam, theta, n) for t in (-h, 0.0, h)]
+        Lw = [O.augmented_lagrangian(v, w_star + t * d, b, J, c, lam, theta, n) for t in (-h, 0.0, h)]
+        for L in (Lv, Lw):
+            assert abs(L[2] - L[0]) / (2 * h) <= 1e-6 * max(1.0, abs(L[1]))
+            assert L[0] > L[1] and L[2] > L[1]
+
+
+def test_register_resumes_from_u0():
+    """Outer steps restart the ADMM state (reading R7), so a + b compositions
+    equal b compositions started from the result of a (the first
+    linearisation is taken at u0)."""
+    p = synth.make_pair((16, 16, 12), seed=6)
+    kw = dict(lam=10.0, theta=0.1, n=2, inner=5)
+    u3 = O.register(p["fixed"], p["moving"], outer=3, **kw)
+    u1 = O.register(p["fixed"], p["moving"], outer=1, **kw)
+    u12 = O.register(p["fixed"], p["moving"], outer=2, u0=u1, **kw)
+    np.testing.assert_array_equal(u12, u3)
+
+
 def test_admm_until_stops_at_the_first_small_change():
     p = synth.make_pair((16, 16, 12), seed=2)
     J, c, _ = O.linearise(p["fixed"], p["moving"], np.zeros((3, 12, 16, 16)))
