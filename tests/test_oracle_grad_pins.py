@@ -113,6 +113,24 @@ def test_bound_scale_vjp(rng, kappa, delta, branch):
         assert not gw.any()
 
 
+@pytest.mark.parametrize("kappa,delta", [(0.01, math.inf), (math.inf, 0.01)])
+def test_bound_scale_vjp_shares_ties(kappa, delta):
+    """Reading R16 at a tie: a field mirror-symmetric in x attains its maximum
+    Jacobian row sum (and its maximum |w|) at mirrored voxels.  Scaling w by
+    (1 + t) moves every tied entry alike, so the derivative of s along w is
+    -s whatever the shares, and the shares must add up to the whole gradient."""
+    nx = 8
+    x = np.arange(nx, dtype=np.float64)
+    g = np.exp(-0.5 * ((x - (nx - 1) / 2.0) / 1.5) ** 2)   # g[i] == g[nx - 1 - i]
+    w = np.zeros((3, 3, 4, nx))
+    w[0] = g[None, None, :]
+    s, m_abs, m_jac = O.bound_scale(w, kappa, delta)
+    assert s < 1.0
+    gw = O.bound_scale_vjp(w, kappa, delta, 1.0)
+    assert np.count_nonzero(gw) >= 2                        # several entries share it
+    close((gw * w).sum(), -s, rel=1e-12)
+
+
 # ---------------------------------------------------------------- Eq. 5 / 6
 def test_spectral_solve_is_symmetric_and_dgamma(rng):
     a = rng.standard_normal((3, 4, 6, 5))

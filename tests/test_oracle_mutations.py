@@ -122,6 +122,37 @@ MUTATIONS = [
     (GRAD, "wbar = wbar + bound_scale_vjp(w, kappa, delta, sbar)", "wbar = wbar"),
     (GRAD, "mult = -Kn / (1.0 + gamma * Kn) ** 2", "mult = -Kn / (1.0 + gamma * Kn)"),
     (GRAD, "inside_x = (px > 0.0) & (px < nx - 1.0)", "inside_x = np.ones_like(px, bool)"),
+    # more reverse mode: adjoint weights and clamp masks, warp and compose
+    # wiring, bound shares at ties, the ADMM recursion
+    (GRAD, "d_fx = sum((corner[dz, dy, 1] - corner[dz, dy, 0]) * wy[dy] * wz[dz]",
+     "d_fx = sum((corner[dz, dy, 1] - corner[dz, dy, 0]) * wy[dy] * wy[dz]"),
+    (GRAD, "return gf, g * d_fx * inside_x, g * d_fy * inside_y, g * d_fz * inside_z",
+     "return gf, g * d_fx * inside_x, g * d_fy * inside_y, g * d_fz * inside_y"),
+    (GRAD, "wx = (1.0 - fx, fx)", "wx = (fx, 1.0 - fx)"),
+    (GRAD, "gI1, gx, gy, gz = trilinear_vjp(I1, x + u[0], y + u[1], z + u[2], g)",
+     "gI1, gx, gy, gz = trilinear_vjp(I1, x + u[0], y + u[1], z + u[1], g)"),
+    (GRAD, "g_w = central_gradient_vjp(gJ) + np.asarray(gc, np.float64)",
+     "g_w = central_gradient_vjp(gJ) - np.asarray(gc, np.float64)"),
+    (GRAD, "gv = g.copy()", "gv = np.zeros_like(g)"),
+    (GRAD, "count = sum(int(h.sum()) for h in hits)", "count = 1"),
+    (GRAD, "gw += np.sign(w) * hits * (ds / int(hits.sum()))", "gw += np.sign(w) * hits * ds"),
+    (GRAD, "G = np.sign(D[i]) * hits[i][None] * (ds / count)",
+     "G = D[i] * hits[i][None] * (ds / count)"),
+    (GRAD, "ds = -delta / (m_abs * m_abs) * gs", "ds = -delta / m_abs * gs"),
+    (GRAD, "gw += np.sign(w) * hits * (ds / int(hits.sum()))",
+     "gw += hits * (ds / int(hits.sum()))"),
+    (GRAD, "u = w_hat - b_hat\n        rho", "u = w_hat + b_hat\n        rho"),
+    (GRAD, "y = W[k] + B[k]", "y = W[k] - B[k]"),
+    (GRAD, "ubar = vbar - J * (Jv / d)[None]", "ubar = vbar"),
+    (GRAD, "gc += -Jv / d", "gc += Jv / d"),
+    (GRAD, "gJ += -(rho / d)[None] * vbar - (Jv / d)[None] * u", "gJ += -(rho / d)[None] * vbar"),
+    (GRAD, "g_lam = g_gamma / theta", "g_lam = g_gamma * theta"),
+    (GRAD, "Bbar[k - 1] += (1.0 + bp) * bhat_bar", "Bbar[k - 1] += bhat_bar"),
+    (GRAD, "if k - 2 >= 0 and bp != 0.0:", "if k - 2 >= 1 and bp != 0.0:"),
+    (GRAD, "bp = 0.0 if (k == 0 or not accelerate) else beta[k - 1]",
+     "bp = 0.0 if (k == 0 or not accelerate) else beta[k]"),
+    (GRAD, "g_gamma += float(((wbar - bbar) * spectral_solve_dgamma(y, lam, theta, n)).sum())",
+     "g_gamma += float((wbar * spectral_solve_dgamma(y, lam, theta, n)).sum())"),
     # Sec. 4 measures
     (EVAL, "return 1.0 if s == 0 else 2.0 * int((A & B).sum()) / s",
      "return 1.0 if s == 0 else int((A & B).sum()) / s"),
