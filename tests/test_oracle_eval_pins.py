@@ -36,6 +36,8 @@ def test_hausdorff_per_slice():
     a[2, 3, 3] = 1                    # slice 2: label absent from b -> skipped
     hd = O.hausdorff_per_slice(a, b, 1, spacing=1.2)
     assert abs(hd - (5.0 + 2.0) / 2 * 1.2) < 1e-12
+    # the default spacing is the data's 1.2 mm isotropic voxel (Sec. 4)
+    assert O.hausdorff_per_slice(a, b, 1) == hd
     rng = np.random.default_rng(0)
     for _ in range(5):
         A = rng.random((1, 9, 11)) < 0.1

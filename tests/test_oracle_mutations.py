@@ -169,6 +169,25 @@ MUTATIONS = [
      "return np.stack([trilinear(uc[i], px, py, pz) for i in range(3)])"),
     (PYR, "return f.reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2).mean(axis=(1, 3, 5))",
      "return f[::2, ::2, ::2]"),
+    # more measures and pyramid: axes, rounding, empty cases, spacing, level
+    # order and inputs, the coarse start, the upsampling axes
+    (EVAL, "return labels[near(z + u[2], nz), near(y + u[1], ny), near(x + u[0], nx)]",
+     "return labels[near(z + u[2], nz), near(y + u[0], ny), near(x + u[1], nx)]"),
+    (EVAL, "return np.clip(np.floor(p + 0.5), 0, n - 1).astype(np.int64)",
+     "return np.floor(p + 0.5).astype(np.int64) % n"),
+    (EVAL, "return 1.0 if s == 0 else 2.0", "return 0.0 if s == 0 else 2.0"),
+    (EVAL, "d = distance_transform_edt(~B)", "d = distance_transform_edt(B)"),
+    (EVAL, "if A.any() and B.any():", "if A.any() or B.any():"),
+    (EVAL, "return float(np.mean(vals)) if vals else float(\"nan\")",
+     "return float(np.max(vals)) if vals else float(\"nan\")"),
+    (EVAL, "def hausdorff_per_slice(a, b, label, spacing=1.2):",
+     "def hausdorff_per_slice(a, b, label, spacing=1.0):"),
+    (PYR, "        I1s.append(downsample2(I1s[-1]))", "        I1s.append(downsample2(I0s[-2]))"),
+    (PYR, "lvl = levels - 1 - i", "lvl = i"),
+    (PYR, "u = register(I0s[lvl], I1s[lvl], outer=outer[i], inner=inner[i], u0=u, **kw)",
+     "u = register(I0s[lvl], I1s[lvl], outer=outer[i], inner=inner[i], **kw)"),
+    (PYR, "px, py, pz = (x - 0.5) / 2.0, (y - 0.5) / 2.0, (z - 0.5) / 2.0",
+     "px, py, pz = (x - 0.5) / 2.0, (z - 0.5) / 2.0, (y - 0.5) / 2.0"),
 ]
 
 CONFTEST = '''import os, sys

@@ -32,6 +32,31 @@ def test_upsample_displacement_constant_and_linear():
     inside = (x >= 1) & (x <= 10)
     expect = np.broadcast_to(0.1 * (x[inside] - 0.5), (8, 10, int(inside.sum())))
     np.testing.assert_allclose(uf[0][:, :, inside], expect, atol=1e-12)
+    # the same along y and z (grid sides differ, so a swapped axis shows)
+    yc, zc = np.arange(5, dtype=float), np.arange(4, dtype=float)
+    uc = np.zeros((3, 4, 5, 6))
+    uc[1] = 0.2 * yc[None, :, None]
+    uc[2] = -0.3 * zc[:, None, None]
+    uf = O.upsample_displacement(uc, (8, 10, 12))
+    y, z = np.arange(10, dtype=float), np.arange(8, dtype=float)
+    iy, iz = (y >= 1) & (y <= 8), (z >= 1) & (z <= 6)
+    np.testing.assert_allclose(uf[1][:, iy, :], np.broadcast_to(
+        0.2 * (y[iy] - 0.5)[None, :, None], (8, int(iy.sum()), 12)), atol=1e-12)
+    np.testing.assert_allclose(uf[2][iz, :, :], np.broadcast_to(
+        -0.3 * (z[iz] - 0.5)[:, None, None], (int(iz.sum()), 10, 12)), atol=1e-12)
+
+
+def test_two_levels_with_no_fine_steps_is_the_upsampled_coarse_result():
+    """Level 0 registers the 2 x 2 x 2 block averages of both images; a fine
+    level with no warps returns the coarse displacement resampled and doubled
+    (reading R18)."""
+    from paper_2109_12688_gb300 import synth
+    p = synth.make_pair((16, 12, 8), seed=7)
+    kw = dict(lam=10.0, theta=0.1, n=2)
+    u = O.register_pyramid(p["fixed"], p["moving"], outer=(2, 0), inner=(3, 3), **kw)
+    uc = O.register(O.downsample2(p["fixed"]), O.downsample2(p["moving"]), outer=2, inner=3, **kw)
+    np.testing.assert_array_equal(u, O.upsample_displacement(uc, (8, 12, 16)))
+    assert np.abs(uc).max() > 0.05  # the coarse level did move
 
 
 def test_one_level_pyramid_is_the_method_and_u0_continues():
