@@ -204,12 +204,13 @@ def test_ssd_after_warp_vjp(rng):
     shape = (4, 5, 6)
     I0, I1 = smooth_image(rng, shape), smooth_image(rng, shape)
     u = 0.9 * rng.standard_normal((3,) + shape)
-    g0, g1, gu = O.ssd_after_warp_vjp(I0, I1, u)
+    gL = 0.7  # the incoming gradient of the loss scales every output
+    g0, g1, gu = O.ssd_after_warp_vjp(I0, I1, u, gL)
     d = rng.standard_normal(shape)
-    close(fd(lambda q: O.ssd_after_warp(q, I1, u), I0, d), (g0 * d).sum())
-    close(fd(lambda q: O.ssd_after_warp(I0, q, u), I1, d), (g1 * d).sum())
+    close(fd(lambda q: gL * O.ssd_after_warp(q, I1, u), I0, d), (g0 * d).sum())
+    close(fd(lambda q: gL * O.ssd_after_warp(I0, q, u), I1, d), (g1 * d).sum())
     du = rng.standard_normal(u.shape)
-    close(fd(lambda q: O.ssd_after_warp(I0, I1, q), u, du), (gu * du).sum())
+    close(fd(lambda q: gL * O.ssd_after_warp(I0, I1, q), u, du), (gu * du).sum())
 
 
 def test_loss_and_gradients_chain(rng):

@@ -153,6 +153,20 @@ MUTATIONS = [
      "bp = 0.0 if (k == 0 or not accelerate) else beta[k]"),
     (GRAD, "g_gamma += float(((wbar - bbar) * spectral_solve_dgamma(y, lam, theta, n)).sum())",
      "g_gamma += float((wbar * spectral_solve_dgamma(y, lam, theta, n)).sum())"),
+    # reverse sweep wiring and the SSD loss
+    (GRAD, "wbar = s * vbar", "wbar = vbar"),
+    (GRAD, "sbar = float((vbar * w).sum())", "sbar = float((vbar * s * w).sum())"),
+    (GRAD, "gu_prev, vbar = compose_vjp(u, s * w, ubar)",
+     "gu_prev, vbar = compose_vjp(u, w, ubar)"),
+    (GRAD, "        g_lam += gl\n", "\n"),
+    (GRAD, "        gI0 += a0\n", "\n"),
+    (GRAD, "for (u, J, c, w, s) in reversed(tape):", "for (u, J, c, w, s) in tape:"),
+    (GRAD, "r = warp(I1, u) - np.asarray(I0, np.float64)\n    return 0.5",
+     "r = warp(I1, u) - np.asarray(I0, np.float64)\n    return 1.0"),
+    (GRAD, "gI1, gu = warp_vjp(I1, u, gL * r)", "gI1, gu = warp_vjp(I1, u, r)"),
+    (GRAD, "return L, d0 + r0, d1 + r1, gl, gt", "return L, d0, d1 + r1, gl, gt"),
+    (GRAD, "J, c, _ = linearise(I0, I1, u)\n        w = admm(",
+     "J, c, _ = linearise(I0, I1, np.zeros_like(u))\n        w = admm("),
     # Sec. 4 measures
     (EVAL, "return 1.0 if s == 0 else 2.0 * int((A & B).sum()) / s",
      "return 1.0 if s == 0 else int((A & B).sum()) / s"),
