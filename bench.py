@@ -9,6 +9,17 @@ Inputs are device-resident when the timed region starts; L2 is flushed
 (a 256 MB write) between timed steps, outside each step's events.
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                [--workload registration|batch64|large|grad|batch16grad|pyramid]
+
+The default line carries, besides the contract keys: latency_ms_one_at_a_time
+(the same pairs one after another on one stream); roofline (dominant kernel
+class: algorithmic bytes per launch over its mean event-timed duration,
+against MEASURED_PEAKS.json, with the ncu DRAM traffic of the committed
+profile when it matches the kernel source); kernels (time, launches, share
+and GB/s per kernel class); cpu_baseline (the FP64 oracle on one host core,
+a bounded sample); cufft_compare (one ADMM iteration with cuFFT, timed only);
+e2e (host buffers through nadmm_register_host, copies timed); gpu_launches;
+clocks (nvidia-smi samples during the timed region).
 
 Multi-GPU: one process per GPU (torchrun); pairs are independent, so every
 rank registers its own pairs with no data-path collective (replicas);
