@@ -362,6 +362,18 @@ def make_config(dims, order_n=2, lam=10.0, theta=0.1, outer=10, inner=10, data_t
     return cfg
 
 
+def _require(t, n, what):
+    """The kernels read or write exactly n float32 values through a device
+    pointer: reject anything else before it reaches them."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{what}: a CUDA tensor is expected")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{what}: float32 expected, got {t.dtype}")
+    if t.numel() != n:
+        raise ValueError(f"{what}: {n} values expected, got {t.numel()}")
+
+
 class Registration:
     """A handle plus a torch-allocated device workspace (PyTorch is used for
     device memory only)."""
@@ -387,8 +399,12 @@ class Registration:
     def register(self, fixed, moving, u_out=None, stream=None):
         import torch
         nx, ny, nz = self.dims
+        V = nx * ny * nz
+        _require(fixed, V, "fixed")
+        _require(moving, V, "moving")
         if u_out is None:
             u_out = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=fixed.device)
+        _require(u_out, 3 * V, "u_out")
         if stream is None:
             stream = torch.cuda.current_stream(fixed.device)
         nadmm_register(self.handle, fixed, moving, u_out, stream)
@@ -405,6 +421,11 @@ class Registration:
         """Gradients (I0, I1, lambda, theta) of <grad_u, u> through the last
         forward pass; lambda/theta as 0-dim device tensors."""
         import torch
+        nx, ny, nz = self.dims
+        V = nx * ny * nz
+        _require(fixed, V, "fixed")
+        _require(moving, V, "moving")
+        _require(grad_u, 3 * V, "grad_u")
         if stream is None:
             stream = torch.cuda.current_stream(fixed.device)
         g0 = torch.empty_like(fixed)
@@ -477,8 +498,12 @@ class PyramidRegistration(Registration):
     def register(self, fixed, moving, u_out=None, stream=None):
         import torch
         nx, ny, nz = self.dims
+        V = nx * ny * nz
+        _require(fixed, V, "fixed")
+        _require(moving, V, "moving")
         if u_out is None:
             u_out = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=fixed.device)
+        _require(u_out, 3 * V, "u_out")
         if stream is None:
             stream = torch.cuda.current_stream(fixed.device)
         nadmm_register_pyramid(self.handle, fixed, moving, u_out, stream)
@@ -510,11 +535,22 @@ class BatchedRegistration(Registration):
         self._ws_ptr = (base + 255) // 256 * 256
         nadmm_set_workspace(self.handle, self._ws_ptr, nbytes)
 
+    def _require_pairs(self, **lists):
+        n = len(self.dims_list)
+        for what, ts in lists.items():
+            if len(ts) != n:
+                raise ValueError(f"{what}: {n} tensors expected, got {len(ts)}")
+            per = 3 if what in ("u_out", "grad_u") else 1
+            for i, ((nx, ny, nz), t) in enumerate(zip(self.dims_list, ts)):
+                _require(t, per * nx * ny * nz, f"{what}[{i}]")
+
     def register(self, fixed, moving, u_out=None, stream=None):
         import torch
+        self._require_pairs(fixed=fixed, moving=moving)
         if u_out is None:
             u_out = [torch.empty((3, nz, ny, nx), dtype=torch.float32, device=f.device)
                      for (nx, ny, nz), f in zip(self.dims_list, fixed)]
+        self._require_pairs(u_out=u_out)
         if stream is None:
             stream = torch.cuda.current_stream(fixed[0].device)
         nadmm_register_batched(self.handle, fixed, moving, u_out, stream)
@@ -525,6 +561,7 @@ class BatchedRegistration(Registration):
         through the last nadmm_register_batched (handle made with
         requires_grad=True)."""
         import torch
+        self._require_pairs(fixed=fixed, moving=moving, grad_u=grad_u)
         if stream is None:
             stream = torch.cuda.current_stream(fixed[0].device)
         g0 = [torch.empty_like(f) for f in fixed]

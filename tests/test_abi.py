@@ -242,3 +242,22 @@ def test_missing_library_fails_loudly(tmp_path):
         "    print('no error')\n" % (ROOT, str(tmp_path / "libnadmm.so")))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert out.stdout.strip() == "raised True", out.stdout + out.stderr
+
+
+def test_high_level_calls_reject_host_tensors(lib):
+    """The Registration classes check their tensors before any device work:
+    a host tensor never reaches a kernel as a device pointer."""
+    torch = pytest.importorskip("torch")
+    reg = object.__new__(lib.Registration)      # no device workspace needed
+    reg.dims, reg.handle = (8, 8, 8), None
+    host = torch.zeros((8, 8, 8))
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        reg.register(host, host)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        reg.backward(host, host, torch.zeros((3, 8, 8, 8)))
+    b = object.__new__(lib.BatchedRegistration)
+    b.dims_list, b.handle = [(8, 8, 8), (4, 4, 4)], None
+    with pytest.raises(ValueError, match="2 tensors expected"):
+        b.register([host], [host])
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        b.register([host, torch.zeros((4, 4, 4))], [host, torch.zeros((4, 4, 4))])
