@@ -12,14 +12,19 @@ python bench.py [--gpus N --steps K --warmup W] [--impl reference]
                 [--workload registration|batch64|large|grad|batch16grad|pyramid]
 
 The default line carries, besides the contract keys: latency_ms_one_at_a_time
-(the same pairs one after another on one stream); roofline (dominant kernel
-class: algorithmic bytes per launch over its mean event-timed duration,
-against MEASURED_PEAKS.json, with the ncu DRAM traffic of the committed
-profile when it matches the kernel source); kernels (time, launches, share
-and GB/s per kernel class); cpu_baseline (the FP64 oracle on one host core,
-a bounded sample); cufft_compare (one ADMM iteration with cuFFT, timed only);
+(the same pairs one after another on one stream, checked bit for bit against
+the concurrent results: a mismatch exits non-zero); roofline (dominant
+kernel class: algorithmic bytes per launch over its mean event-timed
+duration, against MEASURED_PEAKS.json, with the ncu DRAM traffic of the
+committed profile when it matches the kernel source); kernels (time,
+launches, share and GB/s per kernel class); quality (Sec. 4 measures of the
+three registrations: Dice, per-slice Hausdorff, share of det <= 0);
+cpu_baseline (one whole FP64 oracle registration on one pinned host core)
+and cpu_baseline_all_cores (every host core, one pinned process each, on a
+bounded sample); cufft_compare (one ADMM iteration with cuFFT, timed only);
 e2e (host buffers through nadmm_register_host, copies timed); gpu_launches;
-clocks (nvidia-smi samples during the timed region).
+clocks (nvidia-smi samples during the timed region); extras (short runs of
+the batch64, grad, large and pyramid workloads).
 
 Multi-GPU: one process per GPU (torchrun); pairs are independent, so every
 rank registers its own pairs with no data-path collective (replicas);
@@ -70,6 +75,12 @@ def algorithmic_bytes_per_voxel(nx):
         "bound": 12.0,                           # read w
         "compose": 36.0,                         # read w, u; write u
     }
+
+
+# Kernels each profiled class stands for (the pencil class is the y-pass,
+# z-pass and inverse y-pass), and the classes one k >= 2 ADMM iteration runs.
+KERNELS_PER_CLASS = {"pencil": 3}
+ITERATION_CLASSES = ("plane", "pencil")
 
 
 def kernel_source_sha():
@@ -168,6 +179,8 @@ def parse_args():
     ap.add_argument("--orders", default="1,2,3",
                     help="regulariser orders registered per step (profiling runs use one)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the short batch64 / grad / large / pyramid runs of the default line")
     ap.add_argument("--no-cufft-compare", action="store_true",
                     help="skip the timed-only cuFFT comparison of one ADMM iteration")
     ap.add_argument("--workload", choices=("registration", "batch64", "large", "grad", "pyramid",
@@ -204,22 +217,6 @@ def aggregate(total_ms, steps, regs_per_rank_step, world, voxels, outer, inner):
     regs_total = steps * regs_per_rank_step * world
     return (total_ms / regs_total, total_ms / steps,
             voxels * outer * inner * regs_total / (total_ms / 1e3))
-
-
-def oracle_sample_ms(pair, n):
-    """One of the 10 outer steps of the oracle registration (linearise, 10
-    ADMM iterations, bound, compose), timed on the host; returns ms."""
-    import numpy as np
-    import oracle as O
-    I0 = pair["fixed"].astype(np.float64)
-    I1 = pair["moving"].astype(np.float64)
-    t0 = time.perf_counter()
-    u = np.zeros((3,) + I0.shape)
-    J, c, _ = O.linearise(I0, I1, u)
-    w = O.admm(J, c, LAM, THETA, n, INNER)
-    s, _, _ = O.bound_scale(w, 0.5, 1.0)
-    O.compose(u, s * w)
-    return (time.perf_counter() - t0) * 1e3
 
 
 def cufft_iteration_us(dev, n, iters=50):
@@ -278,62 +275,188 @@ def cufft_iteration_us(dev, n, iters=50):
     return e0.elapsed_time(e1) * 1e3 / iters
 
 
-ORACLE_SAMPLE = ("1 of the 10 outer steps (re-linearise + 10 ADMM iterations + bound + compose) "
-                 "of the 128x128x96 n=2 registration, FP64 numpy oracle, extrapolated x10 to one "
-                 "registration")
+# ---------------------------------------------------------------- oracle legs
+# The FP64 oracle as it stands, timed on host cores.  Each timing runs in a
+# process pinned to one core with every math-library thread pool set to one
+# thread, so "cores" is what the measurement actually used.
+_ONE_THREAD = {v: "1" for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                "NUMEXPR_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")}
+
+
+def _pin_this_process(cpu):
+    os.environ.update(_ONE_THREAD)
+    if hasattr(os, "sched_setaffinity"):
+        os.sched_setaffinity(0, {cpu})
+
+
+def _oracle_outer_steps(pair, n, steps, u=None):
+    """`steps` compositions of the oracle registration resumed from u
+    (oracle.register with outer=1 and u0, which continues a registration
+    exactly); returns (u, ms)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u = O.register(pair["fixed"], pair["moving"], lam=LAM, theta=THETA, n=n, outer=1,
+                       inner=INNER, u0=u)
+    return u, (time.perf_counter() - t0) * 1e3
+
+
+def _oracle_job(job):
+    """Spawned worker: (cpu, seed, n, outer steps) -> ms on that one core."""
+    cpu, seed, n, steps = job
+    _pin_this_process(cpu)
+    from paper_2109_12688_gb300 import synth
+    pair = synth.make_pair(DIMS, seed=seed)
+    _, ms = _oracle_outer_steps(pair, n, steps)
+    return ms
+
+
+def _host_cpus():
+    return sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else \
+        list(range(os.cpu_count() or 1))
+
+
+def cpu_baselines():
+    """One whole registration (n = 2, the bench's seed-2 pair, 10 x 10) on one
+    pinned core; then every host core at once, one pinned process per core,
+    each running one composition (linearise + 10 ADMM iterations + bound +
+    compose) of a bench pair: ms per registration = wall time / (cores / 10)."""
+    import multiprocessing as mp
+    cpus = _host_cpus()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        one = pool.map(_oracle_job, [(cpus[-1], 2, 2, OUTER)])[0]
+    jobs = [(c, 1 + i % 3, 1 + i % 3, 1) for i, c in enumerate(cpus)]
+    with ctx.Pool(len(cpus)) as pool:
+        pool.map(_oracle_job, [(c, 2, 2, 0) for c in cpus])  # start-up outside the clock
+        t0 = time.perf_counter()
+        pool.map(_oracle_job, jobs, chunksize=1)
+        wall = (time.perf_counter() - t0) * 1e3
+    single = {"value": one, "unit": "ms", "cores": 1, "kind": "oracle",
+              "sample": "one whole 128x128x96 registration (seed-2 pair, n = 2, 10 x 10), FP64 "
+                        "numpy oracle, one process pinned to one core, math libraries at one "
+                        "thread; not extrapolated"}
+    allc = {"value": wall / (len(cpus) / OUTER), "unit": "ms", "cores": len(cpus),
+            "kind": "oracle",
+            "sample": f"{len(cpus)} processes, one pinned per core, each one of the 10 "
+                      "compositions (linearise + 10 ADMM iterations + bound + compose) of a "
+                      "bench pair (n = 1, 2, 3 in turn); value = wall time per "
+                      f"{len(cpus)} compositions x 10 / {len(cpus)}, i.e. ms per registration "
+                      "at full-host throughput",
+            "wall_ms": wall}
+    return single, allc
 
 
 def run_reference(args, rank):
+    """The oracle as the reference arm: a step is one composition of a whole
+    registration (the bench's pairs, n = 1, 2, 3 in turn, each carried through
+    its 10 compositions), on one pinned core.  value = timed ms / registrations
+    done (timed steps / 10); ms_per_step is the measured time per step."""
     if rank != 0:
         return
-    from paper_2109_12688_gb300 import synth
-    pair = synth.make_pair(DIMS, seed=0)
-    for _ in range(args.warmup):
-        oracle_sample_ms(pair, 2)
-    times = [oracle_sample_ms(pair, 2) * OUTER for _ in range(args.steps)]
-    ms = sum(times) / len(times)
+    orders = (1, 2, 3)
+    data = generate_inputs(("registration",))  # host inputs, generated in parallel
+    pairs = {n: data[("pair", n)] for n in orders}
+    _pin_this_process(_host_cpus()[0])
+    u = None
+    for i in range(args.warmup):  # a registration outside the timed sequence
+        u, _ = _oracle_outer_steps(pairs[2], 2, 1, u if i % OUTER else None)
+    times = []
+    u = None
+    for i in range(args.steps):
+        n = orders[(i // OUTER) % 3]
+        u, ms = _oracle_outer_steps(pairs[n], n, 1, None if i % OUTER == 0 else u)
+        times.append(ms)
+    total = sum(times)
+    regs = args.steps / OUTER
+    ms_reg = total / regs
     V = DIMS[0] * DIMS[1] * DIMS[2]
+    sample = (f"{args.steps} compositions = {regs:g} registrations of the bench's pairs "
+              "(n = 1, 2, 3 in turn, seeds 1, 2, 3, 10 x 10), FP64 numpy oracle on one pinned "
+              "core, math libraries at one thread")
     line = {
-        "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "impl": "reference", "metric": METRIC, "value": ms_reg, "unit": "ms",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD.replace("one pair per regulariser order n = 1, 2, 3",
-                                                "n = 2 pair, bounded sample"),
-                   "dims": list(DIMS), "outer": OUTER, "inner": INNER},
-        "voxel_admm_iters_per_s": V * OUTER * INNER / (ms / 1e3),
-        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": ORACLE_SAMPLE},
-        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": bench_config(orders, 1) | {"reference_step": "one composition of a "
+                                                              "registration (10 per "
+                                                              "registration)"},
+        "voxel_admm_iters_per_s": V * OUTER * INNER / (ms_reg / 1e3),
+        "cpu_baseline": {"value": ms_reg, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": ms_reg, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_extra(args, rank, world):
-    """The batched (64 uneven pairs) and large (256x256x192) workloads, one
-    JSON line each; single GPU, device-resident inputs, events on the stream."""
+def bench_config(orders, world):
+    return {"workload": WORKLOAD, "dims": list(DIMS), "orders": list(orders),
+            "outer": OUTER, "inner": INNER, "registrations_per_step": len(orders),
+            "l2": "flushed between timed steps (256 MB write outside the step events)",
+            "concurrency": f"{len(orders)} registrations in flight per GPU, one stream "
+                           "each (independent pairs); value is their throughput",
+            "parallelism": f"replicas x{world}"}
+
+
+# ---------------------------------------------------------------- other workloads
+def _gen(job):
+    """Spawned worker: one seeded synthetic input (no method arithmetic)."""
+    kind, dims, seed = job
+    from paper_2109_12688_gb300 import synth
+    if kind == "pair":
+        return synth.make_pair(dims, seed=seed)
+    return synth.phase_pair(dims, seed=seed)
+
+
+def generate_inputs(names):
+    """Inputs of the bench's workloads, generated in parallel on the host
+    (spawned processes, before any GPU work)."""
+    import multiprocessing as mp
+    from paper_2109_12688_gb300 import synth
+    jobs = {}
+    if "registration" in names or "pyramid" in names:
+        for n in (1, 2, 3):
+            jobs[("pair", n)] = ("pair", DIMS, n)
+    if "grad" in names:
+        jobs[("pair", 0)] = ("pair", DIMS, 0)
+    if "large" in names:
+        jobs[("large", 0)] = ("phase", (256, 256, 192), 0)
+    if "batch64" in names:
+        for i, d in enumerate(synth.draw_batch_dims(64, seed=1234)):
+            jobs[("b64", i)] = ("phase", d, i)
+    if "batch16grad" in names:
+        for i, d in enumerate(synth.draw_batch_dims(16, seed=4321)):
+            jobs[("b16", i)] = ("phase", d, 100 + i)
+    keys = list(jobs)
+    procs = max(1, min(len(keys), len(_host_cpus())))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        vals = pool.map(_gen, [jobs[k] for k in keys], chunksize=1)
+    return dict(zip(keys, vals))
+
+
+def extra_workload(name, data, steps, warmup, dev, sample_clocks=True):
+    """One of the batch64, large, grad, batch16grad, pyramid workloads on one
+    GPU with device-resident inputs, events on the launching stream; returns
+    its JSON-line dict."""
     import torch
-    if world > 1 and rank != 0:
-        return
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2109_12688_gb300 import nadmm, synth
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     kw = dict(lam=LAM, theta=THETA, outer=OUTER, inner=INNER)
 
     def timed(fn):
-        for i in range(args.warmup):
+        for i in range(warmup):
             flush.fill_(i & 0xFF)
             fn()
         torch.cuda.synchronize()
-        clocks = ClockSampler(0)
-        clocks.start()
-        time.sleep(0.3)
+        clocks = ClockSampler(dev.index) if sample_clocks else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
         total = 0.0
-        for i in range(args.steps):
+        for i in range(steps):
             flush.fill_((i + 7) & 0xFF)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -342,16 +465,17 @@ def run_extra(args, rank, world):
             e1.record(stream)
             torch.cuda.synchronize()
             total += e0.elapsed_time(e1)
-        return total / args.steps, clocks.stop()
+        return total / steps, (clocks.stop() if clocks else None)
 
-    if args.workload == "batch64":
+    head = {"n_gpus": 1, "steps": steps, "warmup": warmup, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    if name == "batch64":
         dims = synth.draw_batch_dims(64, seed=1234)
-        data = [synth.phase_pair(d, seed=i) for i, d in enumerate(dims)]
-        I0 = [torch.from_numpy(f).to(dev) for f, _ in data]
-        I1 = [torch.from_numpy(m).to(dev) for _, m in data]
+        I0 = [torch.from_numpy(data[("b64", i)][0]).to(dev) for i in range(64)]
+        I1 = [torch.from_numpy(data[("b64", i)][1]).to(dev) for i in range(64)]
         U = [torch.empty((3, d[2], d[1], d[0]), device=dev) for d in dims]
         lanes_ms = {}
-        for lanes in (None, 1, 2, 3, 4):  # None: the library's default lane count
+        for lanes in ((None, 1, 2, 3, 4) if sample_clocks else (None,)):
             breg = nadmm.BatchedRegistration(dims, device=dev, lanes=lanes, order_n=2, **kw)
             t, c = timed(lambda: nadmm.nadmm_register_batched(breg.handle, I0, I1, U, stream))
             if lanes is None:
@@ -367,63 +491,52 @@ def run_extra(args, rank, world):
                 nadmm.nadmm_register(r.handle, a, b, u, stream)
         seq_ms, _ = timed(sequential)
         vox = sum(d[0] * d[1] * d[2] for d in dims)
-        line = {
+        return head | {
             "metric": "ms per batch of 64 uneven pairs", "value": ms, "unit": "ms",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
+            "ms_per_step": ms,
             "config": {"workload": "64 pairs, nx, ny from {96,112,128,144,160}, nz from "
                                    "{64,80,96,112} (seed 1234), two-phase phantoms, n=2, 10 x 10 "
                                    "iterations, one batched graph with the default number "
                                    "of concurrent lanes (others in ms_by_lanes)",
-                       "lanes": default_lanes,
-                       "voxels": vox,
+                       "lanes": default_lanes, "voxels": vox,
                        "l2": "flushed between timed steps (256 MB write outside the step events)"},
             "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms,
             "ms_by_lanes": lanes_ms,
             "voxel_admm_iters_per_s": vox * OUTER * INNER / (ms / 1e3),
-            "clocks": clk,
-        }
-    elif args.workload == "pyramid":
-        dims = (128, 128, 96)
+            "clocks": clk}
+    if name == "pyramid":
         # Table 1, first hyper-parameter version, L2 data term: seconds on a 16 GB V100
         paper_s = {1: 2.17, 2: 1.38, 3: 1.37}
-        per = {}
-        clk = None
+        per, clk = {}, None
         for n in (1, 2, 3):
-            p = synth.make_pair(dims, seed=n)
+            p = data[("pair", n)]
             I0 = torch.from_numpy(p["fixed"]).to(dev)
             I1 = torch.from_numpy(p["moving"]).to(dev)
-            reg = nadmm.PyramidRegistration(dims, device=dev, order_n=n, lam=LAM, theta=THETA)
+            reg = nadmm.PyramidRegistration(DIMS, device=dev, order_n=n, lam=LAM, theta=THETA)
             U = torch.empty((3, 96, 128, 128), device=dev)
             per[n], c = timed(lambda: nadmm.nadmm_register_pyramid(reg.handle, I0, I1, U, stream))
             clk = clk or c
         ms = sum(per.values()) / 3
         paper_ms = 1000.0 * sum(paper_s.values()) / 3
-        line = {
+        return head | {
             "metric": "ms per 128x128x96 registration, three-level pyramid (paper's first "
-                      "schedule)", "value": ms, "unit": "ms",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 3 * ms,
-            "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": ms / paper_ms, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "128x128x96 phantom pairs, n = 1, 2, 3, s = 2, lambda=10, "
-                                   "theta=0.1; levels 32x32x24, 64x64x48, 128x128x96 with ADMM "
-                                   "10/5/5 and warpings 10/10/5",
+                      "schedule)", "value": ms, "unit": "ms", "ms_per_step": 3 * ms,
+            "vs_baseline": ms / paper_ms,
+            "config": {"workload": "128x128x96 phantom pairs (seeds 1, 2, 3), n = 1, 2, 3, s = 2, "
+                                   "lambda=10, theta=0.1; levels 32x32x24, 64x64x48, 128x128x96 "
+                                   "with ADMM 10/5/5 and warpings 10/10/5",
                        "l2": "flushed between timed steps (256 MB write outside the step events)"},
-            "ms_by_order": per,
-            "paper_s_by_order": paper_s,
+            "ms_by_order": per, "paper_s_by_order": paper_s,
             "paper_context": "Table 1, L2 + n-th order, first version, 16 GB Tesla V100, "
                              "PyTorch, mean over 100 private test pairs",
-            "clocks": clk,
-        }
-    elif args.workload == "batch16grad":
+            "clocks": clk}
+    if name == "batch16grad":
         dims = synth.draw_batch_dims(16, seed=4321)
-        data = [synth.phase_pair(d, seed=100 + i) for i, d in enumerate(dims)]
         torch.cuda.synchronize()
         torch.cuda.reset_peak_memory_stats(dev)
         base = torch.cuda.memory_allocated(dev)
-        I0 = [torch.from_numpy(f).to(dev) for f, _ in data]
-        I1 = [torch.from_numpy(m).to(dev) for _, m in data]
+        I0 = [torch.from_numpy(data[("b16", i)][0]).to(dev) for i in range(16)]
+        I1 = [torch.from_numpy(data[("b16", i)][1]).to(dev) for i in range(16)]
         breg = nadmm.BatchedRegistration(dims, device=dev, requires_grad=True, order_n=2, **kw)
         U = [torch.empty((3, d[2], d[1], d[0]), device=dev) for d in dims]
         GU = [torch.full((3, d[2], d[1], d[0]), 1e-3, device=dev) for d in dims]
@@ -440,11 +553,9 @@ def run_extra(args, rank, world):
         fwd_ms, _ = timed(lambda: nadmm.nadmm_register_batched(breg.handle, I0, I1, U, stream))
         peak = torch.cuda.max_memory_allocated(dev) - base
         vox = sum(d[0] * d[1] * d[2] for d in dims)
-        line = {
+        return head | {
             "metric": "ms per batch of 16 uneven pairs, forward + backward", "value": ms,
-            "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "unit": "ms", "ms_per_step": ms,
             "config": {"workload": "16 pairs, nx, ny from {96..160}, nz from {64..112} (seed "
                                    "4321), two-phase phantoms, n=2, 10 x 10, forward and reverse "
                                    "mode as two graph replays",
@@ -452,16 +563,14 @@ def run_extra(args, rank, world):
                        "l2": "flushed between timed steps (256 MB write outside the step events)"},
             "forward_only_ms": fwd_ms, "device_bytes_peak": peak,
             "workspace_bytes": nadmm.nadmm_workspace_size(breg.handle),
-            "clocks": clk,
-        }
-    elif args.workload == "grad":
-        dims = (128, 128, 96)
-        p = synth.make_pair(dims, seed=0)
+            "clocks": clk}
+    if name == "grad":
+        p = data[("pair", 0)]
         I0 = torch.from_numpy(p["fixed"]).to(dev)
         I1 = torch.from_numpy(p["moving"]).to(dev)
-        reg = nadmm.Registration(dims, device=dev, requires_grad=True, order_n=2, lam=LAM,
+        reg = nadmm.Registration(DIMS, device=dev, requires_grad=True, order_n=2, lam=LAM,
                                  theta=THETA, outer=8, inner=20)
-        fwd = nadmm.Registration(dims, device=dev, order_n=2, lam=LAM, theta=THETA, outer=8,
+        fwd = nadmm.Registration(DIMS, device=dev, order_n=2, lam=LAM, theta=THETA, outer=8,
                                  inner=20)
         U = torch.empty((3, 96, 128, 128), device=dev)
         loss = torch.zeros(4, device=dev)
@@ -478,44 +587,53 @@ def run_extra(args, rank, world):
                                  par.data_ptr() + 16, stream)
         ms, clk = timed(fwd_bwd)
         fwd_ms, _ = timed(lambda: nadmm.nadmm_register(fwd.handle, I0, I1, U, stream))
-        line = {
+        return head | {
             "metric": "ms per 128x128x96 forward + backward (gradients of the SSD after warp "
                       "w.r.t. I0, I1, lambda, theta)", "value": ms, "unit": "ms",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
+            "ms_per_step": ms,
             "config": {"workload": "128x128x96 phantom pair seed 0, n=2, 8 compositions x 20 "
                                    "ADMM iterations, forward (saving the tape) + SSD + reverse",
                        "l2": "flushed between timed steps (256 MB write outside the step events)"},
             "forward_only_ms": fwd_ms, "backward_over_forward": (ms - fwd_ms) / fwd_ms,
             "workspace_bytes": nadmm.nadmm_workspace_size(reg.handle),
-            "clocks": clk,
-        }
-    else:
-        dims = (256, 256, 192)
-        f, m = synth.phase_pair(dims, seed=0)
-        torch.cuda.synchronize()
-        torch.cuda.reset_peak_memory_stats(dev)
-        base = torch.cuda.memory_allocated(dev)
-        I0 = torch.from_numpy(f).to(dev)
-        I1 = torch.from_numpy(m).to(dev)
-        reg = nadmm.Registration(dims, device=dev, order_n=3, **kw)
-        U = torch.empty((3, 192, 256, 256), device=dev)
-        ms, clk = timed(lambda: nadmm.nadmm_register(reg.handle, I0, I1, U, stream))
-        peak = torch.cuda.max_memory_allocated(dev) - base
-        V = 256 * 256 * 192
-        line = {
-            "metric": "ms per 256x256x192 registration", "value": ms, "unit": "ms",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": "256x256x192 two-phase phantom pair, n=3, 10 x 10 iterations",
-                       "l2": "inputs larger than L2; 256 MB flush between steps"},
-            "voxel_admm_iters_per_s": V * OUTER * INNER / (ms / 1e3),
-            "device_bytes_peak": peak,
-            "workspace_bytes": nadmm.nadmm_workspace_size(reg.handle),
-            "clocks": clk,
-        }
+            "clocks": clk}
+    # large: 256x256x192, n = 3
+    f, m = data[("large", 0)]
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(dev)
+    base = torch.cuda.memory_allocated(dev)
+    I0 = torch.from_numpy(f).to(dev)
+    I1 = torch.from_numpy(m).to(dev)
+    reg = nadmm.Registration((256, 256, 192), device=dev, order_n=3, **kw)
+    U = torch.empty((3, 192, 256, 256), device=dev)
+    ms, clk = timed(lambda: nadmm.nadmm_register(reg.handle, I0, I1, U, stream))
+    peak = torch.cuda.max_memory_allocated(dev) - base
+    V = 256 * 256 * 192
+    return head | {
+        "metric": "ms per 256x256x192 registration", "value": ms, "unit": "ms",
+        "ms_per_step": ms,
+        "config": {"workload": "256x256x192 two-phase phantom pair, n=3, 10 x 10 iterations",
+                   "l2": "inputs larger than L2; 256 MB flush between steps"},
+        "voxel_admm_iters_per_s": V * OUTER * INNER / (ms / 1e3),
+        "device_bytes_peak": peak,
+        "workspace_bytes": nadmm.nadmm_workspace_size(reg.handle),
+        "clocks": clk}
+
+
+EXTRAS = ("batch64", "grad", "large", "pyramid")
+
+
+def run_extra(args, rank, world):
+    """One of the other workloads as its own JSON line (single GPU)."""
+    import torch
+    if world > 1 and rank != 0:
+        return
+    data = generate_inputs([args.workload])
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    line = extra_workload(args.workload, data, args.steps, args.warmup, dev)
     print(json.dumps(line), flush=True)
 
 
@@ -531,6 +649,17 @@ def main():
         run_extra(args, rank, world)
         return
 
+    ORDERS = tuple(int(o) for o in args.orders.split(","))
+    extras = () if (args.no_extras or world > 1) else EXTRAS
+    # host inputs first (spawned generator processes, before any GPU work)
+    if world == 1 and all(1 <= n <= 3 for n in ORDERS):
+        data = generate_inputs(("registration",) + extras)
+        pairs = [data[("pair", n)] for n in ORDERS]
+    else:
+        from paper_2109_12688_gb300 import synth
+        data = {}
+        pairs = [synth.make_pair(DIMS, seed=sd) for sd in rank_seeds(rank, ORDERS)]
+
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -544,13 +673,11 @@ def main():
         __graft_entry__.build()
     if world > 1:
         dist.barrier()
-    from paper_2109_12688_gb300 import nadmm, synth
+    from paper_2109_12688_gb300 import evaluation, nadmm
     nadmm.load()
 
     nx, ny, nz = DIMS
     V = nx * ny * nz
-    ORDERS = tuple(int(o) for o in args.orders.split(","))
-    pairs = [synth.make_pair(DIMS, seed=sd) for sd in rank_seeds(rank, ORDERS)]
     I0 = [torch.from_numpy(p["fixed"]).to(dev) for p in pairs]
     I1 = [torch.from_numpy(p["moving"]).to(dev) for p in pairs]
     U = [torch.empty((3, nz, ny, nx), dtype=torch.float32, device=dev) for _ in ORDERS]
@@ -580,14 +707,17 @@ def main():
         for r, a, b, u in zip(regs, I0, I1, U):
             nadmm.nadmm_register(r.handle, a, b, u, stream)
 
+    def check_status():
+        for r in regs:
+            st = nadmm.nadmm_get_status(r.handle, stream)
+            if st != nadmm.NADMM_OK:
+                raise RuntimeError(f"device status {nadmm.nadmm_status_string(st)}")
+
     for i in range(args.warmup):
         flush.fill_(i & 0xFF)
         step()
     torch.cuda.synchronize()
-    for r in regs:
-        st = nadmm.nadmm_get_status(r.handle, stream)
-        if st != nadmm.NADMM_OK:
-            raise RuntimeError(f"device status {nadmm.nadmm_status_string(st)}")
+    check_status()
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -609,6 +739,8 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world, dev)
+    check_status()
+    timed_u = [u.clone() for u in U]  # outputs of the last timed (concurrent) step
     # latency of one registration at a time (same pairs, one stream)
     seq = []
     for i in range(args.steps):
@@ -620,10 +752,31 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         seq.append(e0.elapsed_time(e1))
+    check_status()
+    # the concurrent streams must give exactly the single-stream results
+    for n, a, b in zip(ORDERS, timed_u, U):
+        if not torch.equal(a, b):
+            print(json.dumps({"error": f"n = {n}: concurrent result differs from the "
+                                       "single-stream result"}), flush=True)
+            sys.exit(3)
     latency_ms = sum(seq) / len(seq) / len(ORDERS)
     regs_total = args.steps * len(ORDERS) * world
     ms_per_reg, ms_per_step, vox_rate = aggregate(total_ms, args.steps, len(ORDERS), world, V,
                                                   OUTER, INNER)
+
+    # Sec. 4 measures of the timed registrations (host scoring, GPU Jacobian)
+    quality = {}
+    for n, p, reg, u in zip(ORDERS, pairs, regs, timed_u):
+        cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+        nadmm.nadmm_jacobian_det(reg.handle, u, None, cnt, stream)
+        sc = evaluation.score(p["labels_fixed"], p["labels_moving"], u.cpu().numpy())
+        quality[f"n{n}"] = {
+            "dice": {k: round(v["dice"], 4) for k, v in sc.items()},
+            "dice_unregistered": {k: round(v["dice_unregistered"], 4) for k, v in sc.items()},
+            "hausdorff_mm": {k: round(v["hausdorff_mm"], 3) for k, v in sc.items()},
+            "hausdorff_mm_unregistered": {k: round(v["hausdorff_mm_unregistered"], 3)
+                                          for k, v in sc.items()},
+            "nonpositive_jacobian_percent": 100.0 * int(cnt.item()) / V}
 
     # end to end through the C ABI with pinned host buffers (copies timed)
     e2e_per_reg = None
@@ -659,8 +812,8 @@ def main():
         for k, (ms, n) in nadmm.nadmm_register_profiled(r.handle, a, b, u, stream).items():
             pm, pn = prof.get(k, (0.0, 0))
             prof[k] = (pm + ms, pn + n)
-    # the pencil class is three kernels (y-pass, z-pass, inverse y-pass)
-    launches_per_reg = (sum(n for _, n in prof.values()) + 2 * prof["pencil"][1]) / len(ORDERS)
+    launches_per_reg = sum(n * KERNELS_PER_CLASS.get(k, 1) for k, (_, n) in prof.items()) \
+        / len(ORDERS)
     bpv = algorithmic_bytes_per_voxel(nx)
     dominant = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_n = prof[dominant]
@@ -674,18 +827,28 @@ def main():
             dist.destroy_process_group()
         return
 
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        ms = oracle_sample_ms(pairs[ORDERS.index(2)] if 2 in ORDERS else pairs[0], 2) * OUTER
-        cpu = {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": ORACLE_SAMPLE}
+    extra_lines = {}
+    for name in extras:
+        ln = extra_workload(name, data, 3, 3, dev, sample_clocks=False)
+        keep = ("metric", "value", "unit", "steps", "warmup", "sequential_ms",
+                "speedup_vs_sequential", "voxel_admm_iters_per_s", "forward_only_ms",
+                "backward_over_forward", "device_bytes_peak", "workspace_bytes", "ms_by_order",
+                "vs_baseline", "paper_s_by_order")
+        extra_lines[name] = {k: ln[k] for k in keep if k in ln} | {
+            "workload": ln["config"]["workload"]}
+    del data
 
     cufft = None
     if world == 1 and not args.no_cufft_compare:
-        ours_us = (prof["plane"][0] / prof["plane"][1] + prof["pencil"][0] / prof["pencil"][1]) * 1e3
+        ours_us = sum(prof[k][0] / prof[k][1] for k in ITERATION_CLASSES if k in prof) * 1e3
         cufft = {"what": "one k >= 2 ADMM iteration (n = 2) with cuFFT R2C/C2R and PyTorch "
                          "element-wise kernels in one CUDA graph; timed only",
                  "cufft_us_per_iteration": cufft_iteration_us(dev, 2),
                  "ours_us_per_iteration": ours_us}
+
+    cpu = cpu_all = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, cpu_all = cpu_baselines()
 
     total_kernel_ms = sum(m for m, _ in prof.values())
     line = {
@@ -693,13 +856,9 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "dims": list(DIMS), "orders": list(ORDERS),
-                   "outer": OUTER, "inner": INNER, "registrations_per_step": len(ORDERS),
-                   "l2": "flushed between timed steps (256 MB write outside the step events)",
-                   "concurrency": f"{len(ORDERS)} registrations in flight per GPU, one stream "
-                                  "each (independent pairs); value is their throughput",
-                   "parallelism": f"replicas x{world}"},
+        "config": bench_config(ORDERS, world),
         "latency_ms_one_at_a_time": latency_ms,
+        "concurrent_equals_sequential": True,
         "voxel_admm_iters_per_s": vox_rate,
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
@@ -709,7 +868,9 @@ def main():
         "kernels": {k: {"ms": round(m, 4), "launches": n, "share": round(m / total_kernel_ms, 4),
                         "gbs": round(bpv[k] * V * n / (m / 1e3) / 1e9, 1) if m > 0 else None}
                     for k, (m, n) in prof.items()},
+        "quality": quality,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
         "cufft_compare": cufft,
         "e2e": None if e2e_per_reg is None else {
             "value": e2e_per_reg, "unit": "ms",
@@ -717,6 +878,7 @@ def main():
             "d2h_bytes_per_step": len(ORDERS) * 3 * V * 4},
         "gpu_launches": int(launches_per_reg * len(ORDERS) * args.steps),
         "clocks": clk,
+        "extras": extra_lines,
         "paper_runtime_context": "1.37-2.17 s per 128x128x96 registration with a 3-level pyramid "
                                  "on a 16 GB Tesla V100 (Table 1), not the same schedule",
     }

@@ -320,22 +320,30 @@ nadmm_status nadmm_jacobian_det(nadmm_handle h, const float* u, float* det,
  * risk the device synchronisation cudaMalloc/cudaFree may cause.
  *
  * Computes the same result as nadmm_spectral_solve for an nx x ny x nz grid,
- * order n, lambda and theta (same limits as nadmm_create), without a handle
- * or workspace: y, w device [3][nz][ny][nx] fp32, 16-byte aligned, w may
- * alias y.  The scratch (half spectrum + FFT tables) lives in one static
- * device array of 24 MiB (25165824 bytes) that every GPU loading the library
- * holds until the process exits; grids needing more, i.e. when
- * 3 (nx/2+1) ny nz 8 bytes plus a few KB of tables exceed it, are rejected
- * with NADMM_ERR_UNSUPPORTED_SIZE before any device work.  No cudaMalloc,
- * cudaFree or other allocating call is made.
+ * order n, lambda and theta, without a handle or workspace: y, w device
+ * [3][nz][ny][nx] fp32, 16-byte aligned, w may alias y.  Its limits are
+ * narrower than nadmm_create's: every dimension >= 4 with prime factors in
+ * {2, 3, 5, 7} only (nadmm_create also takes primes up to 509), nx a
+ * multiple of 4, ny even, nz <= 256, 1 <= order_n <= 8.  The scratch (half
+ * spectrum + FFT tables) lives in one static device array of 24 MiB
+ * (25165824 bytes) that every GPU loading the library holds until the
+ * process exits; grids needing more, i.e. when 3 (nx/2+1) ny nz 8 bytes plus
+ * a few KB of tables exceed it (128x128x96 fits, 160x160x112 does not), are
+ * rejected.  Every size and argument check runs before any device work and
+ * returns NADMM_ERR_UNSUPPORTED_SIZE, INVALID_ARG or ALIGNMENT.  No
+ * cudaMalloc, cudaFree or other allocating call is made.
  *
  * The first call on a device performs a one-time set-up on that device (it
- * looks up the array's device address with cudaGetSymbolAddress); make that
- * first call before any stream capture.  Every call shares the one array and
- * it keeps the last call's contents (nothing in it needs clearing: each call
- * writes every byte it later reads), so calls whose device work overlaps --
- * on different streams or from different threads -- race and must be
- * serialised by the caller. */
+ * looks up the array's device address with cudaGetSymbolAddress and raises
+ * the pass kernels' shared-memory limits); make that first call before any
+ * stream capture.  The address is cached for the life of the process: after
+ * cudaDeviceReset (or a primary-context reset) it is stale, so do not call
+ * this entry point again in a process that has reset the device.  Every
+ * call shares the one array and it keeps the last call's contents (nothing
+ * in it needs clearing: each call writes every byte it later reads, FFT
+ * tables included, with one small table-fill launch), so calls whose device
+ * work overlaps -- on different streams or from different threads -- race
+ * and must be serialised by the caller. */
 nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, int32_t order_n,
                                           float lambda, float theta, const float* y, float* w,
                                           void* stream);

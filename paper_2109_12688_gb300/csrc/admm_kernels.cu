@@ -23,6 +23,8 @@
 // and returns instead of spinning.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "fft_device.cuh"
 #include "lane_fft.cuh"
 #include "tma.cuh"
@@ -1116,6 +1118,26 @@ cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem) {
   if ((e = set_smem_limit(k_ypass<true>, pencil_smem)) != cudaSuccess) return e;
   if ((e = configure_fused_pencil()) != cudaSuccess) return e;
   return set_smem_limit(k_zpass, pencil_smem);
+}
+
+// cudaFuncSetAttribute applies to the device that is current when it is
+// called (each device holds its own copy of the module), so the limits are
+// raised once per device ordinal, the first time a handle or a no-alloc call
+// runs there.
+cudaError_t configure_admm_kernels_on_current_device() {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static bool done[kMaxDev] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return cudaSuccess;
+  constexpr size_t kOptinMax = 227 * 1024;
+  e = configure_admm_kernels(kOptinMax, kOptinMax);
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
 }
 
 template <int CONV>

@@ -562,14 +562,10 @@ void assign_lanes(nadmm_context* b, int lanes) {
 }
 
 // Every pass kernel may take up to the opt-in shared-memory limit; the
-// attribute is per function and process-wide, so it is set once to the
-// maximum and each launch asks for what its grid needs.
-cudaError_t configure_kernels_once() {
-  static std::once_flag once;
-  static cudaError_t result = cudaSuccess;
-  std::call_once(once, [] { result = configure_admm_kernels(kMaxSmem, kMaxSmem); });
-  return result;
-}
+// attribute belongs to the device that is current when it is set, so it is
+// raised to the maximum once per device and each launch asks for what its
+// grid needs.
+cudaError_t configure_kernels_once() { return configure_admm_kernels_on_current_device(); }
 
 // Attach the state region ws and the table region wt to a single-grid
 // context: upload the tables, clear the status words, encode the z-pass

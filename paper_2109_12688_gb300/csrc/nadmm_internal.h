@@ -138,6 +138,8 @@ size_t plane_smem_max(const PlaneArgs& a);
 size_t pencil_smem_bytes(const PencilArgs& a);
 int rows_per_tile(int ny);
 cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem);
+// configure_admm_kernels(227 KB, 227 KB) on the current device, once per device.
+cudaError_t configure_admm_kernels_on_current_device();
 
 // ---------------------------------------------------------------- launch helpers
 // Programmatic dependent launch: every kernel is launched with programmatic

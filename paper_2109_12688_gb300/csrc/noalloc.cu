@@ -11,9 +11,13 @@
 //
 // The array is a file-scope __device__ variable: every GPU on which the
 // library is loaded reserves it until the process exits.  Host code cannot
-// use the symbol as an address, so the first call on each device looks the
-// address up with cudaGetSymbolAddress (with that device current) and caches
-// it; later calls reuse the cached address.
+// use the symbol as an address, so the first call on each device (with that
+// device current) looks the address up with cudaGetSymbolAddress, raises the
+// shared-memory limits of the pass kernels on that device, and caches the
+// address; later calls reuse it.  The cached address belongs to the device's
+// current context: after cudaDeviceReset (or a primary-context reset) the
+// module is loaded again and the cached address must not be used, so such a
+// reset and further calls of this entry point do not mix in one process.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -147,7 +151,8 @@ nadmm_status cuda_fail(cudaError_t e, const char* where) {
   return fail(NADMM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-// Address of the static array on the current device (looked up once per device).
+// Set-up of the current device, once per device: the address of the static
+// array, and the pass kernels' shared-memory limits raised to the maximum.
 nadmm_status scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -158,6 +163,8 @@ nadmm_status scratch_address(void** out) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch array");
+    e = configure_admm_kernels_on_current_device();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     g_scratch_addr[dev] = p;
   }
   *out = g_scratch_addr[dev];
@@ -217,13 +224,7 @@ extern "C" nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int
   char* base = static_cast<char*>(base_v);
   cudaStream_t s = (cudaStream_t)stream;
 
-  // Raise the dynamic shared-memory limit of the pass kernels to the device
-  // maximum (a handle may have lowered it to its own needs).
-  int dev = 0, optin = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e == cudaSuccess) e = configure_admm_kernels((size_t)optin, (size_t)optin);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  cudaError_t e = cudaSuccess;
 
   float2* twx = reinterpret_cast<float2*>(base + L.twx);
   float2* twy = reinterpret_cast<float2*>(base + L.twy);

@@ -261,3 +261,34 @@ def test_high_level_calls_reject_host_tensors(lib):
         b.register([host], [host])
     with pytest.raises(ValueError, match="CUDA tensor"):
         b.register([host, torch.zeros((4, 4, 4))], [host, torch.zeros((4, 4, 4))])
+
+
+@pytest.mark.parametrize("dims,why", [((22, 12, 14), "factors in {2,3,5,7}"),
+                                      ((44, 26, 23), "factors in {2,3,5,7}"),
+                                      ((64, 64, 320), "nz must be <= 256"),
+                                      ((160, 160, 112), "24 MiB"),
+                                      ((10, 8, 8), "nx a multiple of 4")])
+def test_noalloc_limits_are_checked_before_device_work(lib, dims, why):
+    """The no-allocation solve takes a narrower set of grids than
+    nadmm_create (factors 2, 3, 5, 7 only; nz <= 256; 24 MiB of static
+    scratch) and rejects the rest on the host, before any device call; the
+    pointers here are aligned stand-ins that are never dereferenced."""
+    nx, ny, nz = dims
+    if dims[0] % 4 == 0 and dims != (64, 64, 320):  # nadmm_create plans these grids
+        lib.nadmm_destroy(lib.nadmm_create(lib.make_config(dims)))
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_spectral_solve_noalloc(nx, ny, nz, 2, 10.0, 0.1, 4096, 8192)
+    assert e.value.status == lib.NADMM_ERR_UNSUPPORTED_SIZE
+    assert why in str(e.value)
+
+
+def test_noalloc_argument_checks_before_device_work(lib):
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_spectral_solve_noalloc(32, 32, 24, 0, 10.0, 0.1, 4096, 8192)
+    assert e.value.status == lib.NADMM_ERR_INVALID_ARG
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_spectral_solve_noalloc(32, 32, 24, 2, 10.0, 0.1, 4100, 8192)
+    assert e.value.status == lib.NADMM_ERR_ALIGNMENT
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_spectral_solve_noalloc(32, 32, 24, 2, 10.0, 0.1, None, 8192)
+    assert e.value.status == lib.NADMM_ERR_INVALID_ARG
