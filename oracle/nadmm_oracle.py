@@ -60,7 +60,7 @@ __all__ = [
     "spectral_solve", "apply_periodic_laplacian", "admm_step", "admm",
     "trilinear", "warp", "central_gradient", "linearise", "compose",
     "bound_scale", "jacobian_determinant", "register", "admm_until", "energy",
-    "augmented_lagrangian", "dense_minimiser_l2",
+    "augmented_lagrangian", "dense_minimiser_l2", "admm_restart",
 ]
 
 
@@ -200,6 +200,61 @@ def admm(J, c, lam, theta, n, iters, s=2, eps=1e-6, accelerate=True,
     return hist if history else w_km1
 
 
+def admm_restart(J, c, lam, theta, n, iters, s=2, eps=1e-6, eta=0.999,
+                 history=False):
+    """Eq. 5 with adaptive restart (reading R20; not in the paper: the
+    restart rule of Goldstein et al.'s fast ADMM, whose O(1/k^2) rate the
+    paper cites after Eq. 5).
+
+    Combined residual of iteration k: c_k = ||w^k - w_hat^k||^2 +
+    ||b^k - b_hat^k||^2 over the grid (Goldstein et al.'s residual divided by
+    the common factor theta).  With the reference cbar (+inf before the
+    first test): if c_k < eta cbar, no restart and cbar = c_k; otherwise a
+    restart and cbar = cbar / eta.  A restart found at iteration k restarts
+    the momentum of the extrapolation that forms w_hat^{k+2}, b_hat^{k+2}
+    (one iteration late, the first that can see the grid-wide c_k): the
+    factor forming w_hat^j is beta_{j - r}, r the latest iteration whose
+    factor a restart set to zero (r = 1 from the start, as beta_0 = 0), so
+    the factors after a restart run 0, beta_1, beta_2, ...  eta = 0 restarts
+    at every test (plain ADMM); eta = inf never restarts (Eq. 5 as printed).
+
+    Returns w^{iters-1}, or with ``history`` a dict with lists "w", "b",
+    "w_hat", "b_hat" (per iteration), "factor" (factor forming w_hat^k) and
+    "restart" (iterations k whose test restarted)."""
+    J = np.asarray(J, np.float64)
+    c = np.asarray(c, np.float64)
+    _, beta = nesterov_sequence(max(iters, 1) + 1)
+    zero = np.zeros_like(J)
+    w_km1, w_km2, b_km1, b_km2 = zero, zero, zero, zero
+    r = 1                       # latest iteration whose factor is forced to 0
+    pending = []                # iterations at which a found restart takes effect
+    cbar = math.inf
+    hist = {"w": [], "b": [], "w_hat": [], "b_hat": [], "factor": [], "restart": []}
+    for k in range(iters):
+        if k in pending:
+            r = k
+        f = 0.0 if k == 0 else beta[k - r]
+        w_hat = w_km1 + f * (w_km1 - w_km2)
+        b_hat = b_km1 + f * (b_km1 - b_km2)
+        v = _v_step(w_hat - b_hat, J, c, theta, s, eps)
+        w = spectral_solve(v + b_hat, lam, theta, n)
+        b = b_hat + v - w
+        ck = float(((w - w_hat) ** 2).sum() + ((b - b_hat) ** 2).sum())
+        if eta > 0.0 and ck < eta * cbar:
+            cbar = ck
+        else:
+            cbar = cbar / eta if eta > 0.0 else cbar
+            pending.append(k + 2)
+            hist["restart"].append(k)
+        w_km2, b_km2 = w_km1, b_km1
+        w_km1, b_km1 = w, b
+        if history:
+            for key, val in (("w", w), ("b", b), ("w_hat", w_hat), ("b_hat", b_hat),
+                             ("factor", f)):
+                hist[key].append(val)
+    return hist if history else w_km1
+
+
 # ---------------------------------------------------------------- grid ops
 def trilinear(f, px, py, pz):
     """Trilinear interpolation of f [nz][ny][nx] at points (px, py, pz) in
@@ -329,7 +384,7 @@ def admm_until(J, c, lam, theta, n, max_iters, tol, s=2, eps=1e-6):
 def register(I0, I1, lam=10.0, theta=0.1, n=2, outer=5, inner=10, s=2,
              eps=1e-6, kappa=0.5, delta=1.0, accelerate=True,
              return_scales=False, u0=None, admm_tol=0.0, warp_tol=0.0,
-             return_counts=False):
+             return_counts=False, restart_eta=None):
     """Greedy diffeomorphic registration (Sec. 2, text after Eq. 2; Eq. 1
     with N = 1): u <- u0 (default 0); repeat ``outer`` times: linearise at
     the current warp of the original I1, run ``inner`` iterations of Eq. 5,
@@ -340,7 +395,8 @@ def register(I0, I1, lam=10.0, theta=0.1, n=2, outer=5, inner=10, s=2,
     early as in admm_until (then outer/inner are caps); the outer loop stops
     after the re-warp of step o when ||I1w_o - I1w_{o-1}||_2 <= warp_tol
     ||I1w_{o-1}||_2.  return_counts adds the list of ADMM iterations run per
-    outer step."""
+    outer step.  ``restart_eta`` (not None) runs each inner loop as
+    admm_restart with that eta (reading R20)."""
     I0 = np.asarray(I0, np.float64)
     I1 = np.asarray(I1, np.float64)
     u = np.zeros((3,) + I0.shape) if u0 is None else np.array(u0, np.float64)
@@ -350,6 +406,8 @@ def register(I0, I1, lam=10.0, theta=0.1, n=2, outer=5, inner=10, s=2,
     for o in range(outer):
         if admm_tol > 0.0:
             w, k = admm_until(J, c, lam, theta, n, inner, admm_tol, s, eps)
+        elif restart_eta is not None:
+            w, k = admm_restart(J, c, lam, theta, n, inner, s, eps, restart_eta), inner
         else:
             w, k = admm(J, c, lam, theta, n, inner, s, eps, accelerate), inner
         counts.append(k)

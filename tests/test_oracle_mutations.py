@@ -93,6 +93,13 @@ MUTATIONS = [
      "v = _v_step(w_hat + b_hat, J, c, theta, s, eps)"),
     (FWD, "J, c, I1w = linearise(I0, I1, u)\n    for o",
      "J, c, I1w = linearise(I0, I1, np.zeros_like(u))\n    for o"),
+    # adaptive restart (reading R20)
+    (FWD, "pending.append(k + 2)", "pending.append(k + 1)"),
+    (FWD, "            cbar = cbar / eta if eta > 0.0 else cbar", "            cbar = ck"),
+    (FWD, "ck = float(((w - w_hat) ** 2).sum() + ((b - b_hat) ** 2).sum())",
+     "ck = float(((w - w_hat) ** 2).sum())"),
+    (FWD, "f = 0.0 if k == 0 else beta[k - r]", "f = 0.0 if k == 0 else beta[k - r + 1]"),
+    (FWD, "        if k in pending:\n            r = k", "        if k in pending:\n            r = k - 1"),
     # threshold stopping (Sec. 4, second version)
     (FWD, "<= tol * np.sqrt((w_km1 ** 2).sum())", "<= tol * np.sqrt((w_km2 ** 2).sum())"),
     (FWD, "return w_km1, k + 1", "return w_km1, k"),

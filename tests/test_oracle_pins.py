@@ -592,3 +592,79 @@ def test_register_thresholds_reduce_to_caps_and_stop_early():
     u1 = O.register(p["fixed"], p["moving"], admm_tol=0.3, outer=len(counts), inner=6,
                     lam=10.0, theta=0.1, n=2)
     np.testing.assert_array_equal(u, u1)
+
+
+# ------------------------------------------------------------ adaptive restart (R20)
+def _weakly_convex_case(seed=3):
+    """theta << |J|^2: Eq. 5 as printed diverges here while plain ADMM
+    converges (|J| = 1 at every voxel, theta = 0.05)."""
+    rng = np.random.default_rng(seed)
+    J = rng.normal(size=(3, 4, 4, 4))
+    J /= np.sqrt((J ** 2).sum(0, keepdims=True))
+    c = 0.5 * rng.normal(size=(4, 4, 4))
+    return J, c, 1.0, 0.05, 1
+
+
+def test_restart_extremes_are_plain_and_printed_admm():
+    """eta = 0 restarts at every test: every momentum factor is 0, i.e. plain
+    ADMM; eta = inf never restarts: Eq. 5 as printed (same arithmetic,
+    bit-identical)."""
+    rng = np.random.default_rng(21)
+    J = rng.normal(scale=0.4, size=(3, 6, 5, 4))
+    c = rng.normal(scale=0.3, size=(6, 5, 4))
+    for n in (1, 2):
+        plain = O.admm(J, c, 2.0, 0.3, n, 9, accelerate=False)
+        assert np.array_equal(O.admm_restart(J, c, 2.0, 0.3, n, 9, eta=0.0), plain)
+        printed = O.admm(J, c, 2.0, 0.3, n, 9)
+        assert np.array_equal(O.admm_restart(J, c, 2.0, 0.3, n, 9, eta=math.inf), printed)
+
+
+def test_restart_makes_the_weakly_convex_case_converge():
+    J, c, lam, theta, n = _weakly_convex_case()
+    ref = O.dense_minimiser_l2(J, c, lam, n)
+    printed = O.admm(J, c, lam, theta, n, 300)
+    assert np.abs(printed).max() > 1e6                       # Eq. 5 as printed blows up
+    w = O.admm_restart(J, c, lam, theta, n, 300)
+    assert np.abs(w - ref).max() < 1e-6 * np.abs(ref).max()   # restart reaches the minimiser
+    plain = O.admm(J, c, lam, theta, n, 300, accelerate=False)
+    assert np.abs(w - ref).max() <= np.abs(plain - ref).max()  # and no slower than plain ADMM
+
+
+def test_restart_rule_against_the_iterates():
+    """The recorded factors follow the rule from residuals recomputed from the
+    recorded iterates: c_k = ||w^k - w_hat^k||^2 + ||b^k - b_hat^k||^2, a test
+    fails when c_k >= eta cbar (cbar then divided by eta, else cbar = c_k),
+    and a restart found at k zeroes the factor forming w_hat^{k+2}, after
+    which the factors run beta_1, beta_2, ..."""
+    J, c, lam, theta, n = _weakly_convex_case(5)
+    for eta in (0.999, 0.5):
+        _check_restart_rule(J, c, lam, theta, n, eta)
+
+
+def _check_restart_rule(J, c, lam, theta, n, eta):
+    h = O.admm_restart(J, c, lam, theta, n, 60, eta=eta, history=True)
+    _, beta = O.nesterov_sequence(61)
+    cbar, found = math.inf, []
+    for k in range(60):
+        ck = ((h["w"][k] - h["w_hat"][k]) ** 2).sum() + ((h["b"][k] - h["b_hat"][k]) ** 2).sum()
+        if ck < eta * cbar:
+            cbar = ck
+        else:
+            cbar /= eta
+            found.append(k)
+    assert found == h["restart"] and len(found) >= 3
+    last_zero = 1
+    for k in range(2, 60):
+        if k - 2 in found:
+            last_zero = k
+        assert h["factor"][k] == (0.0 if k == last_zero else beta[k - last_zero])
+        # the extrapolation really used that factor
+        np.testing.assert_allclose(h["w_hat"][k], h["w"][k - 1] + h["factor"][k]
+                                   * (h["w"][k - 1] - h["w"][k - 2]), rtol=0, atol=1e-12)
+
+
+def test_register_with_restart_matches_printed_when_never_triggered():
+    pair = synth.make_pair((16, 16, 12), seed=4)
+    a = O.register(pair["fixed"], pair["moving"], n=2, outer=2, inner=6, restart_eta=math.inf)
+    b = O.register(pair["fixed"], pair["moving"], n=2, outer=2, inner=6)
+    assert np.array_equal(a, b)
