@@ -93,6 +93,13 @@ typedef enum nadmm_status {
                                      shared memory) where it applies, instead of
                                      three kernels; nadmm_autotune tries both  */
 
+#define NADMM_FLAG_FOUR_PASS 0x400u /* run every ADMM iteration as four kernels
+                                     (plane pass, y-, z- and inverse y-pass) even
+                                     where the two-kernel slab path applies (one
+                                     cluster of three CTAs per z-plane doing the
+                                     x- and y-DFTs, then one z-pass); same
+                                     arithmetic, different rounding order       */
+
 typedef struct nadmm_config {
   int32_t nx, ny, nz;         /* grid (M, N, H); see NADMM_ERR_UNSUPPORTED_SIZE */
   int32_t order_n;            /* regulariser order n, 1..8 (Eq. 2)            */
@@ -451,7 +458,12 @@ nadmm_status nadmm_selftest_wait_timeout(nadmm_handle h, int32_t attempts, void*
 #define NADMM_KC_GRAD          6  /* gradient + residual                        */
 #define NADMM_KC_BOUND         7  /* velocity bound reduction                   */
 #define NADMM_KC_COMPOSE       8  /* composition u <- s w + u o (Id + s w)      */
-#define NADMM_KC_COUNT         9
+#define NADMM_KC_SLAB_FIRST    9  /* slab pass, k = 0                            */
+#define NADMM_KC_SLAB_K1      10  /* slab pass, k = 1                            */
+#define NADMM_KC_SLAB         11  /* slab pass, k >= 2 (x/y DFTs + point-wise)   */
+#define NADMM_KC_SLAB_FINAL   12  /* slab pass, final inverse x/y DFTs -> w^K    */
+#define NADMM_KC_ZSLAB        13  /* z-pass of the slab path (z-DFT, symbol)     */
+#define NADMM_KC_COUNT        14
 
 /* nadmm_register with direct launches on `stream`, a CUDA event recorded on
  * that stream before and after every kernel, and a stream synchronisation

@@ -30,29 +30,9 @@
 #include "tma.cuh"
 #include "nadmm_internal.h"
 #include "plan.h"
+#include "vstep.cuh"
 
 namespace nadmm {
-
-// ---------------------------------------------------------------- v-step
-// s = 2 (Eq. 6 middle, Sherman-Morrison): v = u - rho(u) J / (theta + |J|^2)
-// s = 1 (Eq. 6 top):  z = theta rho(u) / (|J|^2 + eps),
-//                     v = u - z / max(|z|, 1) * J / theta
-NADMM_HD void v_step(int data_term, float theta, float eps, const float (&J)[3], float c,
-                     const float (&u)[3], float (&v)[3]) {
-  float rho = J[0] * u[0] + J[1] * u[1] + J[2] * u[2] + c;
-  float jj = J[0] * J[0] + J[1] * J[1] + J[2] * J[2];
-  float f;
-  if (data_term == 2) {
-    f = rho / (theta + jj);
-  } else {
-    float z = theta * rho / (jj + eps);
-    float t = z / fmaxf(fabsf(z), 1.0f);
-    f = t / theta;
-  }
-  v[0] = u[0] - f * J[0];
-  v[1] = u[1] - f * J[1];
-  v[2] = u[2] - f * J[2];
-}
 
 // TMA / mbarrier helpers: tma.cuh
 
@@ -1117,6 +1097,7 @@ cudaError_t configure_admm_kernels(size_t plane_smem, size_t pencil_smem) {
   if ((e = set_smem_limit(k_ypass<false>, pencil_smem)) != cudaSuccess) return e;
   if ((e = set_smem_limit(k_ypass<true>, pencil_smem)) != cudaSuccess) return e;
   if ((e = configure_fused_pencil()) != cudaSuccess) return e;
+  if ((e = configure_slab_kernels()) != cudaSuccess) return e;
   return set_smem_limit(k_zpass, pencil_smem);
 }
 

@@ -46,6 +46,13 @@ struct nadmm_context {
   std::vector<int> posx;
   std::vector<float> Kx, Ky, Kz;
   std::vector<float> beta;   // beta_0 .. beta_{K-1}
+  // slab path (two kernels per ADMM iteration): nx/2-point x plan, its
+  // twiddles, positions and their inverse, and e^{-2 pi i k / nx}
+  bool slab = false;
+  AxisPlan pxh;
+  std::vector<float2> twxh, rtx;
+  std::vector<int> posxh, fqxh;
+  size_t o_twxh = 0, o_rtx = 0, o_posxh = 0, o_fqxh = 0;
   int R = 0;
   size_t V = 0, nkx = 0;
   size_t plane_smem = 0, pencil_smem = 0;
@@ -146,7 +153,7 @@ nadmm_status validate(const nadmm_config* c) {
   if (!(c->bound_kappa > 0.0f) || !(c->bound_delta > 0.0f))
     return fail(NADMM_ERR_INVALID_ARG, "bound_kappa and bound_delta must be > 0 (INFINITY disables)");
   if (c->flags & ~(NADMM_FLAG_NO_GRAPH | NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK |
-                   NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_PIPELINED_PLANE))
+                   NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_PIPELINED_PLANE | NADMM_FLAG_FOUR_PASS))
     return fail(NADMM_ERR_INVALID_ARG, "unknown flag bits");
   for (int ax = 0; ax < 3; ++ax)
     if (((c->flags >> NADMM_FLAG_LANE_SHIFT(ax)) & 3u) == 3u)
@@ -238,6 +245,37 @@ PencilArgs pencil_args(const nadmm_context* h) {
   return a;
 }
 
+SlabArgs slab_args(const nadmm_context* h) {
+  SlabArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.spec = h->at<float2>(h->o_spec);
+  a.y = h->at<float>(h->o_y);
+  a.wp = h->at<float>(h->o_wp);
+  a.bp = h->at<float>(h->o_bp);
+  a.J = h->at<float>(h->o_J);
+  a.c = h->at<float>(h->o_c);
+  a.twx = h->tab<float2>(h->o_twxh);
+  a.rtx = h->tab<float2>(h->o_rtx);
+  a.posx = h->tab<int>(h->o_posxh);
+  a.fqx = h->tab<int>(h->o_fqxh);
+  a.twy = h->tab<float2>(h->o_twy);
+  a.status = h->tab<unsigned>(h->o_red) + 2;
+  a.nx = h->cfg.nx;
+  a.ny = h->cfg.ny;
+  a.nz = h->cfg.nz;
+  a.nkx = (int)h->nkx;
+  a.mx = h->cfg.nx / 2;
+  a.qdiv = make_fastdiv((uint32_t)(h->cfg.nx / 4));
+  a.xr1 = h->pxh.radix[0];
+  a.xr2 = h->pxh.radix[1];
+  a.yr1 = h->py.radix[0];
+  a.yr2 = h->py.radix[1];
+  a.theta = h->cfg.theta;
+  a.eps = h->cfg.eps;
+  a.data_term = h->cfg.data_term;
+  return a;
+}
+
 Dims dims_of(const nadmm_context* h) { return Dims{h->cfg.nx, h->cfg.ny, h->cfg.nz}; }
 
 #define TRY(expr)                                  \
@@ -288,9 +326,46 @@ thread_local Profiler* g_prof = nullptr;
 // u^k = w_hat^k - b_hat^k of every iteration go to hist_w + k 3V and
 // hist_u + k 3V: the plane passes write them directly (w^{k-1} by the tile
 // stores, u^k by the point-wise step), w^{K-1} comes from the final pass.
+// The same iterations on the slab path (two kernels per iteration).
+cudaError_t enqueue_inner_slab(nadmm_context* h, const PlaneArgs& first, int in_first, bool prev_first,
+                               int k0, int steps, const float* J, const float* c, float* w_out,
+                               float* b_out, cudaStream_t s) {
+  SlabArgs a = slab_args(h);
+  a.J = J;
+  a.c = c;
+  SlabArgs f = a;
+  int mode = SLAB_FIRST;
+  if (in_first == IN_STATE) {
+    mode = prev_first ? SLAB_STATE_PREV : SLAB_STATE;
+    f.w_in = first.w_in;
+    f.b_in = first.b_in;
+    f.wprev_in = first.wprev_in;
+    f.bprev_in = first.bprev_in;
+  }
+  f.beta = beta_for(h, k0);
+  KLAUNCH(in_first == IN_NONE ? NADMM_KC_SLAB_FIRST : (prev_first ? NADMM_KC_SLAB : NADMM_KC_SLAB_K1),
+          s, launch_slab(mode, f, s));
+  const PencilArgs pa = pencil_args(h);
+  for (int k = k0 + 1; k < k0 + steps; ++k) {
+    KLAUNCH(NADMM_KC_ZSLAB, s, launch_zslab(pa, s));
+    a.beta = beta_for(h, k);
+    KLAUNCH(k >= 2 ? NADMM_KC_SLAB : NADMM_KC_SLAB_K1, s,
+            launch_slab(k >= 2 ? SLAB_SPEC_PREV : SLAB_SPEC, a, s));
+  }
+  KLAUNCH(NADMM_KC_ZSLAB, s, launch_zslab(pa, s));
+  SlabArgs fin = a;
+  fin.w_out = w_out;
+  fin.b_out = b_out;
+  if (b_out == nullptr) fin.y = nullptr;
+  KLAUNCH(NADMM_KC_SLAB_FINAL, s, launch_slab(SLAB_FINAL, fin, s));
+  return cudaSuccess;
+}
+
 cudaError_t enqueue_inner(nadmm_context* h, PlaneArgs first, int in_first, bool prev_first, int k0,
                           int steps, const float* J, const float* c, float* w_out, float* b_out,
                           cudaStream_t s, float* hist_w = nullptr, float* hist_u = nullptr) {
+  if (h->slab && hist_w == nullptr && !thresholds(h) && (in_first == IN_NONE || in_first == IN_STATE))
+    return enqueue_inner_slab(h, first, in_first, prev_first, k0, steps, J, c, w_out, b_out, s);
   const size_t F3 = 3 * h->V;
   auto hw = [&](int k) { return hist_w + (size_t)k * F3; };
   first.J = J;
@@ -463,6 +538,24 @@ nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
   h->Ky = symbol_by_position(h->py);
   h->Kz = symbol_by_position(h->pz);
   compute_beta(h);
+  {
+    const int mx = cfg->nx / 2;
+    if (!(cfg->flags & NADMM_FLAG_FOUR_PASS) && mx % 8 == 0) {
+      two_stage_plan(mx, mx / 8, 8, h->pxh);
+      h->slab = slab_supported(cfg->nx, cfg->ny, cfg->nz, h->pxh, h->py, h->pz);
+    }
+    if (h->slab) {
+      h->twxh = axis_twiddles(h->pxh);
+      h->posxh = pos_table(h->pxh);
+      h->fqxh.assign(mx, 0);
+      for (int k = 0; k < mx; ++k) h->fqxh[h->posxh[k]] = k;
+      const double two_pi = 6.283185307179586476925286766559;
+      for (int k = 0; k <= mx; ++k) {
+        const double a = -two_pi * (double)k / (double)cfg->nx;
+        h->rtx.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+      }
+    }
+  }
   const size_t V = h->V;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -505,6 +598,12 @@ nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
   h->o_Kx = take(h->Kx.size() * sizeof(float));
   h->o_Ky = take(h->Ky.size() * sizeof(float));
   h->o_Kz = take(h->Kz.size() * sizeof(float));
+  if (h->slab) {
+    h->o_twxh = take(h->twxh.size() * sizeof(float2));
+    h->o_rtx = take(h->rtx.size() * sizeof(float2));
+    h->o_posxh = take(h->posxh.size() * sizeof(int));
+    h->o_fqxh = take(h->fqxh.size() * sizeof(int));
+  }
   // the tape belongs to the pair (it must outlive other pairs' use of a
   // shared state region), so it sits with the tables
   if (cfg->flags & NADMM_FLAG_SAVE_FOR_BACKWARD) {
@@ -583,9 +682,14 @@ nadmm_status attach(nadmm_context* h, char* ws, char* wt) {
       {h->o_Kx, h->Kx.data(), h->Kx.size() * sizeof(float)},
       {h->o_Ky, h->Ky.data(), h->Ky.size() * sizeof(float)},
       {h->o_Kz, h->Kz.data(), h->Kz.size() * sizeof(float)},
+      {h->o_twxh, h->twxh.data(), h->twxh.size() * sizeof(float2)},
+      {h->o_rtx, h->rtx.data(), h->rtx.size() * sizeof(float2)},
+      {h->o_posxh, h->posxh.data(), h->posxh.size() * sizeof(int)},
+      {h->o_fqxh, h->fqxh.data(), h->fqxh.size() * sizeof(int)},
   };
   cudaError_t e = cudaSuccess;
   for (const Up& u : ups) {
+    if (u.n == 0) continue;
     e = cudaMemcpy(wt + u.off, u.src, u.n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) break;
   }
@@ -1272,6 +1376,20 @@ nadmm_status nadmm_spectral_solve(nadmm_handle h, const float* y, float* w, void
   if (st != NADMM_OK) return st;
   if ((st = check_dev_ptrs({y, w})) != NADMM_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  if (h->slab) {
+    SlabArgs f = slab_args(h);
+    f.w_in = y;
+    cudaError_t e = launch_slab(SLAB_FIELD, f, s);
+    if (e == cudaSuccess) e = launch_zslab(pencil_args(h), s);
+    if (e == cudaSuccess) {
+      SlabArgs fin = slab_args(h);
+      fin.y = nullptr;
+      fin.w_out = w;
+      fin.b_out = nullptr;
+      e = launch_slab(SLAB_FINAL, fin, s);
+    }
+    return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "nadmm_spectral_solve");
+  }
   PlaneArgs a = plane_args(h);
   a.y = nullptr;
   a.w_in = y;

@@ -91,6 +91,62 @@ struct PencilArgs {
   int fused;               // 1: one fused y/z/y kernel (pencil_fused.cu) runs the pass
 };
 
+// ---------------------------------------------------------------- slab path
+// Two kernels per ADMM iteration on the spectrum layout [z][3][ny][nkx]:
+//   slab pass: one cluster of three CTAs per z-plane, CTA c holding the whole
+//       half-spectrum plane of component c in shared memory: inverse y- and
+//       x-DFTs, the point-wise part of the iteration (every CTA takes a third
+//       of the plane's voxels for all three components, reading and writing
+//       the other CTAs' planes through distributed shared memory), forward x-
+//       and y-DFTs;
+//   z-pass: z-DFT, multiply by 1/(1 + gamma K^n)/(nx ny nz), inverse z-DFT.
+enum SlabMode : int {
+  SLAB_FIRST = 0,       // k = 0: w_hat^0 = b_hat^0 = 0, no spectrum read
+  SLAB_SPEC = 1,        // k = 1: spectrum of y^0 in, beta_0 = 0
+  SLAB_SPEC_PREV = 2,   // k >= 2: spectrum in, w^{k-2}, b^{k-2} from the state slots
+  SLAB_FINAL = 3,       // inverse transforms only: w^{K-1} (and b^{K-1}) out
+  SLAB_FIELD = 4,       // forward transforms of a given field (spectral solve)
+  SLAB_STATE = 5,       // k = 1 from explicit buffers w^{k-1}, b^{k-1}
+  SLAB_STATE_PREV = 6,  // k >= 2 from explicit buffers w^{k-1}, b^{k-1}, w^{k-2}, b^{k-2}
+};
+
+struct SlabArgs {
+  float2* spec;            // [nz][3][ny][nkx] half spectrum (in/out)
+  float* y;                // [3][V] y = v + b_hat (in/out); FINAL: null unless b_out is wanted
+  float* wp;               // [3][V] w state slot (in: w^{k-2}, out: w^{k-1})
+  float* bp;               // [3][V] b state slot
+  const float* J;          // [3][V]
+  const float* c;          // [V]
+  const float* w_in;       // FIELD: the field; STATE*: w^{k-1}
+  const float* b_in;       // STATE*: b^{k-1}
+  const float* wprev_in;   // STATE2: w^{k-2}
+  const float* bprev_in;   // STATE2: b^{k-2}
+  float* w_out;            // FINAL: w^{K-1}
+  float* b_out;            // FINAL: b^{K-1} = y - w^{K-1}, or null
+  const float2* twx;       // stage twiddles of the nx/2-point lane plan [xr1, xr2]
+  const float2* rtx;       // e^{-2 pi i k / nx}, k = 0..nx/2
+  const int* posx;         // position holding frequency k (k < nx/2) after the forward DFT
+  const int* fqx;          // frequency held at position p (inverse of posx)
+  const float2* twy;       // stage twiddles of the y lane plan [yr1, yr2]
+  unsigned* status;        // device status word (bit 1: a bounded wait expired) or null
+  FastDiv qdiv;            // division by nx / 4 (voxel quads per row)
+  int nx, ny, nz, nkx, mx;  // mx = nx / 2
+  int xr1, xr2, yr1, yr2;
+  float beta, theta, eps;
+  int data_term;
+};
+
+// Whether the slab path has kernels for this grid and plans (x: nx/2 split
+// [xr1, 8]; y, z: lane plans), and its shared memory per CTA.
+bool slab_supported(int nx, int ny, int nz, const AxisPlan& pxh, const AxisPlan& py,
+                    const AxisPlan& pz);
+size_t slab_smem_bytes(const SlabArgs& a);
+cudaError_t launch_slab(int mode, const SlabArgs& a, cudaStream_t s);
+// z-pass of the slab layout (uses spec, twz, Kx, Ky, Kz, pz, ny, nz, nkx,
+// order_n, gamma, scale of the pencil arguments)
+cudaError_t launch_zslab(const PencilArgs& a, cudaStream_t s);
+cudaError_t configure_slab_kernels();
+
 constexpr unsigned kStatusNonfinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;
 

@@ -124,6 +124,29 @@ inline bool factor_axis(int n, AxisPlan& p, bool lane_plan = false, int lane_fir
   return true;
 }
 
+// The two-stage plan [r1, r2] of n = r1 r2 (a lane plan when r2 is 8 or 16).
+inline void two_stage_plan(int n, int r1, int r2, AxisPlan& p) {
+  p.n = n;
+  p.nst = 2;
+  const int rad[2] = {r1, r2};
+  int L = n, off = 0;
+  for (int i = 0; i < kMaxStages; ++i) {
+    if (i < 2) {
+      p.radix[i] = rad[i];
+      p.L[i] = L;
+      p.m[i] = L / rad[i];
+      p.tw_off[i] = off;
+      if (p.m[i] > 1) off += (rad[i] - 1) * p.m[i];
+      L /= rad[i];
+    } else {
+      p.radix[i] = 1; p.L[i] = 1; p.m[i] = 1; p.tw_off[i] = off;
+    }
+    p.root_off[i] = -1;
+    p.mdiv[i] = make_fastdiv((uint32_t)p.m[i]);
+  }
+  p.tw_count = off > 0 ? off : 1;
+}
+
 // Stage twiddles: stage i holds w_{L_i}^{n1 k} at [(k-1) m_i + n1].
 inline std::vector<float2> axis_twiddles(const AxisPlan& p) {
   std::vector<float2> tw;

@@ -1,0 +1,531 @@
+// The ADMM iteration of Eq. 5 in two kernels ("slab path").
+//
+// The w-step (Eq. 5 line 2, Eq. 6 last line) is a 3D real DFT, a division
+// by 1 + (lambda/theta) K^n in the spectrum and the inverse DFT.  Here the
+// half spectrum lives as [z][component][y][kx] and one iteration is
+//
+//   slab pass  (one cluster of three CTAs per z-plane; CTA c holds the whole
+//              ny x (nx/2+1) half-spectrum plane of component c in shared
+//              memory):
+//     A  inverse y-DFT of the plane's columns, inverse x-DFT of its rows
+//        (real output, in place) -> w^{k-1} of component c;
+//     B  point-wise: b^{k-1} = y^{k-1} - w^{k-1} (Eq. 5 line 3), the
+//        Nesterov extrapolation (lines 4-6), the closed-form v-step (Eq. 6,
+//        s = 1 / 2) and y^k = v^k + b_hat^k.  The v-step couples the three
+//        components at each voxel, so CTA r of the cluster takes a third of
+//        the plane's voxels for all three components and reads / writes the
+//        other CTAs' planes through distributed shared memory;
+//     C  forward x-DFT of the rows, forward y-DFT of the columns, store;
+//   z-pass: forward z-DFT, multiply by 1/(1 + gamma K^n)/(nx ny nz), inverse
+//     z-DFT, per (component, y, kx) column.
+//
+// Real x-DFTs of length nx use one complex DFT of length nx/2 per row: the
+// even and odd samples form z[m] = x[2m] + i x[2m+1]; the forward spectrum
+// is X_k = E_k + e^{-2 pi i k/nx} O_k with E_k = (Z_k + conj Z_{M-k})/2,
+// O_k = (Z_k - conj Z_{M-k})/(2i); the inverse forms Z_k = (X_k + conj
+// X_{M-k}) + i e^{+2 pi i k/nx} (X_k - conj X_{M-k}) and transforms back
+// (M = nx/2, unnormalised both ways).  Each row is held by a group of 8
+// lanes (lane FFT [xr1, 8]); the row's nx reals occupy nx/2 of its nx/2+1
+// complex slots, starting at slot (y & 1) so that every real row starts on a
+// 16-byte boundary (nx/2 + 1 is odd).
+//
+// Every wait on a bulk copy is bounded; on expiry a CTA records the status
+// bit and still takes part in both cluster barriers, so no peer waits on it.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "fft_device.cuh"
+#include "lane_fft.cuh"
+#include "nadmm_internal.h"
+#include "plan.h"
+#include "tma.cuh"
+#include "vstep.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace nadmm {
+
+constexpr int kSlabThreads = 256;
+constexpr int kSlabWarps = kSlabThreads / 32;
+constexpr int kSlabPad = 8;       // padding of an exchange line (float2)
+constexpr int kSlabXR2 = 8;       // lanes per row of the x-DFT
+
+// Exchange space of one warp (float2): 32/xr2 rows or 32/yr2 columns.
+NADMM_HD size_t slab_xch_per_warp(const SlabArgs& a) {
+  const size_t x = (size_t)(32 / kSlabXR2) * (a.mx + kSlabPad);
+  const size_t y = (size_t)(32 / a.yr2) * (a.ny + kSlabPad);
+  return x > y ? x : y;
+}
+
+// [mbarrier, 16 B][plane: ny nkx float2][exchange: kSlabWarps warps]
+size_t slab_smem_bytes(const SlabArgs& a) {
+  return 16 + (size_t)a.ny * a.nkx * sizeof(float2) +
+         (size_t)kSlabWarps * slab_xch_per_warp(a) * sizeof(float2);
+}
+
+#if defined(__CUDA_ARCH__)
+// ---------------------------------------------------------------- x-DFT of rows
+template <int R1, int R2>
+__device__ __forceinline__ void row_inverse(const SlabArgs& a, float2* row, float2* buf, int l,
+                                            unsigned gmask, int y) {
+  constexpr int M = R1 * R2;
+  for (int b = l; b < R1; b += R2) {
+    float2 w[R2];
+#pragma unroll
+    for (int j = 0; j < R2; ++j) {
+      const int k = __ldg(a.fqx + b * R2 + j);
+      const float2 xa = row[k], xb = row[M - k];
+      const float2 A = make_float2(xa.x + xb.x, xa.y - xb.y);  // X_k + conj X_{M-k}
+      const float2 D = make_float2(xa.x - xb.x, xa.y + xb.y);  // X_k - conj X_{M-k}
+      const float2 B = cmulc(D, __ldg(a.rtx + k));             // D e^{+2 pi i k / nx}
+      w[j] = make_float2(A.x - B.y, A.y + B.x);                // A + i B
+    }
+    dft<R2, true>(w);
+#pragma unroll
+    for (int j = 0; j < R2; ++j) buf[swz<R2>(b * R2 + j)] = w[j];
+  }
+  __syncwarp(gmask);
+  float2 v[R1];
+#pragma unroll
+  for (int k = 0; k < R1; ++k) v[k] = buf[swz<R2>(l + R2 * k)];
+  lane_stage1<R1, R2, true>(v, a.twx, l);
+  float2* re = row + (y & 1);
+#pragma unroll
+  for (int j = 0; j < R1; ++j) re[l + R2 * j] = v[j];
+  __syncwarp(gmask);
+}
+
+template <int R1, int R2>
+__device__ __forceinline__ void row_forward(const SlabArgs& a, float2* row, float2* buf, int l,
+                                            unsigned gmask, int y) {
+  constexpr int M = R1 * R2;
+  const float2* re = row + (y & 1);
+  float2 v[R1];
+#pragma unroll
+  for (int j = 0; j < R1; ++j) v[j] = re[l + R2 * j];
+  lane_stage1<R1, R2, false>(v, a.twx, l);
+#pragma unroll
+  for (int k = 0; k < R1; ++k) buf[swz<R2>(l + R2 * k)] = v[k];
+  __syncwarp(gmask);
+  lane_stage2<R1, R2, false>(buf, l);
+  __syncwarp(gmask);
+  for (int k = l; k <= M; k += R2) {
+    const int k1 = (k == M) ? 0 : k;
+    const int k2 = (k == 0 || k == M) ? 0 : M - k;
+    const float2 zk = buf[swz<R2>(__ldg(a.posx + k1))];
+    const float2 zm = buf[swz<R2>(__ldg(a.posx + k2))];
+    const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    row[k] = cadd(E, cmul(O, __ldg(a.rtx + k)));
+  }
+  __syncwarp(gmask);
+}
+
+// All rows of the plane, groups of R2 lanes per row.
+template <int R1, int R2>
+__device__ __noinline__ void slab_rows(const SlabArgs& a, float2* plane, float2* xch, bool inv) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int G = 32 / R2;
+  const int g = lane / R2, l = lane % R2;
+  const unsigned gmask = ((1u << R2) - 1u) << (g * R2);
+  float2* buf = xch + (size_t)warp * slab_xch_per_warp(a) + (size_t)g * (a.mx + kSlabPad);
+  for (int y0 = warp * G; y0 < a.ny; y0 += kSlabWarps * G) {
+    const int y = y0 + g;
+    if (y < a.ny) {  // uniform over the group
+      float2* row = plane + (size_t)y * a.nkx;
+      if (inv)
+        row_inverse<R1, R2>(a, row, buf, l, gmask, y);
+      else
+        row_forward<R1, R2>(a, row, buf, l, gmask, y);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- y-DFT of columns
+template <int R1, int R2>
+__device__ __noinline__ void slab_cols(const SlabArgs& a, float2* plane, float2* xch, bool inv) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int G = 32 / R2;
+  const int g = lane / R2, l = lane % R2;
+  const unsigned gmask = (R2 == 32 ? 0xffffffffu : ((1u << R2) - 1u)) << (g * R2);
+  float2* buf = xch + (size_t)warp * slab_xch_per_warp(a) + (size_t)g * (a.ny + kSlabPad);
+  const int st = a.nkx;
+  for (int c0 = warp * G; c0 < a.nkx; c0 += kSlabWarps * G) {
+    const int kx = c0 + g;
+    if (kx >= a.nkx) continue;  // uniform over the group
+    float2* col = plane + kx;
+    float2 v[R1];
+    if (!inv) {
+#pragma unroll
+      for (int j = 0; j < R1; ++j) v[j] = col[(l + R2 * j) * st];
+      lane_stage1<R1, R2, false>(v, a.twy, l);
+#pragma unroll
+      for (int k = 0; k < R1; ++k) buf[swz<R2>(l + R2 * k)] = v[k];
+      __syncwarp(gmask);
+      lane_stage2<R1, R2, false>(buf, l);
+      __syncwarp(gmask);
+#pragma unroll
+      for (int k = 0; k < R1; ++k) col[(l + R2 * k) * st] = buf[swz<R2>(l + R2 * k)];
+    } else {
+#pragma unroll
+      for (int k = 0; k < R1; ++k) buf[swz<R2>(l + R2 * k)] = col[(l + R2 * k) * st];
+      __syncwarp(gmask);
+      lane_stage2<R1, R2, true>(buf, l);
+      __syncwarp(gmask);
+#pragma unroll
+      for (int k = 0; k < R1; ++k) v[k] = buf[swz<R2>(l + R2 * k)];
+      lane_stage1<R1, R2, true>(v, a.twy, l);
+#pragma unroll
+      for (int j = 0; j < R1; ++j) col[(l + R2 * j) * st] = v[j];
+    }
+    __syncwarp(gmask);
+  }
+}
+
+#define NADMM_SLAB_X_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(12) X(14) X(16)
+
+__device__ __forceinline__ void rows_rt(const SlabArgs& a, float2* plane, float2* xch, bool inv) {
+#define X(A) \
+  if (a.xr1 == A) { slab_rows<A, kSlabXR2>(a, plane, xch, inv); return; }
+  NADMM_SLAB_X_CASES(X)
+#undef X
+}
+
+__device__ __forceinline__ void cols_rt(const SlabArgs& a, float2* plane, float2* xch, bool inv) {
+#define X(A, B) \
+  if (a.yr1 == A && a.yr2 == B) { slab_cols<A, B>(a, plane, xch, inv); return; }
+  NADMM_LANE_CASES(X)
+#undef X
+}
+
+// ---------------------------------------------------------------- point-wise step
+__device__ __forceinline__ float4 f4sub(float4 p, float4 q) {
+  return make_float4(p.x - q.x, p.y - q.y, p.z - q.z, p.w - q.w);
+}
+__device__ __forceinline__ float4 f4extra(float4 p, float4 q, float beta) {  // p + beta (p - q)
+  return make_float4(p.x + beta * (p.x - q.x), p.y + beta * (p.y - q.y), p.z + beta * (p.z - q.z),
+                     p.w + beta * (p.w - q.w));
+}
+__device__ __forceinline__ float f4get(const float4& v, int e) {
+  return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void f4set(float4& v, int e, float x) {
+  if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
+}
+
+// Real row y of a plane (x0 a multiple of 4).
+__device__ __forceinline__ float4* real_quad(float2* plane, int nkx, int y, int x0) {
+  return reinterpret_cast<float4*>(reinterpret_cast<float*>(plane + (size_t)y * nkx + (y & 1)) + x0);
+}
+
+// The coupled point-wise step on voxel quads [q0, q1) of the plane at z for
+// all three components (planes[c] is component c's plane, local or remote).
+template <int MODE>
+__device__ __forceinline__ void slab_pointwise(const SlabArgs& a, float2* const (&planes)[3], int z,
+                                               int q0, int q1) {
+  const size_t V = (size_t)a.nx * a.ny * a.nz;
+  const int qrow = a.nx >> 2;
+  const bool prev = (MODE == SLAB_SPEC_PREV) || (MODE == SLAB_STATE_PREV);
+  for (int q = q0 + (int)threadIdx.x; q < q1; q += kSlabThreads) {
+    const int yy = (int)fdiv((uint32_t)q, a.qdiv);
+    const int x0 = (q - yy * qrow) << 2;
+    const size_t vox = ((size_t)z * a.ny + yy) * a.nx + x0;
+    float4 wk1[3], bk1[3], wh[3], bh[3], Jq[3];
+    const float4 cq = __ldg(reinterpret_cast<const float4*>(a.c + vox));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t i = c * V + vox;
+      Jq[c] = __ldg(reinterpret_cast<const float4*>(a.J + i));
+      if (MODE == SLAB_FIRST) {
+        wk1[c] = bk1[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else if (MODE == SLAB_STATE || MODE == SLAB_STATE_PREV) {
+        wk1[c] = __ldg(reinterpret_cast<const float4*>(a.w_in + i));
+        bk1[c] = __ldg(reinterpret_cast<const float4*>(a.b_in + i));
+      } else {
+        wk1[c] = *real_quad(planes[c], a.nkx, yy, x0);
+        bk1[c] = f4sub(*reinterpret_cast<const float4*>(a.y + i), wk1[c]);
+      }
+      if (prev) {
+        const float4 wq = (MODE == SLAB_STATE_PREV)
+                              ? __ldg(reinterpret_cast<const float4*>(a.wprev_in + i))
+                              : *reinterpret_cast<const float4*>(a.wp + i);
+        const float4 bq = (MODE == SLAB_STATE_PREV)
+                              ? __ldg(reinterpret_cast<const float4*>(a.bprev_in + i))
+                              : *reinterpret_cast<const float4*>(a.bp + i);
+        wh[c] = f4extra(wk1[c], wq, a.beta);
+        bh[c] = f4extra(bk1[c], bq, a.beta);
+      } else {
+        wh[c] = wk1[c];
+        bh[c] = bk1[c];
+      }
+      if (MODE != SLAB_FIRST) {  // w^{k-1}, b^{k-1} into the state slots
+        *reinterpret_cast<float4*>(a.wp + i) = wk1[c];
+        *reinterpret_cast<float4*>(a.bp + i) = bk1[c];
+      }
+    }
+    float4 yn[3];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float Jv[3], u[3], v[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Jv[c] = f4get(Jq[c], e);
+        u[c] = f4get(wh[c], e) - f4get(bh[c], e);
+      }
+      v_step(a.data_term, a.theta, a.eps, Jv, f4get(cq, e), u, v);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) f4set(yn[c], e, v[c] + f4get(bh[c], e));
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      *reinterpret_cast<float4*>(a.y + c * V + vox) = yn[c];
+      *real_quad(planes[c], a.nkx, yy, x0) = yn[c];
+    }
+  }
+}
+#endif
+
+// MODE: SLAB_FIRST, SLAB_SPEC (k = 1), SLAB_SPEC_PREV (k >= 2), SLAB_FINAL,
+// SLAB_FIELD, SLAB_STATE (k = 1), SLAB_STATE_PREV (k >= 2).
+template <int MODE>
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kSlabThreads, 2)
+    k_slab(const __grid_constant__ SlabArgs a) {
+#if defined(__CUDA_ARCH__)
+  constexpr bool kInverse = (MODE == SLAB_SPEC || MODE == SLAB_SPEC_PREV || MODE == SLAB_FINAL);
+  constexpr bool kForward = (MODE != SLAB_FINAL);
+  constexpr bool kCoupled = (MODE != SLAB_FINAL && MODE != SLAB_FIELD);
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  float2* plane = reinterpret_cast<float2*>(smem + 16);
+  float2* xch = plane + (size_t)a.ny * a.nkx;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int comp = (int)cluster.block_rank();
+  const int z = (int)(blockIdx.x / 3);
+  const int tid = threadIdx.x;
+  const uint32_t plane_bytes = (uint32_t)((size_t)a.ny * a.nkx * sizeof(float2));
+  float2* gplane = a.spec + ((size_t)z * 3 + comp) * a.ny * a.nkx;
+  if (kInverse) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      fence_barrier_init();
+    }
+    __syncthreads();
+  }
+  pdl_wait();  // the spectrum, J and c come from the kernels before
+  pdl_trigger();
+  if (kInverse) {
+    if (tid == 0) {
+      mbar_expect_tx(bar, plane_bytes);
+      bulk_load(plane, gplane, plane_bytes, bar);
+    }
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0));
+    if (!ok) {
+      if (tid == 0 && a.status != nullptr) atomicOr(a.status, kStatusTimeout);
+      mbar_wait_bounded(bar, 0);  // let the copy land before the plane is touched
+    }
+    cols_rt(a, plane, xch, true);
+    __syncthreads();
+    rows_rt(a, plane, xch, true);
+  }
+  const size_t V = (size_t)a.nx * a.ny * a.nz;
+  if (kCoupled) {
+    cluster.sync();  // every component's plane holds w^{k-1} (or is to be written)
+    float2* const planes[3] = {cluster.map_shared_rank(plane, 0), cluster.map_shared_rank(plane, 1),
+                               cluster.map_shared_rank(plane, 2)};
+    const int Q = a.ny * (a.nx >> 2);
+    const int q0 = (int)((long long)Q * comp / 3), q1 = (int)((long long)Q * (comp + 1) / 3);
+    slab_pointwise<MODE>(a, planes, z, q0, q1);
+    cluster.sync();  // every plane holds y^k; no remote access after this
+  } else {
+    __syncthreads();
+    const int Q = a.ny * (a.nx >> 2);
+    const int qrow = a.nx >> 2;
+    for (int q = tid; q < Q; q += kSlabThreads) {
+      const int yy = (int)fdiv((uint32_t)q, a.qdiv);
+      const int x0 = (q - yy * qrow) << 2;
+      const size_t i = comp * V + ((size_t)z * a.ny + yy) * a.nx + x0;
+      float4* rq = real_quad(plane, a.nkx, yy, x0);
+      if (MODE == SLAB_FIELD) {
+        *rq = __ldg(reinterpret_cast<const float4*>(a.w_in + i));
+      } else {  // FINAL
+        const float4 w = *rq;
+        *reinterpret_cast<float4*>(a.w_out + i) = w;
+        if (a.b_out != nullptr)
+          *reinterpret_cast<float4*>(a.b_out + i) = f4sub(*reinterpret_cast<const float4*>(a.y + i), w);
+      }
+    }
+    __syncthreads();
+  }
+  if (kForward) {
+    rows_rt(a, plane, xch, false);
+    __syncthreads();
+    cols_rt(a, plane, xch, false);
+    fence_proxy_async();  // the plane's generic-proxy writes, seen by the bulk store
+    __syncthreads();
+    if (tid == 0) {
+      bulk_store(gplane, plane, plane_bytes);
+      bulk_commit();
+      bulk_wait_read();  // shared memory must stay until the store has read it
+    }
+  }
+#endif
+}
+
+// ---------------------------------------------------------------- z-pass
+constexpr int kZSlabThreads = 128;  // 4 independent warps
+
+template <int R1, int R2>
+constexpr int zslab_min_blocks() {
+  return (R2 == 8 && R1 <= 12) ? 8 : 6;
+}
+
+// One warp: 32/R2 consecutive kx columns of one (component, y) row, R2 lanes
+// per column; lane l holds z positions l + R2 j.  The second stage fuses the
+// last forward stage, the multiply by 1/(1 + gamma K^n)/(nx ny nz) and the
+// first inverse stage.
+template <int R1, int R2>
+__global__ void __launch_bounds__(kZSlabThreads, zslab_min_blocks<R1, R2>())
+    k_zslab(const __grid_constant__ PencilArgs a) {
+  constexpr int N = R1 * R2, CPW = 32 / R2;
+  constexpr int P = N + (R2 == 8 ? 4 : 8);
+  extern __shared__ float2 sm_all[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int l = lane / CPW, col = lane % CPW;
+  float2* sm = sm_all + (warp * CPW + col) * P;
+  const int groups = (a.nkx + CPW - 1) / CPW;  // kx groups per (component, y) row
+  const int tasks = 3 * a.ny * groups;
+  const int task = blockIdx.x * (kZSlabThreads / 32) + warp;
+  const bool task_ok = task < tasks;
+  const int row = task_ok ? task / groups : 0;  // component * ny + y
+  const int kx0 = (task_ok ? task - row * groups : 0) * CPW + col;
+  const bool active = task_ok && kx0 < a.nkx;
+  const int kx = active ? kx0 : 0;
+  const int y = row % a.ny;
+  pdl_wait();
+  pdl_trigger();
+  float2* base = a.spec + (size_t)row * a.nkx + kx;
+  const size_t zs = (size_t)3 * a.ny * a.nkx;
+  float2 v[R1];
+#pragma unroll
+  for (int j = 0; j < R1; ++j) v[j] = active ? __ldcg(base + (l + R2 * j) * zs) : make_float2(0.f, 0.f);
+  lane_stage1<R1, R2, false>(v, a.twz, l);
+#pragma unroll
+  for (int k = 0; k < R1; ++k) sm[swz<R2>(l + R2 * k)] = v[k];
+  __syncwarp();
+  const float kxy = __ldg(a.Kx + kx) + __ldg(a.Ky + y);
+  for (int b = l; b < R1; b += R2) {
+    float2 w[R2];
+#pragma unroll
+    for (int j = 0; j < R2; ++j) w[j] = sm[swz<R2>(b * R2 + j)];
+    dft<R2, false>(w);
+#pragma unroll
+    for (int k = 0; k < R2; ++k) {
+      const float K = kxy + __ldg(a.Kz + b * R2 + k);
+      float Kn = K;
+      for (int i = 1; i < a.order_n; ++i) Kn *= K;
+      w[k] = cscale(w[k], __fdividef(a.scale, 1.0f + a.gamma * Kn));
+    }
+    dft<R2, true>(w);
+#pragma unroll
+    for (int j = 0; j < R2; ++j) sm[swz<R2>(b * R2 + j)] = w[j];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < R1; ++k) v[k] = sm[swz<R2>(l + R2 * k)];
+  lane_stage1<R1, R2, true>(v, a.twz, l);
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < R1; ++j) __stcg(base + (l + R2 * j) * zs, v[j]);
+  }
+}
+
+// ---------------------------------------------------------------- host side
+namespace {
+
+bool slab_x_case(int r1) {
+  for (int r : {2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 16})
+    if (r == r1) return true;
+  return false;
+}
+
+bool lane_case(const AxisPlan& p) {
+  return p.nst == 2 && p.m[1] == 1 && lane_pair_supported(p.radix[0], p.radix[1]);
+}
+
+template <int R1, int R2>
+cudaError_t launch_z(const PencilArgs& a, cudaStream_t s) {
+  constexpr int N = R1 * R2, CPW = 32 / R2;
+  const int groups = (a.nkx + CPW - 1) / CPW;
+  const int tasks = 3 * a.ny * groups;
+  const int per_cta = kZSlabThreads / 32;
+  const dim3 grid((unsigned)((tasks + per_cta - 1) / per_cta));
+  const size_t smem = (size_t)per_cta * CPW * (N + (R2 == 8 ? 4 : 8)) * sizeof(float2);
+  return launch_pdl(k_zslab<R1, R2>, grid, dim3(kZSlabThreads), smem, s, a);
+}
+
+template <typename K>
+cudaError_t raise_smem(K kernel) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  int dev = 0, optin = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
+}  // namespace
+
+bool slab_supported(int nx, int ny, int nz, const AxisPlan& pxh, const AxisPlan& py,
+                    const AxisPlan& pz) {
+  if (nx % 4 != 0 || pxh.n * 2 != nx) return false;
+  if (!(pxh.nst == 2 && pxh.radix[1] == kSlabXR2 && slab_x_case(pxh.radix[0]))) return false;
+  if (!lane_case(py) || !lane_case(pz) || py.n != ny || pz.n != nz) return false;
+  SlabArgs a{};
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  a.nkx = nx / 2 + 1;
+  a.mx = nx / 2;
+  a.yr2 = py.radix[1];
+  return slab_smem_bytes(a) <= 227 * 1024;
+}
+
+cudaError_t launch_slab(int mode, const SlabArgs& a, cudaStream_t s) {
+  const dim3 grid((unsigned)(3 * a.nz)), block(kSlabThreads);
+  const size_t smem = slab_smem_bytes(a);
+  switch (mode) {
+    case SLAB_FIRST: return launch_pdl(k_slab<SLAB_FIRST>, grid, block, smem, s, a);
+    case SLAB_SPEC: return launch_pdl(k_slab<SLAB_SPEC>, grid, block, smem, s, a);
+    case SLAB_SPEC_PREV: return launch_pdl(k_slab<SLAB_SPEC_PREV>, grid, block, smem, s, a);
+    case SLAB_FINAL: return launch_pdl(k_slab<SLAB_FINAL>, grid, block, smem, s, a);
+    case SLAB_FIELD: return launch_pdl(k_slab<SLAB_FIELD>, grid, block, smem, s, a);
+    case SLAB_STATE: return launch_pdl(k_slab<SLAB_STATE>, grid, block, smem, s, a);
+    case SLAB_STATE_PREV: return launch_pdl(k_slab<SLAB_STATE_PREV>, grid, block, smem, s, a);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_zslab(const PencilArgs& a, cudaStream_t s) {
+  const int r1 = a.pz.radix[0], r2 = a.pz.radix[1];
+#define X(A, B) \
+  if (r1 == A && r2 == B) return launch_z<A, B>(a, s);
+  NADMM_LANE_CASES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t configure_slab_kernels() {
+  cudaError_t e;
+  if ((e = raise_smem(k_slab<SLAB_FIRST>)) != cudaSuccess) return e;
+  if ((e = raise_smem(k_slab<SLAB_SPEC>)) != cudaSuccess) return e;
+  if ((e = raise_smem(k_slab<SLAB_SPEC_PREV>)) != cudaSuccess) return e;
+  if ((e = raise_smem(k_slab<SLAB_FINAL>)) != cudaSuccess) return e;
+  if ((e = raise_smem(k_slab<SLAB_FIELD>)) != cudaSuccess) return e;
+  if ((e = raise_smem(k_slab<SLAB_STATE>)) != cudaSuccess) return e;
+  return raise_smem(k_slab<SLAB_STATE_PREV>);
+}
+
+}  // namespace nadmm

@@ -28,6 +28,7 @@ NADMM_FLAG_SAVE_FOR_BACKWARD = 2
 NADMM_FLAG_LANE_MASK = 0xFC
 NADMM_FLAG_FUSED_PENCIL = 0x100
 NADMM_FLAG_PIPELINED_PLANE = 0x200
+NADMM_FLAG_FOUR_PASS = 0x400
 
 
 def NADMM_FLAG_LANE8(axis):
@@ -38,7 +39,7 @@ def NADMM_FLAG_LANE16(axis):
     return 2 << (2 + 2 * axis)
 
 KERNEL_CLASSES = ("plane_first", "plane_k1", "plane", "plane_final", "pencil", "warp", "grad",
-                  "bound", "compose")
+                  "bound", "compose", "slab_first", "slab_k1", "slab", "slab_final", "zslab")
 
 
 class NadmmError(RuntimeError):
