@@ -120,6 +120,21 @@ typedef struct nadmm_config {
                                  when ||I1w_o - I1w_(o-1)||_2 <= warp_tol
                                  ||I1w_(o-1)||_2; outer_iters is then a cap
                                  (the paper's "2 %" is 0.02; default 0)    */
+  float restart_eta;          /* < 0 (default -1): Eq. 5 as printed.  >= 0:
+                                 adaptive restart of the Nesterov momentum
+                                 (not in the paper; the restart of Goldstein
+                                 et al.'s fast ADMM, whose O(1/k^2) rate the
+                                 paper cites after Eq. 5): with c_k =
+                                 ||w^k - w_hat^k||^2 + ||b^k - b_hat^k||^2 and
+                                 cbar (+inf at k = 0), c_k < eta cbar sets
+                                 cbar = c_k, otherwise cbar /= eta and the
+                                 momentum restarts at iteration k + 2 (the
+                                 factors forming w_hat^{k+2}, w_hat^{k+3}, ...
+                                 become beta_0 = 0, beta_1, ...).  eta = 0
+                                 restarts at every test, INFINITY never;
+                                 0.999 is Goldstein et al.'s value.  Needs
+                                 the slab path, fixed iteration counts and no
+                                 NADMM_FLAG_SAVE_FOR_BACKWARD                 */
 } nadmm_config;
 
 typedef struct nadmm_context* nadmm_handle;
@@ -443,6 +458,13 @@ nadmm_status nadmm_ssd_after_warp_backward(nadmm_handle h, const float* fixed,
  * the next nadmm_get_status reports NADMM_ERR_TIMEOUT and the context stays
  * usable.  Errors: INVALID_ARG, NO_WORKSPACE, CUDA. */
 nadmm_status nadmm_selftest_wait_timeout(nadmm_handle h, int32_t attempts, void* stream);
+
+/* Momentum restarts that took effect (config restart_eta >= 0; a test of
+ * iteration k restarts iteration k + 2, so tests of the last two iterations of
+ * a loop have none) counted over all outer steps
+ * of the last nadmm_register on `h` (host int32).  Synchronises `stream`.
+ * Errors: INVALID_ARG (no restart on this handle), NO_WORKSPACE, CUDA. */
+nadmm_status nadmm_get_restarts(nadmm_handle h, void* stream, int32_t* restarts);
 
 /* ---------------------------------------------------------------------
  * Measurement

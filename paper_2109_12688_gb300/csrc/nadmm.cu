@@ -53,6 +53,10 @@ struct nadmm_context {
   std::vector<float2> twxh, rtx;
   std::vector<int> posxh, fqxh;
   size_t o_twxh = 0, o_rtx = 0, o_posxh = 0, o_fqxh = 0;
+  // adaptive restart (cfg.restart_eta >= 0, slab path only): u^k (state
+  // region), the factors in use, beta_0.., the sums and the counters (tables)
+  bool restart = false;
+  size_t o_uprev = 0, o_bdev = 0, o_bseq = 0, o_racc = 0, o_rwords = 0;
   int R = 0;
   size_t V = 0, nkx = 0;
   size_t plane_smem = 0, pencil_smem = 0;
@@ -150,6 +154,12 @@ nadmm_status validate(const nadmm_config* c) {
     return fail(NADMM_ERR_INVALID_ARG, "admm_tol and warp_tol must be finite and >= 0");
   if ((c->admm_tol > 0.0f || c->warp_tol > 0.0f) && (c->flags & NADMM_FLAG_SAVE_FOR_BACKWARD))
     return fail(NADMM_ERR_INVALID_ARG, "the reverse mode needs fixed iteration counts (no thresholds)");
+  if (std::isnan(c->restart_eta))
+    return fail(NADMM_ERR_INVALID_ARG, "restart_eta must not be NaN (< 0 turns restart off)");
+  if (c->restart_eta >= 0.0f && ((c->flags & NADMM_FLAG_SAVE_FOR_BACKWARD) ||
+                                 c->admm_tol > 0.0f || c->warp_tol > 0.0f))
+    return fail(NADMM_ERR_INVALID_ARG,
+                "adaptive restart needs fixed iteration counts and no reverse mode");
   if (!(c->bound_kappa > 0.0f) || !(c->bound_delta > 0.0f))
     return fail(NADMM_ERR_INVALID_ARG, "bound_kappa and bound_delta must be > 0 (INFINITY disables)");
   if (c->flags & ~(NADMM_FLAG_NO_GRAPH | NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK |
@@ -273,6 +283,16 @@ SlabArgs slab_args(const nadmm_context* h) {
   a.theta = h->cfg.theta;
   a.eps = h->cfg.eps;
   a.data_term = h->cfg.data_term;
+  if (h->restart) {
+    a.restart = 1;
+    a.eta = h->cfg.restart_eta;
+    a.kmax = h->cfg.inner_iters - 1;
+    a.beta_dev = h->tab<float>(h->o_bdev);
+    a.beta_seq = h->tab<float>(h->o_bseq);
+    a.u_prev = h->at<float>(h->o_uprev);
+    a.racc = h->tab<double>(h->o_racc);
+    a.rwords = h->tab<unsigned>(h->o_rwords);
+  }
   return a;
 }
 
@@ -333,7 +353,12 @@ cudaError_t enqueue_inner_slab(nadmm_context* h, const PlaneArgs& first, int in_
   SlabArgs a = slab_args(h);
   a.J = J;
   a.c = c;
+  // restart runs over whole inner loops (k0 = 0); a loop resumed from given
+  // state buffers (nadmm_admm_run) runs Eq. 5 as printed
+  if (in_first != IN_NONE || k0 != 0) a.restart = 0;
+  a.kmax = k0 + steps - 1;
   SlabArgs f = a;
+  f.k = k0;
   int mode = SLAB_FIRST;
   if (in_first == IN_STATE) {
     mode = prev_first ? SLAB_STATE_PREV : SLAB_STATE;
@@ -349,6 +374,7 @@ cudaError_t enqueue_inner_slab(nadmm_context* h, const PlaneArgs& first, int in_
   for (int k = k0 + 1; k < k0 + steps; ++k) {
     KLAUNCH(NADMM_KC_ZSLAB, s, launch_zslab(pa, s));
     a.beta = beta_for(h, k);
+    a.k = k;
     KLAUNCH(k >= 2 ? NADMM_KC_SLAB : NADMM_KC_SLAB_K1, s,
             launch_slab(k >= 2 ? SLAB_SPEC_PREV : SLAB_SPEC, a, s));
   }
@@ -416,6 +442,7 @@ cudaError_t enqueue_register(nadmm_context* h, const float* I0, const float* I1,
   auto dst_of = [&](int o) { return ((O - 1 - o) % 2 == 0) ? u_out : ut; };
   float* u_cur = (dst_of(0) == u_out) ? ut : u_out;
   TRY(cudaMemsetAsync(red, 0, 4 * sizeof(unsigned), s));  // red[0..1], status red[2]
+  if (h->restart) TRY(cudaMemsetAsync(h->tab<unsigned>(h->o_rwords), 0, 2 * sizeof(unsigned), s));
   unsigned* conv = thresholds(h) ? h->tab<unsigned>(h->o_conv) : nullptr;
   double* conv_acc = h->tab<double>(h->o_convacc);
   if (conv) {
@@ -540,7 +567,9 @@ nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
   compute_beta(h);
   {
     const int mx = cfg->nx / 2;
-    if (!(cfg->flags & NADMM_FLAG_FOUR_PASS) && mx % 8 == 0) {
+    // the pipelined plane pass and the fused y/z pass are four-kernel variants
+    const uint32_t four = NADMM_FLAG_FOUR_PASS | NADMM_FLAG_PIPELINED_PLANE | NADMM_FLAG_FUSED_PENCIL;
+    if (!(cfg->flags & four) && mx % 8 == 0) {
       two_stage_plan(mx, mx / 8, 8, h->pxh);
       h->slab = slab_supported(cfg->nx, cfg->ny, cfg->nz, h->pxh, h->py, h->pz);
     }
@@ -556,6 +585,15 @@ nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
       }
     }
   }
+  if (cfg->restart_eta >= 0.0f) {
+    if (!h->slab) {
+      delete h;
+      return fail(NADMM_ERR_UNSUPPORTED_SIZE,
+                  "adaptive restart runs on the slab path only (nx/2 a multiple of 8, lane "
+                  "plans for y and z, a z-plane within one CTA, no NADMM_FLAG_FOUR_PASS)");
+    }
+    h->restart = true;
+  }
   const size_t V = h->V;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -564,6 +602,7 @@ nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
     return r;
   };
   h->o_spec = take(3 * h->nkx * cfg->ny * cfg->nz * sizeof(float2));
+  if (h->restart) h->o_uprev = take(3 * V * sizeof(float));
   h->o_y = take(3 * V * sizeof(float));
   h->o_wp = take(3 * V * sizeof(float));
   h->o_bp = take(3 * V * sizeof(float));
@@ -603,6 +642,12 @@ nadmm_status create_single(const nadmm_config* cfg, nadmm_context** out) {
     h->o_rtx = take(h->rtx.size() * sizeof(float2));
     h->o_posxh = take(h->posxh.size() * sizeof(int));
     h->o_fqxh = take(h->fqxh.size() * sizeof(int));
+  }
+  if (h->restart) {
+    h->o_bdev = take((size_t)cfg->inner_iters * sizeof(float));
+    h->o_bseq = take((size_t)cfg->inner_iters * sizeof(float));
+    h->o_racc = take(2 * sizeof(double));
+    h->o_rwords = take(2 * sizeof(unsigned));
   }
   // the tape belongs to the pair (it must outlive other pairs' use of a
   // shared state region), so it sits with the tables
@@ -686,6 +731,7 @@ nadmm_status attach(nadmm_context* h, char* ws, char* wt) {
       {h->o_rtx, h->rtx.data(), h->rtx.size() * sizeof(float2)},
       {h->o_posxh, h->posxh.data(), h->posxh.size() * sizeof(int)},
       {h->o_fqxh, h->fqxh.data(), h->fqxh.size() * sizeof(int)},
+      {h->o_bseq, h->beta.data(), h->restart ? (size_t)h->cfg.inner_iters * sizeof(float) : 0},
   };
   cudaError_t e = cudaSuccess;
   for (const Up& u : ups) {
@@ -990,6 +1036,7 @@ void nadmm_config_init(nadmm_config* c, int32_t nx, int32_t ny, int32_t nz) {
   c->flags = 0;
   c->admm_tol = 0.0f;
   c->warp_tol = 0.0f;
+  c->restart_eta = -1.0f;
 }
 
 const char* nadmm_last_error(void) { return g_err.c_str(); }
@@ -1543,7 +1590,10 @@ nadmm_status nadmm_selftest_wait_timeout(nadmm_handle h, int32_t attempts, void*
 nadmm_status nadmm_autotune_workspace_size(const nadmm_config* cfg, size_t* bytes) {
   if (!bytes) return fail(NADMM_ERR_INVALID_ARG, "bytes is NULL");
   nadmm_config c = *cfg;
-  c.flags &= ~(NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK);
+  c.flags &= ~(NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK | NADMM_FLAG_FOUR_PASS |
+               NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_PIPELINED_PLANE);
+  c.restart_eta = -1.0f;
+  c.admm_tol = c.warp_tol = 0.0f;
   size_t most = 0;
   for (uint32_t combo = 0; combo < 8; ++combo) {
     nadmm_config t = c;
@@ -1581,21 +1631,30 @@ nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t byt
     return cuda_fail(e, "cudaEventCreate");
   }
   nadmm_config c = *cfg;
-  c.flags &= ~(NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL);
+  c.flags &= ~(NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL |
+               NADMM_FLAG_FOUR_PASS | NADMM_FLAG_PIPELINED_PLANE);
+  c.restart_eta = -1.0f;
+  c.admm_tol = c.warp_tol = 0.0f;
   std::vector<std::vector<int>> seen;
   float best = -1.0f;
   uint32_t best_f = c.flags;
-  for (uint32_t combo = 0; combo < 16 && st == NADMM_OK; ++combo) {
+  // bits 0-2: 16 lanes on x / y / z; bit 3: fused y/z pass; bit 4: four-kernel path
+  for (uint32_t combo = 0; combo < 32 && st == NADMM_OK; ++combo) {
     nadmm_config t = c;
     for (int ax = 0; ax < 3; ++ax)
       t.flags |= (((combo >> ax) & 1u) ? 2u : 1u) << NADMM_FLAG_LANE_SHIFT(ax);
     if (combo & 8u) t.flags |= NADMM_FLAG_FUSED_PENCIL;
+    if (combo & 16u) t.flags |= NADMM_FLAG_FOUR_PASS;
+    if ((combo & 8u) && !(combo & 16u)) continue;  // fusion is a four-kernel variant
     nadmm_context* h = nullptr;
     if ((st = create_single(&t, &h)) != NADMM_OK) break;
-    // skip combinations whose kernels coincide with ones already timed
+    // skip combinations whose kernels coincide with ones already timed (a
+    // grid without the slab path runs its four-kernel plan either way)
     const int fused = (combo & 8u) ? (int)fused_pencil_supported(pencil_args(h)) : 0;
-    std::vector<int> key = {h->px.radix[0], h->px.radix[1], h->py.radix[0], h->py.radix[1],
-                            h->pz.radix[0], h->pz.radix[1], fused};
+    const int slab = h->slab ? 1 : 0;
+    std::vector<int> key = {slab ? h->pxh.radix[0] : h->px.radix[0],
+                            slab ? 0 : h->px.radix[1], h->py.radix[0], h->py.radix[1],
+                            h->pz.radix[0], h->pz.radix[1], fused, slab};
     bool dup = false;
     for (const auto& k : seen) dup = dup || k == key;
     if (!dup) {
@@ -1606,12 +1665,19 @@ nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t byt
         a.J = h->at<float>(h->o_J);
         a.c = h->at<float>(h->o_c);
         a.beta = 0.5f;
+        SlabArgs sa = slab_args(h);
+        sa.beta = 0.5f;
         const PencilArgs pa = pencil_args(h);
         float ms = 0.0f, t_min = -1.0f;
         for (int rep = 0; rep < 13 && e == cudaSuccess; ++rep) {
           if (rep >= 3) e = cudaEventRecord(e0, s);
-          if (e == cudaSuccess) e = launch_plane(IN_SPEC, true, true, a, s);
-          if (e == cudaSuccess) e = launch_pencil(pa, s);
+          if (slab) {
+            if (e == cudaSuccess) e = launch_slab(SLAB_SPEC_PREV, sa, s);
+            if (e == cudaSuccess) e = launch_zslab(pa, s);
+          } else {
+            if (e == cudaSuccess) e = launch_plane(IN_SPEC, true, true, a, s);
+            if (e == cudaSuccess) e = launch_pencil(pa, s);
+          }
           if (rep >= 3) {
             if (e == cudaSuccess) e = cudaEventRecord(e1, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -1631,7 +1697,7 @@ nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t byt
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != NADMM_OK) return st;
-  const uint32_t tuned = NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL;
+  const uint32_t tuned = NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_FOUR_PASS;
   *best_flags = (cfg->flags & ~tuned) | (best_f & tuned);
   if (best_ms) *best_ms = best;
   return NADMM_OK;
@@ -1659,6 +1725,20 @@ nadmm_status nadmm_get_iterations(nadmm_handle h, void* stream, int32_t* outer_r
 }
 
 }  // extern "C"
+
+nadmm_status nadmm_get_restarts(nadmm_handle h, void* stream, int32_t* restarts) {
+  nadmm_status st = need_ws(h);
+  if (st != NADMM_OK) return st;
+  if (!restarts) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
+  if (!h->restart) return fail(NADMM_ERR_INVALID_ARG, "the handle has no adaptive restart");
+  unsigned words[2] = {0, 0};
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(words, h->tab<unsigned>(h->o_rwords), sizeof(words), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "nadmm_get_restarts");
+  *restarts = (int32_t)words[1];
+  return NADMM_OK;
+}
 
 namespace nadmm {
 // Lets other translation units of the library report through nadmm_last_error.

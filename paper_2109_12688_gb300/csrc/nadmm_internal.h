@@ -129,6 +129,19 @@ struct SlabArgs {
   const int* fqx;          // frequency held at position p (inverse of posx)
   const float2* twy;       // stage twiddles of the y lane plan [yr1, yr2]
   unsigned* status;        // device status word (bit 1: a bounded wait expired) or null
+  // adaptive restart (restart != 0): the factor forming w_hat^k is
+  // beta_dev[k] (k = the iteration this pass starts); the pass that starts
+  // iteration k >= 1 sums c_{k-1} = ||w^{k-1} - w_hat^{k-1}||^2 +
+  // ||b^{k-1} - b_hat^{k-1}||^2, and its last CTA applies the rule to
+  // beta_dev[k+1 ..]; u^k = w_hat^k - b_hat^k is kept in u_prev for that sum
+  int restart;
+  int k, kmax;             // iteration started by this pass; last iteration of the loop
+  float eta;
+  float* beta_dev;         // [kmax + 1] factors in use (reset by the k = 0 pass)
+  const float* beta_seq;   // [kmax + 1] beta_0 = 0, beta_1, ... (Eq. 5)
+  float* u_prev;           // [3][V] u^{k-1} in, u^k out
+  double* racc;            // [0] running sum of the pass, [1] cbar
+  unsigned* rwords;        // [0] CTAs of the pass that have reported, [1] restarts counted
   FastDiv qdiv;            // division by nx / 4 (voxel quads per row)
   int nx, ny, nz, nkx, mx;  // mx = nx / 2
   int xr1, xr2, yr1, yr2;

@@ -220,17 +220,21 @@ __device__ __forceinline__ float4* real_quad(float2* plane, int nkx, int y, int 
 
 // The coupled point-wise step on voxel quads [q0, q1) of the plane at z for
 // all three components (planes[c] is component c's plane, local or remote).
-template <int MODE>
-__device__ __forceinline__ void slab_pointwise(const SlabArgs& a, float2* const (&planes)[3], int z,
-                                               int q0, int q1) {
+// RST (adaptive restart, SPEC modes): the factor comes from beta_dev[k], u^k
+// is kept, and the thread's share of c_{k-1} is returned.
+template <int MODE, bool RST>
+__device__ __forceinline__ float slab_pointwise(const SlabArgs& a, float2* const (&planes)[3], int z,
+                                                int q0, int q1) {
   const size_t V = (size_t)a.nx * a.ny * a.nz;
   const int qrow = a.nx >> 2;
   const bool prev = (MODE == SLAB_SPEC_PREV) || (MODE == SLAB_STATE_PREV);
+  const float beta = RST ? a.beta_dev[a.k] : a.beta;
+  float racc = 0.0f;
   for (int q = q0 + (int)threadIdx.x; q < q1; q += kSlabThreads) {
     const int yy = (int)fdiv((uint32_t)q, a.qdiv);
     const int x0 = (q - yy * qrow) << 2;
     const size_t vox = ((size_t)z * a.ny + yy) * a.nx + x0;
-    float4 wk1[3], bk1[3], wh[3], bh[3], Jq[3];
+    float4 wk1[3], bk1[3], wh[3], bh[3], Jq[3], yq[3];
     const float4 cq = __ldg(reinterpret_cast<const float4*>(a.c + vox));
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -243,7 +247,8 @@ __device__ __forceinline__ void slab_pointwise(const SlabArgs& a, float2* const 
         bk1[c] = __ldg(reinterpret_cast<const float4*>(a.b_in + i));
       } else {
         wk1[c] = *real_quad(planes[c], a.nkx, yy, x0);
-        bk1[c] = f4sub(*reinterpret_cast<const float4*>(a.y + i), wk1[c]);
+        yq[c] = *reinterpret_cast<const float4*>(a.y + i);
+        bk1[c] = f4sub(yq[c], wk1[c]);
       }
       if (prev) {
         const float4 wq = (MODE == SLAB_STATE_PREV)
@@ -252,8 +257,8 @@ __device__ __forceinline__ void slab_pointwise(const SlabArgs& a, float2* const 
         const float4 bq = (MODE == SLAB_STATE_PREV)
                               ? __ldg(reinterpret_cast<const float4*>(a.bprev_in + i))
                               : *reinterpret_cast<const float4*>(a.bp + i);
-        wh[c] = f4extra(wk1[c], wq, a.beta);
-        bh[c] = f4extra(bk1[c], bq, a.beta);
+        wh[c] = f4extra(wk1[c], wq, beta);
+        bh[c] = f4extra(bk1[c], bq, beta);
       } else {
         wh[c] = wk1[c];
         bh[c] = bk1[c];
@@ -261,6 +266,44 @@ __device__ __forceinline__ void slab_pointwise(const SlabArgs& a, float2* const 
       if (MODE != SLAB_FIRST) {  // w^{k-1}, b^{k-1} into the state slots
         *reinterpret_cast<float4*>(a.wp + i) = wk1[c];
         *reinterpret_cast<float4*>(a.bp + i) = bk1[c];
+      }
+    }
+    if (RST) {
+      // c_{k-1}: w_hat^{k-1}, b_hat^{k-1} from u^{k-1} = w_hat - b_hat and
+      // y^{k-1} = v^{k-1} + b_hat^{k-1}, v^{k-1} the v-step at u^{k-1}
+      // (both zero for k = 1); u^k replaces u^{k-1}
+      float4 up[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const size_t i = c * V + vox;
+        up[c] = (MODE == SLAB_SPEC_PREV) ? *reinterpret_cast<const float4*>(a.u_prev + i)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(a.u_prev + i) = f4sub(wh[c], bh[c]);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (MODE == SLAB_SPEC_PREV) {
+          float Jv[3], u[3], v[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            Jv[c] = f4get(Jq[c], e);
+            u[c] = f4get(up[c], e);
+          }
+          v_step(a.data_term, a.theta, a.eps, Jv, f4get(cq, e), u, v);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float bhat = f4get(yq[c], e) - v[c];
+            const float dw = f4get(wk1[c], e) - (u[c] + bhat);
+            const float db = f4get(bk1[c], e) - bhat;
+            racc += dw * dw + db * db;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float dw = f4get(wk1[c], e), db = f4get(bk1[c], e);
+            racc += dw * dw + db * db;
+          }
+        }
       }
     }
     float4 yn[3];
@@ -280,6 +323,40 @@ __device__ __forceinline__ void slab_pointwise(const SlabArgs& a, float2* const 
     for (int c = 0; c < 3; ++c) {
       *reinterpret_cast<float4*>(a.y + c * V + vox) = yn[c];
       *real_quad(planes[c], a.nkx, yy, x0) = yn[c];
+    }
+  }
+  return racc;
+}
+
+// Restart test of iteration k - 1 (reading of Goldstein et al.'s rule): the
+// CTA's share of c_{k-1} goes into racc[0]; the last CTA of the grid to
+// report compares c_{k-1} with eta cbar and, on a restart, rewrites the
+// factors of iterations k + 1 .. kmax as beta_0, beta_1, ...  All threads of
+// the CTA call this.
+__device__ __forceinline__ void slab_restart_test(const SlabArgs& a, float part) {
+  __shared__ float warp_sum[kSlabWarps];
+  for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double cta = 0.0;
+    for (int w = 0; w < kSlabWarps; ++w) cta += warp_sum[w];
+    atomicAdd(a.racc, cta);
+    __threadfence();
+    if (atomicAdd(a.rwords, 1u) == gridDim.x - 1) {  // every CTA has reported
+      __threadfence();
+      const double ck = atomicAdd(a.racc, 0.0);
+      const double cbar = a.racc[1];
+      if (a.eta > 0.0f && ck < (double)a.eta * cbar) {
+        a.racc[1] = ck;
+      } else {
+        if (a.eta > 0.0f) a.racc[1] = cbar / (double)a.eta;
+        for (int m = 0; a.k + 1 + m <= a.kmax; ++m) a.beta_dev[a.k + 1 + m] = a.beta_seq[m];
+        if (a.k + 1 <= a.kmax) a.rwords[1] += 1u;  // count restarts that take effect
+      }
+      a.racc[0] = 0.0;
+      a.rwords[0] = 0u;
+      __threadfence();
     }
   }
 }
@@ -334,7 +411,19 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kSlabThreads, 2)
                                cluster.map_shared_rank(plane, 2)};
     const int Q = a.ny * (a.nx >> 2);
     const int q0 = (int)((long long)Q * comp / 3), q1 = (int)((long long)Q * (comp + 1) / 3);
-    slab_pointwise<MODE>(a, planes, z, q0, q1);
+    if (MODE == SLAB_FIRST && a.restart && blockIdx.x == 0 && tid == 0) {
+      // a new inner loop: the factors of Eq. 5, cbar = +inf
+      for (int i = 0; i <= a.kmax; ++i) a.beta_dev[i] = (i == 0) ? 0.0f : a.beta_seq[i - 1];
+      a.racc[0] = 0.0;
+      a.racc[1] = __longlong_as_double(0x7ff0000000000000ll);
+      a.rwords[0] = 0u;
+    }
+    if ((MODE == SLAB_SPEC || MODE == SLAB_SPEC_PREV) && a.restart) {
+      const float part = slab_pointwise<MODE, true>(a, planes, z, q0, q1);
+      slab_restart_test(a, part);
+    } else {
+      slab_pointwise<MODE, false>(a, planes, z, q0, q1);
+    }
     cluster.sync();  // every plane holds y^k; no remote access after this
   } else {
     __syncthreads();

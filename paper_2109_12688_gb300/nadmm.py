@@ -29,6 +29,8 @@ NADMM_FLAG_LANE_MASK = 0xFC
 NADMM_FLAG_FUSED_PENCIL = 0x100
 NADMM_FLAG_PIPELINED_PLANE = 0x200
 NADMM_FLAG_FOUR_PASS = 0x400
+# plan bits nadmm_autotune chooses
+PLAN_FLAGS = 0xFC | 0x100 | 0x400
 
 
 def NADMM_FLAG_LANE8(axis):
@@ -55,7 +57,8 @@ class nadmm_config(ctypes.Structure):
                 ("inner_iters", ctypes.c_int32), ("data_term", ctypes.c_int32),
                 ("eps", ctypes.c_float), ("bound_kappa", ctypes.c_float),
                 ("bound_delta", ctypes.c_float), ("flags", ctypes.c_uint32),
-                ("admm_tol", ctypes.c_float), ("warp_tol", ctypes.c_float)]
+                ("admm_tol", ctypes.c_float), ("warp_tol", ctypes.c_float),
+                ("restart_eta", ctypes.c_float)]
 
 
 _lib = None
@@ -71,6 +74,7 @@ _SIGS = {
     "nadmm_register": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "nadmm_register_host": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "nadmm_get_status": (ctypes.c_int, [_P, _P]),
+    "nadmm_get_restarts": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "nadmm_last_error": (ctypes.c_char_p, []),
     "nadmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "nadmm_spectral_solve": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -306,6 +310,12 @@ def nadmm_get_status(h, stream=None):
     return load().nadmm_get_status(h, _stream(stream))
 
 
+def nadmm_get_restarts(h, stream=None):
+    n = ctypes.c_int32(0)
+    _check(load().nadmm_get_restarts(h, _stream(stream), ctypes.byref(n)))
+    return n.value
+
+
 def nadmm_last_error():
     return load().nadmm_last_error().decode()
 
@@ -344,7 +354,8 @@ def nadmm_jacobian_det(h, u, det=None, nonpositive=None, stream=None):
 
 # ---------------------------------------------------------------- convenience
 def make_config(dims, order_n=2, lam=10.0, theta=0.1, outer=10, inner=10, data_term=2,
-                eps=1e-6, kappa=0.5, delta=1.0, flags=0, admm_tol=0.0, warp_tol=0.0):
+                eps=1e-6, kappa=0.5, delta=1.0, flags=0, admm_tol=0.0, warp_tol=0.0,
+                restart_eta=-1.0):
     """nadmm_config for dims = (nx, ny, nz); kappa/delta may be math.inf."""
     nx, ny, nz = dims
     cfg = nadmm_config_init(nx, ny, nz)
@@ -360,6 +371,7 @@ def make_config(dims, order_n=2, lam=10.0, theta=0.1, outer=10, inner=10, data_t
     cfg.flags = flags
     cfg.admm_tol = admm_tol
     cfg.warp_tol = warp_tol
+    cfg.restart_eta = restart_eta
     return cfg
 
 
@@ -386,7 +398,7 @@ class Registration:
         if requires_grad:
             kw["flags"] = kw.get("flags", 0) | NADMM_FLAG_SAVE_FOR_BACKWARD
         if tune or autotune_cache:
-            kw["flags"] = (kw.get("flags", 0) & ~(NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL)) | autotune(
+            kw["flags"] = (kw.get("flags", 0) & ~PLAN_FLAGS) | autotune(
                 self.dims, device, autotune_cache)
         self.cfg = make_config(self.dims, **kw)
         self.serial = 0  # forward passes run on this handle
@@ -469,7 +481,7 @@ def autotune(dims, device="cuda", cache=None, **kw):
     ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
     ptr = (ws.data_ptr() + 255) // 256 * 256
     flags, ms = nadmm_autotune(cfg, ptr, nbytes, torch.cuda.current_stream(dev))
-    plan = flags & (NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL)
+    plan = flags & PLAN_FLAGS
     if cache:
         table[key] = {"plan_flags": plan, "ms_per_iteration": ms}
         with open(cache, "w") as fh:

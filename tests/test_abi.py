@@ -292,3 +292,23 @@ def test_noalloc_argument_checks_before_device_work(lib):
     with pytest.raises(lib.NadmmError) as e:
         lib.nadmm_spectral_solve_noalloc(32, 32, 24, 2, 10.0, 0.1, None, 8192)
     assert e.value.status == lib.NADMM_ERR_INVALID_ARG
+
+
+def test_restart_configuration_checks(lib):
+    """Adaptive restart (restart_eta >= 0) needs the slab path, fixed
+    iteration counts and no reverse mode; NaN is rejected (host only)."""
+    lib.nadmm_destroy(lib.nadmm_create(lib.make_config((128, 128, 96), restart_eta=0.999)))
+    lib.nadmm_destroy(lib.nadmm_create(lib.make_config((32, 32, 24), restart_eta=math.inf)))
+    for kw, status in (({"restart_eta": float("nan")}, lib.NADMM_ERR_INVALID_ARG),
+                       ({"restart_eta": 0.9, "flags": lib.NADMM_FLAG_SAVE_FOR_BACKWARD},
+                        lib.NADMM_ERR_INVALID_ARG),
+                       ({"restart_eta": 0.9, "admm_tol": 0.01}, lib.NADMM_ERR_INVALID_ARG),
+                       ({"restart_eta": 0.9, "flags": lib.NADMM_FLAG_FOUR_PASS},
+                        lib.NADMM_ERR_UNSUPPORTED_SIZE)):
+        with pytest.raises(lib.NadmmError) as e:
+            lib.nadmm_create(lib.make_config((32, 32, 24), **kw))
+        assert e.value.status == status
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_create(lib.make_config((20, 12, 14), restart_eta=0.999))
+    assert e.value.status == lib.NADMM_ERR_UNSUPPORTED_SIZE
+    assert "slab path" in str(e.value)

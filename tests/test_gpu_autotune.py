@@ -34,8 +34,9 @@ def dev(a):
 
 
 @pytest.mark.parametrize("combo", list(itertools.product((8, 16), repeat=3)))
-def test_every_plan_solves_like_the_oracle(lib, combo):
-    flags = 0
+@pytest.mark.parametrize("four", [False, True])
+def test_every_plan_solves_like_the_oracle(lib, combo, four):
+    flags = lib.NADMM_FLAG_FOUR_PASS if four else 0
     for ax, r2 in enumerate(combo):
         flags |= lib.NADMM_FLAG_LANE8(ax) if r2 == 8 else lib.NADMM_FLAG_LANE16(ax)
     nx, ny, nz = DIMS
@@ -51,7 +52,7 @@ def test_every_plan_solves_like_the_oracle(lib, combo):
 def test_autotune_and_cache(lib, tmp_path):
     cache = str(tmp_path / "plans.json")
     plan = lib.autotune(DIMS, DEV, cache)
-    assert plan & ~(lib.NADMM_FLAG_LANE_MASK | lib.NADMM_FLAG_FUSED_PENCIL) == 0
+    assert plan & ~lib.PLAN_FLAGS == 0
     table = json.load(open(cache))
     (key, rec), = table.items()
     assert key.startswith("96,96,64|") and rec["plan_flags"] == plan and rec["ms_per_iteration"] > 0
@@ -86,7 +87,7 @@ def test_fused_pencil_is_the_split_pass(lib, dims):
     registrations are bit-identical; grids it does not cover fall back."""
     pair = synth.make_pair(dims, seed=11)
     kw = dict(outer=2, inner=4)
-    a = lib.Registration(dims, device=DEV, **kw)
+    a = lib.Registration(dims, device=DEV, flags=lib.NADMM_FLAG_FOUR_PASS, **kw)
     b = lib.Registration(dims, device=DEV, flags=lib.NADMM_FLAG_FUSED_PENCIL, **kw)
     ua = a.register(dev(pair["fixed"]), dev(pair["moving"]))
     ub = b.register(dev(pair["fixed"]), dev(pair["moving"]))
@@ -102,7 +103,7 @@ def test_pipelined_plane_pass_is_the_per_tile_pass(lib, dims):
     and tile counts that do not divide evenly over the CTAs are included."""
     pair = synth.make_pair(dims, seed=12)
     kw = dict(outer=2, inner=5)
-    a = lib.Registration(dims, device=DEV, **kw)
+    a = lib.Registration(dims, device=DEV, flags=lib.NADMM_FLAG_FOUR_PASS, **kw)
     b = lib.Registration(dims, device=DEV, flags=lib.NADMM_FLAG_PIPELINED_PLANE, **kw)
     ua = a.register(dev(pair["fixed"]), dev(pair["moving"]))
     ub = b.register(dev(pair["fixed"]), dev(pair["moving"]))
