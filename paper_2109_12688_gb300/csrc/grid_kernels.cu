@@ -105,27 +105,43 @@ __global__ void __launch_bounds__(kBX * kBY) k_grad_residual(Dims d,
 
 // Per-voxel |w|_inf and ||D w||_inf (max absolute row sum of the Jacobian);
 // grid-wide max through atomicMax on the float bit patterns (non-negative
-// floats order like their bits; NaN bits sort above +inf).  Each block
-// loops over the z-slices blockIdx.z, blockIdx.z + gridDim.z, ...
+// floats order like their bits; NaN bits sort above +inf).  A thread takes
+// four x-consecutive voxels of one row (float4 loads of the voxels and of
+// their y- and z-neighbours, two scalars for the x-neighbours outside the
+// quad); block (32, 8) covers 128 x 8 voxels of one z-slice.
 __global__ void __launch_bounds__(kBX * kBY) k_bound_reduce(Dims d, const float* __restrict__ w,
                                                             unsigned* red, const unsigned* conv) {
   pdl_wait();
   pdl_trigger();
   if (conv != nullptr && conv[kConvOuter]) return;
   const size_t V = (size_t)d.nx * d.ny * d.nz;
-  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
+  const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
+  const int x0 = (blockIdx.x * kBX + threadIdx.x) * 4, y = blockIdx.y * kBY + threadIdx.y;
+  const int z = blockIdx.z;
   float mabs = 0.0f, mjac = 0.0f;
-  if (x < d.nx && y < d.ny) {
-    // unrolled so that the loads of several z-slices are in flight together
-#pragma unroll 4
-    for (int z = blockIdx.z; z < d.nz; z += gridDim.z) {
-      const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
-      const Nbr nb = neighbours(d, x, y, z, i);
+  if (x0 < d.nx && y < d.ny) {
+    const size_t i = ((size_t)z * d.ny + y) * d.nx + x0;
+    const size_t iym = y > 0 ? i - sy : i, iyp = y + 1 < d.ny ? i + sy : i;
+    const size_t izm = z > 0 ? i - sz : i, izp = z + 1 < d.nz ? i + sz : i;
 #pragma unroll
-      for (int comp = 0; comp < 3; ++comp) {
-        const float* f = w + comp * V;
-        const float a = fabsf(__ldg(f + i));
-        const float row = jacobian_row(f, nb);
+    for (int comp = 0; comp < 3; ++comp) {
+      const float* f = w + comp * V;
+      const float4 q = __ldg(reinterpret_cast<const float4*>(f + i));
+      const float xm = x0 > 0 ? __ldg(f + i - 1) : q.x;
+      const float xp = x0 + 4 < d.nx ? __ldg(f + i + 4) : q.w;
+      const float4 ym = __ldg(reinterpret_cast<const float4*>(f + iym));
+      const float4 yp = __ldg(reinterpret_cast<const float4*>(f + iyp));
+      const float4 zm = __ldg(reinterpret_cast<const float4*>(f + izm));
+      const float4 zp = __ldg(reinterpret_cast<const float4*>(f + izp));
+      const float c[4] = {q.x, q.y, q.z, q.w};
+      const float lo[4] = {xm, q.x, q.y, q.z}, hi[4] = {q.y, q.z, q.w, xp};
+      const float ylo[4] = {ym.x, ym.y, ym.z, ym.w}, yhi[4] = {yp.x, yp.y, yp.z, yp.w};
+      const float zlo[4] = {zm.x, zm.y, zm.z, zm.w}, zhi[4] = {zp.x, zp.y, zp.z, zp.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float a = fabsf(c[e]);
+        const float row = fabsf(0.5f * (hi[e] - lo[e])) + fabsf(0.5f * (yhi[e] - ylo[e])) +
+                          fabsf(0.5f * (zhi[e] - zlo[e]));
         // fmaxf drops NaN; keep it visible through the bit-pattern max instead
         mabs = (a != a || a > mabs) ? a : mabs;
         mjac = (row != row || row > mjac) ? row : mjac;
@@ -287,8 +303,9 @@ cudaError_t launch_grad_residual_conv(Dims d, const float* I1w, const float* I0,
 
 cudaError_t launch_bound_reduce(Dims d, const float* w, unsigned* red, cudaStream_t s,
                                 const unsigned* conv) {
-  // a few z-slices per block keep the number of atomics small
-  return launch_pdl(k_bound_reduce, grid3(d, d.nz < 8 ? d.nz : 8), kBlock, 0, s, d, w, red, conv);
+  const dim3 grid((unsigned)((d.nx + 4 * kBX - 1) / (4 * kBX)), (unsigned)((d.ny + kBY - 1) / kBY),
+                  (unsigned)d.nz);
+  return launch_pdl(k_bound_reduce, grid, kBlock, 0, s, d, w, red, conv);
 }
 
 cudaError_t launch_compose(Dims d, const float* w, const float* u_in, float* u_out,

@@ -187,18 +187,41 @@ def test_gradients_128x128x96_against_finite_differences(lib):
 
     h = 1e-3
     rng = np.random.default_rng(7)
-    idx = [(int(rng.integers(nz)), int(rng.integers(ny)), int(rng.integers(nx))) for _ in range(16)]
-    for (z, y, x) in idx:
-        for arr, g, name in ((I0, g0, "I0"), (I1, g1, "I1")):
+    # 16 voxels (seed 7) among those whose gradient is at least 0.05 in
+    # magnitude, 25x the absolute allowance for the FP32 rounding noise of the
+    # difference quotient, so the 2 % relative bound is what the check tests
+    for arr, g, name in ((I0, g0, "I0"), (I1, g1, "I1")):
+        big = np.argwhere(np.abs(g) >= 0.05)
+        assert len(big) >= 16, name
+        for z, y, x in big[rng.choice(len(big), size=16, replace=False)]:
             ap, am = arr.copy(), arr.copy()
             ap[z, y, x] += h
             am[z, y, x] -= h
             num = ((loss(a=ap) - loss(a=am)) if name == "I0" else (loss(b=ap) - loss(b=am))) / (2 * h)
-            assert abs(num - g[z, y, x]) <= 0.02 * abs(num) + 5e-3, (name, (z, y, x), num, g[z, y, x])
+            assert abs(num - g[z, y, x]) <= 0.02 * abs(num) + 2e-3, (name, (z, y, x), num, g[z, y, x])
     num_l = (loss(lam_=10.0 + h) - loss(lam_=10.0 - h)) / (2 * h)
     num_t = (loss(th_=0.1 + h) - loss(th_=0.1 - h)) / (2 * h)
     assert abs(num_l - gl) <= 0.02 * abs(num_l) + 5e-3, (num_l, gl)
     assert abs(num_t - gt) <= 0.02 * abs(num_t) + 5e-3, (num_t, gt)
+
+
+def test_backward_128x128x96_matches_oracle_vjp(lib):
+    """Full-size grid, short schedule (2 compositions x 5 ADMM iterations):
+    the GPU reverse sweep against the FP64 oracle's register_vjp."""
+    dims = (128, 128, 96)
+    p = synth.make_pair(dims, seed=0)
+    gu = synth.random_field((3,) + dims[::-1], seed=77)
+    kw = dict(lam=10.0, theta=0.1, n=2, outer=2, inner=5, kappa=0.5, delta=1.0)
+    reg = lib.Registration(dims, device=DEV, requires_grad=True, order_n=2, lam=10.0, theta=0.1,
+                           outer=2, inner=5)
+    f, m = dev(p["fixed"]), dev(p["moving"])
+    reg.register(f, m)
+    g0, g1, gl, gt = reg.backward(f, m, dev(gu))
+    r0, r1, rl, rt = O.register_vjp(p["fixed"], p["moving"], gu, **kw)
+    assert rel_l2(host(g0), r0) <= 1e-4
+    assert rel_l2(host(g1), r1) <= 1e-4
+    assert abs(float(gl) - rl) <= 1e-4 * abs(rl) + 1e-7
+    assert abs(float(gt) - rt) <= 1e-4 * abs(rt) + 1e-7
 
 
 # ---------------------------------------------------------------- batched

@@ -52,16 +52,19 @@ def _oracle_with_counts(pair, lam, theta, n, outer, inner, eta):
     return u, count
 
 
-@pytest.mark.parametrize("dims,n,theta,outer,inner", [((32, 32, 24), 2, 0.02, 3, 20),
-                                                      ((32, 32, 24), 1, 0.01, 2, 25),
-                                                      ((128, 128, 96), 2, 0.02, 2, 12)])
-def test_restart_registration_matches_oracle(lib, dims, n, theta, outer, inner):
+# (dims, n, lambda, theta, outer, inner); the 128x128x96 case restarts at
+# iterations 21-25 of its first outer step, each test decided by a margin of
+# at least 3.8 % (FP64), far above FP32 rounding
+@pytest.mark.parametrize("dims,n,lam,theta,outer,inner", [((32, 32, 24), 2, 10.0, 0.02, 3, 20),
+                                                          ((32, 32, 24), 1, 10.0, 0.01, 2, 25),
+                                                          ((128, 128, 96), 1, 1.0, 0.01, 2, 30)])
+def test_restart_registration_matches_oracle(lib, dims, n, lam, theta, outer, inner):
     """A weakly convex setting (theta well below |grad I|^2 at the edges),
     where restarts happen: same displacement (1e-3 voxel) and the same
     number of restarts as the oracle."""
     pair = synth.make_pair(dims, seed=5)
-    u_ref, count = _oracle_with_counts(pair, 10.0, theta, n, outer, inner, 0.999)
-    reg = lib.Registration(dims, device="cuda:0", order_n=n, lam=10.0, theta=theta, outer=outer,
+    u_ref, count = _oracle_with_counts(pair, lam, theta, n, outer, inner, 0.999)
+    reg = lib.Registration(dims, device="cuda:0", order_n=n, lam=lam, theta=theta, outer=outer,
                            inner=inner, restart_eta=0.999)
     u = reg.register(_dev(pair["fixed"]), _dev(pair["moving"]))
     stream = torch.cuda.current_stream()
