@@ -233,8 +233,8 @@ nadmm_status nadmm_batch_set_lanes(nadmm_handle h, int32_t lanes);
  * Errors: INVALID_ARG (not batched, lanes NULL). */
 nadmm_status nadmm_batch_get_lanes(nadmm_handle h, int32_t* lanes);
 
-/* Replace the NADMM_FLAG_LANE* and NADMM_FLAG_FUSED_PENCIL bits of pair
- * `pair` (0-based) of a
+/* Replace the plan bits (NADMM_FLAG_LANE*, NADMM_FLAG_FUSED_PENCIL,
+ * NADMM_FLAG_FOUR_PASS) of pair `pair` (0-based) of a
  * batched handle before its workspace is attached (e.g. with the result of
  * nadmm_autotune for that pair's grid); the workspace size may change.
  * Errors: INVALID_ARG. */
@@ -378,15 +378,15 @@ nadmm_status nadmm_spectral_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, in
 nadmm_status nadmm_autotune_workspace_size(const nadmm_config* cfg, size_t* bytes);
 
 /* Time every plan choice of `cfg`'s grid -- each axis with both an 8- and a
- * 16-lane split tried both ways, and the fused y/z pass where it applies --
- * on one ADMM iteration (the k >= 2 plane pass and the y/z passes; 3
- * warm-up and 10 timed repetitions, CUDA events
- * on `stream`, minimum kept) in the caller's device workspace (at least
- * nadmm_autotune_workspace_size bytes, 256-byte aligned; its contents are
- * overwritten) and write the fastest choice as NADMM_FLAG_LANE* and
- * NADMM_FLAG_FUSED_PENCIL bits to *best_flags (cfg->flags with those bits
- * replaced) and its time in ms to
- * *best_ms (host pointers; best_ms may be NULL).  Synchronises `stream`.
+ * 16-lane split tried both ways, the two-kernel slab path where it applies,
+ * and the four-kernel path with and without the fused y/z pass -- on one
+ * ADMM iteration (the k >= 2 pass(es); 3 warm-up and 10 timed repetitions,
+ * CUDA events on `stream`, minimum kept) in the caller's device workspace
+ * (at least nadmm_autotune_workspace_size bytes, 256-byte aligned; its
+ * contents are overwritten) and write the fastest choice as NADMM_FLAG_LANE*,
+ * NADMM_FLAG_FUSED_PENCIL and NADMM_FLAG_FOUR_PASS bits to *best_flags
+ * (cfg->flags with those bits replaced) and its time in ms to *best_ms (host
+ * pointers; best_ms may be NULL).  Synchronises `stream`.
  * Errors: INVALID_ARG, UNSUPPORTED_SIZE, ALIGNMENT, NO_WORKSPACE, CUDA. */
 nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t bytes,
                             void* stream, uint32_t* best_flags, float* best_ms);

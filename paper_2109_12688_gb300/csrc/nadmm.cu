@@ -1163,9 +1163,10 @@ nadmm_status nadmm_batch_set_pair_plan(nadmm_handle h, int32_t pair, uint32_t pl
   if (!h || !h->batched) return fail(NADMM_ERR_INVALID_ARG, "not a batched handle");
   if (h->wt) return fail(NADMM_ERR_INVALID_ARG, "set plans before nadmm_set_workspace");
   if (pair < 0 || pair >= (int32_t)h->pairs.size()) return fail(NADMM_ERR_INVALID_ARG, "pair out of range");
-  const uint32_t tuned = NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL;
+  const uint32_t tuned = NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_FOUR_PASS;
   if (plan_flags & ~tuned)
-    return fail(NADMM_ERR_INVALID_ARG, "only NADMM_FLAG_LANE* and NADMM_FLAG_FUSED_PENCIL bits");
+    return fail(NADMM_ERR_INVALID_ARG,
+                "only NADMM_FLAG_LANE*, NADMM_FLAG_FUSED_PENCIL and NADMM_FLAG_FOUR_PASS bits");
   nadmm_config c = h->pairs[pair]->cfg;
   c.flags = (c.flags & ~tuned) | plan_flags;
   nadmm_context* q = nullptr;
