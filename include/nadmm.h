@@ -212,24 +212,31 @@ const char* nadmm_status_string(nadmm_status s);
 /* Create a handle for npairs pairs: pair i has grid dims[3i], dims[3i+1],
  * dims[3i+2] (nx, ny, nz) and every other setting from `base` (its nx, ny,
  * nz are ignored).  Each grid is validated as by nadmm_create; the first
- * failure is returned with "pair i: ..." in nadmm_last_error.  The pairs
- * run in one CUDA graph on `lanes` concurrent branches (default
- * min(npairs, 2), see nadmm_batch_set_lanes), spread longest first to
- * balance voxel counts; pairs of one lane run one after another and share
- * that lane's scratch, so the workspace is one state region per lane (its
- * largest pair's) plus every pair's own region (tables, tape).  Two lanes
- * let one pair's DRAM-heavy plane passes overlap another's L2-resident FFT
- * passes; more lanes can lose again to L2 evictions (64 uneven pairs:
- * 472 / 455 / 479 / 511 ms with 1 / 2 / 3 / 4 lanes).  Host only. */
+ * failure is returned with "pair i: ..." in nadmm_last_error.
+ *
+ * Flat execution (the default when every pair runs on the slab path and
+ * NADMM_FLAG_SAVE_FOR_BACKWARD is not set; lane count 0): every pair keeps
+ * its own state region, and each phase of an ADMM iteration is one launch
+ * over all pairs -- the slab pass of every z-plane of every pair (one launch
+ * per shared-memory class: planes that fit two CTAs per SM, then the rest)
+ * and the z-pass of every pair sharing a z plan (one launch per plan) --
+ * while the outer-step kernels run per pair.  Otherwise the pairs run on
+ * `lanes` concurrent graph branches (default min(npairs, 2)), spread longest
+ * first to balance voxel counts; pairs of one lane run one after another and
+ * share that lane's scratch, so the workspace is one state region per lane
+ * (its largest pair's) plus every pair's own region (tables, tape).  Host
+ * only. */
 nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, const int32_t* dims,
                                   nadmm_handle* out);
 
-/* Change the lane count (1 = all pairs in sequence) of a batched handle
- * before its workspace is attached.  lanes > npairs is clamped to npairs.
- * Errors: INVALID_ARG (not batched, lanes < 1, workspace already attached). */
+/* Change the lane count of a batched handle before its workspace is
+ * attached: 0 = flat execution (needs every pair on the slab path and no
+ * reverse-mode tape), 1 = all pairs in sequence, lanes > npairs is clamped to
+ * npairs.  Errors: INVALID_ARG (not batched, lanes < 0, flat not possible,
+ * workspace already attached). */
 nadmm_status nadmm_batch_set_lanes(nadmm_handle h, int32_t lanes);
 
-/* The lane count of a batched handle (after clamping).  Host only.
+/* The lane count of a batched handle (after clamping; 0 = flat).  Host only.
  * Errors: INVALID_ARG (not batched, lanes NULL). */
 nadmm_status nadmm_batch_get_lanes(nadmm_handle h, int32_t* lanes);
 
@@ -244,8 +251,8 @@ nadmm_status nadmm_batch_set_pair_plan(nadmm_handle h, int32_t pair, uint32_t pl
  * [nz_i][ny_i][nx_i], u_out[i] device [3][nz_i][ny_i][nx_i] (host arrays of
  * npairs device pointers each).  The same computation as nadmm_register on
  * each pair, as one CUDA-graph replay on `stream` (re-captured when any
- * pointer changes) or, with NADMM_FLAG_NO_GRAPH, direct launches of the
- * pairs in order.  nadmm_get_status on the handle reports the first pair
+ * pointer changes) or, with NADMM_FLAG_NO_GRAPH, direct launches (flat: the
+ * phases in order; lanes: the pairs in order).  nadmm_get_status on the handle reports the first pair
  * whose status word is set.  Only nadmm_register_batched,
  * nadmm_backward_batched, nadmm_get_status, nadmm_workspace_size,
  * nadmm_set_workspace, nadmm_batch_set_lanes and nadmm_destroy accept a

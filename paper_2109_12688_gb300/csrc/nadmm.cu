@@ -97,6 +97,25 @@ struct nadmm_context {
   std::vector<size_t> lane_off, tab_off;
   std::vector<cudaStream_t> lane_cap;
   std::vector<cudaEvent_t> lane_ev;  // [0] fork, [1 + l] join of lane l
+  // flat batched execution: every pair has its own state region and each
+  // phase of the iteration is one launch over all pairs (the slab pass) or
+  // one launch per z plan (the z-pass); device tables at o_flat
+  bool flat = false;
+  struct ZGroup {
+    int r1, r2, first, count, blocks;  // pairs zorder[first .. first+count)
+  };
+  std::vector<ZGroup> zgroups;
+  std::vector<int> zorder;
+  // slab-pass launches: pairs grouped by shared-memory class (two CTAs per
+  // SM or one), so small planes keep their occupancy; blocks = CTAs
+  struct SGroup {
+    int first, count, blocks;
+    size_t smem;
+  };
+  std::vector<SGroup> sgroups;
+  std::vector<int> sorder;
+  size_t o_flat = 0, o_flat_args = 0, o_flat_final = 0, o_flat_start = 0, o_flat_pencil = 0,
+         o_flat_zstart = 0;
 
   template <class T>
   T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
@@ -504,6 +523,9 @@ nadmm_status check_dev_ptrs(std::initializer_list<const void*> ptrs) {
 }
 
 constexpr int kDefaultLanes = 2;
+// Largest slab-pass shared memory that still leaves room for two CTAs per SM
+// (228 KB per SM, 1 KB reserved per CTA).
+constexpr size_t kSlabTwoPerSm = 113 * 1024;
 
 // R2 tried first for an axis's lane plan: the flag bits, else the defaults
 // measured on 128x128x96 (x 8, y 16, z 8).
@@ -705,6 +727,78 @@ void assign_lanes(nadmm_context* b, int lanes) {
   b->total = o;
 }
 
+// Whether every pair of a batched handle can run flat: all on the slab path,
+// no reverse-mode tape (the reverse sweep runs per pair on lanes).
+bool flat_possible(const nadmm_context* b) {
+  if (b->cfg.flags & NADMM_FLAG_SAVE_FOR_BACKWARD) return false;
+  for (const nadmm_context* p : b->pairs)
+    if (!p->slab) return false;
+  return true;
+}
+
+// Flat layout: one state region per pair, every pair's tables, then the
+// launch tables (per-pair slab arguments for the passes and for the final
+// pass, CTA starts, per-pair z-pass arguments grouped by z plan, block starts).
+void assign_flat(nadmm_context* b) {
+  const int n = (int)b->pairs.size();
+  assign_lanes(b, n);  // n lanes of one pair each: every pair its own state region
+  b->flat = true;
+  b->zorder.clear();
+  b->zgroups.clear();
+  for (int i = 0; i < n; ++i) {
+    const AxisPlan& pz = b->pairs[i]->pz;
+    bool found = false;
+    for (auto& g : b->zgroups)
+      if (g.r1 == pz.radix[0] && g.r2 == pz.radix[1]) found = true;
+    if (found) continue;
+    nadmm_context::ZGroup g{pz.radix[0], pz.radix[1], (int)b->zorder.size(), 0, 0};
+    for (int j = i; j < n; ++j) {
+      const AxisPlan& qz = b->pairs[j]->pz;
+      if (qz.radix[0] == g.r1 && qz.radix[1] == g.r2) {
+        b->zorder.push_back(j);
+        ++g.count;
+      }
+    }
+    b->zgroups.push_back(g);
+  }
+  // slab groups: planes that leave room for two CTAs per SM, then the rest
+  b->sorder.clear();
+  b->sgroups.clear();
+  for (int cls = 0; cls < 2; ++cls) {
+    nadmm_context::SGroup g{(int)b->sorder.size(), 0, 0, 0};
+    for (int i = 0; i < n; ++i) {
+      const size_t sm = slab_smem_bytes(slab_args(b->pairs[i]));
+      if ((sm <= kSlabTwoPerSm) == (cls == 0)) {
+        b->sorder.push_back(i);
+        ++g.count;
+      }
+    }
+    if (g.count) b->sgroups.push_back(g);
+  }
+  size_t o = b->total;
+  b->o_flat = o;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o = align_up(o + bytes);
+    return r;
+  };
+  b->o_flat_args = take((size_t)n * sizeof(SlabArgs));
+  b->o_flat_final = take((size_t)n * sizeof(SlabArgs));
+  b->o_flat_start = take((size_t)(n + b->sgroups.size()) * sizeof(int));
+  b->o_flat_pencil = take((size_t)n * sizeof(PencilArgs));
+  b->o_flat_zstart = take((size_t)(n + b->zgroups.size()) * sizeof(int));
+  b->total = o;
+}
+
+// Lane count 0 means flat execution.
+void relayout(nadmm_context* b, int lanes) {
+  b->flat = false;
+  if (lanes == 0)
+    assign_flat(b);
+  else
+    assign_lanes(b, lanes);
+}
+
 // Every pass kernel may take up to the opt-in shared-memory limit; the
 // attribute belongs to the device that is current when it is set, so it is
 // raised to the maximum once per device and each launch asks for what its
@@ -813,6 +907,132 @@ nadmm_status replay(nadmm_context* h, int slot, const std::vector<const void*>& 
   }
   cudaError_t e = cudaGraphLaunch(gexec, stream);
   return e == cudaSuccess ? NADMM_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+// The flat launch tables of a batched handle (after its pairs are attached).
+cudaError_t upload_flat(nadmm_context* b) {
+  const int n = (int)b->pairs.size();
+  std::vector<SlabArgs> base(n), fin(n);
+  std::vector<int> start(n + b->sgroups.size(), 0);
+  for (size_t gi = 0; gi < b->sgroups.size(); ++gi) {
+    auto& g = b->sgroups[gi];
+    int ctas = 0;
+    g.smem = 0;
+    for (int j = 0; j < g.count; ++j) {
+      nadmm_context* p = b->pairs[b->sorder[g.first + j]];
+      SlabArgs& a = base[g.first + j];
+      a = slab_args(p);
+      fin[g.first + j] = a;
+      fin[g.first + j].w_out = p->at<float>(p->o_wp);  // the velocity w^K, as in enqueue_register
+      fin[g.first + j].b_out = nullptr;
+      fin[g.first + j].y = nullptr;
+      start[g.first + gi + j] = ctas;
+      ctas += 3 * p->cfg.nz;
+      g.smem = std::max(g.smem, slab_smem_bytes(a));
+    }
+    start[g.first + gi + g.count] = ctas;
+    g.blocks = ctas;
+  }
+  std::vector<PencilArgs> pen(n);
+  std::vector<int> zstart(n + b->zgroups.size(), 0);
+  for (size_t gi = 0; gi < b->zgroups.size(); ++gi) {
+    auto& g = b->zgroups[gi];
+    int blocks = 0;
+    for (int j = 0; j < g.count; ++j) {
+      nadmm_context* p = b->pairs[b->zorder[g.first + j]];
+      pen[g.first + j] = pencil_args(p);
+      zstart[g.first + gi + j] = blocks;
+      blocks += zslab_blocks(pen[g.first + j]);
+    }
+    zstart[g.first + gi + g.count] = blocks;
+    g.blocks = blocks;
+  }
+  char* t = b->ws;
+  TRY(cudaMemcpy(t + b->o_flat_args, base.data(), n * sizeof(SlabArgs), cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(t + b->o_flat_final, fin.data(), n * sizeof(SlabArgs), cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(t + b->o_flat_start, start.data(), start.size() * sizeof(int),
+                 cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(t + b->o_flat_pencil, pen.data(), n * sizeof(PencilArgs), cudaMemcpyHostToDevice));
+  TRY(cudaMemcpy(t + b->o_flat_zstart, zstart.data(), zstart.size() * sizeof(int),
+                 cudaMemcpyHostToDevice));
+  return cudaSuccess;
+}
+
+// All pairs of a flat batched handle: per-pair outer-step kernels, one slab
+// pass over all pairs and one z-pass per z plan for every ADMM iteration.
+cudaError_t enqueue_batched_flat(nadmm_context* b, const float* const* I0, const float* const* I1,
+                                 float* const* u_out, cudaStream_t s) {
+  const int n = (int)b->pairs.size();
+  const int O = b->cfg.outer_iters, K = b->cfg.inner_iters;
+  nadmm_context* p0 = b->pairs[0];
+  const SlabArgs* args = reinterpret_cast<const SlabArgs*>(b->ws + b->o_flat_args);
+  const SlabArgs* fin = reinterpret_cast<const SlabArgs*>(b->ws + b->o_flat_final);
+  const int* start = reinterpret_cast<const int*>(b->ws + b->o_flat_start);
+  const PencilArgs* pen = reinterpret_cast<const PencilArgs*>(b->ws + b->o_flat_pencil);
+  const int* zstart = reinterpret_cast<const int*>(b->ws + b->o_flat_zstart);
+  auto dst_of = [&](int i, int o) {
+    return ((O - 1 - o) % 2 == 0) ? u_out[i] : b->pairs[i]->at<float>(b->pairs[i]->o_ut);
+  };
+  auto slabs = [&](int mode, const SlabArgs* a, float beta, int k) -> cudaError_t {
+    for (size_t gi = 0; gi < b->sgroups.size(); ++gi) {
+      const auto& g = b->sgroups[gi];
+      TRY(launch_slab_multi(mode, a + g.first, start + g.first + gi, g.count, g.blocks, g.smem, beta,
+                            k, s));
+    }
+    return cudaSuccess;
+  };
+  auto zpasses = [&]() -> cudaError_t {
+    for (size_t gi = 0; gi < b->zgroups.size(); ++gi) {
+      const auto& g = b->zgroups[gi];
+      TRY(launch_zslab_multi(g.r1, g.r2, pen + g.first, zstart + g.first + gi, g.count, g.blocks, s));
+    }
+    return cudaSuccess;
+  };
+  std::vector<float*> u_cur(n);
+  for (int i = 0; i < n; ++i) {
+    nadmm_context* p = b->pairs[i];
+    unsigned* red = p->tab<unsigned>(p->o_red);
+    TRY(cudaMemsetAsync(red, 0, 4 * sizeof(unsigned), s));
+    if (p->restart) TRY(cudaMemsetAsync(p->tab<unsigned>(p->o_rwords), 0, 2 * sizeof(unsigned), s));
+    u_cur[i] = (dst_of(i, 0) == u_out[i]) ? p->at<float>(p->o_ut) : u_out[i];
+    TRY(cudaMemsetAsync(u_cur[i], 0, 3 * p->V * sizeof(float), s));
+  }
+  for (int i = 0; i < n; ++i) {
+    nadmm_context* p = b->pairs[i];
+    TRY(launch_warp(dims_of(p), I1[i], u_cur[i], p->at<float>(p->o_I1w), nullptr, s));
+    TRY(launch_grad_residual(dims_of(p), p->at<float>(p->o_I1w), I0[i], p->at<float>(p->o_J),
+                             p->at<float>(p->o_c), s));
+  }
+  for (int o = 0; o < O; ++o) {
+    TRY(slabs(SLAB_FIRST, args, 0.0f, 0));
+    for (int k = 1; k < K; ++k) {
+      TRY(zpasses());
+      TRY(slabs(k >= 2 ? SLAB_SPEC_PREV : SLAB_SPEC, args, beta_for(p0, k), k));
+    }
+    TRY(zpasses());
+    TRY(slabs(SLAB_FINAL, fin, 0.0f, K));
+    for (int i = 0; i < n; ++i) {
+      nadmm_context* p = b->pairs[i];
+      const Dims d = dims_of(p);
+      unsigned* red = p->tab<unsigned>(p->o_red);
+      float* vbuf = p->at<float>(p->o_wp);
+      TRY(launch_bound_reduce(d, vbuf, red, s));
+      float* u_new = dst_of(i, o);
+      TRY(launch_compose(d, vbuf, u_cur[i], u_new, red, p->cfg.bound_kappa, p->cfg.bound_delta,
+                         red + 2, nullptr, s));
+      u_cur[i] = u_new;
+    }
+    if (o + 1 < O) {
+      for (int i = 0; i < n; ++i) {
+        nadmm_context* p = b->pairs[i];
+        TRY(launch_warp(dims_of(p), I1[i], u_cur[i], p->at<float>(p->o_I1w),
+                        p->tab<unsigned>(p->o_red), s));
+        TRY(launch_grad_residual(dims_of(p), p->at<float>(p->o_I1w), I0[i], p->at<float>(p->o_J),
+                                 p->at<float>(p->o_c), s));
+      }
+    }
+  }
+  return cudaSuccess;
 }
 
 // Streams and events of the lanes (created outside any stream capture).
@@ -1090,7 +1310,10 @@ nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, cons
     }
     b->pairs.push_back(p);
   }
-  assign_lanes(b, std::min(npairs, kDefaultLanes));
+  if (flat_possible(b))
+    relayout(b, 0);
+  else
+    relayout(b, std::min(npairs, kDefaultLanes));
   *out = b;
   return NADMM_OK;
 }
@@ -1174,21 +1397,27 @@ nadmm_status nadmm_batch_set_pair_plan(nadmm_handle h, int32_t pair, uint32_t pl
   if (st != NADMM_OK) return st;
   destroy_context(h->pairs[pair]);
   h->pairs[pair] = q;
-  assign_lanes(h, h->lanes);
+  if (h->flat)
+    relayout(h, flat_possible(h) ? 0 : std::min<int>((int)h->pairs.size(), kDefaultLanes));
+  else
+    relayout(h, h->lanes);
   return NADMM_OK;
 }
 
 nadmm_status nadmm_batch_set_lanes(nadmm_handle h, int32_t lanes) {
   if (!h || !h->batched) return fail(NADMM_ERR_INVALID_ARG, "not a batched handle");
-  if (lanes < 1) return fail(NADMM_ERR_INVALID_ARG, "lanes must be >= 1");
+  if (lanes < 0) return fail(NADMM_ERR_INVALID_ARG, "lanes must be >= 0 (0: flat)");
   if (h->wt) return fail(NADMM_ERR_INVALID_ARG, "set the lane count before nadmm_set_workspace");
-  assign_lanes(h, std::min<int>(lanes, (int)h->pairs.size()));
+  if (lanes == 0 && !flat_possible(h))
+    return fail(NADMM_ERR_INVALID_ARG,
+                "flat execution needs every pair on the slab path and no reverse-mode tape");
+  relayout(h, lanes == 0 ? 0 : std::min<int>(lanes, (int)h->pairs.size()));
   return NADMM_OK;
 }
 
 nadmm_status nadmm_batch_get_lanes(nadmm_handle h, int32_t* lanes) {
   if (!h || !h->batched || !lanes) return fail(NADMM_ERR_INVALID_ARG, "not a batched handle");
-  *lanes = h->lanes;
+  *lanes = h->flat ? 0 : h->lanes;
   return NADMM_OK;
 }
 
@@ -1232,13 +1461,14 @@ nadmm_status nadmm_set_workspace(nadmm_handle h, void* dev_ptr, size_t bytes) {
         return st;
       }
     }
-    e = ensure_lanes(h);
-    if (e != cudaSuccess) {
-      for (nadmm_context* q : h->pairs) q->ws = q->wt = nullptr;
-      return cuda_fail(e, "lane streams");
-    }
     h->ws = base;
     h->wt = base;
+    e = h->flat ? upload_flat(h) : ensure_lanes(h);
+    if (e != cudaSuccess) {
+      for (nadmm_context* q : h->pairs) q->ws = q->wt = nullptr;
+      h->ws = h->wt = nullptr;
+      return cuda_fail(e, h->flat ? "flat launch tables" : "lane streams");
+    }
   }
   return NADMM_OK;
 }
@@ -1356,7 +1586,13 @@ nadmm_status nadmm_register_batched(nadmm_handle h, const float* const* fixed,
     key.push_back(u_out[i]);
   }
   cudaStream_t s = (cudaStream_t)stream;
-  if (h->cfg.flags & NADMM_FLAG_NO_GRAPH) {
+  if (h->flat && (h->cfg.flags & NADMM_FLAG_NO_GRAPH)) {
+    cudaError_t e = enqueue_batched_flat(h, fixed, moving, u_out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "nadmm_register_batched");
+  } else if (h->flat) {
+    st = replay(h, 0, key, s, "capture of nadmm_register_batched",
+                [&](cudaStream_t cs) { return enqueue_batched_flat(h, fixed, moving, u_out, cs); });
+  } else if (h->cfg.flags & NADMM_FLAG_NO_GRAPH) {
     for (int i = 0; i < n; ++i) {
       cudaError_t e = enqueue_register(h->pairs[i], fixed[i], moving[i], u_out[i], s);
       if (e != cudaSuccess) return cuda_fail(e, "nadmm_register_batched");

@@ -159,6 +159,15 @@ cudaError_t launch_slab(int mode, const SlabArgs& a, cudaStream_t s);
 // order_n, gamma, scale of the pencil arguments)
 cudaError_t launch_zslab(const PencilArgs& a, cudaStream_t s);
 cudaError_t configure_slab_kernels();
+// Many grids in one launch (batched handles): pairs[p] for the CTAs / blocks
+// [start[p], start[p+1]); the slab pass's CTAs per pair are 3 nz_p, the z-pass
+// blocks per pair zslab_blocks(); every pair of one z-pass launch shares the
+// z plan [r1, r2].  smem: the largest pair's slab_smem_bytes.
+cudaError_t launch_slab_multi(int mode, const SlabArgs* pairs, const int* start, int npairs,
+                              int total_ctas, size_t smem, float beta, int k, cudaStream_t s);
+int zslab_blocks(const PencilArgs& a);
+cudaError_t launch_zslab_multi(int r1, int r2, const PencilArgs* pairs, const int* start, int npairs,
+                               int total_blocks, cudaStream_t s);
 
 constexpr unsigned kStatusNonfinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;

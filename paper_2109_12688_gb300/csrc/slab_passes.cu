@@ -224,62 +224,56 @@ __device__ __forceinline__ float4* real_quad(float2* plane, int nkx, int y, int 
 // is kept, and the thread's share of c_{k-1} is returned.
 template <int MODE, bool RST>
 __device__ __forceinline__ float slab_pointwise(const SlabArgs& a, float2* const (&planes)[3], int z,
-                                                int q0, int q1) {
+                                                int q0, int q1, float beta_k, int k) {
   const size_t V = (size_t)a.nx * a.ny * a.nz;
   const int qrow = a.nx >> 2;
-  const bool prev = (MODE == SLAB_SPEC_PREV) || (MODE == SLAB_STATE_PREV);
-  const float beta = RST ? a.beta_dev[a.k] : a.beta;
+  constexpr bool kPrev = (MODE == SLAB_SPEC_PREV) || (MODE == SLAB_STATE_PREV);
+  constexpr bool kState = (MODE == SLAB_STATE) || (MODE == SLAB_STATE_PREV);
+  constexpr bool kSpec = (MODE == SLAB_SPEC) || (MODE == SLAB_SPEC_PREV);
+  const float beta = RST ? a.beta_dev[k] : beta_k;
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   float racc = 0.0f;
   for (int q = q0 + (int)threadIdx.x; q < q1; q += kSlabThreads) {
     const int yy = (int)fdiv((uint32_t)q, a.qdiv);
     const int x0 = (q - yy * qrow) << 2;
     const size_t vox = ((size_t)z * a.ny + yy) * a.nx + x0;
-    float4 wk1[3], bk1[3], wh[3], bh[3], Jq[3], yq[3];
+    // every load of the quad is issued before the first store (the stores
+    // may alias nothing the quad reads, but the compiler cannot know that)
+    float4 wk1[3], yq[3], wq[3], bq[3], Jq[3], up[3];
     const float4 cq = __ldg(reinterpret_cast<const float4*>(a.c + vox));
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t i = c * V + vox;
       Jq[c] = __ldg(reinterpret_cast<const float4*>(a.J + i));
-      if (MODE == SLAB_FIRST) {
-        wk1[c] = bk1[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-      } else if (MODE == SLAB_STATE || MODE == SLAB_STATE_PREV) {
-        wk1[c] = __ldg(reinterpret_cast<const float4*>(a.w_in + i));
-        bk1[c] = __ldg(reinterpret_cast<const float4*>(a.b_in + i));
-      } else {
+      if (kSpec) {
         wk1[c] = *real_quad(planes[c], a.nkx, yy, x0);
-        yq[c] = *reinterpret_cast<const float4*>(a.y + i);
-        bk1[c] = f4sub(yq[c], wk1[c]);
-      }
-      if (prev) {
-        const float4 wq = (MODE == SLAB_STATE_PREV)
-                              ? __ldg(reinterpret_cast<const float4*>(a.wprev_in + i))
-                              : *reinterpret_cast<const float4*>(a.wp + i);
-        const float4 bq = (MODE == SLAB_STATE_PREV)
-                              ? __ldg(reinterpret_cast<const float4*>(a.bprev_in + i))
-                              : *reinterpret_cast<const float4*>(a.bp + i);
-        wh[c] = f4extra(wk1[c], wq, beta);
-        bh[c] = f4extra(bk1[c], bq, beta);
+        yq[c] = __ldcg(reinterpret_cast<const float4*>(a.y + i));
+      } else if (kState) {
+        wk1[c] = __ldg(reinterpret_cast<const float4*>(a.w_in + i));
+        yq[c] = __ldg(reinterpret_cast<const float4*>(a.b_in + i));  // b^{k-1} itself
       } else {
-        wh[c] = wk1[c];
-        bh[c] = bk1[c];
+        wk1[c] = yq[c] = zero4;
       }
-      if (MODE != SLAB_FIRST) {  // w^{k-1}, b^{k-1} into the state slots
-        *reinterpret_cast<float4*>(a.wp + i) = wk1[c];
-        *reinterpret_cast<float4*>(a.bp + i) = bk1[c];
+      if (kPrev) {
+        wq[c] = (MODE == SLAB_STATE_PREV) ? __ldg(reinterpret_cast<const float4*>(a.wprev_in + i))
+                                          : __ldcg(reinterpret_cast<const float4*>(a.wp + i));
+        bq[c] = (MODE == SLAB_STATE_PREV) ? __ldg(reinterpret_cast<const float4*>(a.bprev_in + i))
+                                          : __ldcg(reinterpret_cast<const float4*>(a.bp + i));
       }
+      if (RST) up[c] = (MODE == SLAB_SPEC_PREV) ? __ldcg(reinterpret_cast<const float4*>(a.u_prev + i))
+                                                : zero4;
+    }
+    float4 bk1[3], wh[3], bh[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      bk1[c] = kSpec ? f4sub(yq[c], wk1[c]) : yq[c];
+      wh[c] = kPrev ? f4extra(wk1[c], wq[c], beta) : wk1[c];
+      bh[c] = kPrev ? f4extra(bk1[c], bq[c], beta) : bk1[c];
     }
     if (RST) {
       // c_{k-1}: w_hat^{k-1}, b_hat^{k-1} from u^{k-1} = w_hat - b_hat and
       // y^{k-1} = v^{k-1} + b_hat^{k-1}, v^{k-1} the v-step at u^{k-1}
-      // (both zero for k = 1); u^k replaces u^{k-1}
-      float4 up[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const size_t i = c * V + vox;
-        up[c] = (MODE == SLAB_SPEC_PREV) ? *reinterpret_cast<const float4*>(a.u_prev + i)
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-        *reinterpret_cast<float4*>(a.u_prev + i) = f4sub(wh[c], bh[c]);
-      }
+      // (both zero for k = 1)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         if (MODE == SLAB_SPEC_PREV) {
@@ -321,7 +315,13 @@ __device__ __forceinline__ float slab_pointwise(const SlabArgs& a, float2* const
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      *reinterpret_cast<float4*>(a.y + c * V + vox) = yn[c];
+      const size_t i = c * V + vox;
+      if (MODE != SLAB_FIRST) {  // w^{k-1}, b^{k-1} into the state slots
+        __stcg(reinterpret_cast<float4*>(a.wp + i), wk1[c]);
+        __stcg(reinterpret_cast<float4*>(a.bp + i), bk1[c]);
+      }
+      if (RST) __stcg(reinterpret_cast<float4*>(a.u_prev + i), f4sub(wh[c], bh[c]));
+      __stcg(reinterpret_cast<float4*>(a.y + i), yn[c]);
       *real_quad(planes[c], a.nkx, yy, x0) = yn[c];
     }
   }
@@ -333,7 +333,8 @@ __device__ __forceinline__ float slab_pointwise(const SlabArgs& a, float2* const
 // report compares c_{k-1} with eta cbar and, on a restart, rewrites the
 // factors of iterations k + 1 .. kmax as beta_0, beta_1, ...  All threads of
 // the CTA call this.
-__device__ __forceinline__ void slab_restart_test(const SlabArgs& a, float part) {
+__device__ __forceinline__ void slab_restart_test(const SlabArgs& a, float part, int k,
+                                                  unsigned nctas) {
   __shared__ float warp_sum[kSlabWarps];
   for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
   if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = part;
@@ -343,7 +344,7 @@ __device__ __forceinline__ void slab_restart_test(const SlabArgs& a, float part)
     for (int w = 0; w < kSlabWarps; ++w) cta += warp_sum[w];
     atomicAdd(a.racc, cta);
     __threadfence();
-    if (atomicAdd(a.rwords, 1u) == gridDim.x - 1) {  // every CTA has reported
+    if (atomicAdd(a.rwords, 1u) == nctas - 1) {  // every CTA of the pair has reported
       __threadfence();
       const double ck = atomicAdd(a.racc, 0.0);
       const double cbar = a.racc[1];
@@ -351,8 +352,8 @@ __device__ __forceinline__ void slab_restart_test(const SlabArgs& a, float part)
         a.racc[1] = ck;
       } else {
         if (a.eta > 0.0f) a.racc[1] = cbar / (double)a.eta;
-        for (int m = 0; a.k + 1 + m <= a.kmax; ++m) a.beta_dev[a.k + 1 + m] = a.beta_seq[m];
-        if (a.k + 1 <= a.kmax) a.rwords[1] += 1u;  // count restarts that take effect
+        for (int m = 0; k + 1 + m <= a.kmax; ++m) a.beta_dev[k + 1 + m] = a.beta_seq[m];
+        if (k + 1 <= a.kmax) a.rwords[1] += 1u;  // count restarts that take effect
       }
       a.racc[0] = 0.0;
       a.rwords[0] = 0u;
@@ -362,12 +363,14 @@ __device__ __forceinline__ void slab_restart_test(const SlabArgs& a, float part)
 }
 #endif
 
-// MODE: SLAB_FIRST, SLAB_SPEC (k = 1), SLAB_SPEC_PREV (k >= 2), SLAB_FINAL,
-// SLAB_FIELD, SLAB_STATE (k = 1), SLAB_STATE_PREV (k >= 2).
-template <int MODE>
-__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kSlabThreads, 2)
-    k_slab(const __grid_constant__ SlabArgs a) {
 #if defined(__CUDA_ARCH__)
+// The slab pass of z-plane z of one grid (pair), run by the cluster of three
+// CTAs that owns it: beta_k and k are the factor and index of the iteration
+// the pass starts, nctas the pair's CTA count, lead the CTA that resets the
+// restart state of a new inner loop.
+template <int MODE>
+__device__ __forceinline__ void slab_body(const SlabArgs& a, int z, float beta_k, int k,
+                                          unsigned nctas, bool lead) {
   constexpr bool kInverse = (MODE == SLAB_SPEC || MODE == SLAB_SPEC_PREV || MODE == SLAB_FINAL);
   constexpr bool kForward = (MODE != SLAB_FINAL);
   constexpr bool kCoupled = (MODE != SLAB_FINAL && MODE != SLAB_FIELD);
@@ -377,7 +380,6 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kSlabThreads, 2)
   float2* xch = plane + (size_t)a.ny * a.nkx;
   cg::cluster_group cluster = cg::this_cluster();
   const int comp = (int)cluster.block_rank();
-  const int z = (int)(blockIdx.x / 3);
   const int tid = threadIdx.x;
   const uint32_t plane_bytes = (uint32_t)((size_t)a.ny * a.nkx * sizeof(float2));
   float2* gplane = a.spec + ((size_t)z * 3 + comp) * a.ny * a.nkx;
@@ -411,7 +413,7 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kSlabThreads, 2)
                                cluster.map_shared_rank(plane, 2)};
     const int Q = a.ny * (a.nx >> 2);
     const int q0 = (int)((long long)Q * comp / 3), q1 = (int)((long long)Q * (comp + 1) / 3);
-    if (MODE == SLAB_FIRST && a.restart && blockIdx.x == 0 && tid == 0) {
+    if (MODE == SLAB_FIRST && a.restart && lead && tid == 0) {
       // a new inner loop: the factors of Eq. 5, cbar = +inf
       for (int i = 0; i <= a.kmax; ++i) a.beta_dev[i] = (i == 0) ? 0.0f : a.beta_seq[i - 1];
       a.racc[0] = 0.0;
@@ -419,10 +421,10 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kSlabThreads, 2)
       a.rwords[0] = 0u;
     }
     if ((MODE == SLAB_SPEC || MODE == SLAB_SPEC_PREV) && a.restart) {
-      const float part = slab_pointwise<MODE, true>(a, planes, z, q0, q1);
-      slab_restart_test(a, part);
+      const float part = slab_pointwise<MODE, true>(a, planes, z, q0, q1, beta_k, k);
+      slab_restart_test(a, part, k, nctas);
     } else {
-      slab_pointwise<MODE, false>(a, planes, z, q0, q1);
+      slab_pointwise<MODE, false>(a, planes, z, q0, q1, beta_k, k);
     }
     cluster.sync();  // every plane holds y^k; no remote access after this
   } else {
@@ -457,8 +459,37 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kSlabThreads, 2)
       bulk_wait_read();  // shared memory must stay until the store has read it
     }
   }
+}
+#endif
+
+// MODE: SLAB_FIRST, SLAB_SPEC (k = 1), SLAB_SPEC_PREV (k >= 2), SLAB_FINAL,
+// SLAB_FIELD, SLAB_STATE (k = 1), SLAB_STATE_PREV (k >= 2).
+template <int MODE>
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kSlabThreads, 2)
+    k_slab(const __grid_constant__ SlabArgs a) {
+#if defined(__CUDA_ARCH__)
+  slab_body<MODE>(a, (int)(blockIdx.x / 3), a.beta, a.k, gridDim.x, blockIdx.x == 0);
 #endif
 }
+
+// The slab pass of many grids in one launch: pair p owns CTAs
+// [start[p], start[p+1]) (3 nz_p of them, so no cluster straddles two pairs).
+template <int MODE>
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kSlabThreads, 2)
+    k_slab_multi(const SlabArgs* __restrict__ pairs, const int* __restrict__ start, int npairs,
+                 float beta_k, int k) {
+#if defined(__CUDA_ARCH__)
+  int lo = 0, hi = npairs - 1;  // the last pair whose first CTA is <= blockIdx.x
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const int local = (int)blockIdx.x - __ldg(start + lo);
+  slab_body<MODE>(pairs[lo], local / 3, beta_k, k, (unsigned)(__ldg(start + lo + 1) - __ldg(start + lo)),
+                  local == 0);
+#endif
+}
+
 
 // ---------------------------------------------------------------- z-pass
 constexpr int kZSlabThreads = 128;  // 4 independent warps
@@ -473,8 +504,7 @@ constexpr int zslab_min_blocks() {
 // last forward stage, the multiply by 1/(1 + gamma K^n)/(nx ny nz) and the
 // first inverse stage.
 template <int R1, int R2>
-__global__ void __launch_bounds__(kZSlabThreads, zslab_min_blocks<R1, R2>())
-    k_zslab(const __grid_constant__ PencilArgs a) {
+__device__ __forceinline__ void zslab_body(const PencilArgs& a, int blk) {
   constexpr int N = R1 * R2, CPW = 32 / R2;
   constexpr int P = N + (R2 == 8 ? 4 : 8);
   extern __shared__ float2 sm_all[];
@@ -483,7 +513,7 @@ __global__ void __launch_bounds__(kZSlabThreads, zslab_min_blocks<R1, R2>())
   float2* sm = sm_all + (warp * CPW + col) * P;
   const int groups = (a.nkx + CPW - 1) / CPW;  // kx groups per (component, y) row
   const int tasks = 3 * a.ny * groups;
-  const int task = blockIdx.x * (kZSlabThreads / 32) + warp;
+  const int task = blk * (kZSlabThreads / 32) + warp;
   const bool task_ok = task < tasks;
   const int row = task_ok ? task / groups : 0;  // component * ny + y
   const int kx0 = (task_ok ? task - row * groups : 0) * CPW + col;
@@ -526,6 +556,25 @@ __global__ void __launch_bounds__(kZSlabThreads, zslab_min_blocks<R1, R2>())
 #pragma unroll
     for (int j = 0; j < R1; ++j) __stcg(base + (l + R2 * j) * zs, v[j]);
   }
+}
+
+template <int R1, int R2>
+__global__ void __launch_bounds__(kZSlabThreads, zslab_min_blocks<R1, R2>())
+    k_zslab(const __grid_constant__ PencilArgs a) {
+  zslab_body<R1, R2>(a, (int)blockIdx.x);
+}
+
+// The z-pass of many grids sharing the z plan [R1, R2] in one launch: pair p
+// owns blocks [start[p], start[p+1]).
+template <int R1, int R2>
+__global__ void __launch_bounds__(kZSlabThreads, zslab_min_blocks<R1, R2>())
+    k_zslab_multi(const PencilArgs* __restrict__ pairs, const int* __restrict__ start, int npairs) {
+  int lo = 0, hi = npairs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  zslab_body<R1, R2>(pairs[lo], (int)blockIdx.x - __ldg(start + lo));
 }
 
 // ---------------------------------------------------------------- host side
@@ -606,8 +655,56 @@ cudaError_t launch_zslab(const PencilArgs& a, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_slab_multi(int mode, const SlabArgs* pairs, const int* start, int npairs,
+                              int total_ctas, size_t smem, float beta, int k, cudaStream_t s) {
+  const dim3 grid((unsigned)total_ctas), block(kSlabThreads);
+  switch (mode) {
+    case SLAB_FIRST:
+      return launch_pdl(k_slab_multi<SLAB_FIRST>, grid, block, smem, s, pairs, start, npairs, beta, k);
+    case SLAB_SPEC:
+      return launch_pdl(k_slab_multi<SLAB_SPEC>, grid, block, smem, s, pairs, start, npairs, beta, k);
+    case SLAB_SPEC_PREV:
+      return launch_pdl(k_slab_multi<SLAB_SPEC_PREV>, grid, block, smem, s, pairs, start, npairs,
+                        beta, k);
+    case SLAB_FINAL:
+      return launch_pdl(k_slab_multi<SLAB_FINAL>, grid, block, smem, s, pairs, start, npairs, beta, k);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int zslab_blocks(const PencilArgs& a) {
+  const int cpw = 32 / a.pz.radix[1];
+  const int tasks = 3 * a.ny * ((a.nkx + cpw - 1) / cpw);
+  const int per_cta = kZSlabThreads / 32;
+  return (tasks + per_cta - 1) / per_cta;
+}
+
+namespace {
+template <int R1, int R2>
+cudaError_t launch_z_multi(const PencilArgs* pairs, const int* start, int npairs, int blocks,
+                           cudaStream_t s) {
+  constexpr int N = R1 * R2, CPW = 32 / R2;
+  const size_t smem = (size_t)(kZSlabThreads / 32) * CPW * (N + (R2 == 8 ? 4 : 8)) * sizeof(float2);
+  return launch_pdl(k_zslab_multi<R1, R2>, dim3((unsigned)blocks), dim3(kZSlabThreads), smem, s,
+                    pairs, start, npairs);
+}
+}  // namespace
+
+cudaError_t launch_zslab_multi(int r1, int r2, const PencilArgs* pairs, const int* start, int npairs,
+                               int total_blocks, cudaStream_t s) {
+#define X(A, B) \
+  if (r1 == A && r2 == B) return launch_z_multi<A, B>(pairs, start, npairs, total_blocks, s);
+  NADMM_LANE_CASES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t configure_slab_kernels() {
   cudaError_t e;
+  if ((e = raise_smem(k_slab_multi<SLAB_FIRST>)) != cudaSuccess) return e;
+  if ((e = raise_smem(k_slab_multi<SLAB_SPEC>)) != cudaSuccess) return e;
+  if ((e = raise_smem(k_slab_multi<SLAB_SPEC_PREV>)) != cudaSuccess) return e;
+  if ((e = raise_smem(k_slab_multi<SLAB_FINAL>)) != cudaSuccess) return e;
   if ((e = raise_smem(k_slab<SLAB_FIRST>)) != cudaSuccess) return e;
   if ((e = raise_smem(k_slab<SLAB_SPEC>)) != cudaSuccess) return e;
   if ((e = raise_smem(k_slab<SLAB_SPEC_PREV>)) != cudaSuccess) return e;

@@ -120,3 +120,51 @@ def test_batch_of_64_uneven_pairs(lib):
         assert int(cnt.item()) == 0, d
         assert torch.isfinite(u).all()
         reg.close()
+
+
+# grids on the slab path, one of them (160 x 160 x 112) in the one-CTA-per-SM
+# shared-memory class, so a flat batch runs two slab launches per phase
+FLAT = [(32, 32, 24), (64, 48, 48), (160, 160, 112), (96, 112, 80), (48, 32, 24), (32, 32, 24)]
+
+
+def test_flat_batch_is_default_and_equals_single_and_lane_runs(lib):
+    """Flat execution (every ADMM phase one launch over all pairs, z-passes
+    one launch per z plan): bit-identical to single-pair calls and to the
+    per-pair lanes, with and without graph capture."""
+    pairs = [synth.make_pair(d, seed=70 + i) for i, d in enumerate(FLAT)]
+    fixed = [dev(p["fixed"]) for p in pairs]
+    moving = [dev(p["moving"]) for p in pairs]
+    flat = lib.BatchedRegistration(FLAT, device=DEV, **KW)
+    assert lib.nadmm_batch_get_lanes(flat.handle) == 0
+    us = [u.clone() for u in flat.register(fixed, moving)]
+    again = flat.register(fixed, moving)  # graph replay
+    lanes = lib.BatchedRegistration(FLAT, device=DEV, lanes=2, **KW).register(fixed, moving)
+    direct = lib.BatchedRegistration(FLAT, device=DEV, lanes=0, flags=lib.NADMM_FLAG_NO_GRAPH,
+                                     **KW).register(fixed, moving)
+    for i, d in enumerate(FLAT):
+        assert torch.equal(us[i], again[i]), d
+        assert torch.equal(us[i], lanes[i]), d
+        assert torch.equal(us[i], direct[i]), d
+        assert np.array_equal(us[i].cpu().numpy(), single(lib, d, fixed[i], moving[i], **KW)), d
+    ref = O.register(pairs[1]["fixed"], pairs[1]["moving"], lam=10.0, theta=0.1, n=2, outer=2,
+                     inner=4)
+    assert np.abs(us[1].cpu().numpy() - ref).max() <= 1e-3
+
+
+def test_flat_batch_with_restart_equals_single(lib):
+    kw = dict(order_n=2, lam=10.0, theta=0.02, outer=2, inner=16, restart_eta=0.999)
+    dims = [FLAT[0], FLAT[1], FLAT[4]]
+    pairs = [synth.make_pair(d, seed=80 + i) for i, d in enumerate(dims)]
+    fixed = [dev(p["fixed"]) for p in pairs]
+    moving = [dev(p["moving"]) for p in pairs]
+    us = lib.BatchedRegistration(dims, device=DEV, **kw).register(fixed, moving)
+    for i, d in enumerate(dims):
+        assert np.array_equal(us[i].cpu().numpy(), single(lib, d, fixed[i], moving[i], **kw)), d
+
+
+def test_flat_needs_slab_pairs(lib):
+    b = lib.nadmm_create_batched(lib.make_config(SMALL[0]), SMALL)
+    assert lib.nadmm_batch_get_lanes(b) == 2  # a pair off the slab path: lanes by default
+    with pytest.raises(lib.NadmmError):
+        lib.nadmm_batch_set_lanes(b, 0)
+    lib.nadmm_destroy(b)
