@@ -635,13 +635,13 @@ cudaError_t launch_slab(int mode, const SlabArgs& a, cudaStream_t s) {
   const dim3 grid((unsigned)(3 * a.nz)), block(kSlabThreads);
   const size_t smem = slab_smem_bytes(a);
   switch (mode) {
-    case SLAB_FIRST: return launch_pdl(k_slab<SLAB_FIRST>, grid, block, smem, s, a);
-    case SLAB_SPEC: return launch_pdl(k_slab<SLAB_SPEC>, grid, block, smem, s, a);
-    case SLAB_SPEC_PREV: return launch_pdl(k_slab<SLAB_SPEC_PREV>, grid, block, smem, s, a);
-    case SLAB_FINAL: return launch_pdl(k_slab<SLAB_FINAL>, grid, block, smem, s, a);
-    case SLAB_FIELD: return launch_pdl(k_slab<SLAB_FIELD>, grid, block, smem, s, a);
-    case SLAB_STATE: return launch_pdl(k_slab<SLAB_STATE>, grid, block, smem, s, a);
-    case SLAB_STATE_PREV: return launch_pdl(k_slab<SLAB_STATE_PREV>, grid, block, smem, s, a);
+    case SLAB_FIRST: return launch_whole(k_slab<SLAB_FIRST>, grid, block, smem, s, a);
+    case SLAB_SPEC: return launch_whole(k_slab<SLAB_SPEC>, grid, block, smem, s, a);
+    case SLAB_SPEC_PREV: return launch_whole(k_slab<SLAB_SPEC_PREV>, grid, block, smem, s, a);
+    case SLAB_FINAL: return launch_whole(k_slab<SLAB_FINAL>, grid, block, smem, s, a);
+    case SLAB_FIELD: return launch_whole(k_slab<SLAB_FIELD>, grid, block, smem, s, a);
+    case SLAB_STATE: return launch_whole(k_slab<SLAB_STATE>, grid, block, smem, s, a);
+    case SLAB_STATE_PREV: return launch_whole(k_slab<SLAB_STATE_PREV>, grid, block, smem, s, a);
   }
   return cudaErrorInvalidValue;
 }
@@ -660,14 +660,14 @@ cudaError_t launch_slab_multi(int mode, const SlabArgs* pairs, const int* start,
   const dim3 grid((unsigned)total_ctas), block(kSlabThreads);
   switch (mode) {
     case SLAB_FIRST:
-      return launch_pdl(k_slab_multi<SLAB_FIRST>, grid, block, smem, s, pairs, start, npairs, beta, k);
+      return launch_whole(k_slab_multi<SLAB_FIRST>, grid, block, smem, s, pairs, start, npairs, beta, k);
     case SLAB_SPEC:
-      return launch_pdl(k_slab_multi<SLAB_SPEC>, grid, block, smem, s, pairs, start, npairs, beta, k);
+      return launch_whole(k_slab_multi<SLAB_SPEC>, grid, block, smem, s, pairs, start, npairs, beta, k);
     case SLAB_SPEC_PREV:
-      return launch_pdl(k_slab_multi<SLAB_SPEC_PREV>, grid, block, smem, s, pairs, start, npairs,
+      return launch_whole(k_slab_multi<SLAB_SPEC_PREV>, grid, block, smem, s, pairs, start, npairs,
                         beta, k);
     case SLAB_FINAL:
-      return launch_pdl(k_slab_multi<SLAB_FINAL>, grid, block, smem, s, pairs, start, npairs, beta, k);
+      return launch_whole(k_slab_multi<SLAB_FINAL>, grid, block, smem, s, pairs, start, npairs, beta, k);
   }
   return cudaErrorInvalidValue;
 }
