@@ -32,6 +32,28 @@ __device__ __forceinline__ void lane_stage1(float2 (&v)[R1], const float2* __res
   }
 }
 
+// lane_stage1 with the lane's twiddles already in registers: twr[k - 1] =
+// tw[(k - 1) R2 + l], k = 1 .. R1 - 1.
+template <int R1, int R2, bool INV>
+__device__ __forceinline__ void lane_stage1_reg(float2 (&v)[R1], const float2 (&twr)[R1 - 1]) {
+  if (!INV) {
+    dft<R1, false>(v);
+#pragma unroll
+    for (int k = 1; k < R1; ++k) v[k] = cmul(v[k], twr[k - 1]);
+  } else {
+#pragma unroll
+    for (int k = 1; k < R1; ++k) v[k] = cmulc(v[k], twr[k - 1]);
+    dft<R1, true>(v);
+  }
+}
+
+template <int R1, int R2>
+__device__ __forceinline__ void lane_twiddles(const float2* __restrict__ tw, int l,
+                                              float2 (&twr)[R1 - 1]) {
+#pragma unroll
+  for (int k = 1; k < R1; ++k) twr[k - 1] = __ldg(tw + (k - 1) * R2 + l);
+}
+
 // Second stage on whole blocks b = l, l + R2, ... < R1 of a swizzled line.
 template <int R1, int R2, bool INV>
 __device__ __forceinline__ void lane_stage2(float2* line, int l) {

@@ -65,19 +65,37 @@ size_t slab_smem_bytes(const SlabArgs& a) {
 
 #if defined(__CUDA_ARCH__)
 // ---------------------------------------------------------------- x-DFT of rows
+// The x plan is [R1, R2] of M = nx/2 (R2 = 8): frequency k sits at position
+// (k mod R1) R2 + k / R1 after the forward transform, position p holds
+// frequency (p mod R2) R1 + p / R2.  Lane l's twiddles and the factors
+// e^{-2 pi i k / nx} of its pre- and post-processing are loop-invariant and
+// held in registers for all rows.
 template <int R1, int R2>
-__device__ __forceinline__ void row_inverse(const SlabArgs& a, float2* row, float2* buf, int l,
-                                            unsigned gmask, int y) {
+struct RowLane {
+  float2 tw[R1 - 1];
+  float2 rt_post[R1 + 1];  // e^{-2 pi i k / nx}, k = l + R2 j (j <= R1; k <= M)
+  float2 rt_pre[R1 > R2 ? 2 * R2 : R2];  // e^{-2 pi i k / nx}, k = b + R1 j of lane l's blocks
+};
+
+template <int R1, int R2>
+__device__ __forceinline__ int row_pos(int k) {
+  return (k % R1) * R2 + k / R1;
+}
+
+template <int R1, int R2>
+__device__ __forceinline__ void row_inverse(float2* row, float2* buf, int l, unsigned gmask, int y,
+                                            const RowLane<R1, R2>& L) {
   constexpr int M = R1 * R2;
-  for (int b = l; b < R1; b += R2) {
+  int blk = 0;
+  for (int b = l; b < R1; b += R2, ++blk) {
     float2 w[R2];
 #pragma unroll
     for (int j = 0; j < R2; ++j) {
-      const int k = __ldg(a.fqx + b * R2 + j);
+      const int k = b + R1 * j;  // frequency held at position b R2 + j
       const float2 xa = row[k], xb = row[M - k];
       const float2 A = make_float2(xa.x + xb.x, xa.y - xb.y);  // X_k + conj X_{M-k}
       const float2 D = make_float2(xa.x - xb.x, xa.y + xb.y);  // X_k - conj X_{M-k}
-      const float2 B = cmulc(D, __ldg(a.rtx + k));             // D e^{+2 pi i k / nx}
+      const float2 B = cmulc(D, L.rt_pre[blk * R2 + j]);       // D e^{+2 pi i k / nx}
       w[j] = make_float2(A.x - B.y, A.y + B.x);                // A + i B
     }
     dft<R2, true>(w);
@@ -88,7 +106,7 @@ __device__ __forceinline__ void row_inverse(const SlabArgs& a, float2* row, floa
   float2 v[R1];
 #pragma unroll
   for (int k = 0; k < R1; ++k) v[k] = buf[swz<R2>(l + R2 * k)];
-  lane_stage1<R1, R2, true>(v, a.twx, l);
+  lane_stage1_reg<R1, R2, true>(v, L.tw);
   float2* re = row + (y & 1);
 #pragma unroll
   for (int j = 0; j < R1; ++j) re[l + R2 * j] = v[j];
@@ -96,27 +114,31 @@ __device__ __forceinline__ void row_inverse(const SlabArgs& a, float2* row, floa
 }
 
 template <int R1, int R2>
-__device__ __forceinline__ void row_forward(const SlabArgs& a, float2* row, float2* buf, int l,
-                                            unsigned gmask, int y) {
+__device__ __forceinline__ void row_forward(float2* row, float2* buf, int l, unsigned gmask, int y,
+                                            const RowLane<R1, R2>& L) {
   constexpr int M = R1 * R2;
   const float2* re = row + (y & 1);
   float2 v[R1];
 #pragma unroll
   for (int j = 0; j < R1; ++j) v[j] = re[l + R2 * j];
-  lane_stage1<R1, R2, false>(v, a.twx, l);
+  lane_stage1_reg<R1, R2, false>(v, L.tw);
 #pragma unroll
   for (int k = 0; k < R1; ++k) buf[swz<R2>(l + R2 * k)] = v[k];
   __syncwarp(gmask);
   lane_stage2<R1, R2, false>(buf, l);
   __syncwarp(gmask);
-  for (int k = l; k <= M; k += R2) {
-    const int k1 = (k == M) ? 0 : k;
-    const int k2 = (k == 0 || k == M) ? 0 : M - k;
-    const float2 zk = buf[swz<R2>(__ldg(a.posx + k1))];
-    const float2 zm = buf[swz<R2>(__ldg(a.posx + k2))];
-    const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-    const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-    row[k] = cadd(E, cmul(O, __ldg(a.rtx + k)));
+#pragma unroll
+  for (int j = 0; j <= R1; ++j) {
+    const int k = l + R2 * j;
+    if (k <= M) {
+      const int k1 = (k == M) ? 0 : k;
+      const int k2 = (k == 0 || k == M) ? 0 : M - k;
+      const float2 zk = buf[swz<R2>(row_pos<R1, R2>(k1))];
+      const float2 zm = buf[swz<R2>(row_pos<R1, R2>(k2))];
+      const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      row[k] = cadd(E, cmul(O, L.rt_post[j]));
+    }
   }
   __syncwarp(gmask);
 }
@@ -124,19 +146,34 @@ __device__ __forceinline__ void row_forward(const SlabArgs& a, float2* row, floa
 // All rows of the plane, groups of R2 lanes per row.
 template <int R1, int R2>
 __device__ __noinline__ void slab_rows(const SlabArgs& a, float2* plane, float2* xch, bool inv) {
+  constexpr int M = R1 * R2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int G = 32 / R2;
   const int g = lane / R2, l = lane % R2;
   const unsigned gmask = ((1u << R2) - 1u) << (g * R2);
   float2* buf = xch + (size_t)warp * slab_xch_per_warp(a) + (size_t)g * (a.mx + kSlabPad);
+  RowLane<R1, R2> L;
+  lane_twiddles<R1, R2>(a.twx, l, L.tw);
+#pragma unroll
+  for (int j = 0; j <= R1; ++j) {
+    const int k = l + R2 * j;
+    L.rt_post[j] = __ldg(a.rtx + (k <= M ? k : 0));
+  }
+  {
+    int blk = 0;
+    for (int b = l; b < R1; b += R2, ++blk) {
+#pragma unroll
+      for (int j = 0; j < R2; ++j) L.rt_pre[blk * R2 + j] = __ldg(a.rtx + b + R1 * j);
+    }
+  }
   for (int y0 = warp * G; y0 < a.ny; y0 += kSlabWarps * G) {
     const int y = y0 + g;
     if (y < a.ny) {  // uniform over the group
       float2* row = plane + (size_t)y * a.nkx;
       if (inv)
-        row_inverse<R1, R2>(a, row, buf, l, gmask, y);
+        row_inverse<R1, R2>(row, buf, l, gmask, y, L);
       else
-        row_forward<R1, R2>(a, row, buf, l, gmask, y);
+        row_forward<R1, R2>(row, buf, l, gmask, y, L);
     }
   }
 }
@@ -150,6 +187,8 @@ __device__ __noinline__ void slab_cols(const SlabArgs& a, float2* plane, float2*
   const unsigned gmask = (R2 == 32 ? 0xffffffffu : ((1u << R2) - 1u)) << (g * R2);
   float2* buf = xch + (size_t)warp * slab_xch_per_warp(a) + (size_t)g * (a.ny + kSlabPad);
   const int st = a.nkx;
+  float2 twr[R1 - 1];
+  lane_twiddles<R1, R2>(a.twy, l, twr);
   for (int c0 = warp * G; c0 < a.nkx; c0 += kSlabWarps * G) {
     const int kx = c0 + g;
     if (kx >= a.nkx) continue;  // uniform over the group
@@ -158,7 +197,7 @@ __device__ __noinline__ void slab_cols(const SlabArgs& a, float2* plane, float2*
     if (!inv) {
 #pragma unroll
       for (int j = 0; j < R1; ++j) v[j] = col[(l + R2 * j) * st];
-      lane_stage1<R1, R2, false>(v, a.twy, l);
+      lane_stage1_reg<R1, R2, false>(v, twr);
 #pragma unroll
       for (int k = 0; k < R1; ++k) buf[swz<R2>(l + R2 * k)] = v[k];
       __syncwarp(gmask);
@@ -174,7 +213,7 @@ __device__ __noinline__ void slab_cols(const SlabArgs& a, float2* plane, float2*
       __syncwarp(gmask);
 #pragma unroll
       for (int k = 0; k < R1; ++k) v[k] = buf[swz<R2>(l + R2 * k)];
-      lane_stage1<R1, R2, true>(v, a.twy, l);
+      lane_stage1_reg<R1, R2, true>(v, twr);
 #pragma unroll
       for (int j = 0; j < R1; ++j) col[(l + R2 * j) * st] = v[j];
     }
