@@ -95,9 +95,19 @@ def iteration_classes(prof):
     return ("slab", "zslab") if prof.get("slab", (0.0, 0))[1] > 0 else ("plane", "pencil")
 
 
-def kernel_source_sha():
+# Sources of each profiled kernel class and the committed ncu summary that
+# holds its DRAM traffic per launch.
+PROFILE_OF = {
+    "plane": ("ncu_plane_pass_128x128x96.md",
+              ("admm_kernels.cu", "fft_device.cuh", "nadmm_internal.h")),
+    "slab": ("ncu_slab_pass_128x128x96.md",
+             ("slab_passes.cu", "lane_fft.cuh", "fft_device.cuh", "vstep.cuh", "nadmm_internal.h")),
+}
+
+
+def kernel_source_sha(kernel_class="plane"):
     h = hashlib.sha256()
-    for f in ("admm_kernels.cu", "fft_device.cuh", "nadmm_internal.h"):
+    for f in PROFILE_OF[kernel_class][1]:
         with open(os.path.join(ROOT, "paper_2109_12688_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -106,13 +116,15 @@ def kernel_source_sha():
 def ncu_traffic(kernel_class):
     """dram bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "ncu_plane_pass_128x128x96.md")
+    if kernel_class not in PROFILE_OF:
+        return None
+    path = os.path.join(ROOT, "profiles", PROFILE_OF[kernel_class][0])
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"traffic_bytes_per_launch\[%s\]:\s*([0-9.]+)\s+kernel_sha:\s*([0-9a-f]+)"
                   % re.escape(kernel_class), text)
-    if not m or m.group(2) != kernel_source_sha():
+    if not m or m.group(2) != kernel_source_sha(kernel_class):
         return None
     return float(m.group(1))
 
@@ -407,8 +419,10 @@ def bench_config(orders, world):
     return {"workload": WORKLOAD, "dims": list(DIMS), "orders": list(orders),
             "outer": OUTER, "inner": INNER, "registrations_per_step": len(orders),
             "l2": "flushed between timed steps (256 MB write outside the step events)",
-            "concurrency": f"{len(orders)} registrations in flight per GPU, one stream "
-                           "each (independent pairs); value is their throughput",
+            "concurrency": f"the {len(orders)} registrations of a step as one batched call "
+                           "(nadmm_register_batched, flat execution: each ADMM phase one "
+                           "launch over all pairs); value is their throughput; the same step "
+                           "on three streams and on one stream is reported beside it",
             "parallelism": f"replicas x{world}"}
 
 
@@ -719,14 +733,38 @@ def main():
         for r, a, b, u in zip(regs, I0, I1, U):
             nadmm.nadmm_register(r.handle, a, b, u, stream)
 
+    # the same three registrations as one batched call (flat execution: one
+    # slab-pass launch and one z-pass launch per ADMM phase over all pairs)
+    batch = nadmm.BatchedRegistration([DIMS] * len(ORDERS), device=dev, lam=LAM, theta=THETA,
+                                      outer=OUTER, inner=INNER,
+                                      per_pair=[{"order_n": n} for n in ORDERS])
+    UB = [torch.empty_like(u) for u in U]
+
+    def step_batched():
+        nadmm.nadmm_register_batched(batch.handle, I0, I1, UB, stream)
+
     def check_status():
-        for r in regs:
+        for r in regs + [batch]:
             st = nadmm.nadmm_get_status(r.handle, stream)
             if st != nadmm.NADMM_OK:
                 raise RuntimeError(f"device status {nadmm.nadmm_status_string(st)}")
 
+    def timed_steps(fn, salt):
+        evs = []
+        for i in range(args.steps):
+            flush.fill_((i + salt) & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
     for i in range(args.warmup):
         flush.fill_(i & 0xFF)
+        step_batched()
         step()
     torch.cuda.synchronize()
     check_status()
@@ -737,22 +775,21 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    evs = []
-    for i in range(args.steps):
-        flush.fill_((i + 7) & 0xFF)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        evs.append((e0, e1))
-    torch.cuda.synchronize()
+    total_ms = timed_steps(step_batched, 7)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world, dev)
+    total_ms = max_over_ranks(total_ms, world, dev)
     check_status()
-    timed_u = [u.clone() for u in U]  # outputs of the last timed (concurrent) step
+    timed_u = [u.clone() for u in UB]  # outputs of the last timed (batched) step
+    # the same step as three registrations on three streams
+    streams_ms = timed_steps(step, 11)
+    check_status()
+    for n, a, b in zip(ORDERS, timed_u, U):
+        if not torch.equal(a, b):
+            print(json.dumps({"error": f"n = {n}: three-stream result differs from the batched "
+                                       "result"}), flush=True)
+            sys.exit(3)
     # latency of one registration at a time (same pairs, one stream)
     seq = []
     for i in range(args.steps):
@@ -765,11 +802,11 @@ def main():
         torch.cuda.synchronize()
         seq.append(e0.elapsed_time(e1))
     check_status()
-    # the concurrent streams must give exactly the single-stream results
+    # and one after another on one stream: the same results, bit for bit
     for n, a, b in zip(ORDERS, timed_u, U):
         if not torch.equal(a, b):
-            print(json.dumps({"error": f"n = {n}: concurrent result differs from the "
-                                       "single-stream result"}), flush=True)
+            print(json.dumps({"error": f"n = {n}: single-stream result differs from the "
+                                       "batched result"}), flush=True)
             sys.exit(3)
     latency_ms = sum(seq) / len(seq) / len(ORDERS)
     regs_total = args.steps * len(ORDERS) * world
@@ -871,7 +908,8 @@ def main():
         "data": "synthetic",
         "config": bench_config(ORDERS, world),
         "latency_ms_one_at_a_time": latency_ms,
-        "concurrent_equals_sequential": True,
+        "three_streams_ms_per_registration": streams_ms / (args.steps * len(ORDERS)),
+        "batched_equals_streams_and_sequential": True,
         "voxel_admm_iters_per_s": vox_rate,
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,

@@ -100,6 +100,15 @@ typedef enum nadmm_status {
                                      x- and y-DFTs, then one z-pass); same
                                      arithmetic, different rounding order       */
 
+#define NADMM_FLAG_SLAB_PATH 0x800u /* run the slab path wherever the grid
+                                     supports it.  Without this flag or
+                                     NADMM_FLAG_FOUR_PASS a single grid takes
+                                     the slab path only when its 3 nz CTAs fill
+                                     at least 80 % of the waves the device
+                                     holds (one wave of three-CTA clusters per
+                                     z-plane each; decided when the workspace
+                                     is attached); flat batches always take it */
+
 typedef struct nadmm_config {
   int32_t nx, ny, nz;         /* grid (M, N, H); see NADMM_ERR_UNSUPPORTED_SIZE */
   int32_t order_n;            /* regulariser order n, 1..8 (Eq. 2)            */
@@ -228,6 +237,14 @@ const char* nadmm_status_string(nadmm_status s);
  * only. */
 nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, const int32_t* dims,
                                   nadmm_handle* out);
+
+/* nadmm_create_batched with a whole configuration per pair: pair i is
+ * registered with cfgs[i] (its grid, order, lambda, theta, data term, bound
+ * ...).  Every pair must have the same outer_iters, inner_iters and flags (one
+ * schedule); errors as nadmm_create_batched, INVALID_ARG when they differ.
+ * The paper has no counterpart; host only. */
+nadmm_status nadmm_create_batched_configs(const nadmm_config* cfgs, int32_t npairs,
+                                          nadmm_handle* out);
 
 /* Change the lane count of a batched handle before its workspace is
  * attached: 0 = flat execution (needs every pair on the slab path and no

@@ -48,7 +48,8 @@ struct nadmm_context {
   std::vector<float> beta;   // beta_0 .. beta_{K-1}
   // slab path (two kernels per ADMM iteration): nx/2-point x plan, its
   // twiddles, positions and their inverse, and e^{-2 pi i k / nx}
-  bool slab = false;
+  bool slab = false;      // the grid supports the slab path (its tables exist)
+  bool use_slab = false;  // ... and runs it (decided when the workspace is attached)
   AxisPlan pxh;
   std::vector<float2> twxh, rtx;
   std::vector<int> posxh, fqxh;
@@ -182,8 +183,11 @@ nadmm_status validate(const nadmm_config* c) {
   if (!(c->bound_kappa > 0.0f) || !(c->bound_delta > 0.0f))
     return fail(NADMM_ERR_INVALID_ARG, "bound_kappa and bound_delta must be > 0 (INFINITY disables)");
   if (c->flags & ~(NADMM_FLAG_NO_GRAPH | NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK |
-                   NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_PIPELINED_PLANE | NADMM_FLAG_FOUR_PASS))
+                   NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_PIPELINED_PLANE | NADMM_FLAG_FOUR_PASS |
+                   NADMM_FLAG_SLAB_PATH))
     return fail(NADMM_ERR_INVALID_ARG, "unknown flag bits");
+  if ((c->flags & NADMM_FLAG_FOUR_PASS) && (c->flags & NADMM_FLAG_SLAB_PATH))
+    return fail(NADMM_ERR_INVALID_ARG, "NADMM_FLAG_FOUR_PASS and NADMM_FLAG_SLAB_PATH exclude each other");
   for (int ax = 0; ax < 3; ++ax)
     if (((c->flags >> NADMM_FLAG_LANE_SHIFT(ax)) & 3u) == 3u)
       return fail(NADMM_ERR_INVALID_ARG, "plan bits of an axis ask for both 8 and 16 lanes");
@@ -409,7 +413,8 @@ cudaError_t enqueue_inner_slab(nadmm_context* h, const PlaneArgs& first, int in_
 cudaError_t enqueue_inner(nadmm_context* h, PlaneArgs first, int in_first, bool prev_first, int k0,
                           int steps, const float* J, const float* c, float* w_out, float* b_out,
                           cudaStream_t s, float* hist_w = nullptr, float* hist_u = nullptr) {
-  if (h->slab && hist_w == nullptr && !thresholds(h) && (in_first == IN_NONE || in_first == IN_STATE))
+  if (h->use_slab && hist_w == nullptr && !thresholds(h) &&
+      (in_first == IN_NONE || in_first == IN_STATE))
     return enqueue_inner_slab(h, first, in_first, prev_first, k0, steps, J, c, w_out, b_out, s);
   const size_t F3 = 3 * h->V;
   auto hw = [&](int k) { return hist_w + (size_t)k * F3; };
@@ -856,6 +861,25 @@ nadmm_status attach(nadmm_context* h, char* ws, char* wt) {
     h->smap = sa.smap;
     h->smap_ok = true;
   }
+  // the slab path for this grid on its own: forced by the flag or by restart
+  // (which only the slab path implements), else when its clusters fill the
+  // device's waves well
+  h->use_slab = false;
+  if (h->slab) {
+    if ((h->cfg.flags & NADMM_FLAG_SLAB_PATH) || h->restart) {
+      h->use_slab = true;
+    } else {
+      int clusters = 0;
+      e = slab_max_clusters(slab_args(h), &clusters);
+      if (e != cudaSuccess) {
+        h->ws = h->wt = nullptr;
+        return cuda_fail(e, "cudaOccupancyMaxActiveClusters");
+      }
+      const int ctas = 3 * h->cfg.nz, cap = 3 * std::max(clusters, 1);
+      const int waves = (ctas + cap - 1) / cap;
+      h->use_slab = (double)ctas >= 0.8 * (double)waves * (double)cap;
+    }
+  }
   return NADMM_OK;
 }
 
@@ -1287,20 +1311,22 @@ nadmm_status nadmm_create(const nadmm_config* cfg, nadmm_handle* out) {
   return NADMM_OK;
 }
 
-nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, const int32_t* dims,
-                                  nadmm_handle* out) {
-  if (!out) return fail(NADMM_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
-  if (!base || !dims) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
-  if (npairs < 1) return fail(NADMM_ERR_INVALID_ARG, "npairs must be >= 1");
+// A batched handle from one configuration per pair (cfgs[i].nx/ny/nz are
+// pair i's grid); shared by nadmm_create_batched and
+// nadmm_create_batched_configs.
+nadmm_status create_batched_from(const nadmm_config* cfgs, int32_t npairs, nadmm_handle* out) {
   nadmm_context* b = new nadmm_context();
-  b->cfg = *base;
+  b->cfg = cfgs[0];
   b->batched = true;
   for (int i = 0; i < npairs; ++i) {
-    nadmm_config c = *base;
-    c.nx = dims[3 * i];
-    c.ny = dims[3 * i + 1];
-    c.nz = dims[3 * i + 2];
+    const nadmm_config& c = cfgs[i];
+    if (c.outer_iters != cfgs[0].outer_iters || c.inner_iters != cfgs[0].inner_iters ||
+        c.flags != cfgs[0].flags) {
+      destroy_context(b);
+      return fail(NADMM_ERR_INVALID_ARG,
+                  "pair " + std::to_string(i) +
+                      ": every pair of a batch needs the same outer_iters, inner_iters and flags");
+    }
     nadmm_context* p = nullptr;
     nadmm_status st = create_single(&c, &p);
     if (st != NADMM_OK) {
@@ -1316,6 +1342,30 @@ nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, cons
     relayout(b, std::min(npairs, kDefaultLanes));
   *out = b;
   return NADMM_OK;
+}
+
+nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, const int32_t* dims,
+                                  nadmm_handle* out) {
+  if (!out) return fail(NADMM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!base || !dims) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
+  if (npairs < 1) return fail(NADMM_ERR_INVALID_ARG, "npairs must be >= 1");
+  std::vector<nadmm_config> cfgs(npairs, *base);
+  for (int i = 0; i < npairs; ++i) {
+    cfgs[i].nx = dims[3 * i];
+    cfgs[i].ny = dims[3 * i + 1];
+    cfgs[i].nz = dims[3 * i + 2];
+  }
+  return create_batched_from(cfgs.data(), npairs, out);
+}
+
+nadmm_status nadmm_create_batched_configs(const nadmm_config* cfgs, int32_t npairs,
+                                          nadmm_handle* out) {
+  if (!out) return fail(NADMM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfgs) return fail(NADMM_ERR_INVALID_ARG, "NULL argument");
+  if (npairs < 1) return fail(NADMM_ERR_INVALID_ARG, "npairs must be >= 1");
+  return create_batched_from(cfgs, npairs, out);
 }
 
 nadmm_status nadmm_create_pyramid(const nadmm_config* finest, int32_t levels, const int32_t* outer,
@@ -1386,10 +1436,12 @@ nadmm_status nadmm_batch_set_pair_plan(nadmm_handle h, int32_t pair, uint32_t pl
   if (!h || !h->batched) return fail(NADMM_ERR_INVALID_ARG, "not a batched handle");
   if (h->wt) return fail(NADMM_ERR_INVALID_ARG, "set plans before nadmm_set_workspace");
   if (pair < 0 || pair >= (int32_t)h->pairs.size()) return fail(NADMM_ERR_INVALID_ARG, "pair out of range");
-  const uint32_t tuned = NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_FOUR_PASS;
+  const uint32_t tuned = NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_FOUR_PASS |
+                         NADMM_FLAG_SLAB_PATH;
   if (plan_flags & ~tuned)
     return fail(NADMM_ERR_INVALID_ARG,
-                "only NADMM_FLAG_LANE*, NADMM_FLAG_FUSED_PENCIL and NADMM_FLAG_FOUR_PASS bits");
+                "only NADMM_FLAG_LANE*, NADMM_FLAG_FUSED_PENCIL, NADMM_FLAG_FOUR_PASS and "
+                "NADMM_FLAG_SLAB_PATH bits");
   nadmm_config c = h->pairs[pair]->cfg;
   c.flags = (c.flags & ~tuned) | plan_flags;
   nadmm_context* q = nullptr;
@@ -1463,6 +1515,8 @@ nadmm_status nadmm_set_workspace(nadmm_handle h, void* dev_ptr, size_t bytes) {
     }
     h->ws = base;
     h->wt = base;
+    if (h->flat)
+      for (nadmm_context* q : h->pairs) q->use_slab = true;
     e = h->flat ? upload_flat(h) : ensure_lanes(h);
     if (e != cudaSuccess) {
       for (nadmm_context* q : h->pairs) q->ws = q->wt = nullptr;
@@ -1660,7 +1714,7 @@ nadmm_status nadmm_spectral_solve(nadmm_handle h, const float* y, float* w, void
   if (st != NADMM_OK) return st;
   if ((st = check_dev_ptrs({y, w})) != NADMM_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  if (h->slab) {
+  if (h->use_slab) {
     SlabArgs f = slab_args(h);
     f.w_in = y;
     cudaError_t e = launch_slab(SLAB_FIELD, f, s);
@@ -1869,7 +1923,7 @@ nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t byt
   }
   nadmm_config c = *cfg;
   c.flags &= ~(NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL |
-               NADMM_FLAG_FOUR_PASS | NADMM_FLAG_PIPELINED_PLANE);
+               NADMM_FLAG_FOUR_PASS | NADMM_FLAG_PIPELINED_PLANE | NADMM_FLAG_SLAB_PATH);
   c.restart_eta = -1.0f;
   c.admm_tol = c.warp_tol = 0.0f;
   std::vector<std::vector<int>> seen;
@@ -1881,7 +1935,7 @@ nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t byt
     for (int ax = 0; ax < 3; ++ax)
       t.flags |= (((combo >> ax) & 1u) ? 2u : 1u) << NADMM_FLAG_LANE_SHIFT(ax);
     if (combo & 8u) t.flags |= NADMM_FLAG_FUSED_PENCIL;
-    if (combo & 16u) t.flags |= NADMM_FLAG_FOUR_PASS;
+    t.flags |= (combo & 16u) ? NADMM_FLAG_FOUR_PASS : NADMM_FLAG_SLAB_PATH;
     if ((combo & 8u) && !(combo & 16u)) continue;  // fusion is a four-kernel variant
     nadmm_context* h = nullptr;
     if ((st = create_single(&t, &h)) != NADMM_OK) break;
@@ -1934,7 +1988,8 @@ nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t byt
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != NADMM_OK) return st;
-  const uint32_t tuned = NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_FOUR_PASS;
+  const uint32_t tuned = NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_FOUR_PASS |
+                         NADMM_FLAG_SLAB_PATH;
   *best_flags = (cfg->flags & ~tuned) | (best_f & tuned);
   if (best_ms) *best_ms = best;
   return NADMM_OK;

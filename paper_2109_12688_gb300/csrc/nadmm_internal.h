@@ -155,6 +155,8 @@ bool slab_supported(int nx, int ny, int nz, const AxisPlan& pxh, const AxisPlan&
                     const AxisPlan& pz);
 size_t slab_smem_bytes(const SlabArgs& a);
 cudaError_t launch_slab(int mode, const SlabArgs& a, cudaStream_t s);
+// Clusters of the slab pass that the current device holds at once for grid a.
+cudaError_t slab_max_clusters(const SlabArgs& a, int* clusters);
 // z-pass of the slab layout (uses spec, twz, Kx, Ky, Kz, pz, ny, nz, nkx,
 // order_n, gamma, scale of the pencil arguments)
 cudaError_t launch_zslab(const PencilArgs& a, cudaStream_t s);

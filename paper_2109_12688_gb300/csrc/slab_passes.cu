@@ -694,6 +694,21 @@ cudaError_t launch_zslab(const PencilArgs& a, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+cudaError_t slab_max_clusters(const SlabArgs& a, int* clusters) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(3 * a.nz));
+  cfg.blockDim = dim3(kSlabThreads);
+  cfg.dynamicSmemBytes = slab_smem_bytes(a);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 3;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaOccupancyMaxActiveClusters(clusters, (void*)k_slab<SLAB_SPEC_PREV>, &cfg);
+}
+
 cudaError_t launch_slab_multi(int mode, const SlabArgs* pairs, const int* start, int npairs,
                               int total_ctas, size_t smem, float beta, int k, cudaStream_t s) {
   const dim3 grid((unsigned)total_ctas), block(kSlabThreads);

@@ -29,8 +29,9 @@ NADMM_FLAG_LANE_MASK = 0xFC
 NADMM_FLAG_FUSED_PENCIL = 0x100
 NADMM_FLAG_PIPELINED_PLANE = 0x200
 NADMM_FLAG_FOUR_PASS = 0x400
+NADMM_FLAG_SLAB_PATH = 0x800
 # plan bits nadmm_autotune chooses
-PLAN_FLAGS = 0xFC | 0x100 | 0x400
+PLAN_FLAGS = 0xFC | 0x100 | 0x400 | 0x800
 
 
 def NADMM_FLAG_LANE8(axis):
@@ -74,6 +75,8 @@ _SIGS = {
     "nadmm_register": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "nadmm_register_host": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "nadmm_get_status": (ctypes.c_int, [_P, _P]),
+    "nadmm_create_batched_configs": (ctypes.c_int, [ctypes.POINTER(nadmm_config), ctypes.c_int32,
+                                                    ctypes.POINTER(_P)]),
     "nadmm_get_restarts": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "nadmm_last_error": (ctypes.c_char_p, []),
     "nadmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -175,6 +178,13 @@ def nadmm_create_batched(base, dims_list):
     arr = (ctypes.c_int32 * (3 * n))(*[int(v) for d in dims_list for v in d])
     h = _P()
     _check(load().nadmm_create_batched(ctypes.byref(base), n, arr, ctypes.byref(h)))
+    return h
+
+
+def nadmm_create_batched_configs(cfgs):
+    arr = (nadmm_config * len(cfgs))(*cfgs)
+    h = _P()
+    _check(load().nadmm_create_batched_configs(arr, len(cfgs), ctypes.byref(h)))
     return h
 
 
@@ -527,13 +537,19 @@ class BatchedRegistration(Registration):
     """A batched handle (pairs of different grid sizes) plus its workspace."""
 
     def __init__(self, dims_list, device="cuda", lanes=None, requires_grad=False,
-                 autotune_cache=None, tune=False, **kw):
+                 autotune_cache=None, tune=False, per_pair=None, **kw):
+        """per_pair: optional list of dicts of make_config arguments that
+        override kw for each pair (e.g. a regulariser order per pair)."""
         import torch
         self.dims_list = [tuple(d) for d in dims_list]
         if requires_grad:
             kw["flags"] = kw.get("flags", 0) | NADMM_FLAG_SAVE_FOR_BACKWARD
         self.cfg = make_config(self.dims_list[0], **kw)
-        self.handle = nadmm_create_batched(self.cfg, self.dims_list)
+        if per_pair is None:
+            self.handle = nadmm_create_batched(self.cfg, self.dims_list)
+        else:
+            cfgs = [make_config(d, **{**kw, **extra}) for d, extra in zip(self.dims_list, per_pair)]
+            self.handle = nadmm_create_batched_configs(cfgs)
         if lanes is not None:
             nadmm_batch_set_lanes(self.handle, lanes)
         if tune or autotune_cache:

@@ -111,8 +111,9 @@ def test_batch_of_64_uneven_pairs(lib):
     breg = lib.BatchedRegistration(dims, device=DEV, **kw)
     us = breg.register(fixed, moving)
     assert lib.nadmm_get_status(breg.handle, torch.cuda.current_stream()) == lib.NADMM_OK
-    for i in range(0, 64, 9):  # a sample of the pairs through the single-pair path
-        assert np.array_equal(us[i].cpu().numpy(), single(lib, dims[i], fixed[i], moving[i], **kw))
+    for i in range(0, 64, 9):  # a sample of the pairs through the single-pair slab path
+        assert np.array_equal(us[i].cpu().numpy(), single(lib, dims[i], fixed[i], moving[i],
+                                                          flags=lib.NADMM_FLAG_SLAB_PATH, **kw))
     for d, u in zip(dims, us):
         reg = lib.Registration(d, device=DEV, **kw)
         cnt = torch.zeros(1, dtype=torch.int32, device=DEV)
@@ -138,14 +139,17 @@ def test_flat_batch_is_default_and_equals_single_and_lane_runs(lib):
     assert lib.nadmm_batch_get_lanes(flat.handle) == 0
     us = [u.clone() for u in flat.register(fixed, moving)]
     again = flat.register(fixed, moving)  # graph replay
-    lanes = lib.BatchedRegistration(FLAT, device=DEV, lanes=2, **KW).register(fixed, moving)
+    slab = lib.NADMM_FLAG_SLAB_PATH  # the per-pair runs on the same (slab) kernels
+    lanes = lib.BatchedRegistration(FLAT, device=DEV, lanes=2, flags=slab, **KW).register(fixed,
+                                                                                        moving)
     direct = lib.BatchedRegistration(FLAT, device=DEV, lanes=0, flags=lib.NADMM_FLAG_NO_GRAPH,
                                      **KW).register(fixed, moving)
     for i, d in enumerate(FLAT):
         assert torch.equal(us[i], again[i]), d
         assert torch.equal(us[i], lanes[i]), d
         assert torch.equal(us[i], direct[i]), d
-        assert np.array_equal(us[i].cpu().numpy(), single(lib, d, fixed[i], moving[i], **KW)), d
+        assert np.array_equal(us[i].cpu().numpy(),
+                              single(lib, d, fixed[i], moving[i], flags=slab, **KW)), d
     ref = O.register(pairs[1]["fixed"], pairs[1]["moving"], lam=10.0, theta=0.1, n=2, outer=2,
                      inner=4)
     assert np.abs(us[1].cpu().numpy() - ref).max() <= 1e-3

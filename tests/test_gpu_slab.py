@@ -39,27 +39,36 @@ def _classes(lib, reg, pair):
     return {k: n for k, (_, n) in prof.items() if n > 0}
 
 
-@pytest.mark.parametrize("dims,slab", [((128, 128, 96), True), ((32, 32, 24), True),
-                                       ((160, 160, 112), True), ((96, 112, 80), True),
-                                       ((20, 12, 14), False), ((256, 256, 192), False)])
-def test_path_selection(lib, dims, slab):
-    """Grids whose planes fit a CTA and whose axes have lane plans take the
-    slab path (two kernels per iteration); the flag forces the four-kernel
-    path; the others keep it."""
+@pytest.mark.parametrize("dims,default,eligible", [((128, 128, 96), True, True),
+                                                   ((32, 32, 24), False, True),
+                                                   ((160, 160, 112), True, True),
+                                                   ((96, 112, 80), False, True),
+                                                   ((20, 12, 14), False, False),
+                                                   ((256, 256, 192), False, False)])
+def test_path_selection(lib, dims, default, eligible):
+    """Grids whose planes fit a CTA and whose axes have lane plans can take
+    the slab path (two kernels per iteration): by default when their
+    three-CTA clusters fill at least 80 % of the device's waves (96 z-planes
+    on 97 resident clusters at 128 x 128 x 96; 112 z-planes of 160 x 160 one
+    CTA per SM: 3 waves, 81 %), always with NADMM_FLAG_SLAB_PATH; the
+    four-kernel flag keeps the plane pass and its y/z/y passes."""
     pair = synth.make_pair(dims, seed=1) if max(dims) <= 160 else None
     if pair is None:
         f, m = synth.phase_pair(dims, seed=1)
         pair = {"fixed": f, "moving": m}
-    reg = lib.Registration(dims, device="cuda:0", outer=1, inner=4)
-    n = _classes(lib, reg, pair)
-    if slab:
-        assert n.get("slab_first") == 1 and n.get("slab_k1") == 1 and n.get("slab") == 2
-        assert n.get("zslab") == 4 and n.get("slab_final") == 1 and "plane" not in n
-    else:
-        assert "slab" not in n and n.get("plane") == 2
-    four = lib.Registration(dims, device="cuda:0", outer=1, inner=4, flags=lib.NADMM_FLAG_FOUR_PASS)
-    n4 = _classes(lib, four, pair)
-    assert "slab" not in n4 and n4.get("plane") == 2
+
+    def classes(flags):
+        reg = lib.Registration(dims, device="cuda:0", outer=1, inner=4, flags=flags)
+        return _classes(lib, reg, pair)
+
+    for flags, slab in ((0, default), (lib.NADMM_FLAG_SLAB_PATH, eligible),
+                        (lib.NADMM_FLAG_FOUR_PASS, False)):
+        n = classes(flags)
+        if slab:
+            assert n.get("slab_first") == 1 and n.get("slab_k1") == 1 and n.get("slab") == 2
+            assert n.get("zslab") == 4 and n.get("slab_final") == 1 and "plane" not in n
+        else:
+            assert "slab" not in n and n.get("plane") == 2, (flags, n)
 
 
 @pytest.mark.parametrize("dims,n", [((128, 128, 96), 2), ((32, 32, 24), 1), ((96, 112, 80), 3),
@@ -68,7 +77,8 @@ def test_slab_registration_matches_four_pass_and_oracle(lib, dims, n):
     pair = synth.make_pair(dims, seed=n + 3)
     kw = dict(order_n=n, lam=10.0, theta=0.1, outer=2, inner=6)
     I0, I1 = _dev(pair["fixed"]), _dev(pair["moving"])
-    slab = lib.Registration(dims, device="cuda:0", **kw).register(I0, I1)
+    slab = lib.Registration(dims, device="cuda:0", flags=lib.NADMM_FLAG_SLAB_PATH,
+                            **kw).register(I0, I1)
     four = lib.Registration(dims, device="cuda:0", flags=lib.NADMM_FLAG_FOUR_PASS,
                             **kw).register(I0, I1)
     torch.cuda.synchronize()
@@ -88,7 +98,8 @@ def test_slab_spectral_solve_matches_oracle(lib, dims, n):
     x/y DFTs of a field, the z-pass, the inverse x/y DFTs."""
     nx, ny, nz = dims
     y = synth.random_field((3, nz, ny, nx), seed=7 + n)
-    reg = lib.Registration(dims, device="cuda:0", order_n=n, lam=10.0, theta=0.1)
+    reg = lib.Registration(dims, device="cuda:0", order_n=n, lam=10.0, theta=0.1,
+                           flags=lib.NADMM_FLAG_SLAB_PATH)
     yd = _dev(y)
     w = torch.full_like(yd, float("nan"))
     lib.nadmm_spectral_solve(reg.handle, yd, w, torch.cuda.current_stream())
@@ -107,7 +118,8 @@ def test_slab_teacher_forced_iterate(lib, k):
     J, c = synth.random_linearisation(dims, seed=30 + k)
     shape = (3, nz, ny, nx)
     st = [synth.random_field(shape, seed=40 + k + i, scale=0.3) for i in range(4)]
-    reg = lib.Registration(dims, device="cuda:0", order_n=2, lam=10.0, theta=0.1, inner=12)
+    reg = lib.Registration(dims, device="cuda:0", order_n=2, lam=10.0, theta=0.1, inner=12,
+                           flags=lib.NADMM_FLAG_SLAB_PATH)
     _, beta = O.nesterov_sequence(12)
     bk = 0.0 if k == 0 else beta[k - 1]
     zero = np.zeros(shape)
