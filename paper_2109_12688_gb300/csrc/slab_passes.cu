@@ -571,18 +571,30 @@ __device__ __forceinline__ void zslab_body(const PencilArgs& a, int blk) {
   for (int k = 0; k < R1; ++k) sm[swz<R2>(l + R2 * k)] = v[k];
   __syncwarp();
   const float kxy = __ldg(a.Kx + kx) + __ldg(a.Ky + y);
+  const int order = a.order_n;
   for (int b = l; b < R1; b += R2) {
     float2 w[R2];
 #pragma unroll
     for (int j = 0; j < R2; ++j) w[j] = sm[swz<R2>(b * R2 + j)];
     dft<R2, false>(w);
+    float Kn[R2];
 #pragma unroll
-    for (int k = 0; k < R2; ++k) {
-      const float K = kxy + __ldg(a.Kz + b * R2 + k);
-      float Kn = K;
-      for (int i = 1; i < a.order_n; ++i) Kn *= K;
-      w[k] = cscale(w[k], __fdividef(a.scale, 1.0f + a.gamma * Kn));
+    for (int k = 0; k < R2; ++k) Kn[k] = kxy + __ldg(a.Kz + b * R2 + k);
+    if (order == 2) {  // the orders of the paper's experiments without a loop
+#pragma unroll
+      for (int k = 0; k < R2; ++k) Kn[k] *= Kn[k];
+    } else if (order == 3) {
+#pragma unroll
+      for (int k = 0; k < R2; ++k) Kn[k] *= Kn[k] * Kn[k];
+    } else if (order != 1) {
+#pragma unroll
+      for (int k = 0; k < R2; ++k) {
+        const float K = Kn[k];
+        for (int i = 1; i < order; ++i) Kn[k] *= K;
+      }
     }
+#pragma unroll
+    for (int k = 0; k < R2; ++k) w[k] = cscale(w[k], __fdividef(a.scale, 1.0f + a.gamma * Kn[k]));
     dft<R2, true>(w);
 #pragma unroll
     for (int j = 0; j < R2; ++j) sm[swz<R2>(b * R2 + j)] = w[j];

@@ -42,15 +42,16 @@ def _classes(lib, reg, pair):
 @pytest.mark.parametrize("dims,default,eligible", [((128, 128, 96), True, True),
                                                    ((32, 32, 24), False, True),
                                                    ((160, 160, 112), True, True),
-                                                   ((96, 112, 80), False, True),
+                                                   ((96, 112, 80), True, True),
                                                    ((20, 12, 14), False, False),
                                                    ((256, 256, 192), False, False)])
 def test_path_selection(lib, dims, default, eligible):
     """Grids whose planes fit a CTA and whose axes have lane plans can take
     the slab path (two kernels per iteration): by default when their
     three-CTA clusters fill at least 80 % of the device's waves (96 z-planes
-    on 97 resident clusters at 128 x 128 x 96; 112 z-planes of 160 x 160 one
-    CTA per SM: 3 waves, 81 %), always with NADMM_FLAG_SLAB_PATH; the
+    on 97 resident clusters at 128 x 128 x 96, 80 of 97 at 96 x 112 x 80,
+    24 of several hundred at 32 x 32 x 24; 112 z-planes of 160 x 160 one CTA
+    per SM: 3 waves, 81 %), always with NADMM_FLAG_SLAB_PATH; the
     four-kernel flag keeps the plane pass and its y/z/y passes."""
     pair = synth.make_pair(dims, seed=1) if max(dims) <= 160 else None
     if pair is None:
