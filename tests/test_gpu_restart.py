@@ -83,7 +83,8 @@ def test_restart_extremes(lib):
     pair = synth.make_pair(dims, seed=2)
     I0, I1 = _dev(pair["fixed"]), _dev(pair["moving"])
     kw = dict(device="cuda:0", order_n=2, lam=10.0, theta=0.1, outer=2, inner=8)
-    plain_gpu = lib.Registration(dims, **kw).register(I0, I1)
+    # restart runs on the slab path; the handle without it is put there too
+    plain_gpu = lib.Registration(dims, flags=lib.NADMM_FLAG_SLAB_PATH, **kw).register(I0, I1)
     never = lib.Registration(dims, restart_eta=math.inf, **kw)
     u_never = never.register(I0, I1)
     torch.cuda.synchronize()
