@@ -109,6 +109,13 @@ typedef enum nadmm_status {
                                      z-plane each; decided when the workspace
                                      is attached); flat batches always take it */
 
+/* z-slices per thread of the re-warp, gradient and compose kernels (bits
+ * 12-13): 0 one, NADMM_FLAG_OUTER_Z2 two, NADMM_FLAG_OUTER_Z4 four; the same
+ * results either way, nadmm_autotune picks one. */
+#define NADMM_FLAG_OUTER_Z2 0x1000u
+#define NADMM_FLAG_OUTER_Z4 0x2000u
+#define NADMM_FLAG_OUTER_MASK 0x3000u
+
 typedef struct nadmm_config {
   int32_t nx, ny, nz;         /* grid (M, N, H); see NADMM_ERR_UNSUPPORTED_SIZE */
   int32_t order_n;            /* regulariser order n, 1..8 (Eq. 2)            */
@@ -408,7 +415,10 @@ nadmm_status nadmm_autotune_workspace_size(const nadmm_config* cfg, size_t* byte
  * CUDA events on `stream`, minimum kept) in the caller's device workspace
  * (at least nadmm_autotune_workspace_size bytes, 256-byte aligned; its
  * contents are overwritten) and write the fastest choice as NADMM_FLAG_LANE*,
- * NADMM_FLAG_FUSED_PENCIL and NADMM_FLAG_FOUR_PASS bits to *best_flags
+ * NADMM_FLAG_FUSED_PENCIL and NADMM_FLAG_FOUR_PASS / NADMM_FLAG_SLAB_PATH bits, then
+ * for that plan the z-slices per thread of the outer-step kernels (re-warp,
+ * gradient, bound, compose of one outer step timed with 1, 2 and 4) as
+ * NADMM_FLAG_OUTER_* bits, to *best_flags
  * (cfg->flags with those bits replaced) and its time in ms to *best_ms (host
  * pointers; best_ms may be NULL).  Synchronises `stream`.
  * Errors: INVALID_ARG, UNSUPPORTED_SIZE, ALIGNMENT, NO_WORKSPACE, CUDA. */

@@ -39,28 +39,38 @@ __device__ __forceinline__ void block_add2(float a, float b, double* acc) {
 // outer step (the compose that read them has completed).  With `measure`,
 // the change against the previous I1w is summed, and the last block to
 // finish decides the outer stop (sqrt(sum d^2) <= warp_tol sqrt(sum old^2)).
+// ZV z-slices per thread (blockIdx.z covers slices ZV blockIdx.z ..): more
+// independent gathers in flight per thread; the same result for every ZV.
+template <int ZV>
 __global__ void __launch_bounds__(kBX * kBY)
-    k_warp(Dims d, const float* __restrict__ I1, const float* __restrict__ u, float* I1w,
-           unsigned* red, unsigned* conv, double* conv_acc, float warp_tol, int measure) {
+    k_warp(Dims d, const float* __restrict__ I1, const float* __restrict__ u,
+           float* __restrict__ I1w, unsigned* red, unsigned* conv, double* conv_acc,
+           float warp_tol, int measure) {
   const size_t V = (size_t)d.nx * d.ny * d.nz;
   pdl_wait();
   pdl_trigger();
   if (conv != nullptr && conv[kConvOuter]) return;
   const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
-  const int z = blockIdx.z;
   if (red != nullptr && (blockIdx.x | blockIdx.y | blockIdx.z) == 0 && threadIdx.y == 0 &&
       threadIdx.x < 2)
     red[threadIdx.x] = 0u;
   float dd = 0.0f, oo = 0.0f;
   if (x < d.nx && y < d.ny) {
-    const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
-    const float v = trilerp(I1, d, (float)x + u[i], (float)y + u[V + i], (float)z + u[2 * V + i]);
-    if (measure) {
-      const float old = I1w[i];
-      dd = (v - old) * (v - old);
-      oo = old * old;
+#pragma unroll
+    for (int zz = 0; zz < ZV; ++zz) {
+      const int z = blockIdx.z * ZV + zz;
+      if (z < d.nz) {
+        const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
+        const float v =
+            trilerp(I1, d, (float)x + u[i], (float)y + u[V + i], (float)z + u[2 * V + i]);
+        if (measure) {
+          const float old = I1w[i];
+          dd += (v - old) * (v - old);
+          oo += old * old;
+        }
+        I1w[i] = v;
+      }
     }
-    I1w[i] = v;
   }
   if (!measure) return;
   block_add2(dd, oo, conv_acc + 2);
@@ -79,6 +89,7 @@ __global__ void __launch_bounds__(kBX * kBY)
 }
 
 // J = grad I1w (clamped central differences), c = I1w - I0
+template <int ZV>
 __global__ void __launch_bounds__(kBX * kBY) k_grad_residual(Dims d,
                                                              const float* __restrict__ I1w,
                                                              const float* __restrict__ I0,
@@ -91,16 +102,21 @@ __global__ void __launch_bounds__(kBX * kBY) k_grad_residual(Dims d,
   const size_t V = (size_t)d.nx * d.ny * d.nz;
   const size_t sy = (size_t)d.nx, sz = (size_t)d.nx * d.ny;
   const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
-  const int z = blockIdx.z;
   if (x >= d.nx || y >= d.ny) return;
-  const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
-  const size_t xp = i + (x + 1 < d.nx ? 1 : 0), xm = i - (x > 0 ? 1 : 0);
-  const size_t yp = i + (y + 1 < d.ny ? sy : 0), ym = i - (y > 0 ? sy : 0);
-  const size_t zp = i + (z + 1 < d.nz ? sz : 0), zm = i - (z > 0 ? sz : 0);
-  J[i] = 0.5f * (__ldg(I1w + xp) - __ldg(I1w + xm));
-  J[V + i] = 0.5f * (__ldg(I1w + yp) - __ldg(I1w + ym));
-  J[2 * V + i] = 0.5f * (__ldg(I1w + zp) - __ldg(I1w + zm));
-  c[i] = __ldg(I1w + i) - __ldg(I0 + i);
+#pragma unroll
+  for (int zz = 0; zz < ZV; ++zz) {
+    const int z = blockIdx.z * ZV + zz;
+    if (z < d.nz) {
+      const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
+      const size_t xp = i + (x + 1 < d.nx ? 1 : 0), xm = i - (x > 0 ? 1 : 0);
+      const size_t yp = i + (y + 1 < d.ny ? sy : 0), ym = i - (y > 0 ? sy : 0);
+      const size_t zp = i + (z + 1 < d.nz ? sz : 0), zm = i - (z > 0 ? sz : 0);
+      J[i] = 0.5f * (__ldg(I1w + xp) - __ldg(I1w + xm));
+      J[V + i] = 0.5f * (__ldg(I1w + yp) - __ldg(I1w + ym));
+      J[2 * V + i] = 0.5f * (__ldg(I1w + zp) - __ldg(I1w + zm));
+      c[i] = __ldg(I1w + i) - __ldg(I0 + i);
+    }
+  }
 }
 
 // Per-voxel |w|_inf and ||D w||_inf (max absolute row sum of the Jacobian);
@@ -170,6 +186,7 @@ __global__ void __launch_bounds__(kBX * kBY) k_bound_reduce(Dims d, const float*
 }
 
 // u_out(x) = v(x) + u_in(x + v(x)), v = s w
+template <int ZV>
 __global__ void __launch_bounds__(kBX * kBY) k_compose(Dims d, const float* __restrict__ w,
                                                        const float* __restrict__ u_in,
                                                        float* __restrict__ u_out,
@@ -179,13 +196,17 @@ __global__ void __launch_bounds__(kBX * kBY) k_compose(Dims d, const float* __re
   pdl_wait();
   pdl_trigger();
   const size_t V = (size_t)d.nx * d.ny * d.nz;
+  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
   if (conv != nullptr && conv[kConvOuter]) {  // stopped: carry u over to u_out
-    const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
     if (x >= d.nx || y >= d.ny || u_in == u_out) return;
-    const size_t i = ((size_t)blockIdx.z * d.ny + y) * d.nx + x;
-    u_out[i] = u_in[i];
-    u_out[V + i] = u_in[V + i];
-    u_out[2 * V + i] = u_in[2 * V + i];
+    for (int zz = 0; zz < ZV; ++zz) {
+      const int z = blockIdx.z * ZV + zz;
+      if (z >= d.nz) break;
+      const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
+      u_out[i] = u_in[i];
+      u_out[V + i] = u_in[V + i];
+      u_out[2 * V + i] = u_in[2 * V + i];
+    }
     return;
   }
   if (conv != nullptr && (blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0)
@@ -194,15 +215,19 @@ __global__ void __launch_bounds__(kBX * kBY) k_compose(Dims d, const float* __re
                      threadIdx.y == 0;
   const float s = bound_factor(red, kappa, delta, first ? status : nullptr);
   if (scale_out != nullptr && first) *scale_out = s;
-  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
-  const int z = blockIdx.z;
   if (x >= d.nx || y >= d.ny) return;
-  const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
-  const float vx = s * w[i], vy = s * w[V + i], vz = s * w[2 * V + i];
-  const float px = (float)x + vx, py = (float)y + vy, pz = (float)z + vz;
-  u_out[i] = vx + trilerp(u_in, d, px, py, pz);
-  u_out[V + i] = vy + trilerp(u_in + V, d, px, py, pz);
-  u_out[2 * V + i] = vz + trilerp(u_in + 2 * V, d, px, py, pz);
+#pragma unroll
+  for (int zz = 0; zz < ZV; ++zz) {
+    const int z = blockIdx.z * ZV + zz;
+    if (z < d.nz) {
+      const size_t i = ((size_t)z * d.ny + y) * d.nx + x;
+      const float vx = s * w[i], vy = s * w[V + i], vz = s * w[2 * V + i];
+      const float px = (float)x + vx, py = (float)y + vy, pz = (float)z + vz;
+      u_out[i] = vx + trilerp(u_in, d, px, py, pz);
+      u_out[V + i] = vy + trilerp(u_in + V, d, px, py, pz);
+      u_out[2 * V + i] = vz + trilerp(u_in + 2 * V, d, px, py, pz);
+    }
+  }
 }
 
 // det(I + D u) per voxel, count of det <= 0
@@ -277,28 +302,39 @@ static dim3 grid3(Dims d, int zslices) {
 }
 static const dim3 kBlock(kBX, kBY);
 
+static unsigned zgroups(Dims d) { return (unsigned)((d.nz + d.zv - 1) / d.zv); }
+
+// The kernel of a ZV-templated family for d.zv (1, 2 or 4; other values run 1).
+#define NADMM_ZV_LAUNCH(kernel, d, ...)                                                         \
+  ((d).zv == 4 ? launch_pdl(kernel<4>, grid3((d), zgroups(d)), kBlock, 0, __VA_ARGS__)        \
+   : (d).zv == 2 ? launch_pdl(kernel<2>, grid3((d), zgroups(d)), kBlock, 0, __VA_ARGS__)      \
+                 : launch_pdl(kernel<1>, grid3((d), (d).nz), kBlock, 0, __VA_ARGS__))
+
 cudaError_t launch_warp(Dims d, const float* I1, const float* u, float* I1w, unsigned* red_reset,
                         cudaStream_t s) {
-  return launch_pdl(k_warp, grid3(d, d.nz), kBlock, 0, s, d, I1, u, I1w, red_reset,
-                    (unsigned*)nullptr, (double*)nullptr, 0.0f, 0);
+  if (d.zv != 2 && d.zv != 4) d.zv = 1;
+  return NADMM_ZV_LAUNCH(k_warp, d, s, d, I1, u, I1w, red_reset, (unsigned*)nullptr,
+                         (double*)nullptr, 0.0f, 0);
 }
 
 cudaError_t launch_warp_measured(Dims d, const float* I1, const float* u, float* I1w,
                                  unsigned* red_reset, unsigned* conv, double* conv_acc,
                                  float warp_tol, bool measure, cudaStream_t s) {
-  return launch_pdl(k_warp, grid3(d, d.nz), kBlock, 0, s, d, I1, u, I1w, red_reset, conv, conv_acc,
-                    warp_tol, measure ? 1 : 0);
+  if (d.zv != 2 && d.zv != 4) d.zv = 1;
+  return NADMM_ZV_LAUNCH(k_warp, d, s, d, I1, u, I1w, red_reset, conv, conv_acc, warp_tol,
+                         measure ? 1 : 0);
 }
 
 cudaError_t launch_grad_residual(Dims d, const float* I1w, const float* I0, float* J, float* c,
                                  cudaStream_t s) {
-  return launch_pdl(k_grad_residual, grid3(d, d.nz), kBlock, 0, s, d, I1w, I0, J, c,
-                    (const unsigned*)nullptr);
+  if (d.zv != 2 && d.zv != 4) d.zv = 1;
+  return NADMM_ZV_LAUNCH(k_grad_residual, d, s, d, I1w, I0, J, c, (const unsigned*)nullptr);
 }
 
 cudaError_t launch_grad_residual_conv(Dims d, const float* I1w, const float* I0, float* J, float* c,
                                       const unsigned* conv, cudaStream_t s) {
-  return launch_pdl(k_grad_residual, grid3(d, d.nz), kBlock, 0, s, d, I1w, I0, J, c, conv);
+  if (d.zv != 2 && d.zv != 4) d.zv = 1;
+  return NADMM_ZV_LAUNCH(k_grad_residual, d, s, d, I1w, I0, J, c, conv);
 }
 
 cudaError_t launch_bound_reduce(Dims d, const float* w, unsigned* red, cudaStream_t s,
@@ -311,8 +347,9 @@ cudaError_t launch_bound_reduce(Dims d, const float* w, unsigned* red, cudaStrea
 cudaError_t launch_compose(Dims d, const float* w, const float* u_in, float* u_out,
                            const unsigned* red, float kappa, float delta, unsigned* status,
                            float* scale_out, cudaStream_t s, unsigned* conv) {
-  return launch_pdl(k_compose, grid3(d, d.nz), kBlock, 0, s, d, w, u_in, u_out,
-                    (const unsigned*)red, kappa, delta, status, scale_out, conv);
+  if (d.zv != 2 && d.zv != 4) d.zv = 1;
+  return NADMM_ZV_LAUNCH(k_compose, d, s, d, w, u_in, u_out, (const unsigned*)red, kappa, delta,
+                         status, scale_out, conv);
 }
 
 cudaError_t launch_downsample2(Dims coarse, const float* fine, float* out, cudaStream_t s) {

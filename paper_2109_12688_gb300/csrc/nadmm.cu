@@ -184,8 +184,10 @@ nadmm_status validate(const nadmm_config* c) {
     return fail(NADMM_ERR_INVALID_ARG, "bound_kappa and bound_delta must be > 0 (INFINITY disables)");
   if (c->flags & ~(NADMM_FLAG_NO_GRAPH | NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK |
                    NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_PIPELINED_PLANE | NADMM_FLAG_FOUR_PASS |
-                   NADMM_FLAG_SLAB_PATH))
+                   NADMM_FLAG_SLAB_PATH | NADMM_FLAG_OUTER_MASK))
     return fail(NADMM_ERR_INVALID_ARG, "unknown flag bits");
+  if ((c->flags & NADMM_FLAG_OUTER_MASK) == NADMM_FLAG_OUTER_MASK)
+    return fail(NADMM_ERR_INVALID_ARG, "NADMM_FLAG_OUTER_Z2 and NADMM_FLAG_OUTER_Z4 exclude each other");
   if ((c->flags & NADMM_FLAG_FOUR_PASS) && (c->flags & NADMM_FLAG_SLAB_PATH))
     return fail(NADMM_ERR_INVALID_ARG, "NADMM_FLAG_FOUR_PASS and NADMM_FLAG_SLAB_PATH exclude each other");
   for (int ax = 0; ax < 3; ++ax)
@@ -319,7 +321,12 @@ SlabArgs slab_args(const nadmm_context* h) {
   return a;
 }
 
-Dims dims_of(const nadmm_context* h) { return Dims{h->cfg.nx, h->cfg.ny, h->cfg.nz}; }
+Dims dims_of(const nadmm_context* h) {
+  Dims d{h->cfg.nx, h->cfg.ny, h->cfg.nz};
+  const uint32_t z = h->cfg.flags & NADMM_FLAG_OUTER_MASK;
+  d.zv = z == NADMM_FLAG_OUTER_Z4 ? 4 : z == NADMM_FLAG_OUTER_Z2 ? 2 : 1;
+  return d;
+}
 
 #define TRY(expr)                                  \
   do {                                             \
@@ -1437,11 +1444,11 @@ nadmm_status nadmm_batch_set_pair_plan(nadmm_handle h, int32_t pair, uint32_t pl
   if (h->wt) return fail(NADMM_ERR_INVALID_ARG, "set plans before nadmm_set_workspace");
   if (pair < 0 || pair >= (int32_t)h->pairs.size()) return fail(NADMM_ERR_INVALID_ARG, "pair out of range");
   const uint32_t tuned = NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_FOUR_PASS |
-                         NADMM_FLAG_SLAB_PATH;
+                         NADMM_FLAG_SLAB_PATH | NADMM_FLAG_OUTER_MASK;
   if (plan_flags & ~tuned)
     return fail(NADMM_ERR_INVALID_ARG,
-                "only NADMM_FLAG_LANE*, NADMM_FLAG_FUSED_PENCIL, NADMM_FLAG_FOUR_PASS and "
-                "NADMM_FLAG_SLAB_PATH bits");
+                "only NADMM_FLAG_LANE*, NADMM_FLAG_FUSED_PENCIL, NADMM_FLAG_FOUR_PASS, "
+                "NADMM_FLAG_SLAB_PATH and NADMM_FLAG_OUTER_* bits");
   nadmm_config c = h->pairs[pair]->cfg;
   c.flags = (c.flags & ~tuned) | plan_flags;
   nadmm_context* q = nullptr;
@@ -1923,7 +1930,8 @@ nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t byt
   }
   nadmm_config c = *cfg;
   c.flags &= ~(NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL |
-               NADMM_FLAG_FOUR_PASS | NADMM_FLAG_PIPELINED_PLANE | NADMM_FLAG_SLAB_PATH);
+               NADMM_FLAG_FOUR_PASS | NADMM_FLAG_PIPELINED_PLANE | NADMM_FLAG_SLAB_PATH |
+               NADMM_FLAG_OUTER_MASK);
   c.restart_eta = -1.0f;
   c.admm_tol = c.warp_tol = 0.0f;
   std::vector<std::vector<int>> seen;
@@ -1985,11 +1993,56 @@ nadmm_status nadmm_autotune(const nadmm_config* cfg, void* workspace, size_t byt
     }
     destroy_context(h);
   }
+  // the outer-step kernels of the chosen plan with 1, 2 and 4 z-slices per thread
+  if (st == NADMM_OK) {
+    nadmm_config t = c;
+    t.flags = best_f;
+    nadmm_context* h = nullptr;
+    if ((st = create_single(&t, &h)) == NADMM_OK &&
+        (st = attach(h, base, base + align_up(h->state_total))) == NADMM_OK) {
+      float* u0 = h->at<float>(h->o_io_u);
+      float* u1 = h->at<float>(h->o_ut);
+      float* w = h->at<float>(h->o_wp);
+      float* I = h->at<float>(h->o_io_f);
+      unsigned* red = h->tab<unsigned>(h->o_red);
+      float best_outer = -1.0f;
+      uint32_t best_z = 0;
+      const uint32_t zbits[3] = {0u, NADMM_FLAG_OUTER_Z2, NADMM_FLAG_OUTER_Z4};
+      for (int zi = 0; zi < 3 && e == cudaSuccess; ++zi) {
+        Dims d = dims_of(h);
+        d.zv = 1 << zi;
+        float ms = 0.0f, t_min = -1.0f;
+        for (int rep = 0; rep < 13 && e == cudaSuccess; ++rep) {
+          if (rep >= 3) e = cudaEventRecord(e0, s);
+          if (e == cudaSuccess) e = launch_warp(d, I, u0, h->at<float>(h->o_I1w), red, s);
+          if (e == cudaSuccess)
+            e = launch_grad_residual(d, h->at<float>(h->o_I1w), I, h->at<float>(h->o_J),
+                                     h->at<float>(h->o_c), s);
+          if (e == cudaSuccess) e = launch_bound_reduce(d, w, red, s);
+          if (e == cudaSuccess)
+            e = launch_compose(d, w, u0, u1, red, t.bound_kappa, t.bound_delta, red + 2, nullptr, s);
+          if (rep >= 3) {
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && (t_min < 0.0f || ms < t_min)) t_min = ms;
+          }
+        }
+        if (e == cudaSuccess && (best_outer < 0.0f || t_min < best_outer)) {
+          best_outer = t_min;
+          best_z = zbits[zi];
+        }
+      }
+      if (e != cudaSuccess) st = cuda_fail(e, "autotune trial (outer step)");
+      else best_f |= best_z;
+    }
+    destroy_context(h);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != NADMM_OK) return st;
   const uint32_t tuned = NADMM_FLAG_LANE_MASK | NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_FOUR_PASS |
-                         NADMM_FLAG_SLAB_PATH;
+                         NADMM_FLAG_SLAB_PATH | NADMM_FLAG_OUTER_MASK;
   *best_flags = (cfg->flags & ~tuned) | (best_f & tuned);
   if (best_ms) *best_ms = best;
   return NADMM_OK;

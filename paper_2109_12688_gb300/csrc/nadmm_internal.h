@@ -273,7 +273,12 @@ cudaError_t launch_whole(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t
 #endif
 
 // ---------------------------------------------------------------- grid ops
-struct Dims { int nx, ny, nz; };
+// zv: z-slices per thread of the re-warp, gradient and compose kernels (1, 2
+// or 4; a tuned plan choice, same results)
+struct Dims {
+  int nx, ny, nz;
+  int zv = 1;
+};
 
 // red_reset (or null): two words zeroed for the next bound reduction
 cudaError_t launch_warp(Dims d, const float* I1, const float* u, float* I1w, unsigned* red_reset,

@@ -30,8 +30,11 @@ NADMM_FLAG_FUSED_PENCIL = 0x100
 NADMM_FLAG_PIPELINED_PLANE = 0x200
 NADMM_FLAG_FOUR_PASS = 0x400
 NADMM_FLAG_SLAB_PATH = 0x800
+NADMM_FLAG_OUTER_Z2 = 0x1000
+NADMM_FLAG_OUTER_Z4 = 0x2000
+NADMM_FLAG_OUTER_MASK = 0x3000
 # plan bits nadmm_autotune chooses
-PLAN_FLAGS = 0xFC | 0x100 | 0x400 | 0x800
+PLAN_FLAGS = 0xFC | 0x100 | 0x400 | 0x800 | 0x3000
 
 
 def NADMM_FLAG_LANE8(axis):

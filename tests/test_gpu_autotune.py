@@ -109,3 +109,30 @@ def test_pipelined_plane_pass_is_the_per_tile_pass(lib, dims):
     ub = b.register(dev(pair["fixed"]), dev(pair["moving"]))
     assert lib.nadmm_get_status(b.handle, torch.cuda.current_stream()) == lib.NADMM_OK
     assert torch.equal(ua, ub)
+
+
+@pytest.mark.parametrize("dims", [(128, 128, 96), (20, 12, 14), (96, 112, 80)])
+def test_outer_step_slices_per_thread_give_the_same_result(lib, dims):
+    """The re-warp, gradient and compose kernels with 1, 2 or 4 z-slices per
+    thread (an odd nz leaves a ragged last group) compute the same
+    registration bit for bit."""
+    pair = synth.make_pair(dims, seed=13)
+    kw = dict(outer=3, inner=3)
+    ref = None
+    for f in (0, lib.NADMM_FLAG_OUTER_Z2, lib.NADMM_FLAG_OUTER_Z4):
+        u = lib.Registration(dims, device=DEV, flags=f, **kw).register(dev(pair["fixed"]),
+                                                                       dev(pair["moving"]))
+        if ref is None:
+            ref = u
+        else:
+            assert torch.equal(u, ref), f
+
+
+def test_autotune_picks_outer_slices(lib):
+    cfg = lib.make_config((96, 112, 80))
+    need = lib.nadmm_autotune_workspace_size(cfg)
+    ws = torch.empty(need + 256, dtype=torch.uint8, device=DEV)
+    ptr = (ws.data_ptr() + 255) // 256 * 256
+    flags, ms = lib.nadmm_autotune(cfg, ptr, need, torch.cuda.current_stream())
+    assert flags & lib.NADMM_FLAG_OUTER_MASK != lib.NADMM_FLAG_OUTER_MASK
+    assert flags & ~lib.PLAN_FLAGS == 0 and ms > 0
