@@ -109,6 +109,13 @@ typedef enum nadmm_status {
                                      z-plane each; decided when the workspace
                                      is attached); flat batches always take it */
 
+#define NADMM_FLAG_SLAB_PAIRS 0x4000u /* slab path with every cluster taking two
+                                     z-planes in turn: a slab pass needs half the
+                                     GPU's clusters, so the passes of
+                                     registrations running on several streams
+                                     share the GPU (implies NADMM_FLAG_SLAB_PATH
+                                     where the grid supports the slab path)    */
+
 /* z-slices per thread of the re-warp, gradient and compose kernels (bits
  * 12-13): 0 one, NADMM_FLAG_OUTER_Z2 two, NADMM_FLAG_OUTER_Z4 four; the same
  * results either way, nadmm_autotune picks one. */

@@ -184,7 +184,7 @@ nadmm_status validate(const nadmm_config* c) {
     return fail(NADMM_ERR_INVALID_ARG, "bound_kappa and bound_delta must be > 0 (INFINITY disables)");
   if (c->flags & ~(NADMM_FLAG_NO_GRAPH | NADMM_FLAG_SAVE_FOR_BACKWARD | NADMM_FLAG_LANE_MASK |
                    NADMM_FLAG_FUSED_PENCIL | NADMM_FLAG_PIPELINED_PLANE | NADMM_FLAG_FOUR_PASS |
-                   NADMM_FLAG_SLAB_PATH | NADMM_FLAG_OUTER_MASK))
+                   NADMM_FLAG_SLAB_PATH | NADMM_FLAG_OUTER_MASK | NADMM_FLAG_SLAB_PAIRS))
     return fail(NADMM_ERR_INVALID_ARG, "unknown flag bits");
   if ((c->flags & NADMM_FLAG_OUTER_MASK) == NADMM_FLAG_OUTER_MASK)
     return fail(NADMM_ERR_INVALID_ARG, "NADMM_FLAG_OUTER_Z2 and NADMM_FLAG_OUTER_Z4 exclude each other");
@@ -301,6 +301,7 @@ SlabArgs slab_args(const nadmm_context* h) {
   a.nkx = (int)h->nkx;
   a.mx = h->cfg.nx / 2;
   a.qdiv = make_fastdiv((uint32_t)(h->cfg.nx / 4));
+  a.zper = (h->cfg.flags & NADMM_FLAG_SLAB_PAIRS) ? 2 : 1;
   a.xr1 = h->pxh.radix[0];
   a.xr2 = h->pxh.radix[1];
   a.yr1 = h->py.radix[0];
@@ -873,7 +874,7 @@ nadmm_status attach(nadmm_context* h, char* ws, char* wt) {
   // device's waves well
   h->use_slab = false;
   if (h->slab) {
-    if ((h->cfg.flags & NADMM_FLAG_SLAB_PATH) || h->restart) {
+    if ((h->cfg.flags & (NADMM_FLAG_SLAB_PATH | NADMM_FLAG_SLAB_PAIRS)) || h->restart) {
       h->use_slab = true;
     } else {
       int clusters = 0;

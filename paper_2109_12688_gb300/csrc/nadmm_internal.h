@@ -142,6 +142,7 @@ struct SlabArgs {
   float* u_prev;           // [3][V] u^{k-1} in, u^k out
   double* racc;            // [0] running sum of the pass, [1] cbar
   unsigned* rwords;        // [0] CTAs of the pass that have reported, [1] restarts counted
+  int zper;                // z-planes per cluster in one launch (1, or 2 for half the clusters)
   FastDiv qdiv;            // division by nx / 4 (voxel quads per row)
   int nx, ny, nz, nkx, mx;  // mx = nx / 2
   int xr1, xr2, yr1, yr2;

@@ -407,9 +407,11 @@ __device__ __forceinline__ void slab_restart_test(const SlabArgs& a, float part,
 // CTAs that owns it: beta_k and k are the factor and index of the iteration
 // the pass starts, nctas the pair's CTA count, lead the CTA that resets the
 // restart state of a new inner loop.
+// pass: how many planes this CTA has already taken in this launch (the
+// mbarrier is set up on the first and its phase alternates).
 template <int MODE>
 __device__ __forceinline__ void slab_body(const SlabArgs& a, int z, float beta_k, int k,
-                                          unsigned nctas, bool lead) {
+                                          unsigned nctas, bool lead, int pass) {
   constexpr bool kInverse = (MODE == SLAB_SPEC || MODE == SLAB_SPEC_PREV || MODE == SLAB_FINAL);
   constexpr bool kForward = (MODE != SLAB_FINAL);
   constexpr bool kCoupled = (MODE != SLAB_FINAL && MODE != SLAB_FIELD);
@@ -422,24 +424,27 @@ __device__ __forceinline__ void slab_body(const SlabArgs& a, int z, float beta_k
   const int tid = threadIdx.x;
   const uint32_t plane_bytes = (uint32_t)((size_t)a.ny * a.nkx * sizeof(float2));
   float2* gplane = a.spec + ((size_t)z * 3 + comp) * a.ny * a.nkx;
-  if (kInverse) {
-    if (tid == 0) {
-      mbar_init(bar, 1);
-      fence_barrier_init();
+  if (pass == 0) {
+    if (kInverse) {
+      if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    pdl_wait();  // the spectrum, J and c come from the kernels before
+    pdl_trigger();
   }
-  pdl_wait();  // the spectrum, J and c come from the kernels before
-  pdl_trigger();
   if (kInverse) {
-    if (tid == 0) {
+    const uint32_t parity = (uint32_t)(pass & 1);
+    if (tid == 0) {  // the previous plane's store has read the buffer (bulk_wait_read)
       mbar_expect_tx(bar, plane_bytes);
       bulk_load(plane, gplane, plane_bytes, bar);
     }
-    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0));
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, parity));
     if (!ok) {
       if (tid == 0 && a.status != nullptr) atomicOr(a.status, kStatusTimeout);
-      mbar_wait_bounded(bar, 0);  // let the copy land before the plane is touched
+      mbar_wait_bounded(bar, parity);  // let the copy land before the plane is touched
     }
     cols_rt(a, plane, xch, true);
     __syncthreads();
@@ -503,11 +508,16 @@ __device__ __forceinline__ void slab_body(const SlabArgs& a, int z, float beta_k
 
 // MODE: SLAB_FIRST, SLAB_SPEC (k = 1), SLAB_SPEC_PREV (k >= 2), SLAB_FINAL,
 // SLAB_FIELD, SLAB_STATE (k = 1), SLAB_STATE_PREV (k >= 2).
+// A cluster takes planes z = cluster, cluster + clusters, ... (one plane
+// each when the grid has nz clusters; a.zper planes each with fewer).
 template <int MODE>
 __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kSlabThreads, 2)
     k_slab(const __grid_constant__ SlabArgs a) {
 #if defined(__CUDA_ARCH__)
-  slab_body<MODE>(a, (int)(blockIdx.x / 3), a.beta, a.k, gridDim.x, blockIdx.x == 0);
+  const int clusters = (int)(gridDim.x / 3);
+  int pass = 0;
+  for (int z = (int)(blockIdx.x / 3); z < a.nz; z += clusters, ++pass)
+    slab_body<MODE>(a, z, a.beta, a.k, 3u * (unsigned)a.nz, blockIdx.x == 0 && pass == 0, pass);
 #endif
 }
 
@@ -525,7 +535,7 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kSlabThreads, 2)
   }
   const int local = (int)blockIdx.x - __ldg(start + lo);
   slab_body<MODE>(pairs[lo], local / 3, beta_k, k, (unsigned)(__ldg(start + lo + 1) - __ldg(start + lo)),
-                  local == 0);
+                  local == 0, 0);
 #endif
 }
 
@@ -683,7 +693,8 @@ bool slab_supported(int nx, int ny, int nz, const AxisPlan& pxh, const AxisPlan&
 }
 
 cudaError_t launch_slab(int mode, const SlabArgs& a, cudaStream_t s) {
-  const dim3 grid((unsigned)(3 * a.nz)), block(kSlabThreads);
+  const int zper = a.zper > 1 ? a.zper : 1;
+  const dim3 grid((unsigned)(3 * ((a.nz + zper - 1) / zper))), block(kSlabThreads);
   const size_t smem = slab_smem_bytes(a);
   switch (mode) {
     case SLAB_FIRST: return launch_whole(k_slab<SLAB_FIRST>, grid, block, smem, s, a);

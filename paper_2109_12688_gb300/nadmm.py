@@ -33,6 +33,7 @@ NADMM_FLAG_SLAB_PATH = 0x800
 NADMM_FLAG_OUTER_Z2 = 0x1000
 NADMM_FLAG_OUTER_Z4 = 0x2000
 NADMM_FLAG_OUTER_MASK = 0x3000
+NADMM_FLAG_SLAB_PAIRS = 0x4000
 # plan bits nadmm_autotune chooses
 PLAN_FLAGS = 0xFC | 0x100 | 0x400 | 0x800 | 0x3000
 
