@@ -5,15 +5,24 @@ Metric: ms per 128x128x96 registration (plus voxel-ADMM-iters/s and the
 dominant kernel's HBM GB/s against the measured peak).  A step registers one
 synthetic cardiac-shaped pair for each regulariser order n = 1, 2, 3 with
 10 compositions x 10 ADMM iterations (lambda = 10, theta = 0.1, s = 2).
-Inputs are device-resident when the timed region starts; L2 is flushed
-(a 256 MB write) between timed steps, outside each step's events.
+The three registrations of a step run on three streams.  Two plans compute
+them: the slab path (two kernels per ADMM iteration) and the four-kernel
+path; both are timed on three streams after the warm-up and the faster one
+runs the timed region (key plan).  Inputs are device-resident when the timed
+region starts; L2 is flushed (a 256 MB write) between timed steps, outside
+each step's events.
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
                 [--workload registration|batch64|large|grad|batch16grad|pyramid]
 
-The default line carries, besides the contract keys: latency_ms_one_at_a_time
-(the same pairs one after another on one stream, checked bit for bit against
-the concurrent results: a mismatch exits non-zero); roofline (dominant
+The default line carries, besides the contract keys: plan and
+plan_trial_ms_per_registration; latency_ms_one_at_a_time (the same pairs one
+after another on one stream in the chosen plan, checked bit for bit against
+the concurrent results: a mismatch exits non-zero) and its value for both
+plans; the other plan on three streams (its results within 1e-4 voxel of the
+chosen plan's); batched_call_ms_per_registration (the three pairs as one
+nadmm_register_batched call, checked bit for bit against the slab plan's
+single calls); roofline (dominant
 kernel class: algorithmic bytes per launch over its mean event-timed
 duration, against MEASURED_PEAKS.json, with the ncu DRAM traffic of the
 committed profile when it matches the kernel source); kernels (time,
@@ -419,10 +428,10 @@ def bench_config(orders, world):
     return {"workload": WORKLOAD, "dims": list(DIMS), "orders": list(orders),
             "outer": OUTER, "inner": INNER, "registrations_per_step": len(orders),
             "l2": "flushed between timed steps (256 MB write outside the step events)",
-            "concurrency": f"the {len(orders)} registrations of a step as one batched call "
-                           "(nadmm_register_batched, flat execution: each ADMM phase one "
-                           "launch over all pairs); value is their throughput; the same step "
-                           "on three streams and on one stream is reported beside it",
+            "concurrency": f"the {len(orders)} registrations of a step on {len(orders)} streams "
+                           "(nadmm_register each) in the faster of the slab and four-kernel "
+                           "plans, chosen by timing both after the warm-up; value is their "
+                           "throughput",
             "parallelism": f"replicas x{world}"}
 
 
@@ -726,20 +735,27 @@ def main():
     I0 = [torch.from_numpy(p["fixed"]).to(dev) for p in pairs]
     I1 = [torch.from_numpy(p["moving"]).to(dev) for p in pairs]
     U = [torch.empty((3, nz, ny, nx), dtype=torch.float32, device=dev) for _ in ORDERS]
-    regs = [nadmm.Registration(DIMS, device=dev, order_n=n, lam=LAM, theta=THETA, outer=OUTER,
-                               inner=INNER) for n in ORDERS]
+    # Two plans of the same registrations: the slab path (two kernels per ADMM
+    # iteration) and the four-kernel path; the step runs whichever is faster on
+    # three streams, chosen by timing both after the warm-up.
+    PLANS = {"slab": nadmm.NADMM_FLAG_SLAB_PATH, "four_kernel": nadmm.NADMM_FLAG_FOUR_PASS}
+    regs_of = {p: [nadmm.Registration(DIMS, device=dev, order_n=n, lam=LAM, theta=THETA,
+                                      outer=OUTER, inner=INNER, flags=f) for n in ORDERS]
+               for p, f in PLANS.items()}
+    U_of = {p: [torch.empty((3, nz, ny, nx), dtype=torch.float32, device=dev) for _ in ORDERS]
+            for p in PLANS}
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     # The step's registrations are independent: each runs on its own stream,
     # forked from and joined back into the timed stream, so that one pair's
-    # DRAM-bound plane passes overlap another's L2-resident FFT passes.
+    # DRAM-bound passes overlap another's L2-resident FFT passes.
     side = [torch.cuda.Stream(dev) for _ in ORDERS]
 
-    def step():
+    def step_streams(plan):
         fork = torch.cuda.Event()
         fork.record(stream)
         joins = []
-        for r, a, b, u, sd in zip(regs, I0, I1, U, side):
+        for r, a, b, u, sd in zip(regs_of[plan], I0, I1, U_of[plan], side):
             sd.wait_event(fork)
             nadmm.nadmm_register(r.handle, a, b, u, sd)
             ev = torch.cuda.Event()
@@ -748,29 +764,29 @@ def main():
         for ev in joins:
             stream.wait_event(ev)
 
-    def step_sequential():
-        for r, a, b, u in zip(regs, I0, I1, U):
+    def step_sequential(plan):
+        for r, a, b, u in zip(regs_of[plan], I0, I1, U_of[plan]):
             nadmm.nadmm_register(r.handle, a, b, u, stream)
 
-    # the same three registrations as one batched call (flat execution: one
-    # slab-pass launch and one z-pass launch per ADMM phase over all pairs)
+    # the same three registrations as one batched call (flat execution on the
+    # slab path: one slab-pass launch and one z-pass launch per ADMM phase)
     batch = nadmm.BatchedRegistration([DIMS] * len(ORDERS), device=dev, lam=LAM, theta=THETA,
                                       outer=OUTER, inner=INNER,
                                       per_pair=[{"order_n": n} for n in ORDERS])
-    UB = [torch.empty_like(u) for u in U]
+    UB = [torch.empty_like(u) for u in U_of["slab"]]
 
     def step_batched():
         nadmm.nadmm_register_batched(batch.handle, I0, I1, UB, stream)
 
     def check_status():
-        for r in regs + [batch]:
+        for r in [r for p in PLANS for r in regs_of[p]] + [batch]:
             st = nadmm.nadmm_get_status(r.handle, stream)
             if st != nadmm.NADMM_OK:
                 raise RuntimeError(f"device status {nadmm.nadmm_status_string(st)}")
 
-    def timed_steps(fn, salt):
+    def timed_steps(fn, salt, steps):
         evs = []
-        for i in range(args.steps):
+        for i in range(steps):
             flush.fill_((i + salt) & 0xFF)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -781,12 +797,31 @@ def main():
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in evs)
 
+    def per_reg(ms, steps):
+        return ms / (steps * len(ORDERS))
+
+    def fail(msg):
+        print(json.dumps({"error": msg}), flush=True)
+        sys.exit(3)
+
     for i in range(args.warmup):
+        for p in PLANS:
+            flush.fill_(i & 0xFF)
+            step_streams(p)
         flush.fill_(i & 0xFF)
         step_batched()
-        step()
     torch.cuda.synchronize()
     check_status()
+    # plan choice (not part of the timed region): three-stream steps of each plan
+    trial_steps = max(3, args.warmup)
+    trial = {p: per_reg(timed_steps(lambda p=p: step_streams(p), 5, trial_steps), trial_steps)
+             for p in PLANS}
+    if world > 1:  # every rank runs the plan rank 0 chose
+        choice = torch.tensor([0 if trial["slab"] <= trial["four_kernel"] else 1], device=dev)
+        dist.broadcast(choice, 0)
+        plan = ("slab", "four_kernel")[int(choice.item())]
+    else:
+        plan = min(trial, key=trial.get)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -794,40 +829,35 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms = timed_steps(step_batched, 7)
+    total_ms = timed_steps(lambda: step_streams(plan), 7, args.steps)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
     total_ms = max_over_ranks(total_ms, world, dev)
     check_status()
-    timed_u = [u.clone() for u in UB]  # outputs of the last timed (batched) step
-    # the same step as three registrations on three streams
-    streams_ms = timed_steps(step, 11)
-    check_status()
-    for n, a, b in zip(ORDERS, timed_u, U):
+    regs = regs_of[plan]
+    timed_u = [u.clone() for u in U_of[plan]]  # outputs of the last timed step
+    # the same plan one registration after another on one stream: bit for bit
+    latency = {plan: per_reg(timed_steps(lambda: step_sequential(plan), 3, args.steps), args.steps)}
+    for n, a, b in zip(ORDERS, timed_u, U_of[plan]):
         if not torch.equal(a, b):
-            print(json.dumps({"error": f"n = {n}: three-stream result differs from the batched "
-                                       "result"}), flush=True)
-            sys.exit(3)
-    # latency of one registration at a time (same pairs, one stream)
-    seq = []
-    for i in range(args.steps):
-        flush.fill_((i + 3) & 0xFF)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step_sequential()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        seq.append(e0.elapsed_time(e1))
+            fail(f"n = {n}: single-stream result differs from the three-stream result")
+    other = "four_kernel" if plan == "slab" else "slab"
+    latency[other] = per_reg(timed_steps(lambda: step_sequential(other), 3, args.steps),
+                             args.steps)
+    streams_other = per_reg(timed_steps(lambda: step_streams(other), 11, args.steps), args.steps)
     check_status()
-    # and one after another on one stream: the same results, bit for bit
-    for n, a, b in zip(ORDERS, timed_u, U):
+    # the other plan computes the same arithmetic in another rounding order
+    plan_diff = max(float((a - b).abs().max()) for a, b in zip(timed_u, U_of[other]))
+    if not plan_diff <= 1e-4:
+        fail(f"the slab and four-kernel plans differ by {plan_diff} voxel")
+    # the batched call: the slab plan's results bit for bit
+    batched_ms = per_reg(timed_steps(step_batched, 9, args.steps), args.steps)
+    check_status()
+    for n, a, b in zip(ORDERS, UB, U_of["slab"]):
         if not torch.equal(a, b):
-            print(json.dumps({"error": f"n = {n}: single-stream result differs from the "
-                                       "batched result"}), flush=True)
-            sys.exit(3)
-    latency_ms = sum(seq) / len(seq) / len(ORDERS)
+            fail(f"n = {n}: batched result differs from the slab plan's single calls")
+    U = U_of[plan]
     regs_total = args.steps * len(ORDERS) * world
     ms_per_reg, ms_per_step, vox_rate = aggregate(total_ms, args.steps, len(ORDERS), world, V,
                                                   OUTER, INNER)
@@ -926,9 +956,15 @@ def main():
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": bench_config(ORDERS, world),
-        "latency_ms_one_at_a_time": latency_ms,
-        "three_streams_ms_per_registration": streams_ms / (args.steps * len(ORDERS)),
-        "batched_equals_streams_and_sequential": True,
+        "plan": plan,
+        "plan_trial_ms_per_registration": trial,
+        "latency_ms_one_at_a_time": latency[plan],
+        "latency_ms_one_at_a_time_by_plan": latency,
+        "three_streams_ms_per_registration_other_plan": {other: streams_other},
+        "batched_call_ms_per_registration": batched_ms,
+        "checks": {"one_stream_equals_three_streams": True,
+                   "batched_call_equals_slab_plan": True,
+                   "max_abs_diff_between_plans_voxel": plan_diff},
         "voxel_admm_iters_per_s": vox_rate,
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,

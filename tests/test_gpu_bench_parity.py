@@ -3,8 +3,9 @@
 bench.py times three 128x128x96 registrations per step: the phantom pairs of
 seeds 1, 2, 3 with regulariser orders n = 1, 2, 3, s = 2, lambda = 10,
 theta = 0.1, kappa = 0.5, delta = 1, 10 compositions x 10 ADMM iterations,
-each registration on its own stream.  Here the same pairs run the same way
-(three streams, one graph replay each) and every displacement is compared
+each registration on its own stream, in the faster of two plans (the slab
+path or the four-kernel path).  Here the same pairs run the same way in both
+plans (three streams, one graph replay each) and every displacement is compared
 with the oracle's free-running registration (Sec. 2 outer loop after Eq. 2,
 Eq. 5 and Eq. 6): max |u_gpu - u_oracle| <= 1e-3 voxel, and the Jacobian
 determinant is positive everywhere on both.  One s = 1 pair at the same size
@@ -65,7 +66,7 @@ def _nonpositive(lib, reg, u, stream):
     return int(cnt.item())
 
 
-def _run(lib, cases, concurrent):
+def _run(lib, cases, concurrent, flags=0):
     dev = torch.device("cuda:0")
     nx, ny, nz = DIMS
     regs, I0, I1, U = [], [], [], []
@@ -75,7 +76,7 @@ def _run(lib, cases, concurrent):
         I1.append(torch.from_numpy(pair["moving"]).to(dev))
         U.append(torch.full((3, nz, ny, nx), float("nan"), device=dev))
         regs.append(lib.Registration(DIMS, device=dev, order_n=n, lam=LAM, theta=THETA,
-                                     outer=OUTER, inner=INNER, data_term=s))
+                                     outer=OUTER, inner=INNER, data_term=s, flags=flags))
     main = torch.cuda.current_stream(dev)
     if concurrent:  # as bench.py: one stream per registration, forked from the main one
         side = [torch.cuda.Stream(dev) for _ in cases]
@@ -95,9 +96,11 @@ def _run(lib, cases, concurrent):
     return regs, U
 
 
-def test_benchmarked_registrations_match_oracle(lib, oracle_results):
+@pytest.mark.parametrize("plan", ["slab", "four_kernel"])
+def test_benchmarked_registrations_match_oracle(lib, oracle_results, plan):
     bench_cases = CASES[:3]
-    regs, U = _run(lib, bench_cases, concurrent=True)
+    flags = {"slab": lib.NADMM_FLAG_SLAB_PATH, "four_kernel": lib.NADMM_FLAG_FOUR_PASS}[plan]
+    regs, U = _run(lib, bench_cases, concurrent=True, flags=flags)
     stream = torch.cuda.current_stream()
     for case, reg, u in zip(bench_cases, regs, U):
         u_ref, det_min_ref = oracle_results[case]
@@ -107,7 +110,7 @@ def test_benchmarked_registrations_match_oracle(lib, oracle_results):
         assert det_min_ref > 0.0, case
         assert _nonpositive(lib, reg, u, stream) == 0, case
     # the same registrations one after another on one stream: bit-identical
-    _, U_seq = _run(lib, bench_cases, concurrent=False)
+    _, U_seq = _run(lib, bench_cases, concurrent=False, flags=flags)
     for case, a, b in zip(bench_cases, U, U_seq):
         assert torch.equal(a, b), case
 
