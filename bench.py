@@ -21,8 +21,9 @@ after another on one stream in the chosen plan, checked bit for bit against
 the concurrent results: a mismatch exits non-zero) and its value for both
 plans; the other plan on three streams (its results within 1e-4 voxel of the
 chosen plan's); batched_call_ms_per_registration (the three pairs as one
-nadmm_register_batched call, checked bit for bit against the slab plan's
-single calls); roofline (dominant
+nadmm_register_batched call, flat on the slab path and on the four-kernel
+path with three concurrent lanes, each checked bit for bit against its
+plan's single calls); roofline (dominant
 kernel class: algorithmic bytes per launch over its mean event-timed
 duration, against MEASURED_PEAKS.json, with the ncu DRAM traffic of the
 committed profile when it matches the kernel source); kernels (time,
@@ -509,16 +510,23 @@ def extra_workload(name, data, steps, warmup, dev, sample_clocks=True):
         I0 = [torch.from_numpy(data[("b64", i)][0]).to(dev) for i in range(64)]
         I1 = [torch.from_numpy(data[("b64", i)][1]).to(dev) for i in range(64)]
         U = [torch.empty((3, d[2], d[1], d[0]), device=dev) for d in dims]
-        lanes_ms = {}
-        for lanes in ((None, 1, 2, 3, 4) if sample_clocks else (None,)):
-            breg = nadmm.BatchedRegistration(dims, device=dev, lanes=lanes, order_n=2, **kw)
-            t, c = timed(lambda: nadmm.nadmm_register_batched(breg.handle, I0, I1, U, stream))
-            if lanes is None:
-                ms, clk = t, c
-                default_lanes = nadmm.nadmm_batch_get_lanes(breg.handle)
-            else:
-                lanes_ms[lanes] = t
+        # execution plans of the batched handle: the default (flat execution on
+        # the slab path: each ADMM phase one launch over all pairs) and the
+        # four-kernel path with the pairs spread over 2 or 3 concurrent lanes
+        # (graph branches); value is the fastest, all are reported
+        plans = {"flat": (None, 0), "four_kernel_lanes2": (2, nadmm.NADMM_FLAG_FOUR_PASS),
+                 "four_kernel_lanes3": (3, nadmm.NADMM_FLAG_FOUR_PASS)}
+        if sample_clocks:
+            plans |= {f"lanes{n}": (n, 0) for n in (1, 2, 3, 4)}
+        plan_ms, plan_clk = {}, {}
+        for pname, (lanes, flags) in plans.items():
+            breg = nadmm.BatchedRegistration(dims, device=dev, lanes=lanes, order_n=2, flags=flags,
+                                             **kw)
+            plan_ms[pname], plan_clk[pname] = timed(
+                lambda: nadmm.nadmm_register_batched(breg.handle, I0, I1, U, stream))
             del breg
+        best = min(plan_ms, key=plan_ms.get)
+        ms, clk = plan_ms[best], plan_clk[best]
         regs = [nadmm.Registration(d, device=dev, order_n=2, **kw) for d in dims]
 
         def sequential():
@@ -531,12 +539,12 @@ def extra_workload(name, data, steps, warmup, dev, sample_clocks=True):
             "ms_per_step": ms,
             "config": {"workload": "64 pairs, nx, ny from {96,112,128,144,160}, nz from "
                                    "{64,80,96,112} (seed 1234), two-phase phantoms, n=2, 10 x 10 "
-                                   "iterations, one batched graph with the default number "
-                                   "of concurrent lanes (others in ms_by_lanes)",
-                       "lanes": default_lanes, "voxels": vox,
+                                   "iterations, one batched graph; value: the fastest execution "
+                                   "plan (all in ms_by_plan)",
+                       "plan": best, "voxels": vox,
                        "l2": "flushed between timed steps (256 MB write outside the step events)"},
             "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms,
-            "ms_by_lanes": lanes_ms,
+            "ms_by_plan": plan_ms,
             "voxel_admm_iters_per_s": vox * OUTER * INNER / (ms / 1e3),
             "clocks": clk}
     if name == "pyramid":
@@ -774,12 +782,21 @@ def main():
                                       outer=OUTER, inner=INNER,
                                       per_pair=[{"order_n": n} for n in ORDERS])
     UB = [torch.empty_like(u) for u in U_of["slab"]]
+    # and on the four-kernel path with one concurrent lane (graph branch) per pair
+    batch4 = nadmm.BatchedRegistration([DIMS] * len(ORDERS), device=dev, lanes=len(ORDERS),
+                                       lam=LAM, theta=THETA, outer=OUTER, inner=INNER,
+                                       flags=nadmm.NADMM_FLAG_FOUR_PASS,
+                                       per_pair=[{"order_n": n} for n in ORDERS])
+    UB4 = [torch.empty_like(u) for u in U_of["slab"]]
 
     def step_batched():
         nadmm.nadmm_register_batched(batch.handle, I0, I1, UB, stream)
 
+    def step_batched4():
+        nadmm.nadmm_register_batched(batch4.handle, I0, I1, UB4, stream)
+
     def check_status():
-        for r in [r for p in PLANS for r in regs_of[p]] + [batch]:
+        for r in [r for p in PLANS for r in regs_of[p]] + [batch, batch4]:
             st = nadmm.nadmm_get_status(r.handle, stream)
             if st != nadmm.NADMM_OK:
                 raise RuntimeError(f"device status {nadmm.nadmm_status_string(st)}")
@@ -810,6 +827,8 @@ def main():
             step_streams(p)
         flush.fill_(i & 0xFF)
         step_batched()
+        flush.fill_(i & 0xFF)
+        step_batched4()
     torch.cuda.synchronize()
     check_status()
     # plan choice (not part of the timed region): three-stream steps of each plan
@@ -857,6 +876,11 @@ def main():
     for n, a, b in zip(ORDERS, UB, U_of["slab"]):
         if not torch.equal(a, b):
             fail(f"n = {n}: batched result differs from the slab plan's single calls")
+    batched4_ms = per_reg(timed_steps(step_batched4, 13, args.steps), args.steps)
+    check_status()
+    for n, a, b in zip(ORDERS, UB4, U_of["four_kernel"]):
+        if not torch.equal(a, b):
+            fail(f"n = {n}: batched result differs from the four-kernel plan's single calls")
     U = U_of[plan]
     regs_total = args.steps * len(ORDERS) * world
     ms_per_reg, ms_per_step, vox_rate = aggregate(total_ms, args.steps, len(ORDERS), world, V,
@@ -930,7 +954,7 @@ def main():
     for name in extras:
         ln = extra_workload(name, data, 3, 3, dev, sample_clocks=False)
         keep = ("metric", "value", "unit", "steps", "warmup", "sequential_ms",
-                "speedup_vs_sequential", "voxel_admm_iters_per_s", "forward_only_ms",
+                "speedup_vs_sequential", "ms_by_plan", "voxel_admm_iters_per_s", "forward_only_ms",
                 "backward_over_forward", "device_bytes_peak", "workspace_bytes", "ms_by_order",
                 "vs_baseline", "paper_s_by_order")
         extra_lines[name] = {k: ln[k] for k in keep if k in ln} | {
@@ -961,9 +985,10 @@ def main():
         "latency_ms_one_at_a_time": latency[plan],
         "latency_ms_one_at_a_time_by_plan": latency,
         "three_streams_ms_per_registration_other_plan": {other: streams_other},
-        "batched_call_ms_per_registration": batched_ms,
+        "batched_call_ms_per_registration": {"flat_slab": batched_ms,
+                                             "four_kernel_lanes3": batched4_ms},
         "checks": {"one_stream_equals_three_streams": True,
-                   "batched_call_equals_slab_plan": True,
+                   "batched_call_equals_single_calls_of_its_plan": True,
                    "max_abs_diff_between_plans_voxel": plan_diff},
         "voxel_admm_iters_per_s": vox_rate,
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,

@@ -166,8 +166,16 @@ __device__ __noinline__ void slab_rows(const SlabArgs& a, float2* plane, float2*
       for (int j = 0; j < R2; ++j) L.rt_pre[blk * R2 + j] = __ldg(a.rtx + b + R1 * j);
     }
   }
+  const int ny16 = a.ny & ~15;
   for (int y0 = warp * G; y0 < a.ny; y0 += kSlabWarps * G) {
-    const int y = y0 + g;
+    // Row r = y0 + g is transformed at y: within each block of 16 rows the two
+    // groups of a half-warp take rows 8 apart, whose slots lie 8 (nx/2 + 1)
+    // float2 = 16 banks (mod 32) apart (nx/2 + 1 is odd), so their accesses
+    // never share a bank; adjacent rows (2 banks apart) would.
+    const int r = y0 + g;
+    const int y = (G == 4 && r < ny16)
+                      ? (r & ~15) + ((r >> 1) & 6) + ((r & 3) >> 1) + ((r & 1) << 3)
+                      : r;
     if (y < a.ny) {  // uniform over the group
       float2* row = plane + (size_t)y * a.nkx;
       if (inv)
