@@ -377,10 +377,14 @@ thread_local Profiler* g_prof = nullptr;
 // u^k = w_hat^k - b_hat^k of every iteration go to hist_w + k 3V and
 // hist_u + k 3V: the plane passes write them directly (w^{k-1} by the tile
 // stores, u^k by the point-wise step), w^{K-1} comes from the final pass.
-// The same iterations on the slab path (two kernels per iteration).
+// The same iterations on the slab path (two kernels per iteration); with
+// hist_w/hist_u the slab passes write w^{k-1} to the history instead of the
+// w state slot, read w^{k-2} from it, and record u^k.
 cudaError_t enqueue_inner_slab(nadmm_context* h, const PlaneArgs& first, int in_first, bool prev_first,
                                int k0, int steps, const float* J, const float* c, float* w_out,
-                               float* b_out, cudaStream_t s) {
+                               float* b_out, cudaStream_t s, float* hist_w = nullptr,
+                               float* hist_u = nullptr) {
+  const size_t F3 = 3 * h->V;
   SlabArgs a = slab_args(h);
   a.J = J;
   a.c = c;
@@ -399,6 +403,7 @@ cudaError_t enqueue_inner_slab(nadmm_context* h, const PlaneArgs& first, int in_
     f.bprev_in = first.bprev_in;
   }
   f.beta = beta_for(h, k0);
+  if (hist_w != nullptr) f.u_hist = hist_u + (size_t)k0 * F3;
   KLAUNCH(in_first == IN_NONE ? NADMM_KC_SLAB_FIRST : (prev_first ? NADMM_KC_SLAB : NADMM_KC_SLAB_K1),
           s, launch_slab(mode, f, s));
   const PencilArgs pa = pencil_args(h);
@@ -406,6 +411,11 @@ cudaError_t enqueue_inner_slab(nadmm_context* h, const PlaneArgs& first, int in_
     KLAUNCH(NADMM_KC_ZSLAB, s, launch_zslab(pa, s));
     a.beta = beta_for(h, k);
     a.k = k;
+    if (hist_w != nullptr) {  // w^{k-2} from the history, w^{k-1} into it, u^k recorded
+      a.u_hist = hist_u + (size_t)k * F3;
+      a.wp = hist_w + (size_t)(k >= 2 ? k - 2 : 0) * F3;  // k = 1 reads no w state
+      a.wp_out = hist_w + (size_t)(k - 1) * F3;
+    }
     KLAUNCH(k >= 2 ? NADMM_KC_SLAB : NADMM_KC_SLAB_K1, s,
             launch_slab(k >= 2 ? SLAB_SPEC_PREV : SLAB_SPEC, a, s));
   }
@@ -413,6 +423,8 @@ cudaError_t enqueue_inner_slab(nadmm_context* h, const PlaneArgs& first, int in_
   SlabArgs fin = a;
   fin.w_out = w_out;
   fin.b_out = b_out;
+  fin.u_hist = nullptr;
+  fin.wp_out = nullptr;
   if (b_out == nullptr) fin.y = nullptr;
   KLAUNCH(NADMM_KC_SLAB_FINAL, s, launch_slab(SLAB_FINAL, fin, s));
   return cudaSuccess;
@@ -421,9 +433,10 @@ cudaError_t enqueue_inner_slab(nadmm_context* h, const PlaneArgs& first, int in_
 cudaError_t enqueue_inner(nadmm_context* h, PlaneArgs first, int in_first, bool prev_first, int k0,
                           int steps, const float* J, const float* c, float* w_out, float* b_out,
                           cudaStream_t s, float* hist_w = nullptr, float* hist_u = nullptr) {
-  if (h->use_slab && hist_w == nullptr && !thresholds(h) &&
-      (in_first == IN_NONE || in_first == IN_STATE))
-    return enqueue_inner_slab(h, first, in_first, prev_first, k0, steps, J, c, w_out, b_out, s);
+  if (h->use_slab && !thresholds(h) && (in_first == IN_NONE || in_first == IN_STATE) &&
+      (hist_w == nullptr || (k0 == 0 && in_first == IN_NONE)))
+    return enqueue_inner_slab(h, first, in_first, prev_first, k0, steps, J, c, w_out, b_out, s,
+                              hist_w, hist_u);
   const size_t F3 = 3 * h->V;
   auto hw = [&](int k) { return hist_w + (size_t)k * F3; };
   first.J = J;
@@ -1171,6 +1184,34 @@ nadmm_status run_register(nadmm_context* h, const float* I0, const float* I1, fl
 // each recomputes its linearisation and its ADMM iterates from the saved u
 // at its start, then runs the adjoints of compose, bound, the K ADMM steps
 // and the linearisation.
+// w = S y (the w-step's spectral solve, Eq. 6 last line) on the handle's
+// path: forward x/y DFTs, z-pass with the filter, inverse x/y DFTs (three
+// kernels) on the slab path; plane pass, y/z/y passes, final plane pass on
+// the four-kernel path.
+cudaError_t enqueue_solve(nadmm_context* h, const float* y, float* w, cudaStream_t s) {
+  if (h->use_slab) {
+    SlabArgs f = slab_args(h);
+    f.w_in = y;
+    TRY(launch_slab(SLAB_FIELD, f, s));
+    TRY(launch_zslab(pencil_args(h), s));
+    SlabArgs fin = slab_args(h);
+    fin.y = nullptr;
+    fin.w_out = w;
+    fin.b_out = nullptr;
+    return launch_slab(SLAB_FINAL, fin, s);
+  }
+  PlaneArgs a = plane_args(h);
+  a.y = nullptr;
+  a.w_in = y;
+  TRY(launch_plane(IN_FIELD, false, true, a, s));
+  TRY(launch_pencil(pencil_args(h), s));
+  PlaneArgs f = plane_args(h);
+  f.y = nullptr;
+  f.w_out = w;
+  f.b_out = nullptr;
+  return launch_plane(IN_SPEC, false, false, f, s);
+}
+
 cudaError_t enqueue_backward(nadmm_context* h, const float* I0, const float* I1, const float* gu,
                              float* gI0, float* gI1, float* glam, float* gtheta, cudaStream_t s) {
   const Dims d = dims_of(h);
@@ -1195,7 +1236,6 @@ cudaError_t enqueue_backward(nadmm_context* h, const float* I0, const float* I1,
   float* ub1 = h->at<float>(h->o_ub1);
   unsigned* red = h->tab<unsigned>(h->o_red);
   double* acc = h->tab<double>(h->o_acc);
-  PencilArgs pa = pencil_args(h);
 
   TRY(cudaMemsetAsync(gI0, 0, V * sizeof(float), s));
   TRY(cudaMemsetAsync(gI1, 0, V * sizeof(float), s));
@@ -1221,17 +1261,46 @@ cudaError_t enqueue_backward(nadmm_context* h, const float* I0, const float* I1,
     TRY(cudaMemsetAsync(gJ, 0, F3, s));
     TRY(cudaMemsetAsync(gc, 0, V * sizeof(float), s));
     const float* g_in = Wbar(K - 1);  // bbar^{K-1} = 0
+    if (h->use_slab) {
+      // slab path: the spectrum of g^{K-1}, then per reverse step one slab
+      // pass (S g^k in, the adjoint point-wise step, the spectrum of g^{k-1}
+      // out) and one z-pass
+      SlabArgs f = slab_args(h);
+      f.w_in = g_in;
+      TRY(launch_slab(SLAB_FIELD, f, s));
+      TRY(launch_zslab(pencil_args(h), s));
+      for (int k = K - 1; k >= 0; --k) {
+        SlabArgs a = slab_args(h);
+        a.beta = beta_for(h, k);
+        a.J = J;
+        a.c = c;
+        SlabAdj& r = a.adj;
+        r.wk = hist(hw, k);
+        r.uk = hist(hu, k);
+        r.Bk = Bbar(k);
+        if (k >= 1) {
+          r.W1bar = Wbar(k - 1);
+          r.B1bar = Bbar(k - 1);
+        }
+        if (k >= 2) {
+          r.W2bar = Wbar(k - 2);
+          r.B2bar = Bbar(k - 2);
+        }
+        r.g_in = g_in;
+        r.g_out = g;
+        r.gJ = gJ;
+        r.gc = gc;
+        r.acc = acc;
+        r.inv_gamma = h->cfg.theta / h->cfg.lambda;
+        TRY(launch_slab(k >= 1 ? SLAB_ADJ : SLAB_ADJ_LAST, a, s));
+        if (k >= 1) TRY(launch_zslab(pencil_args(h), s));
+        g_in = g;
+      }
+      TRY(launch_linearise_vjp(d, I1, u_o, gJ, gc, gI0, gI1, ub1, ub0, s));
+      continue;
+    }
     for (int k = K - 1; k >= 0; --k) {
-      PlaneArgs fa = plane_args(h);
-      fa.y = nullptr;
-      fa.w_in = g_in;
-      TRY(launch_plane(IN_FIELD, false, true, fa, s));
-      TRY(launch_pencil(pa, s));
-      PlaneArgs fb = plane_args(h);
-      fb.y = nullptr;
-      fb.w_out = Sg;
-      fb.b_out = nullptr;
-      TRY(launch_plane(IN_SPEC, false, false, fb, s));
+      TRY(enqueue_solve(h, g_in, Sg, s));
       AdjArgs a;
       std::memset(&a, 0, sizeof(a));
       a.d = d;

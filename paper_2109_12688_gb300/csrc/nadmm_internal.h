@@ -108,12 +108,34 @@ enum SlabMode : int {
   SLAB_FIELD = 4,       // forward transforms of a given field (spectral solve)
   SLAB_STATE = 5,       // k = 1 from explicit buffers w^{k-1}, b^{k-1}
   SLAB_STATE_PREV = 6,  // k >= 2 from explicit buffers w^{k-1}, b^{k-1}, w^{k-2}, b^{k-2}
+  SLAB_ADJ = 7,         // reverse step k >= 1: S g in, adjoint point-wise step, F(g') out
+  SLAB_ADJ_LAST = 8,    // reverse step k = 0: S g in, adjoint point-wise step, no transform out
+};
+
+// Reverse step k of Eq. 5 (s = 2) inside a slab pass (modes SLAB_ADJ*): the
+// plane holds S g^k after the inverse transforms, g^k = wbar^k - bbar^k; the
+// point-wise step adds the contributions to J, c, theta, gamma and to the
+// adjoint slots of iterations k - 1 (added) and k - 2 (stored), and leaves
+// g^{k-1} = wbar^{k-1} - bbar^{k-1} in the plane (and in g) for the forward
+// transforms.
+struct SlabAdj {
+  const float *wk, *uk;    // [3][V] w^k, u^k = w_hat^k - b_hat^k of the recomputed forward
+  const float* Bk;         // [3][V] bbar^k
+  float *W1bar, *B1bar;    // [3][V] wbar^{k-1}, bbar^{k-1} (+=), null for k = 0
+  float *W2bar, *B2bar;    // [3][V] wbar^{k-2}, bbar^{k-2} (stored), null for k <= 1
+  const float* g_in;       // [3][V] g^k
+  float* g_out;            // [3][V] g^{k-1} (k >= 1; may be g_in: each quad is read first)
+  float *gJ, *gc;          // [3][V], [V] (+=)
+  double* acc;             // [1] += dL/dtheta part, [2] += dL/dgamma part
+  float inv_gamma;         // theta / lambda
 };
 
 struct SlabArgs {
   float2* spec;            // [nz][3][ny][nkx] half spectrum (in/out)
   float* y;                // [3][V] y = v + b_hat (in/out); FINAL: null unless b_out is wanted
   float* wp;               // [3][V] w state slot (in: w^{k-2}, out: w^{k-1})
+  float* wp_out;           // where w^{k-1} goes when not back to wp (reverse-mode history), or null
+  float* u_hist;           // [3][V] u^k = w_hat^k - b_hat^k recorded (reverse-mode history), or null
   float* bp;               // [3][V] b state slot
   const float* J;          // [3][V]
   const float* c;          // [V]
@@ -148,6 +170,7 @@ struct SlabArgs {
   int xr1, xr2, yr1, yr2;
   float beta, theta, eps;
   int data_term;
+  SlabAdj adj;             // modes SLAB_ADJ, SLAB_ADJ_LAST
 };
 
 // Whether the slab path has kernels for this grid and plans (x: nx/2 split

@@ -360,19 +360,149 @@ __device__ __forceinline__ float slab_pointwise(const SlabArgs& a, float2* const
 #pragma unroll
       for (int c = 0; c < 3; ++c) f4set(yn[c], e, v[c] + f4get(bh[c], e));
     }
+    float* const wdst = a.wp_out != nullptr ? a.wp_out : a.wp;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t i = c * V + vox;
       if (MODE != SLAB_FIRST) {  // w^{k-1}, b^{k-1} into the state slots
-        __stcg(reinterpret_cast<float4*>(a.wp + i), wk1[c]);
+        __stcg(reinterpret_cast<float4*>(wdst + i), wk1[c]);
         __stcg(reinterpret_cast<float4*>(a.bp + i), bk1[c]);
       }
       if (RST) __stcg(reinterpret_cast<float4*>(a.u_prev + i), f4sub(wh[c], bh[c]));
+      if (a.u_hist != nullptr) __stcg(reinterpret_cast<float4*>(a.u_hist + i), f4sub(wh[c], bh[c]));
       __stcg(reinterpret_cast<float4*>(a.y + i), yn[c]);
       *real_quad(planes[c], a.nkx, yy, x0) = yn[c];
     }
   }
   return racc;
+}
+
+// Reverse step k of Eq. 5 with the s = 2 data step (the adjoint of the
+// point-wise part of the iteration) on voxel quads [q0, q1) of plane z, all
+// three components: the planes hold S g^k on entry and g^{k-1} (MODE
+// SLAB_ADJ) on exit.  Per voxel, with rho = c + J.u^k, d = theta + |J|^2,
+// y_bar = S g^k + bbar^k, q = J.y_bar / d:
+//   c_bar -= q,  J_bar += -(rho/d) y_bar - q u^k + 2 rho q J / d,
+//   u_bar = y_bar - J q (the adjoint of w_hat), b_hat_bar = y_bar - u_bar,
+//   wbar^{k-1} += (1 + beta_k) u_bar, bbar^{k-1} += (1 + beta_k) b_hat_bar,
+//   wbar^{k-2} = -beta_k u_bar, bbar^{k-2} = -beta_k b_hat_bar,
+// and the thread's shares of dL/dtheta (rho J.y_bar / d^2) and dL/dgamma
+// (-<g^k - S g^k, w^k> theta / lambda).
+template <int MODE>
+__device__ __forceinline__ void slab_adjoint(const SlabArgs& a, float2* const (&planes)[3], int z,
+                                             int q0, int q1, double& p_theta, double& p_gamma) {
+  const size_t V = (size_t)a.nx * a.ny * a.nz;
+  const int qrow = a.nx >> 2;
+  const SlabAdj& d = a.adj;
+  const float beta = a.beta;
+  for (int q = q0 + (int)threadIdx.x; q < q1; q += kSlabThreads) {
+    const int yy = (int)fdiv((uint32_t)q, a.qdiv);
+    const int x0 = (q - yy * qrow) << 2;
+    const size_t vox = ((size_t)z * a.ny + yy) * a.nx + x0;
+    float4 J4[3], u4[3], yb4[3];
+    const float4 c4 = __ldg(reinterpret_cast<const float4*>(a.c + vox));
+    double pg = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t i = c * V + vox;
+      J4[c] = __ldg(reinterpret_cast<const float4*>(a.J + i));
+      u4[c] = __ldg(reinterpret_cast<const float4*>(d.uk + i));
+      const float4 sg = *real_quad(planes[c], a.nkx, yy, x0);
+      const float4 gi = __ldcg(reinterpret_cast<const float4*>(d.g_in + i));
+      const float4 wv = __ldg(reinterpret_cast<const float4*>(d.wk + i));
+      const float4 bk = __ldg(reinterpret_cast<const float4*>(d.Bk + i));
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        pg += (double)(f4get(gi, e) - f4get(sg, e)) * f4get(wv, e);
+        f4set(yb4[c], e, f4get(sg, e) + f4get(bk, e));
+      }
+    }
+    p_gamma += pg;
+    float qv[4], ri[4], tt[4];
+    float4 gc4 = __ldcg(reinterpret_cast<const float4*>(d.gc + vox));
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float rho = f4get(c4, e), dd = a.theta, jy = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float Jv = f4get(J4[c], e);
+        rho += Jv * f4get(u4[c], e);
+        dd += Jv * Jv;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) jy += f4get(J4[c], e) * f4get(yb4[c], e);
+      const float inv_d = 1.0f / dd;
+      const float qq = jy * inv_d;
+      f4set(gc4, e, f4get(gc4, e) + -qq);
+      p_theta += (double)rho * jy * inv_d * inv_d;
+      qv[e] = qq;
+      ri[e] = rho * inv_d;
+      tt[e] = 2.0f * rho * qq * inv_d;
+    }
+    __stcg(reinterpret_cast<float4*>(d.gc + vox), gc4);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t i = c * V + vox;
+      float4 gJ4 = __ldcg(reinterpret_cast<const float4*>(d.gJ + i));
+      float4 ub4, bb4;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float yb = f4get(yb4[c], e), Jv = f4get(J4[c], e);
+        f4set(gJ4, e, f4get(gJ4, e) + (-ri[e] * yb - qv[e] * f4get(u4[c], e) + tt[e] * Jv));
+        const float ub = yb - Jv * qv[e];
+        f4set(ub4, e, ub);
+        f4set(bb4, e, yb - ub);
+      }
+      __stcg(reinterpret_cast<float4*>(d.gJ + i), gJ4);
+      if (MODE == SLAB_ADJ) {
+        float4 w1 = __ldcg(reinterpret_cast<const float4*>(d.W1bar + i));
+        float4 b1 = __ldcg(reinterpret_cast<const float4*>(d.B1bar + i));
+        float4 go;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float nw = f4get(w1, e) + (1.0f + beta) * f4get(ub4, e);
+          const float nb = f4get(b1, e) + (1.0f + beta) * f4get(bb4, e);
+          f4set(w1, e, nw);
+          f4set(b1, e, nb);
+          f4set(go, e, nw - nb);
+        }
+        __stcg(reinterpret_cast<float4*>(d.W1bar + i), w1);
+        __stcg(reinterpret_cast<float4*>(d.B1bar + i), b1);
+        __stcg(reinterpret_cast<float4*>(d.g_out + i), go);
+        *real_quad(planes[c], a.nkx, yy, x0) = go;
+      }
+      if (d.W2bar != nullptr) {  // slot of iteration k + 1, dead: plain stores
+        __stcg(reinterpret_cast<float4*>(d.W2bar + i),
+               make_float4(-beta * ub4.x, -beta * ub4.y, -beta * ub4.z, -beta * ub4.w));
+        __stcg(reinterpret_cast<float4*>(d.B2bar + i),
+               make_float4(-beta * bb4.x, -beta * bb4.y, -beta * bb4.z, -beta * bb4.w));
+      }
+    }
+  }
+  p_gamma *= -(double)d.inv_gamma;
+}
+
+// Sum of two doubles over the CTA, added to acc[0], acc[1] by one thread.
+__device__ __forceinline__ void slab_cta_add2(double v0, double v1, double* acc) {
+  __shared__ double part[2][kSlabWarps];
+  for (int off = 16; off > 0; off >>= 1) {
+    v0 += __shfl_xor_sync(0xffffffffu, v0, off);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    part[0][threadIdx.x >> 5] = v0;
+    part[1][threadIdx.x >> 5] = v1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int w = 0; w < kSlabWarps; ++w) {
+      t0 += part[0][w];
+      t1 += part[1][w];
+    }
+    atomicAdd(acc, t0);
+    atomicAdd(acc + 1, t1);
+  }
 }
 
 // Restart test of iteration k - 1 (reading of Goldstein et al.'s rule): the
@@ -420,8 +550,10 @@ __device__ __forceinline__ void slab_restart_test(const SlabArgs& a, float part,
 template <int MODE>
 __device__ __forceinline__ void slab_body(const SlabArgs& a, int z, float beta_k, int k,
                                           unsigned nctas, bool lead, int pass) {
-  constexpr bool kInverse = (MODE == SLAB_SPEC || MODE == SLAB_SPEC_PREV || MODE == SLAB_FINAL);
-  constexpr bool kForward = (MODE != SLAB_FINAL);
+  constexpr bool kAdjoint = (MODE == SLAB_ADJ || MODE == SLAB_ADJ_LAST);
+  constexpr bool kInverse = (MODE == SLAB_SPEC || MODE == SLAB_SPEC_PREV || MODE == SLAB_FINAL ||
+                             kAdjoint);
+  constexpr bool kForward = (MODE != SLAB_FINAL && MODE != SLAB_ADJ_LAST);
   constexpr bool kCoupled = (MODE != SLAB_FINAL && MODE != SLAB_FIELD);
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -472,7 +604,11 @@ __device__ __forceinline__ void slab_body(const SlabArgs& a, int z, float beta_k
       a.racc[1] = __longlong_as_double(0x7ff0000000000000ll);
       a.rwords[0] = 0u;
     }
-    if ((MODE == SLAB_SPEC || MODE == SLAB_SPEC_PREV) && a.restart) {
+    if (kAdjoint) {
+      double p_theta = 0.0, p_gamma = 0.0;
+      slab_adjoint<MODE>(a, planes, z, q0, q1, p_theta, p_gamma);
+      slab_cta_add2(p_theta, p_gamma, a.adj.acc + 1);
+    } else if ((MODE == SLAB_SPEC || MODE == SLAB_SPEC_PREV) && a.restart) {
       const float part = slab_pointwise<MODE, true>(a, planes, z, q0, q1, beta_k, k);
       slab_restart_test(a, part, k, nctas);
     } else {
@@ -515,7 +651,8 @@ __device__ __forceinline__ void slab_body(const SlabArgs& a, int z, float beta_k
 #endif
 
 // MODE: SLAB_FIRST, SLAB_SPEC (k = 1), SLAB_SPEC_PREV (k >= 2), SLAB_FINAL,
-// SLAB_FIELD, SLAB_STATE (k = 1), SLAB_STATE_PREV (k >= 2).
+// SLAB_FIELD, SLAB_STATE (k = 1), SLAB_STATE_PREV (k >= 2), SLAB_ADJ,
+// SLAB_ADJ_LAST (reverse steps k >= 1 and k = 0).
 // A cluster takes planes z = cluster, cluster + clusters, ... (one plane
 // each when the grid has nz clusters; a.zper planes each with fewer).
 template <int MODE>
@@ -712,6 +849,8 @@ cudaError_t launch_slab(int mode, const SlabArgs& a, cudaStream_t s) {
     case SLAB_FIELD: return launch_whole(k_slab<SLAB_FIELD>, grid, block, smem, s, a);
     case SLAB_STATE: return launch_whole(k_slab<SLAB_STATE>, grid, block, smem, s, a);
     case SLAB_STATE_PREV: return launch_whole(k_slab<SLAB_STATE_PREV>, grid, block, smem, s, a);
+    case SLAB_ADJ: return launch_whole(k_slab<SLAB_ADJ>, grid, block, smem, s, a);
+    case SLAB_ADJ_LAST: return launch_whole(k_slab<SLAB_ADJ_LAST>, grid, block, smem, s, a);
   }
   return cudaErrorInvalidValue;
 }
@@ -796,6 +935,8 @@ cudaError_t configure_slab_kernels() {
   if ((e = raise_smem(k_slab<SLAB_FINAL>)) != cudaSuccess) return e;
   if ((e = raise_smem(k_slab<SLAB_FIELD>)) != cudaSuccess) return e;
   if ((e = raise_smem(k_slab<SLAB_STATE>)) != cudaSuccess) return e;
+  if ((e = raise_smem(k_slab<SLAB_ADJ>)) != cudaSuccess) return e;
+  if ((e = raise_smem(k_slab<SLAB_ADJ_LAST>)) != cudaSuccess) return e;
   return raise_smem(k_slab<SLAB_STATE_PREV>);
 }
 

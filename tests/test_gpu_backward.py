@@ -75,17 +75,23 @@ CASES = [dict(n=2, outer=3, inner=5, kappa=0.5, delta=1.0),
          dict(n=3, outer=3, inner=4, kappa=0.05, delta=math.inf)]
 
 
+@pytest.mark.parametrize("path", ["four_kernel", "slab"])
 @pytest.mark.parametrize("case", range(len(CASES)))
-def test_backward_matches_oracle_vjp(lib, case):
+def test_backward_matches_oracle_vjp(lib, case, path):
+    """Both paths' reverse sweeps: the four-kernel path solves each reverse
+    step's S g with five kernels and a separate adjoint kernel; the slab
+    path fuses the adjoint point-wise step between the inverse and forward
+    transforms of one slab pass (two kernels per reverse step)."""
     c = CASES[case]
     dims = (32, 32, 24)
     p = synth.make_pair(dims, seed=case)
     gu = synth.random_field((3,) + dims[::-1], seed=40 + case)
     kw = dict(lam=10.0, theta=0.1, n=c["n"], outer=c["outer"], inner=c["inner"],
               kappa=c["kappa"], delta=c["delta"])
+    flags = {"four_kernel": lib.NADMM_FLAG_FOUR_PASS, "slab": lib.NADMM_FLAG_SLAB_PATH}[path]
     reg = lib.Registration(dims, device=DEV, requires_grad=True, order_n=c["n"], lam=10.0,
                            theta=0.1, outer=c["outer"], inner=c["inner"], kappa=c["kappa"],
-                           delta=c["delta"])
+                           delta=c["delta"], flags=flags)
     f, m = dev(p["fixed"]), dev(p["moving"])
     u = reg.register(f, m)
     u_ref, tape = O.register_tape(p["fixed"], p["moving"], **kw)
