@@ -187,6 +187,23 @@ __device__ __noinline__ void slab_rows(const SlabArgs& a, float2* plane, float2*
 }
 
 // ---------------------------------------------------------------- y-DFT of columns
+// Columns kx = 1 .. M-1 one by one; the columns kx = 0 and kx = M (M = nx/2)
+// as one complex column Z = X_0 + i X_M.  Both hold the y-DFT of a real
+// sequence (the x-DFT of real rows at frequency 0 and M is real), so
+//   inverse: IDFT(X_0 + i X_M) = x_0 + i x_M with x_0, x_M real;
+//   forward: Z = x_0 + i x_M, X_0[f] = (Z_f + conj Z_{-f}) / 2,
+//            X_M[f] = (Z_f - conj Z_{-f}) / (2i),
+// which makes M transforms of the plane's M + 1 columns.  Position p of the
+// forward output holds frequency (p mod R2) R1 + p / R2; frequency f sits at
+// position (f mod R1) R2 + f / R1.
+template <int R1, int R2>
+__device__ __forceinline__ int col_neg_pos(int p) {
+  constexpr int N = R1 * R2;
+  const int f = (p % R2) * R1 + p / R2;
+  const int nf = f == 0 ? 0 : N - f;
+  return (nf % R1) * R2 + nf / R1;
+}
+
 template <int R1, int R2>
 __device__ __noinline__ void slab_cols(const SlabArgs& a, float2* plane, float2* xch, bool inv) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -197,25 +214,48 @@ __device__ __noinline__ void slab_cols(const SlabArgs& a, float2* plane, float2*
   const int st = a.nkx;
   float2 twr[R1 - 1];
   lane_twiddles<R1, R2>(a.twy, l, twr);
-  for (int c0 = warp * G; c0 < a.nkx; c0 += kSlabWarps * G) {
-    const int kx = c0 + g;
-    if (kx >= a.nkx) continue;  // uniform over the group
-    float2* col = plane + kx;
+  for (int c0 = warp * G; c0 < a.mx; c0 += kSlabWarps * G) {
+    const int t = c0 + g;
+    if (t >= a.mx) continue;  // uniform over the group
+    const bool pair = (t == 0);  // columns 0 and M together
+    float2* col = plane + t;
+    float2* colm = plane + a.mx;
     float2 v[R1];
     if (!inv) {
 #pragma unroll
-      for (int j = 0; j < R1; ++j) v[j] = col[(l + R2 * j) * st];
+      for (int j = 0; j < R1; ++j) {
+        const int y = l + R2 * j;
+        v[j] = pair ? make_float2(col[y * st].x, colm[y * st].x) : col[y * st];
+      }
       lane_stage1_reg<R1, R2, false>(v, twr);
 #pragma unroll
       for (int k = 0; k < R1; ++k) buf[swz<R2>(l + R2 * k)] = v[k];
       __syncwarp(gmask);
       lane_stage2<R1, R2, false>(buf, l);
       __syncwarp(gmask);
+      if (pair) {
 #pragma unroll
-      for (int k = 0; k < R1; ++k) col[(l + R2 * k) * st] = buf[swz<R2>(l + R2 * k)];
+        for (int k = 0; k < R1; ++k) {
+          const int p = l + R2 * k;
+          const float2 zp = buf[swz<R2>(p)], zq = buf[swz<R2>(col_neg_pos<R1, R2>(p))];
+          col[p * st] = make_float2(0.5f * (zp.x + zq.x), 0.5f * (zp.y - zq.y));
+          colm[p * st] = make_float2(0.5f * (zp.y + zq.y), -0.5f * (zp.x - zq.x));
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < R1; ++k) col[(l + R2 * k) * st] = buf[swz<R2>(l + R2 * k)];
+      }
     } else {
 #pragma unroll
-      for (int k = 0; k < R1; ++k) buf[swz<R2>(l + R2 * k)] = col[(l + R2 * k) * st];
+      for (int k = 0; k < R1; ++k) {
+        const int p = l + R2 * k;
+        float2 z = col[p * st];
+        if (pair) {  // X_0 + i X_M
+          const float2 b = colm[p * st];
+          z = make_float2(z.x - b.y, z.y + b.x);
+        }
+        buf[swz<R2>(p)] = z;
+      }
       __syncwarp(gmask);
       lane_stage2<R1, R2, true>(buf, l);
       __syncwarp(gmask);
@@ -223,7 +263,15 @@ __device__ __noinline__ void slab_cols(const SlabArgs& a, float2* plane, float2*
       for (int k = 0; k < R1; ++k) v[k] = buf[swz<R2>(l + R2 * k)];
       lane_stage1_reg<R1, R2, true>(v, twr);
 #pragma unroll
-      for (int j = 0; j < R1; ++j) col[(l + R2 * j) * st] = v[j];
+      for (int j = 0; j < R1; ++j) {
+        const int y = l + R2 * j;
+        if (pair) {
+          col[y * st] = make_float2(v[j].x, 0.0f);
+          colm[y * st] = make_float2(v[j].y, 0.0f);
+        } else {
+          col[y * st] = v[j];
+        }
+      }
     }
     __syncwarp(gmask);
   }
