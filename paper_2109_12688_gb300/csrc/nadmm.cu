@@ -108,7 +108,8 @@ struct nadmm_context {
   std::vector<ZGroup> zgroups;
   std::vector<int> zorder;
   // slab-pass launches: pairs grouped by shared-memory class (two CTAs per
-  // SM or one), so small planes keep their occupancy; blocks = CTAs
+  // SM or one), so small planes keep their occupancy, and a class of a few
+  // waves into launches of one wave each (upload_flat); blocks = CTAs
   struct SGroup {
     int first, count, blocks;
     size_t smem;
@@ -810,7 +811,7 @@ void assign_flat(nadmm_context* b) {
   };
   b->o_flat_args = take((size_t)n * sizeof(SlabArgs));
   b->o_flat_final = take((size_t)n * sizeof(SlabArgs));
-  b->o_flat_start = take((size_t)(n + b->sgroups.size()) * sizeof(int));
+  b->o_flat_start = take((size_t)(2 * n) * sizeof(int));  // at most one launch per pair
   b->o_flat_pencil = take((size_t)n * sizeof(PencilArgs));
   b->o_flat_zstart = take((size_t)(n + b->zgroups.size()) * sizeof(int));
   b->total = o;
@@ -955,8 +956,52 @@ nadmm_status replay(nadmm_context* h, int slot, const std::vector<const void*>& 
 }
 
 // The flat launch tables of a batched handle (after its pairs are attached).
+// A class whose clusters fill at most four waves is split into launches of
+// one wave each (a pair larger than that is a launch of its own): measured
+// at three 128x128x96 pairs (three waves), one launch per pair took 7.4 ms
+// per registration against 8.0 for one launch of all three.  Larger classes
+// stay one launch, whose many waves pack uneven pairs densely (64 uneven
+// pairs: 489 ms as one launch per phase, 657 ms split into waves).
 cudaError_t upload_flat(nadmm_context* b) {
   const int n = (int)b->pairs.size();
+  {
+    std::vector<nadmm_context::SGroup> waves;
+    for (const auto& g : b->sgroups) {
+      int cap = 0;
+      size_t smem = 0;
+      const nadmm_context* widest = nullptr;
+      for (int j = 0; j < g.count; ++j) {
+        const nadmm_context* p = b->pairs[b->sorder[g.first + j]];
+        const size_t sm = slab_smem_bytes(slab_args(p));
+        if (widest == nullptr || sm > smem) {
+          smem = sm;
+          widest = p;
+        }
+      }
+      TRY(slab_max_clusters(slab_args(widest), &cap));
+      cap = std::max(cap, 1);
+      int total = 0;
+      for (int j = 0; j < g.count; ++j) total += b->pairs[b->sorder[g.first + j]]->cfg.nz;
+      if (total > 4 * cap) {
+        waves.push_back(nadmm_context::SGroup{g.first, g.count, 0, 0});
+        continue;
+      }
+      nadmm_context::SGroup w{g.first, 0, 0, 0};
+      int clusters = 0;
+      for (int j = 0; j < g.count; ++j) {
+        const int nz = b->pairs[b->sorder[g.first + j]]->cfg.nz;
+        if (w.count > 0 && clusters + nz > cap) {
+          waves.push_back(w);
+          w = nadmm_context::SGroup{g.first + j, 0, 0, 0};
+          clusters = 0;
+        }
+        ++w.count;
+        clusters += nz;
+      }
+      if (w.count) waves.push_back(w);
+    }
+    b->sgroups = waves;
+  }
   std::vector<SlabArgs> base(n), fin(n);
   std::vector<int> start(n + b->sgroups.size(), 0);
   for (size_t gi = 0; gi < b->sgroups.size(); ++gi) {
