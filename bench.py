@@ -28,7 +28,9 @@ kernel class: algorithmic bytes per launch over its mean event-timed
 duration, against MEASURED_PEAKS.json, with the ncu DRAM traffic of the
 committed profile when it matches the kernel source); kernels (time,
 launches, share and GB/s per kernel class); quality (Sec. 4 measures of the
-three registrations: Dice, per-slice Hausdorff, share of det <= 0);
+three registrations: Dice, per-slice Hausdorff, share of det <= 0) and
+quality_seeds_0_19 (their means over the pairs of seeds 0-19, each
+registered with n = 1, 2, 3 after the timed region);
 cpu_baseline (one whole FP64 oracle registration on one pinned host core)
 and cpu_baseline_all_cores (every host core, one pinned process each, on a
 bounded sample); cufft_compare (one ADMM iteration with cuFFT, timed only);
@@ -437,6 +439,30 @@ def bench_config(orders, world):
 
 
 # ---------------------------------------------------------------- other workloads
+# seeds of the 128x128x96 pairs whose registrations are scored (Sec. 4 measures)
+QUALITY_SEEDS = tuple(range(20))
+
+
+def _score_job(job):
+    """Spawned worker: Sec. 4 measures of one registration (host scoring)."""
+    labels_fixed, labels_moving, u = job
+    from paper_2109_12688_gb300 import evaluation
+    return evaluation.score(labels_fixed, labels_moving, u)
+
+
+def summarize_scores(scores, nonpositive_percent):
+    """Means over pairs of each class's Dice and per-slice Hausdorff (after
+    and before registration) and the largest share of det <= 0."""
+    import numpy as np
+    out = {}
+    for key in ("dice", "dice_unregistered", "hausdorff_mm", "hausdorff_mm_unregistered"):
+        out[key + "_mean"] = {c: round(float(np.nanmean([sc[c][key] for sc in scores])), 4)
+                              for c in scores[0]}
+    out["nonpositive_jacobian_percent_max"] = float(max(nonpositive_percent))
+    out["pairs"] = len(scores)
+    return out
+
+
 def _gen(job):
     """Spawned worker: one seeded synthetic input (no method arithmetic)."""
     kind, dims, seed = job
@@ -455,6 +481,9 @@ def generate_inputs(names):
     if "registration" in names or "pyramid" in names:
         for n in (1, 2, 3):
             jobs[("pair", n)] = ("pair", DIMS, n)
+    if "registration" in names:
+        for sd in QUALITY_SEEDS:
+            jobs[("pair", sd)] = ("pair", DIMS, sd)
     if "grad" in names:
         jobs[("pair", 0)] = ("pair", DIMS, 0)
     if "large" in names:
@@ -899,6 +928,34 @@ def main():
             "hausdorff_mm_unregistered": {k: round(v["hausdorff_mm_unregistered"], 3)
                                           for k, v in sc.items()},
             "nonpositive_jacobian_percent": 100.0 * int(cnt.item()) / V}
+    # the same measures over the pairs of seeds 0-19, each registered with
+    # every order of the step (the timed handles, one device buffer set)
+    quality_seeds = None
+    if world == 1 and all(("pair", sd) in data for sd in QUALITY_SEEDS):
+        import multiprocessing as mp
+        qa, qb = torch.empty_like(I0[0]), torch.empty_like(I1[0])
+        qu = torch.empty_like(U[0])
+        jobs, nonpos = {n: [] for n in ORDERS}, {n: [] for n in ORDERS}
+        for sd in QUALITY_SEEDS:
+            p = data[("pair", sd)]
+            qa.copy_(torch.from_numpy(p["fixed"]))
+            qb.copy_(torch.from_numpy(p["moving"]))
+            for n, reg in zip(ORDERS, regs):
+                nadmm.nadmm_register(reg.handle, qa, qb, qu, stream)
+                cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+                nadmm.nadmm_jacobian_det(reg.handle, qu, None, cnt, stream)
+                jobs[n].append((p["labels_fixed"], p["labels_moving"], qu.cpu().numpy()))
+                nonpos[n].append(100.0 * int(cnt.item()) / V)
+        check_status()
+        flat_jobs = [j for n in ORDERS for j in jobs[n]]
+        procs = max(1, min(len(flat_jobs), len(_host_cpus())))
+        with mp.get_context("spawn").Pool(procs) as qpool:
+            flat_scores = qpool.map(_score_job, flat_jobs, chunksize=1)
+        quality_seeds = {}
+        for i, n in enumerate(ORDERS):
+            part = flat_scores[i * len(QUALITY_SEEDS):(i + 1) * len(QUALITY_SEEDS)]
+            quality_seeds[f"n{n}"] = summarize_scores(part, nonpos[n])
+        del jobs, flat_jobs
 
     # end to end through the C ABI with pinned host buffers (copies timed)
     e2e_per_reg = None
@@ -1000,6 +1057,7 @@ def main():
                         "gbs": round(bpv[k] * V * n / (m / 1e3) / 1e9, 1) if m > 0 else None}
                     for k, (m, n) in prof.items()},
         "quality": quality,
+        "quality_seeds_0_19": quality_seeds,
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,
         "cufft_compare": cufft,
