@@ -391,7 +391,7 @@ def run_reference(args, rank):
     if rank != 0:
         return
     orders = (1, 2, 3)
-    data = generate_inputs(("registration",))  # host inputs, generated in parallel
+    data = generate_inputs(("reference",))  # the three pairs, generated in parallel
     pairs = {n: data[("pair", n)] for n in orders}
     _pin_this_process(_host_cpus()[0])
     u = None
@@ -478,7 +478,7 @@ def generate_inputs(names):
     import multiprocessing as mp
     from paper_2109_12688_gb300 import synth
     jobs = {}
-    if "registration" in names or "pyramid" in names:
+    if "registration" in names or "pyramid" in names or "reference" in names:
         for n in (1, 2, 3):
             jobs[("pair", n)] = ("pair", DIMS, n)
     if "registration" in names:
