@@ -539,14 +539,14 @@ def extra_workload(name, data, steps, warmup, dev, sample_clocks=True):
         I0 = [torch.from_numpy(data[("b64", i)][0]).to(dev) for i in range(64)]
         I1 = [torch.from_numpy(data[("b64", i)][1]).to(dev) for i in range(64)]
         U = [torch.empty((3, d[2], d[1], d[0]), device=dev) for d in dims]
-        # execution plans of the batched handle: the default (flat execution on
-        # the slab path: each ADMM phase one launch over all pairs) and the
-        # four-kernel path with the pairs spread over 2 or 3 concurrent lanes
-        # (graph branches); value is the fastest, all are reported
-        plans = {"flat": (None, 0), "four_kernel_lanes2": (2, nadmm.NADMM_FLAG_FOUR_PASS),
-                 "four_kernel_lanes3": (3, nadmm.NADMM_FLAG_FOUR_PASS)}
+        # execution plans of the batched handle: the default (two concurrent
+        # lanes, graph branches, the pairs on the four-kernel path), three
+        # lanes, and flat execution on the slab path (each ADMM phase one
+        # launch over all pairs); value is the fastest, all are reported
+        plans = {"flat": (0, 0), "lanes2": (2, 0), "lanes3": (3, 0)}
         if sample_clocks:
-            plans |= {f"lanes{n}": (n, 0) for n in (1, 2, 3, 4)}
+            plans |= {"lanes1": (1, 0), "lanes4": (4, 0),
+                      "slab_lanes2": (2, nadmm.NADMM_FLAG_SLAB_PATH)}
         plan_ms, plan_clk = {}, {}
         for pname, (lanes, flags) in plans.items():
             breg = nadmm.BatchedRegistration(dims, device=dev, lanes=lanes, order_n=2, flags=flags,
@@ -807,8 +807,8 @@ def main():
 
     # the same three registrations as one batched call (flat execution on the
     # slab path: one slab-pass launch and one z-pass launch per ADMM phase)
-    batch = nadmm.BatchedRegistration([DIMS] * len(ORDERS), device=dev, lam=LAM, theta=THETA,
-                                      outer=OUTER, inner=INNER,
+    batch = nadmm.BatchedRegistration([DIMS] * len(ORDERS), device=dev, lanes=0, lam=LAM,
+                                      theta=THETA, outer=OUTER, inner=INNER,
                                       per_pair=[{"order_n": n} for n in ORDERS])
     UB = [torch.empty_like(u) for u in U_of["slab"]]
     # and on the four-kernel path with one concurrent lane (graph branch) per pair

@@ -107,7 +107,8 @@ typedef enum nadmm_status {
                                      at least 80 % of the waves the device
                                      holds (one wave of three-CTA clusters per
                                      z-plane each; decided when the workspace
-                                     is attached); flat batches always take it */
+                                     is attached); flat batches always take it,
+                                     pairs on concurrent lanes do not      */
 
 #define NADMM_FLAG_SLAB_PAIRS 0x4000u /* slab path with every cluster taking two
                                      z-planes in turn: a slab pass needs half the
@@ -237,18 +238,23 @@ const char* nadmm_status_string(nadmm_status s);
  * nz are ignored).  Each grid is validated as by nadmm_create; the first
  * failure is returned with "pair i: ..." in nadmm_last_error.
  *
- * Flat execution (the default when every pair runs on the slab path and
- * NADMM_FLAG_SAVE_FOR_BACKWARD is not set; lane count 0): every pair keeps
- * its own state region, and each phase of an ADMM iteration is one launch
- * over all pairs -- the slab pass of every z-plane of every pair (one launch
- * per shared-memory class: planes that fit two CTAs per SM, then the rest)
- * and the z-pass of every pair sharing a z plan (one launch per plan) --
- * while the outer-step kernels run per pair.  Otherwise the pairs run on
- * `lanes` concurrent graph branches (default min(npairs, 2)), spread longest
- * first to balance voxel counts; pairs of one lane run one after another and
- * share that lane's scratch, so the workspace is one state region per lane
- * (its largest pair's) plus every pair's own region (tables, tape).  Host
- * only. */
+ * By default the pairs run on `lanes` concurrent graph branches (default
+ * min(npairs, 2); nadmm_batch_set_lanes), spread longest first to balance
+ * voxel counts; pairs of one lane run one after another and share that
+ * lane's scratch, so the workspace is one state region per lane (its largest
+ * pair's) plus every pair's own region (tables, tape).  With two or more
+ * lanes every pair takes the four-kernel path unless its flags force the
+ * slab path, it uses adaptive restart or the handle keeps the reverse-mode
+ * tape (NADMM_FLAG_SAVE_FOR_BACKWARD): four-kernel passes overlap across
+ * lanes, and the slab path's reverse sweep is the faster one.
+ * Flat execution (lane count 0, when every pair can take the slab path and
+ * NADMM_FLAG_SAVE_FOR_BACKWARD is not set): every pair keeps its own state
+ * region, and each phase of an ADMM iteration is one launch over all pairs
+ * -- the slab pass of every z-plane of every pair (per shared-memory class:
+ * planes that fit two CTAs per SM, then the rest; a class of at most four
+ * waves of clusters one wave per launch) and the z-pass of every pair
+ * sharing a z plan (one launch per plan) -- while the outer-step kernels run
+ * per pair.  Host only. */
 nadmm_status nadmm_create_batched(const nadmm_config* base, int32_t npairs, const int32_t* dims,
                                   nadmm_handle* out);
 

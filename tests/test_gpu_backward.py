@@ -271,7 +271,7 @@ def test_batch_of_16_forward_and_backward(lib):
     g0, g1, gl, gt = breg.backward(f, m, gu)
     assert lib.nadmm_get_status(breg.handle, torch.cuda.current_stream()) == lib.NADMM_OK
     assert torch.isfinite(gl).all() and torch.isfinite(gt).all()
-    for i in range(0, 16, 5):
+    for i in range(0, 16, 5):  # with the tape, each pair keeps its own path on the lanes
         assert torch.isfinite(g0[i]).all() and torch.isfinite(g1[i]).all()
         single = lib.Registration(dims[i], device=DEV, requires_grad=True, **kw)
         u = single.register(f[i], m[i])

@@ -101,8 +101,8 @@ def test_batched_rejects_single_calls(lib):
 
 def test_batch_of_64_uneven_pairs(lib):
     """64 pairs, nx, ny from {96..160}, nz from {64..112} (seed 1234), n = 2,
-    10 x 10 iterations, one graph: bit-identical to 64 single-pair calls and
-    free of folds."""
+    10 x 10 iterations, one graph (two lanes, the pairs on the four-kernel
+    path): bit-identical to 64 single-pair calls and free of folds."""
     dims = synth.draw_batch_dims(64, seed=1234)
     data = [synth.phase_pair(d, seed=i) for i, d in enumerate(dims)]
     fixed = [dev(f) for f, _ in data]
@@ -111,9 +111,10 @@ def test_batch_of_64_uneven_pairs(lib):
     breg = lib.BatchedRegistration(dims, device=DEV, **kw)
     us = breg.register(fixed, moving)
     assert lib.nadmm_get_status(breg.handle, torch.cuda.current_stream()) == lib.NADMM_OK
-    for i in range(0, 64, 9):  # a sample of the pairs through the single-pair slab path
+    assert lib.nadmm_batch_get_lanes(breg.handle) == 2
+    for i in range(0, 64, 9):  # a sample of the pairs through the single-pair four-kernel path
         assert np.array_equal(us[i].cpu().numpy(), single(lib, dims[i], fixed[i], moving[i],
-                                                          flags=lib.NADMM_FLAG_SLAB_PATH, **kw))
+                                                          flags=lib.NADMM_FLAG_FOUR_PASS, **kw))
     for d, u in zip(dims, us):
         reg = lib.Registration(d, device=DEV, **kw)
         cnt = torch.zeros(1, dtype=torch.int32, device=DEV)
@@ -128,14 +129,16 @@ def test_batch_of_64_uneven_pairs(lib):
 FLAT = [(32, 32, 24), (64, 48, 48), (160, 160, 112), (96, 112, 80), (48, 32, 24), (32, 32, 24)]
 
 
-def test_flat_batch_is_default_and_equals_single_and_lane_runs(lib):
-    """Flat execution (every ADMM phase one launch over all pairs, z-passes
-    one launch per z plan): bit-identical to single-pair calls and to the
-    per-pair lanes, with and without graph capture."""
+def test_flat_batch_equals_single_and_lane_runs(lib):
+    """Flat execution (lane count 0: every ADMM phase one launch over all
+    pairs, z-passes one launch per z plan): bit-identical to single-pair
+    calls and to the per-pair lanes, with and without graph capture.  The
+    default is two concurrent lanes."""
     pairs = [synth.make_pair(d, seed=70 + i) for i, d in enumerate(FLAT)]
     fixed = [dev(p["fixed"]) for p in pairs]
     moving = [dev(p["moving"]) for p in pairs]
-    flat = lib.BatchedRegistration(FLAT, device=DEV, **KW)
+    assert lib.nadmm_batch_get_lanes(lib.BatchedRegistration(FLAT, device=DEV, **KW).handle) == 2
+    flat = lib.BatchedRegistration(FLAT, device=DEV, lanes=0, **KW)
     assert lib.nadmm_batch_get_lanes(flat.handle) == 0
     us = [u.clone() for u in flat.register(fixed, moving)]
     again = flat.register(fixed, moving)  # graph replay
@@ -161,9 +164,11 @@ def test_flat_batch_with_restart_equals_single(lib):
     pairs = [synth.make_pair(d, seed=80 + i) for i, d in enumerate(dims)]
     fixed = [dev(p["fixed"]) for p in pairs]
     moving = [dev(p["moving"]) for p in pairs]
-    us = lib.BatchedRegistration(dims, device=DEV, **kw).register(fixed, moving)
-    for i, d in enumerate(dims):
-        assert np.array_equal(us[i].cpu().numpy(), single(lib, d, fixed[i], moving[i], **kw)), d
+    for lanes in (0, 2):  # flat, and lanes (restart keeps every pair on the slab path)
+        us = lib.BatchedRegistration(dims, device=DEV, lanes=lanes, **kw).register(fixed, moving)
+        for i, d in enumerate(dims):
+            assert np.array_equal(us[i].cpu().numpy(),
+                                  single(lib, d, fixed[i], moving[i], **kw)), (lanes, d)
 
 
 def test_flat_needs_slab_pairs(lib):
