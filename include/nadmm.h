@@ -278,7 +278,8 @@ nadmm_status nadmm_batch_set_lanes(nadmm_handle h, int32_t lanes);
 nadmm_status nadmm_batch_get_lanes(nadmm_handle h, int32_t* lanes);
 
 /* Replace the plan bits (NADMM_FLAG_LANE*, NADMM_FLAG_FUSED_PENCIL,
- * NADMM_FLAG_FOUR_PASS) of pair `pair` (0-based) of a
+ * NADMM_FLAG_FOUR_PASS, NADMM_FLAG_SLAB_PATH, NADMM_FLAG_OUTER_*) of pair
+ * `pair` (0-based) of a
  * batched handle before its workspace is attached (e.g. with the result of
  * nadmm_autotune for that pair's grid); the workspace size may change.
  * Errors: INVALID_ARG. */
@@ -287,7 +288,9 @@ nadmm_status nadmm_batch_set_pair_plan(nadmm_handle h, int32_t pair, uint32_t pl
 /* Register every pair of a batched handle: fixed[i], moving[i] device
  * [nz_i][ny_i][nx_i], u_out[i] device [3][nz_i][ny_i][nx_i] (host arrays of
  * npairs device pointers each).  The same computation as nadmm_register on
- * each pair, as one CUDA-graph replay on `stream` (re-captured when any
+ * each pair (bit for bit that of a single handle on the path the pair takes:
+ * the slab path when flat, the four-kernel path on two or more lanes unless
+ * forced, see nadmm_create_batched), as one CUDA-graph replay on `stream` (re-captured when any
  * pointer changes) or, with NADMM_FLAG_NO_GRAPH, direct launches (flat: the
  * phases in order; lanes: the pairs in order).  nadmm_get_status on the handle reports the first pair
  * whose status word is set.  Only nadmm_register_batched,
