@@ -290,10 +290,11 @@ nadmm_status nadmm_batch_set_pair_plan(nadmm_handle h, int32_t pair, uint32_t pl
  * npairs device pointers each).  The same computation as nadmm_register on
  * each pair (bit for bit that of a single handle on the path the pair takes:
  * the slab path when flat, the four-kernel path on two or more lanes unless
- * forced, see nadmm_create_batched), as one CUDA-graph replay on `stream` (re-captured when any
- * pointer changes) or, with NADMM_FLAG_NO_GRAPH, direct launches (flat: the
- * phases in order; lanes: the pairs in order).  nadmm_get_status on the handle reports the first pair
- * whose status word is set.  Only nadmm_register_batched,
+ * forced, see nadmm_create_batched), as one CUDA-graph replay on `stream`
+ * (re-captured when any pointer changes) or, with NADMM_FLAG_NO_GRAPH,
+ * direct launches (flat: the phases in order; lanes: the pairs in order).
+ * nadmm_get_status on the handle reports the first pair whose status word
+ * is set.  Only nadmm_register_batched,
  * nadmm_backward_batched, nadmm_get_status, nadmm_workspace_size,
  * nadmm_set_workspace, nadmm_batch_set_lanes and nadmm_destroy accept a
  * batched handle.
