@@ -158,6 +158,27 @@ def test_batched_create_layout(lib):
     lib.nadmm_destroy(h)
 
 
+def test_batched_default_lanes_and_flat_on_request(lib):
+    """Batched handles start with two concurrent lanes even when every pair
+    can take the slab path; flat execution (lane count 0) is on request and
+    refused with the reverse-mode tape (host logic, no device work)."""
+    dims = [(32, 32, 24), (64, 48, 48), (96, 112, 80)]
+    h = lib.nadmm_create_batched(lib.make_config(dims[0]), dims)
+    assert lib.nadmm_batch_get_lanes(h) == 2
+    lib.nadmm_batch_set_lanes(h, 0)
+    assert lib.nadmm_batch_get_lanes(h) == 0
+    lib.nadmm_batch_set_lanes(h, 3)
+    assert lib.nadmm_batch_get_lanes(h) == 3
+    lib.nadmm_destroy(h)
+    taped = lib.nadmm_create_batched(
+        lib.make_config(dims[0], flags=lib.NADMM_FLAG_SAVE_FOR_BACKWARD), dims)
+    assert lib.nadmm_batch_get_lanes(taped) == 2
+    with pytest.raises(lib.NadmmError) as e:
+        lib.nadmm_batch_set_lanes(taped, 0)
+    assert e.value.status == lib.NADMM_ERR_INVALID_ARG
+    lib.nadmm_destroy(taped)
+
+
 def test_batched_create_rejects_bad_pair(lib):
     dims = [(32, 32, 24), (10, 8, 8)]
     with pytest.raises(lib.NadmmError) as e:
