@@ -86,7 +86,8 @@ def test_sizes_with_prime_factors_above_7_are_planned(lib, dims):
                                          ("lambda_", float("nan")), ("outer_iters", 0),
                                          ("inner_iters", 0), ("data_term", 3), ("eps", 0.0),
                                          ("bound_kappa", 0.0), ("bound_delta", -1.0),
-                                         ("flags", 0x8000), ("flags", 0x3000), ("flags", 12)])
+                                         ("flags", 0x8000), ("flags", 0x3000), ("flags", 12),
+                                         ("flags", 0x400 | 0x800)])
 def test_bad_parameters_are_rejected(lib, field, value):
     cfg = lib.make_config((32, 32, 24))
     setattr(cfg, field, value)
